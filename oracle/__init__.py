@@ -1,0 +1,128 @@
+"""Scalar MSV/SSV oracle (test infrastructure).
+
+This package is the checker, not the product: only the test suite,
+``__graft_entry__.smoke()`` and the CPU-baseline leg of ``bench.py`` use it.
+It wraps ``mpf_oracle.c`` (plain C, one scalar loop per cell, every byte
+saturation of Alg. 2 / Alg. 7 written out) through ctypes.  It imports
+nothing from the CUDA library and the library imports nothing from here.
+
+``build()`` compiles the C file with gcc into ``oracle/_build/``;
+``scan()`` scores sequences of a database against one profile.
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+import subprocess
+
+import numpy as np
+
+_HERE = os.path.dirname(os.path.abspath(__file__))
+_SRC = os.path.join(_HERE, "mpf_oracle.c")
+_BUILD = os.path.join(_HERE, "_build")
+_LIB_PATH = os.path.join(_BUILD, "libmpf_oracle.so")
+_lib = None
+
+MSV = 0
+SSV = 1
+
+
+def compile_source(src: str, out: str) -> str:
+    """Compile an oracle C source file into the shared library ``out``."""
+    tmp = out + f".{os.getpid()}.tmp"
+    cmd = ["gcc", "-O2", "-std=c11", "-fPIC", "-shared", "-pthread",
+           "-ffp-contract=off", "-fno-fast-math", "-o", tmp, src, "-lm"]
+    subprocess.run(cmd, check=True)
+    os.replace(tmp, out)
+    return out
+
+
+def build(force: bool = False) -> str:
+    """Compile the oracle into a shared library and return its path."""
+    if (not force and os.path.exists(_LIB_PATH)
+            and os.path.getmtime(_LIB_PATH) >= os.path.getmtime(_SRC)):
+        return _LIB_PATH
+    os.makedirs(_BUILD, exist_ok=True)
+    return compile_source(_SRC, _LIB_PATH)
+
+
+def load_library(path: str):
+    """Open a compiled oracle library (the default one, or a test build)."""
+    lib = ctypes.CDLL(path)
+    u8p = ctypes.POINTER(ctypes.c_uint8)
+    lib.oracle_scan.argtypes = [
+        ctypes.c_int, ctypes.c_int, ctypes.c_int, u8p,
+        ctypes.c_uint8, ctypes.c_uint8, ctypes.c_uint8, ctypes.c_uint8,
+        u8p, ctypes.c_uint32, ctypes.c_float, ctypes.c_uint8,
+        u8p, ctypes.POINTER(ctypes.c_uint64), ctypes.POINTER(ctypes.c_uint32),
+        ctypes.POINTER(ctypes.c_uint64), ctypes.c_uint64,
+        u8p, u8p, ctypes.POINTER(ctypes.c_float), ctypes.c_int]
+    lib.oracle_scan.restype = ctypes.c_int
+    return lib
+
+
+def _load():
+    global _lib
+    if _lib is None:
+        _lib = load_library(build())
+    return _lib
+
+
+def _ptr(a, ctype):
+    if a is None:
+        return None
+    return a.ctypes.data_as(ctypes.POINTER(ctype))
+
+
+def scan(filter: int, prof, residues, offsets, lengths, index=None, nthreads: int = 1):
+    """Score sequences against one profile with the scalar oracle.
+
+    ``prof`` is any object with the profile fields ``M, K, cost (K x M
+    uint8), bias, tbm, tec, tjb_fixed, tjb_by_len (uint8 array or None),
+    scale, base``.  ``residues`` (uint8), ``offsets`` (uint64) and ``lengths``
+    (uint32) describe the database; ``index`` optionally selects sequences.
+    Returns ``(raw uint8, flag uint8, nat float32)`` arrays.
+    """
+    lib = _load()
+    cost = np.ascontiguousarray(prof.cost, dtype=np.uint8)
+    K, M = cost.shape
+    assert M == prof.M and K == prof.K
+    tjb = None
+    n_tjb = 0
+    if getattr(prof, "tjb_by_len", None) is not None:
+        tjb = np.ascontiguousarray(prof.tjb_by_len, dtype=np.uint8)
+        n_tjb = int(tjb.size)
+    residues = np.ascontiguousarray(residues, dtype=np.uint8)
+    offsets = np.ascontiguousarray(offsets, dtype=np.uint64)
+    lengths = np.ascontiguousarray(lengths, dtype=np.uint32)
+    if index is not None:
+        index = np.ascontiguousarray(index, dtype=np.uint64)
+        n = int(index.size)
+    else:
+        n = int(lengths.size)
+    raw = np.zeros(n, np.uint8)
+    flag = np.zeros(n, np.uint8)
+    nat = np.zeros(n, np.float32)
+    if residues.size == 0:
+        residues = np.zeros(1, np.uint8)
+    rc = lib.oracle_scan(
+        int(filter), int(M), int(K), _ptr(cost, ctypes.c_uint8),
+        int(prof.bias), int(prof.tbm), int(prof.tec), int(prof.tjb_fixed),
+        _ptr(tjb, ctypes.c_uint8), n_tjb, float(prof.scale), int(prof.base),
+        _ptr(residues, ctypes.c_uint8), _ptr(offsets, ctypes.c_uint64),
+        _ptr(lengths, ctypes.c_uint32), _ptr(index, ctypes.c_uint64), n,
+        _ptr(raw, ctypes.c_uint8), _ptr(flag, ctypes.c_uint8), _ptr(nat, ctypes.c_float),
+        int(nthreads))
+    if rc != 0:
+        raise RuntimeError(f"oracle_scan failed with status {rc}")
+    return raw, flag, nat
+
+
+def msv(prof, residues, offsets, lengths, index=None, nthreads: int = 1):
+    """MSV scores (Alg. 2 with the J/B special-state update)."""
+    return scan(MSV, prof, residues, offsets, lengths, index, nthreads)
+
+
+def ssv(prof, residues, offsets, lengths, index=None, nthreads: int = 1):
+    """SSV scores (Alg. 7, single segment, no J state)."""
+    return scan(SSV, prof, residues, offsets, lengths, index, nthreads)
