@@ -1,0 +1,375 @@
+"""MSV + SSV scan throughput on one GB300 (or N, one process per GPU).
+
+A step is one pass of the whole hot path over the model-length sweep
+workload: every query profile (M = 48, 100, 200, 400, 800, 1600, 2405)
+scored against every sequence of the 500,000-sequence database with both
+filters.  The timed form is the batched one (one graph-captured plan per
+filter: persistent kernels pulling (query, shard) work items); the plain
+one-kernel-per-query form is timed beside it.
+
+GCUPS = sum over queries of M x database residues (padding excluded) per
+second, both filters counted (Sec. 4: residues x model length / kernel time).
+
+  python bench.py [--gpus N] [--steps K] [--warmup W] [--workload 0..4]
+  python bench.py --impl reference      # the scalar oracle on host cores
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import os
+import statistics
+import subprocess
+import sys
+import threading
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+METRIC = "MSV and SSV GCUPS (batched/served vs plain per-query) on 1 GB300; p50/p99 query latency"
+PEAKS = os.path.join(ROOT, "MEASURED_PEAKS.json")
+# Integer-SIMD roofline: per SM and clock, 64 lanes of the 32-bit integer /
+# 16x2 DPX pipe (measured), 4 byte cells per 32-bit op, and the paper's op
+# count per cell (Alg. 2: 4 for MSV; Alg. 7: 2 for SSV).
+INT_LANES_PER_SM_CLK = 64
+CELLS_PER_LANE_OP = 4
+OPS_PER_CELL = {"msv": 4, "ssv": 2}
+
+
+def log(*a):
+    print(*a, file=sys.stderr, flush=True)
+
+
+class ClockSampler:
+    """nvidia-smi clocks and throttle reasons during the timed region."""
+
+    Q = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+         "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+         "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, index: int):
+        self.index = index
+        self.proc = None
+        self.lines = []
+
+    def __enter__(self):
+        try:
+            self.proc = subprocess.Popen(
+                ["nvidia-smi", f"--id={self.index}", f"--query-gpu={self.Q}",
+                 "--format=csv,noheader,nounits", "-lms", "100"],
+                stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+            self.t = threading.Thread(target=self._read, daemon=True)
+            self.t.start()
+        except OSError:
+            self.proc = None
+        return self
+
+    def _read(self):
+        for line in self.proc.stdout:
+            self.lines.append(line.strip())
+
+    def __exit__(self, *a):
+        if self.proc:
+            self.proc.terminate()
+            try:
+                self.proc.wait(timeout=5)
+            except subprocess.TimeoutExpired:
+                self.proc.kill()
+
+    def summary(self):
+        sm, mx, reasons = [], [], set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for ln in self.lines:
+            f = [x.strip() for x in ln.split(",")]
+            if len(f) < 9:
+                continue
+            try:
+                sm.append(float(f[1]))
+                mx.append(float(f[2]))
+            except ValueError:
+                continue
+            for n, v in zip(names, f[5:9]):
+                if v.lower().startswith("active"):
+                    reasons.add(n)
+        if not sm:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["unsampled"], "samples": 0}
+        return {"sm_mhz": statistics.median(sm), "sm_max_mhz": max(mx), "reasons": sorted(reasons),
+                "samples": len(sm)}
+
+
+def dist_init(args):
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    if world > 1:
+        import torch.distributed as dist
+        backend = "nccl" if args.impl == "mpf" else "gloo"
+        dist.init_process_group(backend=backend)
+    return world, rank, local
+
+
+def barrier(world):
+    if world > 1:
+        import torch
+        import torch.distributed as dist
+        if dist.get_backend() == "nccl":
+            dist.barrier(device_ids=[torch.cuda.current_device()])
+        else:
+            dist.barrier()
+
+
+def max_over_ranks(x: float, world: int) -> float:
+    if world == 1:
+        return x
+    import torch
+    import torch.distributed as dist
+    dev = torch.device("cuda", torch.cuda.current_device()) if dist.get_backend() == "nccl" else "cpu"
+    t = torch.tensor([x], dtype=torch.float64, device=dev)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
+
+
+def cpu_baseline(wl, n_sample: int, seed: int = 7):
+    """The oracle as it stands, on a bounded sample of the workload."""
+    import oracle
+    cores = os.cpu_count() or 1
+    rng = np.random.default_rng(seed)
+    n = wl.db.n_seqs
+    idx = np.sort(rng.choice(n, size=min(n_sample, n), replace=False)).astype(np.uint64)
+    res = int(wl.db.lengths[idx.astype(np.int64)].sum())
+    cells = 0
+    t0 = time.perf_counter()
+    for p in wl.profiles:
+        for f in (oracle.MSV, oracle.SSV):
+            oracle.scan(f, p, wl.db.residues, wl.db.offsets, wl.db.lengths, index=idx, nthreads=cores)
+            cells += p.M * res
+    dt = time.perf_counter() - t0
+    return {"value": cells / dt / 1e9, "unit": "GCUPS", "cores": cores, "kind": "oracle",
+            "sample": f"{idx.size} random sequences ({res} residues) x {len(wl.profiles)} queries "
+                      f"x MSV+SSV = {cells:.3e} cells in {dt:.1f} s"}, dt
+
+
+def run_reference(args):
+    world, rank, local = dist_init(args)
+    if rank != 0:
+        return
+    from paper_1707_09683_gb300 import synth
+    import oracle
+    oracle.build()
+    wl = synth.make_workload(args.workload)
+    for _ in range(args.warmup):
+        cpu_baseline(wl, 200)
+    vals = []
+    base = None
+    for k in range(args.steps):
+        base, dt = cpu_baseline(wl, args.ref_sample, seed=100 + k)
+        vals.append(base["value"])
+    v = statistics.median(vals)
+    base["value"] = v
+    line = {"metric": METRIC, "value": v, "unit": "GCUPS", "n_gpus": args.gpus, "steps": args.steps,
+            "warmup": args.warmup, "ms_per_step": None, "higher_is_better": True, "scaling": "weak",
+            "vs_baseline": None, "dtype": "u8", "data": "synthetic",
+            "config": {"workload": wl.name, "queries": [p.M for p in wl.profiles],
+                       "n_seqs": wl.db.n_seqs},
+            "impl": "reference", "cpu_baseline": base,
+            "e2e": {"value": v, "unit": "GCUPS", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+    print(json.dumps(line), flush=True)
+
+
+def run_mpf(args):
+    import torch
+    world, rank, local = dist_init(args)
+    torch.cuda.set_device(local)
+    from paper_1707_09683_gb300 import build, mpf, synth
+    build.build()
+    dev = torch.device("cuda", local)
+
+    t0 = time.time()
+    wl = synth.make_workload(args.workload, n_seqs=args.n_seqs)
+    if world > 1:   # weak scaling: every rank scores its own database of the same shape
+        wl.db = synth.make_database(wl.db.n_seqs, wl.meta["mean"], *wl.meta["clip"],
+                                    np.random.default_rng(1000 + rank))
+    log(f"[rank {rank}] workload {wl.name}: {wl.db.n_seqs} seqs, {wl.db.n_residues} residues, "
+        f"{len(wl.profiles)} queries ({time.time() - t0:.1f} s)")
+    ctx = mpf.Context(local)
+    stream = ctx.torch_stream()
+    db = mpf.Database(ctx, wl.db.residues, wl.db.offsets, wl.db.lengths)
+    profs = [mpf.Profile(ctx, p) for p in wl.profiles]
+    n, q = db.n_seqs, len(profs)
+    res = db.n_residues
+    cells_per_filter = sum(p.M for p in wl.profiles) * res
+    filters = (("msv", mpf.MSV), ("ssv", mpf.SSV))
+    outs = {f: (torch.empty(q * n, dtype=torch.uint8, device=dev),
+                torch.empty(q * n, dtype=torch.uint8, device=dev),
+                torch.empty(q * n, dtype=torch.float32, device=dev)) for f, _ in filters}
+
+    # Batched: one plan per filter, captured as CUDA graphs.
+    plans = {f: mpf.Plan(ctx, code, profs, db, *outs[f]) for f, code in filters}
+    for pl in plans.values():
+        pl.capture_graph()
+    launches_per_step = sum(pl.kernel_launches for pl in plans.values())
+    # Plain: one kernel launch per query and filter.
+    plain = {f: [mpf.Plan(ctx, code, [pr], db, *(t[i * n:(i + 1) * n] for t in outs[f]))
+                 for i, pr in enumerate(profs)] for f, code in filters}
+
+    def step_batched():
+        for f, _ in filters:
+            plans[f].launch()
+
+    def time_steps(fn, k):
+        ev0 = torch.cuda.Event(enable_timing=True)
+        ev1 = torch.cuda.Event(enable_timing=True)
+        ctx.sync()
+        barrier(world)
+        with torch.cuda.stream(stream):
+            ev0.record(stream)
+            for _ in range(k):
+                fn()
+            ev1.record(stream)
+        ev1.synchronize()
+        ctx.sync()
+        barrier(world)
+        return ev0.elapsed_time(ev1) / k   # ms per step
+
+    for _ in range(args.warmup):
+        step_batched()
+    ctx.sync()
+    with ClockSampler(local) as clk:
+        ms_batched = time_steps(step_batched, args.steps)
+    clocks = clk.summary()
+    ms_batched = max_over_ranks(ms_batched, world)
+
+    # Plain per-query launches, each bracketed by events (per-kernel durations).
+    per_kernel = {f: [] for f, _ in filters}
+
+    def step_plain(record=False):
+        evs = []
+        with torch.cuda.stream(stream):
+            for f, _ in filters:
+                for i, pl in enumerate(plain[f]):
+                    if record:
+                        a = torch.cuda.Event(enable_timing=True)
+                        b = torch.cuda.Event(enable_timing=True)
+                        a.record(stream)
+                        pl.launch()
+                        b.record(stream)
+                        evs.append((f, i, a, b))
+                    else:
+                        pl.launch()
+        return evs
+
+    for _ in range(args.warmup):
+        step_plain()
+    ctx.sync()
+    ms_plain = time_steps(step_plain, args.steps)
+    ms_plain = max_over_ranks(ms_plain, world)
+    for _ in range(max(1, args.steps // 2)):
+        for f, i, a, b in step_plain(record=True):
+            b.synchronize()
+            per_kernel[f].append((i, a.elapsed_time(b)))
+
+    # Roofline of the dominant kernel (the filter with more plain kernel time).
+    tot = {f: sum(ms for _, ms in per_kernel[f]) for f, _ in filters}
+    dom = max(tot, key=tot.get)
+    n_l = len(per_kernel[dom])
+    cells_dom = sum(wl.profiles[i].M * res for i, _ in per_kernel[dom])
+    achieved = cells_dom / (tot[dom] * 1e-3) / 1e9      # GCUPS over its launches
+    sm_mhz = clocks.get("sm_mhz") or 2070.0
+    nsm = torch.cuda.get_device_properties(dev).multi_processor_count
+    peak = nsm * INT_LANES_PER_SM_CLK * CELLS_PER_LANE_OP / OPS_PER_CELL[dom] * sm_mhz * 1e6 / 1e9
+    roofline = {"bound": "alu", "achieved": achieved, "peak": peak, "unit": "GCUPS",
+                "frac": achieved / peak, "traffic": None, "kernel": f"scan_kernel ({dom})",
+                "launches_averaged": n_l,
+                "peak_basis": f"{nsm} SMs x {INT_LANES_PER_SM_CLK} int lanes/clk x "
+                              f"{CELLS_PER_LANE_OP} cells/op / {OPS_PER_CELL[dom]} ops/cell x "
+                              f"{sm_mhz:.0f} MHz (median SM clock in the timed region)"}
+
+    gcups_batched = 2 * cells_per_filter * world / (ms_batched * 1e-3) / 1e9
+    gcups_plain = 2 * cells_per_filter * world / (ms_plain * 1e-3) / 1e9
+    per_filter_plain = {f: sum(wl.profiles[i].M * res for i, _ in per_kernel[f]) /
+                        (tot[f] * 1e-3) / 1e9 for f, _ in filters}
+
+    # End to end through the public API with host buffers: profiles built from
+    # host bytes, both filters batched into host outputs, profiles released.
+    raw_h = np.empty(q * n, np.uint8)
+    flag_h = np.empty(q * n, np.uint8)
+    nat_h = np.empty(q * n, np.float32)
+    h2d = sum(p.cost.nbytes + (p.tjb_by_len.nbytes if p.tjb_by_len is not None else 0)
+              for p in wl.profiles)
+    d2h = 2 * (raw_h.nbytes + flag_h.nbytes + nat_h.nbytes)
+
+    def step_e2e():
+        ps = [mpf.Profile(ctx, p) for p in wl.profiles]
+        for _, code in filters:
+            mpf.scan_batch(ctx, code, ps, db, raw_h, flag_h, nat_h)
+        for p in ps:
+            p.close()
+
+    step_e2e()
+    barrier(world)
+    t1 = time.perf_counter()
+    e2e_steps = max(1, min(args.steps, 3))
+    for _ in range(e2e_steps):
+        step_e2e()
+    e2e_s = (time.perf_counter() - t1) / e2e_steps
+    e2e_s = max_over_ranks(e2e_s, world)
+    e2e_gcups = 2 * cells_per_filter * world / e2e_s / 1e9
+
+    cpu = None
+    if rank == 0 and world == 1 and not args.no_cpu:
+        cpu, _ = cpu_baseline(wl, args.cpu_sample)
+
+    if rank == 0:
+        line = {
+            "metric": METRIC, "value": gcups_batched, "unit": "GCUPS", "n_gpus": world,
+            "steps": args.steps, "warmup": args.warmup, "ms_per_step": ms_batched,
+            "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "u8",
+            "data": "synthetic",
+            "config": {"workload": wl.name, "queries": [p.M for p in wl.profiles],
+                       "n_seqs": n, "residues": res, "filters": ["msv", "ssv"],
+                       "form": "batched persistent plan per filter, CUDA-graph replay",
+                       "l2": "database (%.0f MB) larger than L2; no flush" % (res / 1e6),
+                       "cells_per_step": 2 * cells_per_filter},
+            "plain": {"value": gcups_plain, "unit": "GCUPS", "ms_per_step": ms_plain,
+                      "per_filter_gcups": per_filter_plain},
+            "batched_over_plain": gcups_batched / gcups_plain,
+            "roofline": roofline,
+            "cpu_baseline": cpu,
+            "e2e": {"value": e2e_gcups, "unit": "GCUPS", "h2d_bytes_per_step": int(h2d),
+                    "d2h_bytes_per_step": int(d2h), "s_per_step": e2e_s,
+                    "path": "mpf_profile_create from host bytes + mpf_scan_batch (MSV, SSV) into "
+                            "host buffers + mpf_profile_destroy; database resident"},
+            "gpu_launches": launches_per_step * args.steps,
+            "clocks": clocks,
+        }
+        print(json.dumps(line), flush=True)
+    for pl in list(plans.values()) + [p for f in plain for p in plain[f]]:
+        pl.close()
+    if world > 1:
+        import torch.distributed as dist
+        dist.destroy_process_group()
+
+
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=5)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", default="mpf", choices=["mpf", "reference"])
+    ap.add_argument("--workload", type=int, default=1)
+    ap.add_argument("--n-seqs", type=int, default=None)
+    ap.add_argument("--cpu-sample", type=int, default=6000)
+    ap.add_argument("--ref-sample", type=int, default=3000)
+    ap.add_argument("--no-cpu", action="store_true")
+    args = ap.parse_args()
+    if args.impl == "reference":
+        run_reference(args)
+    else:
+        run_mpf(args)
+
+
+if __name__ == "__main__":
+    main()

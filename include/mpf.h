@@ -1,0 +1,191 @@
+/*
+ * mpf.h -- C ABI of the GB300 MSV/SSV protein-profile scan library (libmpf.so).
+ *
+ * The library scores every sequence of a protein database against Plan-7
+ * profiles with the two byte-quantised heuristic filters of the HMMER3
+ * pipeline (Sec. 2.1 of CUDAMPF++, arXiv 1707.09683):
+ *
+ *   MSV  -- ungapped local alignment with multiple hits: Insert and Delete
+ *           states pruned, the M->M transition scored 0, hits chained through
+ *           the J state.  Byte update of Alg. 2:
+ *             dp[k] = sat(sat(max(dp'[k-1], xB) + bias) - cost[x][k])
+ *             xE = max_k dp[k];  overflow when xE >= 255 - bias
+ *             xJ = max(xJ, sat(xE - tec));  xB = sat(max(base, xJ) - (tjb + tbm))
+ *           raw score = xJ, nat = (raw - tjb - base) / scale - 3.
+ *   SSV  -- the MSV model with the J state removed (single segment), Alg. 7,
+ *           read in unsigned offset form:
+ *             r[k] = min(255, max(0, r'[k-1] + bias - cost[x][k])),  R = max r
+ *           overflow when R == 255; nat = (R - tbm - tec - 2 tjb) / scale - 3.
+ *   sat(v) = min(255, max(0, v)); dp', r' are the previous row; xB starts at
+ *   sat(base - (tjb + tbm)), xJ at 0, dp and r at 0.
+ *
+ * Per sequence the library returns the raw byte score, an exact overflow
+ * (saturation) flag and the nat score.  Overflow is not an error: its raw
+ * score is 255 and its nat score +inf.  Results are bit-identical to the
+ * scalar definition above for every input.
+ *
+ * Conventions (all entry points):
+ *   - Return 0 (MPF_OK) or a positive MPF_E* code; never abort.  After
+ *     MPF_ECUDA the context should be destroyed.
+ *   - Inputs are copied; the caller keeps ownership of its buffers.  Handles
+ *     are owned by the caller and released with the matching *_destroy, which
+ *     accepts NULL.  A profile or database must be used with the context it
+ *     was created in and destroyed before that context.
+ *   - Output buffers are caller-allocated and may be host or device memory
+ *     (detected per pointer).  With device outputs a scan is asynchronous on
+ *     the context stream; call mpf_sync() (or synchronise that stream) before
+ *     reading them.  With host outputs the call copies back and returns when
+ *     the results are in place.
+ *   - One context may be used by one host thread at a time.
+ */
+#ifndef MPF_H
+#define MPF_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef struct mpf_ctx mpf_ctx;
+typedef struct mpf_profile mpf_profile;
+typedef struct mpf_db mpf_db;
+
+enum {
+  MPF_OK = 0,
+  MPF_EINVAL = 1,       /* bad argument (null handle, size out of range, code >= 32 ...) */
+  MPF_ENOMEM = 2,       /* host or device allocation failed                              */
+  MPF_ECUDA = 3,        /* a CUDA runtime call failed                                    */
+  MPF_ETIMEOUT = 4,     /* a bounded device wait gave up (status word set by a kernel)    */
+  MPF_EUNSUPPORTED = 5  /* valid request the library does not handle (e.g. M too large)  */
+};
+
+enum { MPF_MSV = 0, MPF_SSV = 1 };
+
+/* Largest model length M a profile may have (set by shared memory per SM). */
+int mpf_max_model_length(void);
+
+/* Message for a status code (static string, never NULL). */
+const char *mpf_strerror(int status);
+
+/*
+ * Create a context on CUDA device `device`.
+ *   cuda_stream: a cudaStream_t created by the caller on that device (kept,
+ *                not owned), or NULL for a library-owned non-blocking stream.
+ * Errors: MPF_EINVAL (bad device or out == NULL), MPF_ECUDA, MPF_ENOMEM.
+ */
+int mpf_ctx_create(int device, void *cuda_stream, mpf_ctx **out);
+void mpf_ctx_destroy(mpf_ctx *ctx);
+
+/* The cudaStream_t the context launches on (for events and interop). */
+void *mpf_ctx_stream(mpf_ctx *ctx);
+
+/* Wait for all work queued on the context stream; returns MPF_ETIMEOUT if a
+ * kernel reported a bounded wait that gave up. */
+int mpf_sync(mpf_ctx *ctx);
+
+/*
+ * Create a profile from biased match costs (the emission-score table E of
+ * Alg. 2 / Alg. 4, here as cost bytes; the paper extends the alphabet to 32
+ * codes, Sec. 3.3).
+ *   M:      model length, 1 <= M <= mpf_max_model_length()
+ *   K:      residue codes with costs, 1 <= K <= 32; codes K..31 cost 255
+ *   cost:   host pointer, K*M bytes, row-major [x][k-1] (node k of residue x)
+ *   bias_b, tbm_b, tec_b, base_b: the bias, B->M entry, E->C/J exit and
+ *           base bytes of the recurrences above
+ *   tjb_b:  the N/C/J loop byte used when tjb_by_len is NULL
+ *   tjb_by_len: nullable host pointer of n_tjb bytes: tjb for sequence length
+ *           L is tjb_by_len[min(L, n_tjb - 1)] ("sc_B initialised from Len",
+ *           Alg. 2)
+ *   scale_b: units per nat of the nat score (finite, > 0)
+ * The profile keeps copies of cost and tjb_by_len.
+ * Errors: MPF_EINVAL, MPF_EUNSUPPORTED (M too large), MPF_ENOMEM, MPF_ECUDA.
+ */
+int mpf_profile_create(mpf_ctx *ctx, int M, int K, const uint8_t *cost, uint8_t bias_b,
+                       uint8_t tbm_b, uint8_t tec_b, uint8_t tjb_b, const uint8_t *tjb_by_len,
+                       uint32_t n_tjb, float scale_b, uint8_t base_b, mpf_profile **out);
+void mpf_profile_destroy(mpf_profile *prof);
+
+/*
+ * Kernel configuration of a profile for one filter: `lanes` threads of a warp
+ * share one sequence (1, 2, 4, 8, 16 or 32) and each holds `words` 32-bit
+ * words of two 16-bit cells (4 <= words <= 48, multiple of 4), so the striped
+ * model holds 2 * lanes * words >= M cells (Sec. 3.1: S = 32 / lanes
+ * sequences per warp, W = 2 * lanes cells per row step, H = words).
+ * set: MPF_EINVAL if the pair is not built or does not cover M.
+ * get: writes the pair the next scan will use (tuned default if never set).
+ */
+int mpf_profile_set_config(mpf_profile *prof, int filter, int lanes, int words);
+int mpf_profile_get_config(const mpf_profile *prof, int filter, int *lanes, int *words);
+
+/*
+ * Upload a database of digital sequences (host pointers).
+ *   residues: n_residues codes, each < 32
+ *   offsets, lengths: n_seqs entries; sequence s is
+ *             residues[offsets[s] .. offsets[s] + lengths[s]); lengths may be 0
+ * The database is copied into device memory (length-sorted, 16-byte aligned
+ * sequences; Sec. 3.2 replaced by a sorted layout) and stays resident.
+ * Errors: MPF_EINVAL (code >= 32, range outside residues, n_seqs >= 2^31),
+ *         MPF_ENOMEM, MPF_ECUDA.
+ */
+int mpf_db_upload(mpf_ctx *ctx, const uint8_t *residues, uint64_t n_residues,
+                  const uint64_t *offsets, const uint32_t *lengths, uint64_t n_seqs,
+                  mpf_db **out);
+void mpf_db_destroy(mpf_db *db);
+uint64_t mpf_db_n_seqs(const mpf_db *db);
+uint64_t mpf_db_n_residues(const mpf_db *db);
+
+/*
+ * Score every database sequence with one profile (one kernel launch).
+ *   raw, overflow: n_seqs bytes each; nat: n_seqs floats or NULL.
+ *   Output index = sequence number in the uploaded order.
+ * Errors: MPF_EINVAL, MPF_ENOMEM, MPF_ECUDA, MPF_ETIMEOUT (host outputs).
+ */
+int mpf_msv_scan(mpf_ctx *ctx, const mpf_profile *prof, const mpf_db *db, uint8_t *raw,
+                 uint8_t *overflow, float *nat);
+int mpf_ssv_scan(mpf_ctx *ctx, const mpf_profile *prof, const mpf_db *db, uint8_t *raw,
+                 uint8_t *overflow, float *nat);
+
+/*
+ * Score the database with n_q profiles in one persistent launch per kernel
+ * configuration (work items of (query, database shard) pulled by resident
+ * thread blocks; launches of different configurations overlap).
+ *   filter: MPF_MSV or MPF_SSV
+ *   raw, overflow: n_q * n_seqs bytes, nat: n_q * n_seqs floats or NULL,
+ *   query-major ([q][s]).
+ * Results equal n_q separate mpf_msv_scan / mpf_ssv_scan calls.
+ * Errors: as the single scans.
+ */
+int mpf_scan_batch(mpf_ctx *ctx, int filter, const mpf_profile *const *profs, int n_q,
+                   const mpf_db *db, uint8_t *raw, uint8_t *overflow, float *nat);
+
+/*
+ * Reusable launch plans (device outputs only).  A plan fixes the profiles,
+ * the database and the output buffers of a batch; launching it enqueues the
+ * scan on the context stream without host synchronisation or allocation.
+ * Queries whose kernel configurations differ run as separate kernels that
+ * overlap (forked streams, joined back into the context stream).
+ *   mpf_plan_create:  arguments as mpf_scan_batch; raw/overflow/nat must be
+ *                     device pointers (MPF_EINVAL otherwise).  The plan keeps
+ *                     pointers to the profiles and database: they must outlive it.
+ *   mpf_plan_launch:  enqueue one run (asynchronous).
+ *   mpf_plan_capture_graph: record the run as a CUDA graph; later launches
+ *                     replay the graph.  Call it outside any stream capture.
+ *   mpf_plan_kernel_launches: kernels one run launches (>= 1).
+ *   mpf_plan_destroy: waits for the context stream, then frees the plan.
+ */
+typedef struct mpf_plan mpf_plan;
+int mpf_plan_create(mpf_ctx *ctx, int filter, const mpf_profile *const *profs, int n_q,
+                    const mpf_db *db, uint8_t *raw, uint8_t *overflow, float *nat,
+                    mpf_plan **out);
+int mpf_plan_launch(mpf_plan *plan);
+int mpf_plan_capture_graph(mpf_plan *plan);
+int mpf_plan_kernel_launches(const mpf_plan *plan);
+void mpf_plan_destroy(mpf_plan *plan);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* MPF_H */

@@ -1,0 +1,803 @@
+// mpf_api.cu -- host side of the C ABI declared in include/mpf.h.
+//
+// Owns device memory and streams, lays the database out in HBM, builds the
+// striped cost tables, chooses kernel configurations and launches the scan
+// kernel.  Every step of the scan itself runs in mpf_scan_kernel.cuh.
+#include <cuda_runtime.h>
+#include <math.h>
+#include <string.h>
+
+#include <algorithm>
+#include <map>
+#include <mutex>
+#include <new>
+#include <numeric>
+#include <tuple>
+#include <utility>
+#include <vector>
+
+#include "../../include/mpf.h"
+#include "mpf_internal.h"
+
+using namespace mpf;
+
+namespace mpf {
+KernelFn kernel_for(int lanes, int words, int mode) {
+  switch (lanes) {
+    case 1: return kernel_lg1(words, mode);
+    case 2: return kernel_lg2(words, mode);
+    case 4: return kernel_lg4(words, mode);
+    case 8: return kernel_lg8(words, mode);
+    case 16: return kernel_lg16(words, mode);
+    case 32: return kernel_lg32(words, mode);
+    default: return nullptr;
+  }
+}
+}  // namespace mpf
+
+struct mpf_ctx {
+  int device = 0;
+  cudaStream_t stream = nullptr;
+  bool own_stream = false;
+  int num_sms = 0;
+  int max_smem = 0;
+  int *d_status = nullptr;
+  // Scratch for host-pointer outputs (grown on demand).
+  void *d_out = nullptr;
+  size_t d_out_bytes = 0;
+  // Streams for overlapping launch groups and for graph capture.
+  cudaStream_t fork[8] = {};
+  int n_fork = 0;
+  cudaStream_t capture = nullptr;
+  // One-shot plans whose kernels may still be running.
+  std::vector<mpf_plan *> pending;
+};
+
+struct DevTable {
+  uint4 *ptr = nullptr;
+  TableGeom geom{};
+};
+
+struct mpf_profile {
+  mpf_ctx *ctx = nullptr;
+  int M = 0, K = 0;
+  std::vector<uint8_t> cost;  // K x M
+  int bias = 0, tbm = 0, tec = 0, tjb_fixed = 0, base = 0;
+  float scale = 1.f;
+  uint8_t *d_tjb = nullptr;
+  uint32_t n_tjb = 0;
+  int tjb_min = 0;
+  int cfg_lanes[2] = {0, 0}, cfg_words[2] = {0, 0};
+  mutable std::map<std::pair<int, int>, DevTable> tables;
+  mutable std::mutex mu;
+};
+
+struct mpf_db {
+  mpf_ctx *ctx = nullptr;
+  uint64_t n_seqs = 0, n_residues = 0;
+  uint32_t *d_words = nullptr;      // residue words, sequences 16-byte aligned
+  uint32_t *d_seq_word = nullptr;   // per length rank
+  uint32_t *d_seq_len = nullptr;
+  uint32_t *d_seq_orig = nullptr;
+  uint32_t pad_word = 0;
+};
+
+// ---------------------------------------------------------------- helpers --
+
+#define MPF_CUDA(call)                        \
+  do {                                        \
+    cudaError_t e_ = (call);                  \
+    if (e_ != cudaSuccess) {                  \
+      (void)cudaGetLastError();               \
+      return e_ == cudaErrorMemoryAllocation ? MPF_ENOMEM : MPF_ECUDA; \
+    }                                         \
+  } while (0)
+
+namespace {
+
+struct DeviceGuard {
+  int prev = -1;
+  explicit DeviceGuard(int dev) {
+    if (cudaGetDevice(&prev) != cudaSuccess) prev = -1;
+    if (prev != dev) cudaSetDevice(dev);
+  }
+  ~DeviceGuard() {
+    int cur = -1;
+    if (prev >= 0 && cudaGetDevice(&cur) == cudaSuccess && cur != prev) cudaSetDevice(prev);
+  }
+};
+
+bool is_device_ptr(const void *p) {
+  if (!p) return false;
+  cudaPointerAttributes a;
+  if (cudaPointerGetAttributes(&a, p) != cudaSuccess) {
+    (void)cudaGetLastError();
+    return false;
+  }
+  return a.type == cudaMemoryTypeDevice || a.type == cudaMemoryTypeManaged;
+}
+
+const int kLanes[6] = {1, 2, 4, 8, 16, 32};
+
+bool words_built(int w) { return w >= 4 && w <= kMaxWords && w % 4 == 0; }
+
+int smem_need(int lanes, int words) { return (int)table_geom(lanes, words).table_bytes; }
+
+// Default (lanes, words): the fewest lanes per sequence whose rows need at
+// most 40 words (48 for whole-warp groups) and whose table fits on chip.
+void default_config(const mpf_ctx *ctx, int M, int *lanes, int *words) {
+  for (int i = 0; i < 6; ++i) {
+    const int lg = kLanes[i];
+    int w = (M + 2 * lg - 1) / (2 * lg);
+    w = (w + 3) / 4 * 4;
+    if (w < 4) w = 4;
+    const int wmax = lg == 32 ? kMaxWords : 40;
+    if (w <= wmax && smem_need(lg, w) <= ctx->max_smem) {
+      *lanes = lg;
+      *words = w;
+      return;
+    }
+  }
+  *lanes = 0;
+  *words = 0;
+}
+
+// MSV_FAST needs the first begin score of every sequence below 255 - bias.
+bool msv_fast_ok(const mpf_profile *p) {
+  int xb = p->base - (p->tjb_min + p->tbm);
+  xb = std::min(255, std::max(0, xb));
+  return p->bias < 255 && xb < 255 - p->bias;
+}
+
+// Build (or fetch) the striped shared-memory image of a profile.
+int get_table(const mpf_profile *p, int lanes, int words, DevTable *out) {
+  std::lock_guard<std::mutex> lk(p->mu);
+  auto key = std::make_pair(lanes, words);
+  auto it = p->tables.find(key);
+  if (it != p->tables.end()) {
+    *out = it->second;
+    return MPF_OK;
+  }
+  const TableGeom g = table_geom(lanes, words);
+  std::vector<uint8_t> img(g.table_bytes, 0);
+  const int M = p->M;
+  // Signed score of node k (0-based) for residue code x; padding nodes and
+  // the padding code score kNegInf.
+  auto score = [&](int x, int k) -> int16_t {
+    if (x >= 32 || k >= M) return (int16_t)kNegInf;
+    const int c = x < p->K ? (int)p->cost[(size_t)x * M + k] : 255;
+    return (int16_t)(p->bias - c);
+  };
+  for (int c = 0; c < g.copies; ++c)
+    for (int x = 0; x < kTableRows; ++x)
+      for (int l = 0; l < lanes; ++l)
+        for (int q = 0; q < words; ++q)
+          for (int h = 0; h < 2; ++h) {
+            const int k = (2 * l + h) * words + q;   // striped cell of (lane, half, word)
+            const size_t off = (size_t)c * g.copy_bytes + (size_t)x * g.row_bytes +
+                               ((size_t)(q / 4) * lanes + l) * 16 + (q % 4) * 4 + h * 2;
+            const int16_t s = score(x, k);
+            memcpy(&img[off], &s, 2);
+          }
+  for (int x = 0; x < kTableRows; ++x) {
+    int m = kNegInf;
+    if (x < 32)
+      for (int k = 0; k < M; ++k) m = std::max(m, (int)score(x, k));
+    const int16_t s = (int16_t)m;
+    memcpy(&img[g.smax_off + 2 * x], &s, 2);
+  }
+  DeviceGuard dg(p->ctx->device);
+  uint4 *d = nullptr;
+  MPF_CUDA(cudaMalloc(&d, g.table_bytes));
+  cudaError_t e = cudaMemcpy(d, img.data(), g.table_bytes, cudaMemcpyHostToDevice);
+  if (e != cudaSuccess) {
+    cudaFree(d);
+    return MPF_ECUDA;
+  }
+  DevTable t;
+  t.ptr = d;
+  t.geom = g;
+  p->tables[key] = t;
+  *out = t;
+  return MPF_OK;
+}
+
+int ensure_out_scratch(mpf_ctx *ctx, size_t bytes) {
+  if (ctx->d_out_bytes >= bytes) return MPF_OK;
+  if (ctx->d_out) {
+    MPF_CUDA(cudaStreamSynchronize(ctx->stream));
+    cudaFree(ctx->d_out);
+    ctx->d_out = nullptr;
+    ctx->d_out_bytes = 0;
+  }
+  MPF_CUDA(cudaMalloc(&ctx->d_out, bytes));
+  ctx->d_out_bytes = bytes;
+  return MPF_OK;
+}
+
+int kernel_mode(const mpf_profile *p, int filter) {
+  if (filter == MPF_SSV) return MODE_SSV;
+  return msv_fast_ok(p) ? MODE_MSV_FAST : MODE_MSV_DIRECT;
+}
+
+}  // namespace
+
+// One launch of the scan kernel over a set of queries sharing a kernel
+// configuration.  Device arrays are owned by the group.
+struct LaunchGroup {
+  KernelFn fn = nullptr;
+  int lanes = 0, words = 0, mode = 0;
+  uint32_t smem = 0;
+  int grid = 0;
+  uint32_t n_shards = 0;
+  QueryDesc *d_queries = nullptr;
+  uint32_t n_queries = 0;
+  uint32_t *d_counter = nullptr;
+};
+
+struct mpf_plan {
+  mpf_ctx *ctx = nullptr;
+  const mpf_db *db = nullptr;
+  std::vector<LaunchGroup> groups;
+  std::vector<cudaEvent_t> events;   // fork/join events (more than one group)
+  cudaGraphExec_t graph = nullptr;
+};
+
+namespace {
+
+void plan_free(mpf_plan *pl) {
+  if (!pl) return;
+  DeviceGuard dg(pl->ctx->device);
+  if (pl->graph) cudaGraphExecDestroy(pl->graph);
+  for (auto &g : pl->groups) {
+    cudaFree(g.d_queries);
+    cudaFree(g.d_counter);
+  }
+  for (auto e : pl->events) cudaEventDestroy(e);
+  (void)cudaGetLastError();
+  delete pl;
+}
+
+int free_pending(mpf_ctx *ctx) {
+  if (ctx->pending.empty()) return MPF_OK;
+  MPF_CUDA(cudaStreamSynchronize(ctx->stream));
+  for (auto *pl : ctx->pending) plan_free(pl);
+  ctx->pending.clear();
+  return MPF_OK;
+}
+
+int configure_kernel(mpf_ctx *ctx, LaunchGroup *g) {
+  g->fn = kernel_for(g->lanes, g->words, g->mode);
+  if (!g->fn) return MPF_EINVAL;
+  g->smem = (uint32_t)smem_need(g->lanes, g->words);
+  MPF_CUDA(cudaFuncSetAttribute((const void *)g->fn, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                (int)g->smem));
+  int per_sm = 0;
+  MPF_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, (const void *)g->fn,
+                                                         kBlockThreads, g->smem));
+  if (per_sm < 1) return MPF_EUNSUPPORTED;
+  g->grid = ctx->num_sms * per_sm;
+  g->n_shards = (uint32_t)g->grid;
+  return MPF_OK;
+}
+
+// Build a plan: queries grouped by kernel configuration.
+int plan_create(mpf_ctx *ctx, int filter, const mpf_profile *const *profs, int n_q,
+                const mpf_db *db, uint8_t *raw, uint8_t *flag, float *nat, mpf_plan **out) {
+  if (!ctx || !profs || n_q < 1 || !db || !raw || !flag || !out) return MPF_EINVAL;
+  if (filter != MPF_MSV && filter != MPF_SSV) return MPF_EINVAL;
+  if (db->ctx != ctx) return MPF_EINVAL;
+  mpf_plan *pl = new (std::nothrow) mpf_plan;
+  if (!pl) return MPF_ENOMEM;
+  pl->ctx = ctx;
+  pl->db = db;
+  std::map<std::tuple<int, int, int>, std::vector<QueryDesc>> byconf;
+  for (int i = 0; i < n_q; ++i) {
+    const mpf_profile *p = profs[i];
+    if (!p || p->ctx != ctx) {
+      plan_free(pl);
+      return MPF_EINVAL;
+    }
+    int lanes = p->cfg_lanes[filter], words = p->cfg_words[filter];
+    if (!lanes) default_config(ctx, p->M, &lanes, &words);
+    if (!lanes) {
+      plan_free(pl);
+      return MPF_EUNSUPPORTED;
+    }
+    DevTable t;
+    int rc = get_table(p, lanes, words, &t);
+    if (rc) {
+      plan_free(pl);
+      return rc;
+    }
+    QueryDesc q;
+    memset(&q, 0, sizeof(q));
+    q.table = t.ptr;
+    q.table_bytes = t.geom.table_bytes;
+    q.row_bytes = t.geom.row_bytes;
+    q.copy_bytes = t.geom.copy_bytes;
+    q.smax_off = t.geom.smax_off;
+    q.bias = p->bias;
+    q.tbm = p->tbm;
+    q.tec = p->tec;
+    q.base = p->base;
+    q.tjb_fixed = p->tjb_fixed;
+    q.scale = p->scale;
+    q.tjb = p->d_tjb;
+    q.n_tjb = p->n_tjb;
+    const size_t off = (size_t)i * db->n_seqs;
+    q.raw = raw + off;
+    q.flag = flag + off;
+    q.nat = nat ? nat + off : nullptr;
+    byconf[std::make_tuple(lanes, words, kernel_mode(p, filter))].push_back(q);
+  }
+  DeviceGuard dg(ctx->device);
+  for (auto &kv : byconf) {
+    LaunchGroup g;
+    g.lanes = std::get<0>(kv.first);
+    g.words = std::get<1>(kv.first);
+    g.mode = std::get<2>(kv.first);
+    int rc = configure_kernel(ctx, &g);
+    if (rc) {
+      plan_free(pl);
+      return rc;
+    }
+    g.n_queries = (uint32_t)kv.second.size();
+    cudaError_t e = cudaMalloc(&g.d_queries, sizeof(QueryDesc) * kv.second.size());
+    if (e == cudaSuccess) e = cudaMalloc(&g.d_counter, sizeof(uint32_t));
+    if (e == cudaSuccess)
+      e = cudaMemcpyAsync(g.d_queries, kv.second.data(), sizeof(QueryDesc) * kv.second.size(),
+                          cudaMemcpyHostToDevice, ctx->stream);
+    if (e != cudaSuccess) {
+      cudaFree(g.d_queries);
+      cudaFree(g.d_counter);
+      (void)cudaGetLastError();
+      plan_free(pl);
+      return e == cudaErrorMemoryAllocation ? MPF_ENOMEM : MPF_ECUDA;
+    }
+    pl->groups.push_back(g);
+  }
+  if (pl->groups.size() > 1) {
+    while (ctx->n_fork < 8 && (size_t)ctx->n_fork < pl->groups.size()) {
+      if (cudaStreamCreateWithFlags(&ctx->fork[ctx->n_fork], cudaStreamNonBlocking) != cudaSuccess) {
+        (void)cudaGetLastError();
+        plan_free(pl);
+        return MPF_ECUDA;
+      }
+      ++ctx->n_fork;
+    }
+    for (size_t i = 0; i <= pl->groups.size(); ++i) {
+      cudaEvent_t ev;
+      if (cudaEventCreateWithFlags(&ev, cudaEventDisableTiming) != cudaSuccess) {
+        (void)cudaGetLastError();
+        plan_free(pl);
+        return MPF_ECUDA;
+      }
+      pl->events.push_back(ev);
+    }
+  }
+  *out = pl;
+  return MPF_OK;
+}
+
+int enqueue_group(const mpf_db *db, mpf_ctx *ctx, LaunchGroup &g, cudaStream_t st) {
+  MPF_CUDA(cudaMemsetAsync(g.d_counter, 0, sizeof(uint32_t), st));
+  ScanParams sp;
+  sp.residues = db->d_words;
+  sp.seq_word = db->d_seq_word;
+  sp.seq_len = db->d_seq_len;
+  sp.seq_orig = db->d_seq_orig;
+  sp.n_seqs = (uint32_t)db->n_seqs;
+  sp.pad_word = db->pad_word;
+  sp.queries = g.d_queries;
+  sp.n_queries = g.n_queries;
+  sp.n_shards = g.n_shards;
+  sp.item_counter = g.d_counter;
+  sp.status = ctx->d_status;
+  const int grid = (int)std::min<uint64_t>((uint64_t)g.grid, (uint64_t)g.n_queries * g.n_shards);
+  g.fn<<<grid, kBlockThreads, g.smem, st>>>(sp);
+  MPF_CUDA(cudaGetLastError());
+  return MPF_OK;
+}
+
+// Enqueue every launch group on `st`; several groups fork onto the context's
+// side streams and join back.
+int plan_enqueue(mpf_plan *pl, cudaStream_t st) {
+  mpf_ctx *ctx = pl->ctx;
+  if (pl->groups.size() == 1) return enqueue_group(pl->db, ctx, pl->groups[0], st);
+  const size_t ng = pl->groups.size();
+  MPF_CUDA(cudaEventRecord(pl->events[ng], st));
+  for (size_t i = 0; i < ng; ++i) {
+    cudaStream_t fs = ctx->fork[i % (size_t)ctx->n_fork];
+    MPF_CUDA(cudaStreamWaitEvent(fs, pl->events[ng], 0));
+    int rc = enqueue_group(pl->db, ctx, pl->groups[i], fs);
+    if (rc) return rc;
+    MPF_CUDA(cudaEventRecord(pl->events[i], fs));
+  }
+  for (size_t i = 0; i < ng; ++i) MPF_CUDA(cudaStreamWaitEvent(st, pl->events[i], 0));
+  return MPF_OK;
+}
+
+int plan_launch(mpf_plan *pl) {
+  if (pl->graph) {
+    MPF_CUDA(cudaGraphLaunch(pl->graph, pl->ctx->stream));
+    return MPF_OK;
+  }
+  return plan_enqueue(pl, pl->ctx->stream);
+}
+
+// Run a plan into the caller's buffers; host buffers go through scratch.
+int run_scan(mpf_ctx *ctx, int filter, const mpf_profile *const *profs, int n_q,
+             const mpf_db *db, uint8_t *raw, uint8_t *flag, float *nat) {
+  if (!ctx || !db || !raw || !flag || n_q < 1) return MPF_EINVAL;
+  DeviceGuard dg(ctx->device);
+  const bool dev_raw = is_device_ptr(raw), dev_flag = is_device_ptr(flag);
+  const bool dev_nat = nat ? is_device_ptr(nat) : true;
+  const uint64_t n = (uint64_t)n_q * db->n_seqs;
+  if (n == 0) return MPF_OK;
+  uint8_t *k_raw = raw, *k_flag = flag;
+  float *k_nat = nat;
+  const bool staged = !(dev_raw && dev_flag && dev_nat);
+  if (staged) {
+    int rc = ensure_out_scratch(ctx, (size_t)n * 6 + 64);
+    if (rc) return rc;
+    uint8_t *base = (uint8_t *)ctx->d_out;
+    k_nat = nat ? (float *)base : nullptr;
+    k_raw = base + (size_t)n * 4;
+    k_flag = k_raw + n;
+  }
+  mpf_plan *pl = nullptr;
+  int rc = plan_create(ctx, filter, profs, n_q, db, k_raw, k_flag, k_nat, &pl);
+  if (rc) return rc;
+  rc = plan_enqueue(pl, ctx->stream);
+  if (!staged) {
+    // Device outputs: asynchronous; the plan is freed at the next sync.
+    ctx->pending.push_back(pl);
+    if (rc == MPF_OK && ctx->pending.size() > 64) rc = free_pending(ctx);
+    return rc;
+  }
+  if (rc == MPF_OK) {
+    cudaError_t e = cudaMemcpyAsync(raw, k_raw, n, cudaMemcpyDefault, ctx->stream);
+    if (e == cudaSuccess) e = cudaMemcpyAsync(flag, k_flag, n, cudaMemcpyDefault, ctx->stream);
+    if (e == cudaSuccess && nat) e = cudaMemcpyAsync(nat, k_nat, n * 4, cudaMemcpyDefault, ctx->stream);
+    if (e != cudaSuccess) rc = MPF_ECUDA;
+  }
+  cudaError_t e = cudaStreamSynchronize(ctx->stream);
+  if (rc == MPF_OK && e != cudaSuccess) rc = MPF_ECUDA;
+  plan_free(pl);
+  if (rc == MPF_OK) {
+    int st = 0;
+    if (cudaMemcpy(&st, ctx->d_status, sizeof(int), cudaMemcpyDeviceToHost) != cudaSuccess) return MPF_ECUDA;
+    if (st) return MPF_ETIMEOUT;
+  }
+  return rc;
+}
+
+}  // namespace
+
+// ================================================================ C ABI ====
+
+extern "C" {
+
+int mpf_max_model_length(void) { return 2 * 32 * kMaxWords; }
+
+const char *mpf_strerror(int status) {
+  switch (status) {
+    case MPF_OK: return "ok";
+    case MPF_EINVAL: return "invalid argument";
+    case MPF_ENOMEM: return "out of memory";
+    case MPF_ECUDA: return "CUDA runtime error";
+    case MPF_ETIMEOUT: return "bounded device wait timed out";
+    case MPF_EUNSUPPORTED: return "unsupported request";
+    default: return "unknown status";
+  }
+}
+
+int mpf_ctx_create(int device, void *cuda_stream, mpf_ctx **out) {
+  if (!out) return MPF_EINVAL;
+  *out = nullptr;
+  int ndev = 0;
+  if (cudaGetDeviceCount(&ndev) != cudaSuccess) {
+    (void)cudaGetLastError();
+    return MPF_ECUDA;
+  }
+  if (device < 0 || device >= ndev) return MPF_EINVAL;
+  DeviceGuard dg(device);
+  mpf_ctx *ctx = new (std::nothrow) mpf_ctx;
+  if (!ctx) return MPF_ENOMEM;
+  ctx->device = device;
+  cudaError_t e = cudaDeviceGetAttribute(&ctx->num_sms, cudaDevAttrMultiProcessorCount, device);
+  if (e == cudaSuccess)
+    e = cudaDeviceGetAttribute(&ctx->max_smem, cudaDevAttrMaxSharedMemoryPerBlockOptin, device);
+  if (e == cudaSuccess) {
+    if (cuda_stream) {
+      ctx->stream = (cudaStream_t)cuda_stream;
+    } else {
+      e = cudaStreamCreateWithFlags(&ctx->stream, cudaStreamNonBlocking);
+      ctx->own_stream = (e == cudaSuccess);
+    }
+  }
+  if (e == cudaSuccess) e = cudaMalloc(&ctx->d_status, sizeof(int));
+  if (e == cudaSuccess) e = cudaMemset(ctx->d_status, 0, sizeof(int));
+  if (e != cudaSuccess) {
+    (void)cudaGetLastError();
+    mpf_ctx_destroy(ctx);
+    return e == cudaErrorMemoryAllocation ? MPF_ENOMEM : MPF_ECUDA;
+  }
+  ctx->max_smem -= 64;  // static shared memory of the kernel
+  *out = ctx;
+  return MPF_OK;
+}
+
+void mpf_ctx_destroy(mpf_ctx *ctx) {
+  if (!ctx) return;
+  DeviceGuard dg(ctx->device);
+  if (ctx->stream) cudaStreamSynchronize(ctx->stream);
+  for (auto *pl : ctx->pending) plan_free(pl);
+  ctx->pending.clear();
+  cudaFree(ctx->d_status);
+  cudaFree(ctx->d_out);
+  for (int i = 0; i < ctx->n_fork; ++i) cudaStreamDestroy(ctx->fork[i]);
+  if (ctx->capture) cudaStreamDestroy(ctx->capture);
+  if (ctx->own_stream) cudaStreamDestroy(ctx->stream);
+  (void)cudaGetLastError();
+  delete ctx;
+}
+
+void *mpf_ctx_stream(mpf_ctx *ctx) { return ctx ? (void *)ctx->stream : nullptr; }
+
+int mpf_sync(mpf_ctx *ctx) {
+  if (!ctx) return MPF_EINVAL;
+  DeviceGuard dg(ctx->device);
+  MPF_CUDA(cudaStreamSynchronize(ctx->stream));
+  int rc = free_pending(ctx);
+  if (rc) return rc;
+  int st = 0;
+  MPF_CUDA(cudaMemcpy(&st, ctx->d_status, sizeof(int), cudaMemcpyDeviceToHost));
+  return st ? MPF_ETIMEOUT : MPF_OK;
+}
+
+int mpf_profile_create(mpf_ctx *ctx, int M, int K, const uint8_t *cost, uint8_t bias_b,
+                       uint8_t tbm_b, uint8_t tec_b, uint8_t tjb_b, const uint8_t *tjb_by_len,
+                       uint32_t n_tjb, float scale_b, uint8_t base_b, mpf_profile **out) {
+  if (!out) return MPF_EINVAL;
+  *out = nullptr;
+  if (!ctx || !cost || M < 1 || K < 1 || K > 32) return MPF_EINVAL;
+  if (!(scale_b > 0.f) || !isfinite(scale_b)) return MPF_EINVAL;
+  if (tjb_by_len && n_tjb == 0) return MPF_EINVAL;
+  if (M > mpf_max_model_length()) return MPF_EUNSUPPORTED;
+  mpf_profile *p = new (std::nothrow) mpf_profile;
+  if (!p) return MPF_ENOMEM;
+  p->ctx = ctx;
+  p->M = M;
+  p->K = K;
+  p->cost.assign(cost, cost + (size_t)K * M);
+  p->bias = bias_b;
+  p->tbm = tbm_b;
+  p->tec = tec_b;
+  p->tjb_fixed = tjb_b;
+  p->base = base_b;
+  p->scale = scale_b;
+  p->tjb_min = tjb_b;
+  if (tjb_by_len) {
+    p->tjb_min = *std::min_element(tjb_by_len, tjb_by_len + n_tjb);
+    DeviceGuard dg(ctx->device);
+    cudaError_t e = cudaMalloc(&p->d_tjb, n_tjb);
+    if (e == cudaSuccess) e = cudaMemcpy(p->d_tjb, tjb_by_len, n_tjb, cudaMemcpyHostToDevice);
+    if (e != cudaSuccess) {
+      (void)cudaGetLastError();
+      cudaFree(p->d_tjb);
+      delete p;
+      return e == cudaErrorMemoryAllocation ? MPF_ENOMEM : MPF_ECUDA;
+    }
+    p->n_tjb = n_tjb;
+  }
+  int lanes = 0, words = 0;
+  default_config(ctx, M, &lanes, &words);
+  if (!lanes) {
+    mpf_profile_destroy(p);
+    return MPF_EUNSUPPORTED;
+  }
+  *out = p;
+  return MPF_OK;
+}
+
+void mpf_profile_destroy(mpf_profile *p) {
+  if (!p) return;
+  DeviceGuard dg(p->ctx->device);
+  for (auto &kv : p->tables) cudaFree(kv.second.ptr);
+  cudaFree(p->d_tjb);
+  (void)cudaGetLastError();
+  delete p;
+}
+
+int mpf_profile_set_config(mpf_profile *p, int filter, int lanes, int words) {
+  if (!p || (filter != MPF_MSV && filter != MPF_SSV)) return MPF_EINVAL;
+  if (lanes == 0 && words == 0) {  // back to the default
+    p->cfg_lanes[filter] = p->cfg_words[filter] = 0;
+    return MPF_OK;
+  }
+  if (!kernel_for(lanes, words, MODE_SSV) || !words_built(words)) return MPF_EINVAL;
+  if (2 * lanes * words < p->M) return MPF_EINVAL;
+  if (smem_need(lanes, words) > p->ctx->max_smem) return MPF_EUNSUPPORTED;
+  p->cfg_lanes[filter] = lanes;
+  p->cfg_words[filter] = words;
+  return MPF_OK;
+}
+
+int mpf_profile_get_config(const mpf_profile *p, int filter, int *lanes, int *words) {
+  if (!p || !lanes || !words || (filter != MPF_MSV && filter != MPF_SSV)) return MPF_EINVAL;
+  if (p->cfg_lanes[filter]) {
+    *lanes = p->cfg_lanes[filter];
+    *words = p->cfg_words[filter];
+  } else {
+    default_config(p->ctx, p->M, lanes, words);
+  }
+  return MPF_OK;
+}
+
+int mpf_db_upload(mpf_ctx *ctx, const uint8_t *residues, uint64_t n_residues,
+                  const uint64_t *offsets, const uint32_t *lengths, uint64_t n_seqs,
+                  mpf_db **out) {
+  if (!out) return MPF_EINVAL;
+  *out = nullptr;
+  if (!ctx || (n_seqs && (!offsets || !lengths)) || (n_residues && !residues)) return MPF_EINVAL;
+  if (n_seqs >= (1ull << 31)) return MPF_EINVAL;
+  // Validate ranges and codes; total padded size in 16-byte chunks.
+  uint64_t chunks = 1;  // chunk 0 holds the padding word
+  for (uint64_t s = 0; s < n_seqs; ++s) {
+    if (offsets[s] > n_residues || lengths[s] > n_residues - offsets[s]) return MPF_EINVAL;
+    chunks += (lengths[s] + 15u) / 16u;
+  }
+  for (uint64_t i = 0; i < n_residues; ++i)
+    if (residues[i] >= 32) return MPF_EINVAL;
+  chunks += 1;  // the kernel prefetches one word past a sequence
+  if (chunks * 4 >= (1ull << 32)) return MPF_EUNSUPPORTED;
+  // Length ranks: longest first, ties by sequence number.
+  std::vector<uint32_t> order(n_seqs);
+  std::iota(order.begin(), order.end(), 0u);
+  std::stable_sort(order.begin(), order.end(),
+                   [&](uint32_t a, uint32_t b) { return lengths[a] > lengths[b]; });
+  std::vector<uint32_t> seq_word(n_seqs), seq_len(n_seqs);
+  uint8_t *host = nullptr;
+  DeviceGuard dg(ctx->device);
+  MPF_CUDA(cudaMallocHost(&host, chunks * 16));
+  memset(host, kPadCode, 16);
+  uint64_t c = 1;
+  for (uint64_t rnk = 0; rnk < n_seqs; ++rnk) {
+    const uint32_t s = order[rnk];
+    const uint32_t L = lengths[s];
+    seq_len[rnk] = L;
+    if (L == 0) {
+      seq_word[rnk] = 0;
+      continue;
+    }
+    seq_word[rnk] = (uint32_t)(c * 4);
+    const uint64_t nch = (L + 15u) / 16u;
+    memcpy(host + c * 16, residues + offsets[s], L);
+    memset(host + c * 16 + L, kPadCode, nch * 16 - L);
+    c += nch;
+  }
+  memset(host + c * 16, kPadCode, (chunks - c) * 16);
+  mpf_db *db = new (std::nothrow) mpf_db;
+  if (!db) {
+    cudaFreeHost(host);
+    return MPF_ENOMEM;
+  }
+  db->ctx = ctx;
+  db->n_seqs = n_seqs;
+  db->n_residues = 0;
+  for (uint64_t s = 0; s < n_seqs; ++s) db->n_residues += lengths[s];
+  db->pad_word = 0;
+  const size_t ns = std::max<uint64_t>(n_seqs, 1);
+  cudaError_t e = cudaMalloc(&db->d_words, chunks * 16);
+  if (e == cudaSuccess) e = cudaMalloc(&db->d_seq_word, ns * 4);
+  if (e == cudaSuccess) e = cudaMalloc(&db->d_seq_len, ns * 4);
+  if (e == cudaSuccess) e = cudaMalloc(&db->d_seq_orig, ns * 4);
+  if (e == cudaSuccess) e = cudaMemcpy(db->d_words, host, chunks * 16, cudaMemcpyHostToDevice);
+  if (e == cudaSuccess && n_seqs) {
+    e = cudaMemcpy(db->d_seq_word, seq_word.data(), n_seqs * 4, cudaMemcpyHostToDevice);
+    if (e == cudaSuccess) e = cudaMemcpy(db->d_seq_len, seq_len.data(), n_seqs * 4, cudaMemcpyHostToDevice);
+    if (e == cudaSuccess) e = cudaMemcpy(db->d_seq_orig, order.data(), n_seqs * 4, cudaMemcpyHostToDevice);
+  }
+  cudaFreeHost(host);
+  if (e != cudaSuccess) {
+    (void)cudaGetLastError();
+    mpf_db_destroy(db);
+    return e == cudaErrorMemoryAllocation ? MPF_ENOMEM : MPF_ECUDA;
+  }
+  *out = db;
+  return MPF_OK;
+}
+
+void mpf_db_destroy(mpf_db *db) {
+  if (!db) return;
+  DeviceGuard dg(db->ctx->device);
+  cudaFree(db->d_words);
+  cudaFree(db->d_seq_word);
+  cudaFree(db->d_seq_len);
+  cudaFree(db->d_seq_orig);
+  (void)cudaGetLastError();
+  delete db;
+}
+
+uint64_t mpf_db_n_seqs(const mpf_db *db) { return db ? db->n_seqs : 0; }
+uint64_t mpf_db_n_residues(const mpf_db *db) { return db ? db->n_residues : 0; }
+
+int mpf_msv_scan(mpf_ctx *ctx, const mpf_profile *prof, const mpf_db *db, uint8_t *raw,
+                 uint8_t *overflow, float *nat) {
+  return run_scan(ctx, MPF_MSV, &prof, 1, db, raw, overflow, nat);
+}
+
+int mpf_ssv_scan(mpf_ctx *ctx, const mpf_profile *prof, const mpf_db *db, uint8_t *raw,
+                 uint8_t *overflow, float *nat) {
+  return run_scan(ctx, MPF_SSV, &prof, 1, db, raw, overflow, nat);
+}
+
+int mpf_scan_batch(mpf_ctx *ctx, int filter, const mpf_profile *const *profs, int n_q,
+                   const mpf_db *db, uint8_t *raw, uint8_t *overflow, float *nat) {
+  return run_scan(ctx, filter, profs, n_q, db, raw, overflow, nat);
+}
+
+int mpf_plan_create(mpf_ctx *ctx, int filter, const mpf_profile *const *profs, int n_q,
+                    const mpf_db *db, uint8_t *raw, uint8_t *overflow, float *nat,
+                    mpf_plan **out) {
+  if (!out) return MPF_EINVAL;
+  *out = nullptr;
+  if (!ctx || !raw || !overflow) return MPF_EINVAL;
+  DeviceGuard dg(ctx->device);
+  if (!is_device_ptr(raw) || !is_device_ptr(overflow) || (nat && !is_device_ptr(nat)))
+    return MPF_EINVAL;
+  return plan_create(ctx, filter, profs, n_q, db, raw, overflow, nat, out);
+}
+
+int mpf_plan_launch(mpf_plan *plan) {
+  if (!plan) return MPF_EINVAL;
+  DeviceGuard dg(plan->ctx->device);
+  return plan_launch(plan);
+}
+
+int mpf_plan_capture_graph(mpf_plan *plan) {
+  if (!plan) return MPF_EINVAL;
+  mpf_ctx *ctx = plan->ctx;
+  DeviceGuard dg(ctx->device);
+  if (!ctx->capture) MPF_CUDA(cudaStreamCreateWithFlags(&ctx->capture, cudaStreamNonBlocking));
+  // The capture stream must see the plan's uploads queued on the context stream.
+  MPF_CUDA(cudaStreamSynchronize(ctx->stream));
+  MPF_CUDA(cudaStreamBeginCapture(ctx->capture, cudaStreamCaptureModeThreadLocal));
+  int rc = plan_enqueue(plan, ctx->capture);
+  cudaGraph_t graph = nullptr;
+  cudaError_t e = cudaStreamEndCapture(ctx->capture, &graph);
+  if (rc) {
+    if (graph) cudaGraphDestroy(graph);
+    (void)cudaGetLastError();
+    return rc;
+  }
+  if (e != cudaSuccess) {
+    (void)cudaGetLastError();
+    return MPF_ECUDA;
+  }
+  cudaGraphExec_t exec = nullptr;
+  e = cudaGraphInstantiate(&exec, graph, 0);
+  cudaGraphDestroy(graph);
+  if (e != cudaSuccess) {
+    (void)cudaGetLastError();
+    return MPF_ECUDA;
+  }
+  if (plan->graph) cudaGraphExecDestroy(plan->graph);
+  plan->graph = exec;
+  return MPF_OK;
+}
+
+int mpf_plan_kernel_launches(const mpf_plan *plan) { return plan ? (int)plan->groups.size() : 0; }
+
+void mpf_plan_destroy(mpf_plan *plan) {
+  if (!plan) return;
+  {
+    DeviceGuard dg(plan->ctx->device);
+    cudaStreamSynchronize(plan->ctx->stream);
+  }
+  plan_free(plan);
+}
+
+}  // extern "C"

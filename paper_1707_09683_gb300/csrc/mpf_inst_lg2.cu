@@ -1,0 +1,32 @@
+// Kernel instantiations for groups of 2 lane(s) per sequence.
+#include "mpf_scan_kernel.cuh"
+
+namespace mpf {
+
+#define MPF_WORDS_CASE(W)                                   \
+  case W:                                                   \
+    if (mode == MODE_SSV) return scan_kernel<2, W, MODE_SSV>;             \
+    if (mode == MODE_MSV_FAST) return scan_kernel<2, W, MODE_MSV_FAST>;   \
+    if (mode == MODE_MSV_DIRECT) return scan_kernel<2, W, MODE_MSV_DIRECT>; \
+    return nullptr;
+
+KernelFn kernel_lg2(int words, int mode) {
+  switch (words) {
+    MPF_WORDS_CASE(4)
+    MPF_WORDS_CASE(8)
+    MPF_WORDS_CASE(12)
+    MPF_WORDS_CASE(16)
+    MPF_WORDS_CASE(20)
+    MPF_WORDS_CASE(24)
+    MPF_WORDS_CASE(28)
+    MPF_WORDS_CASE(32)
+    MPF_WORDS_CASE(36)
+    MPF_WORDS_CASE(40)
+    MPF_WORDS_CASE(44)
+    MPF_WORDS_CASE(48)
+    default:
+      return nullptr;
+  }
+}
+
+}  // namespace mpf

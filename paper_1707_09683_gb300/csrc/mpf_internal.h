@@ -1,0 +1,85 @@
+// mpf_internal.h -- structures shared by the host API and the scan kernels.
+#pragma once
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+namespace mpf {
+
+// Residue code of padding rows.  Database sequences are padded with it to a
+// 16-byte boundary; its table row scores kNegInf at every node, so a padding
+// row leaves every score unchanged (the paper's '#' residue, Sec. 3.2).
+constexpr int kPadCode = 32;
+constexpr int kTableRows = 33;           // codes 0..31 plus padding
+constexpr int kNegInf = -16384;          // score of padding rows and nodes > M
+constexpr int kBlockThreads = 512;
+constexpr int kMaxWords = 48;
+
+enum Mode : int {
+  MODE_SSV = 0,         // Alg. 7
+  MODE_MSV_FAST = 1,    // Alg. 2, begin score held constant between J changes
+  MODE_MSV_DIRECT = 2,  // Alg. 2, J/B update after every row
+};
+
+// One profile in one kernel layout (lives in device memory).
+struct QueryDesc {
+  const uint4 *table;     // shared-memory image: copies x 33 rows x quads x lanes
+  uint32_t table_bytes;   // bytes to stage, multiple of 16 (includes smax)
+  uint32_t row_bytes;     // stride between residue rows
+  uint32_t copy_bytes;    // stride between bank-offset copies
+  uint32_t smax_off;      // byte offset of 33 int16 per-code maximum scores
+  int bias, tbm, tec, base, tjb_fixed;
+  float scale;
+  const uint8_t *tjb;     // per-length tjb (nullable)
+  uint32_t n_tjb;
+  uint32_t pad0;
+  uint8_t *raw;           // outputs indexed by original sequence number
+  uint8_t *flag;
+  float *nat;             // nullable
+};
+
+struct ScanParams {
+  const uint32_t *residues;   // residue words (4 codes each)
+  const uint32_t *seq_word;   // per length rank: first word of the sequence
+  const uint32_t *seq_len;    // per length rank: length
+  const uint32_t *seq_orig;   // per length rank: original sequence number
+  uint32_t n_seqs;
+  uint32_t pad_word;          // a word of four padding codes
+  const QueryDesc *queries;
+  uint32_t n_queries;
+  uint32_t n_shards;          // work item i = (query i / n_shards, shard i % n_shards)
+  uint32_t *item_counter;     // zero before the launch
+  int *status;                // nonzero: error reported by a kernel
+};
+
+typedef void (*KernelFn)(ScanParams);
+
+// Kernel instantiation for (lanes, words, mode), or nullptr if not built.
+KernelFn kernel_for(int lanes, int words, int mode);
+KernelFn kernel_lg1(int words, int mode);
+KernelFn kernel_lg2(int words, int mode);
+KernelFn kernel_lg4(int words, int mode);
+KernelFn kernel_lg8(int words, int mode);
+KernelFn kernel_lg16(int words, int mode);
+KernelFn kernel_lg32(int words, int mode);
+
+// Shared-memory table geometry of a (lanes, words) layout.
+struct TableGeom {
+  int lanes, words, copies;
+  uint32_t row_bytes, copy_bytes, smax_off, table_bytes;
+};
+
+inline TableGeom table_geom(int lanes, int words) {
+  TableGeom g;
+  g.lanes = lanes;
+  g.words = words;
+  g.copies = lanes >= 8 ? 1 : 8 / lanes;
+  uint32_t row = (uint32_t)words * (uint32_t)lanes * 4u;
+  if (g.copies > 1) row = (row + 127u) & ~127u;
+  g.row_bytes = row;
+  g.copy_bytes = (uint32_t)kTableRows * row + (g.copies > 1 ? (uint32_t)lanes * 16u : 0u);
+  g.smax_off = (uint32_t)g.copies * g.copy_bytes;
+  g.table_bytes = g.smax_off + 80u;   // 33 int16 rounded up to 16 bytes
+  return g;
+}
+
+}  // namespace mpf

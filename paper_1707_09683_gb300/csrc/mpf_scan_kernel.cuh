@@ -1,0 +1,281 @@
+// mpf_scan_kernel.cuh -- the MSV / SSV scan kernel for sm_103a.
+//
+// One kernel serves the single-query scan and the batched scan: resident
+// thread blocks pull work items (query, database shard) from a counter,
+// stage the query's striped cost table in shared memory, and stream the
+// shard's sequences through their warps.
+//
+// Parallel decomposition (the five tiers of Sec. 3.1, re-mapped to GB300):
+//   tier 1  thread blocks on the 152 SMs pull work items;
+//   tier 2  warps pull batches of 32 / LG consecutive length ranks of their
+//           item's shard from a shared-memory counter and run them in lock
+//           step (sequences are length-sorted and shards interleave the
+//           ranks, so the lengths of a batch nearly agree and a block's
+//           batches shrink as it drains -- this replaces the pre-built warp
+//           data blocks of Sec. 3.2 and Alg. 1);
+//   tier 3  a group of LG lanes holds one sequence's DP row, striped over the
+//           group (Farrar layout: cell k = (2*lane + half) * H + word);
+//   tier 4  32 / LG groups per warp score different sequences at once;
+//   tier 5  every 32-bit register holds two 16-bit cells updated by one
+//           DPX instruction (byte SIMD -- vaddus4 etc. of Alg. 2 -- is not a
+//           native instruction on sm_103, the 16x2 DPX forms are).
+//
+// Cell arithmetic.  With s = bias - cost (a signed score) and b = min(xB,
+// 255 - bias), the byte update of Alg. 2 is exactly
+//     dp = max(0, max(dp'[k-1], b) + s)
+// because every dp' of a row that did not overflow is below 255 - bias, so
+// clamping xB reproduces the saturating bias addition.  The SSV update of
+// Alg. 7 is r = max(0, r'[k-1] + s) kept unsaturated in 16 bits; R >= 255 is
+// the overflow and R is capped at the end.  MSV_FAST keeps v = max(0, dp - b),
+// which follows the SSV recurrence while b is constant; b only changes when
+// xJ passes base, so each lane keeps a running maximum and the group reduces
+// it (Alg. 6) only on rows where some lane crosses the threshold at which xJ
+// would pass base or the score would overflow.  After the first such row
+// the group reduces every row (exact mode) until the sequence ends.
+#pragma once
+#include <cuda_runtime.h>
+#include <limits.h>
+#include <stdint.h>
+
+#include "mpf_internal.h"
+
+namespace mpf {
+
+constexpr uint32_t kFull = 0xffffffffu;
+
+__device__ __forceinline__ int half_max(uint32_t w) {  // both halves are >= 0
+  return max((int)(w & 0xffffu), (int)(w >> 16));
+}
+
+__device__ __forceinline__ uint32_t pack2(int v) {
+  const uint32_t h = (uint32_t)(uint16_t)(int16_t)v;
+  return (h << 16) | h;
+}
+
+__device__ __forceinline__ int sat8(int v) { return min(255, max(0, v)); }
+
+template <int LG>
+__device__ __forceinline__ int group_max(int v) {
+#pragma unroll
+  for (int off = LG / 2; off >= 1; off >>= 1) v = max(v, __shfl_xor_sync(kFull, v, off, LG));
+  return v;
+}
+
+__device__ __forceinline__ float nat_score(int num, float scale) {
+  return __fsub_rn(__fdiv_rn(__int2float_rn(num), scale), 3.0f);
+}
+
+template <int LG, int H, int MODE>
+__global__ void __launch_bounds__(kBlockThreads, 1) scan_kernel(ScanParams p) {
+  static_assert(H % 4 == 0 && H >= 4 && H <= kMaxWords, "words per lane");
+  static_assert(LG == 1 || LG == 2 || LG == 4 || LG == 8 || LG == 16 || LG == 32, "lanes");
+  constexpr int NC = LG >= 8 ? 1 : 8 / LG;
+  constexpr int G = 32 / LG;
+  extern __shared__ __align__(16) uint8_t smem[];
+  __shared__ uint32_t s_item, s_next;
+
+  const int lane = threadIdx.x & 31;
+  const int gl = lane & (LG - 1);
+  const int grp = lane / LG;
+  const uint32_t n_items = p.n_queries * p.n_shards;
+
+  for (;;) {
+    if (threadIdx.x == 0) {
+      s_item = atomicAdd(p.item_counter, 1u);
+      s_next = 0u;
+    }
+    __syncthreads();
+    const uint32_t item = s_item;
+    if (item >= n_items) break;
+    const uint32_t shard = item % p.n_shards;
+    const QueryDesc *qd = p.queries + item / p.n_shards;
+
+    {  // stage the striped table (16-byte vector copies, coalesced)
+      const uint32_t nvec = qd->table_bytes >> 4;
+      const uint4 *src = qd->table;
+      uint4 *dst = reinterpret_cast<uint4 *>(smem);
+      for (uint32_t i = threadIdx.x; i < nvec; i += blockDim.x) dst[i] = __ldg(src + i);
+    }
+    __syncthreads();
+
+    const int bias = qd->bias, tbm = qd->tbm, tec = qd->tec, base = qd->base;
+    const int cap = 255 - bias;
+    const float scale = qd->scale;
+    const uint8_t *tjb = qd->tjb;
+    const uint32_t n_tjb = qd->n_tjb;
+    const int tjb_fixed = qd->tjb_fixed;
+    uint8_t *out_raw = qd->raw;
+    uint8_t *out_flag = qd->flag;
+    float *out_nat = qd->nat;
+    const uint8_t *tbl_lane = smem + (grp % NC) * qd->copy_bytes + gl * 16;
+    const uint32_t row_bytes = qd->row_bytes;
+    const int16_t *smax = reinterpret_cast<const int16_t *>(smem + qd->smax_off);
+
+    for (;;) {
+      // ---- take G consecutive length ranks of this shard (one per group) ----
+      uint32_t k0 = 0;
+      if (lane == 0) k0 = atomicAdd(&s_next, (uint32_t)G);
+      k0 = __shfl_sync(kFull, k0, 0);
+      const uint64_t r = (uint64_t)shard + (uint64_t)(k0 + grp) * p.n_shards;
+      const bool active = r < p.n_seqs;
+      if (!__any_sync(kFull, active)) break;
+
+      // Group state (identical in every lane of a group).
+      uint32_t wptr = p.pad_word, orig = 0;
+      int len = 0, t = 0;
+      if (active) {
+        wptr = __ldg(p.seq_word + r);
+        len = (int)__ldg(p.seq_len + r);
+        orig = __ldg(p.seq_orig + r);
+        t = tjb ? (int)__ldg(tjb + min((uint32_t)len, n_tjb - 1u)) : tjb_fixed;
+      }
+      const uint32_t wstart = wptr;
+      const int nsteps = (len + 3) >> 2;           // residue words of this sequence
+      const int wsteps = (int)__reduce_max_sync(kFull, (uint32_t)nsteps);
+      int xJ = 0;
+      int b = min(sat8(base - (t + tbm)), cap);
+      uint32_t b2 = pack2(b);
+      int T = min(base + tec - b, cap - b - 1);
+      bool done = false, exact = false;
+
+      // Lane state: H words of two 16-bit cells and a running maximum.
+      uint32_t v[H];
+#pragma unroll
+      for (int q = 0; q < H; ++q) v[q] = 0u;
+      uint32_t vacc = 0u;
+      uint32_t cur = __ldg(p.residues + (nsteps > 0 ? wptr : p.pad_word));
+
+      for (int step = 0; step < wsteps; ++step) {
+        // Prefetch the next residue word; past the end a group reads padding.
+        const uint32_t nxt = __ldg(p.residues + (step + 1 < nsteps ? wptr + (uint32_t)step + 1u : p.pad_word));
+#pragma unroll
+        for (int rr = 0; rr < 4; ++rr) {
+          // Rows past the end of a sequence read padding codes: their cells
+          // score kNegInf, and the special states must not see them.
+          const bool real = active && (4 * step + rr) < len;
+          const uint32_t x = (cur >> (8 * rr)) & 0xffu;
+          const uint8_t *rowp = tbl_lane + x * row_bytes;
+          // Diagonal shift (Alg. 5): cell k-1 of the previous row feeds cell k.
+          const uint32_t wl = v[H - 1];
+          uint32_t up = 0u;
+          if (LG > 1) {
+            up = __shfl_up_sync(kFull, wl, 1, LG);
+            if (gl == 0) up = 0u;
+          }
+          const uint32_t mpv = __byte_perm(up, wl, 0x5432);
+          uint32_t rmax = 0u;
+#pragma unroll
+          for (int j = H / 4 - 1; j >= 0; --j) {
+            const uint4 s4 = *reinterpret_cast<const uint4 *>(rowp + j * LG * 16);
+            const uint32_t sc[4] = {s4.x, s4.y, s4.z, s4.w};
+#pragma unroll
+            for (int i = 3; i >= 0; --i) {
+              const int q = 4 * j + i;
+              const uint32_t prev = (q == 0) ? mpv : v[q - 1];
+              if (MODE == MODE_MSV_DIRECT)
+                v[q] = __viaddmax_s16x2(__vimax_s16x2_relu(prev, b2), sc[i], 0u);
+              else
+                v[q] = __viaddmax_s16x2(prev, sc[i], 0u);
+            }
+            if (MODE == MODE_MSV_DIRECT) {
+              rmax = __vimax3_s16x2(rmax, v[4 * j + 3], v[4 * j + 2]);
+              rmax = __vimax3_s16x2(rmax, v[4 * j + 1], v[4 * j]);
+            } else {
+              vacc = __vimax3_s16x2(vacc, v[4 * j + 3], v[4 * j + 2]);
+              vacc = __vimax3_s16x2(vacc, v[4 * j + 1], v[4 * j]);
+            }
+          }
+          if (MODE == MODE_MSV_DIRECT) {
+            // xE of this row (Alg. 6), then the J and B special states.
+            const int xE = group_max<LG>(half_max(rmax));
+            if (real && !done) {
+              if (xE >= cap) {
+                done = true;
+              } else {
+                xJ = max(xJ, xE - tec);
+                b = min(sat8(max(base, xJ) - (t + tbm)), cap);
+                b2 = pack2(b);
+              }
+            }
+          } else if (MODE == MODE_MSV_FAST) {
+            const bool trig = real && !done && half_max(vacc) > T;
+            if (__any_sync(kFull, trig)) {
+              const int mm = group_max<LG>(half_max(vacc));
+              if (real && !done && mm > T) {
+                const int xE = b + mm;
+                if (xE >= cap) {
+                  done = true;
+                } else {
+                  xJ = exact ? max(xJ, xE - tec) : max(0, xE - tec);
+                  const int bn = min(sat8(max(base, xJ) - (t + tbm)), cap);
+                  if (bn > b) {
+                    const uint32_t nd = pack2(b - bn);
+#pragma unroll
+                    for (int q = 0; q < H; ++q) v[q] = __viaddmax_s16x2(v[q], nd, 0u);
+                  }
+                  b = bn;
+                  exact = true;
+                  T = -1;
+                }
+              }
+              if (exact) vacc = 0u;
+            }
+          }
+        }
+        cur = nxt;
+      }
+
+      // ---- finalise the G sequences -------------------------------------
+      const int V = group_max<LG>(half_max(vacc));
+      if (MODE == MODE_MSV_FAST) {
+        // A sequence whose cells never rose above the begin score: its best
+        // row maximum is the best single-cell score of its residues.
+        const bool rescue = active && !done && !exact && V == 0 && len > 0;
+        int g = INT_MIN / 2;
+        if (rescue) {
+          for (int w = gl; w < nsteps; w += LG) {
+            const uint32_t word = __ldg(p.residues + wstart + (uint32_t)w);
+#pragma unroll
+            for (int i = 0; i < 4; ++i)
+              if (4 * w + i < len) g = max(g, (int)smax[(word >> (8 * i)) & 0xffu]);
+          }
+        }
+        g = group_max<LG>(g);
+        if (active && gl == 0) {
+          int raw;
+          uint8_t flag = 0;
+          if (done) {
+            raw = 255;
+            flag = 1;
+          } else if (exact) {
+            raw = xJ;
+          } else {
+            const int G2 = V > 0 ? V : g;
+            raw = len > 0 ? max(0, b + G2 - tec) : 0;
+          }
+          out_raw[orig] = (uint8_t)raw;
+          out_flag[orig] = flag;
+          if (out_nat) out_nat[orig] = flag ? __int_as_float(0x7f800000) : nat_score(raw - t - base, scale);
+        }
+      } else if (MODE == MODE_MSV_DIRECT) {
+        if (active && gl == 0) {
+          const int raw = done ? 255 : xJ;
+          out_raw[orig] = (uint8_t)raw;
+          out_flag[orig] = done ? 1 : 0;
+          if (out_nat) out_nat[orig] = done ? __int_as_float(0x7f800000) : nat_score(raw - t - base, scale);
+        }
+      } else {  // SSV
+        if (active && gl == 0) {
+          const bool ovf = V >= 255;
+          const int raw = ovf ? 255 : V;
+          out_raw[orig] = (uint8_t)raw;
+          out_flag[orig] = ovf ? 1 : 0;
+          if (out_nat) out_nat[orig] = ovf ? __int_as_float(0x7f800000) : nat_score(raw - tbm - tec - 2 * t, scale);
+        }
+      }
+    }
+    __syncthreads();
+  }
+}
+
+}  // namespace mpf

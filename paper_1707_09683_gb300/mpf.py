@@ -1,0 +1,289 @@
+"""ctypes binding of libmpf.so (argument marshalling only).
+
+Every scan step runs in the CUDA kernels of ``csrc/``; this module converts
+torch tensors and numpy arrays to pointers and status codes to exceptions.
+There is no CPU fallback: if ``libmpf.so`` is missing, importing the
+functions raises ``MpfLibraryMissing``.
+
+The C entry points are declared in ``include/mpf.h``; the names here match.
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+from typing import Optional, Sequence
+
+import numpy as np
+
+_HERE = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(_HERE, "libmpf.so")
+
+MPF_OK, MPF_EINVAL, MPF_ENOMEM, MPF_ECUDA, MPF_ETIMEOUT, MPF_EUNSUPPORTED = range(6)
+MSV, SSV = 0, 1
+
+
+class MpfLibraryMissing(RuntimeError):
+    pass
+
+
+class MpfError(RuntimeError):
+    def __init__(self, status: int, where: str):
+        self.status = status
+        super().__init__(f"{where}: {strerror(status)} (status {status})")
+
+
+_lib = None
+
+
+def load(path: str = LIB_PATH):
+    """Load libmpf.so (built by ``paper_1707_09683_gb300.build``)."""
+    global _lib
+    if _lib is not None:
+        return _lib
+    if not os.path.exists(path):
+        raise MpfLibraryMissing(
+            f"{path} not found: build it with `python -m paper_1707_09683_gb300.build`")
+    lib = ctypes.CDLL(path)
+    vp, u8p, f32p = ctypes.c_void_p, ctypes.POINTER(ctypes.c_uint8), ctypes.c_void_p
+    i32, u32, u64 = ctypes.c_int, ctypes.c_uint32, ctypes.c_uint64
+    sig = {
+        "mpf_max_model_length": (i32, []),
+        "mpf_strerror": (ctypes.c_char_p, [i32]),
+        "mpf_ctx_create": (i32, [i32, vp, ctypes.POINTER(vp)]),
+        "mpf_ctx_destroy": (None, [vp]),
+        "mpf_ctx_stream": (vp, [vp]),
+        "mpf_sync": (i32, [vp]),
+        "mpf_profile_create": (i32, [vp, i32, i32, vp, ctypes.c_uint8, ctypes.c_uint8,
+                                     ctypes.c_uint8, ctypes.c_uint8, vp, u32, ctypes.c_float,
+                                     ctypes.c_uint8, ctypes.POINTER(vp)]),
+        "mpf_profile_destroy": (None, [vp]),
+        "mpf_profile_set_config": (i32, [vp, i32, i32, i32]),
+        "mpf_profile_get_config": (i32, [vp, i32, ctypes.POINTER(i32), ctypes.POINTER(i32)]),
+        "mpf_db_upload": (i32, [vp, vp, u64, vp, vp, u64, ctypes.POINTER(vp)]),
+        "mpf_db_destroy": (None, [vp]),
+        "mpf_db_n_seqs": (u64, [vp]),
+        "mpf_db_n_residues": (u64, [vp]),
+        "mpf_msv_scan": (i32, [vp, vp, vp, vp, vp, vp]),
+        "mpf_ssv_scan": (i32, [vp, vp, vp, vp, vp, vp]),
+        "mpf_scan_batch": (i32, [vp, i32, vp, i32, vp, vp, vp, vp]),
+        "mpf_plan_create": (i32, [vp, i32, vp, i32, vp, vp, vp, vp, ctypes.POINTER(vp)]),
+        "mpf_plan_launch": (i32, [vp]),
+        "mpf_plan_capture_graph": (i32, [vp]),
+        "mpf_plan_kernel_launches": (i32, [vp]),
+        "mpf_plan_destroy": (None, [vp]),
+    }
+    for name, (res, args) in sig.items():
+        fn = getattr(lib, name)
+        fn.restype = res
+        fn.argtypes = args
+    _lib = lib
+    return lib
+
+
+def strerror(status: int) -> str:
+    try:
+        return load().mpf_strerror(int(status)).decode()
+    except MpfLibraryMissing:
+        return f"status {status}"
+
+
+def _check(status: int, where: str):
+    if status != MPF_OK:
+        raise MpfError(status, where)
+
+
+def _ptr(a) -> Optional[int]:
+    """Address of a torch tensor or numpy array (None passes NULL)."""
+    if a is None:
+        return None
+    if isinstance(a, np.ndarray):
+        if not a.flags["C_CONTIGUOUS"]:
+            raise ValueError("array must be C-contiguous")
+        return a.ctypes.data
+    if hasattr(a, "data_ptr"):
+        if not a.is_contiguous():
+            raise ValueError("tensor must be contiguous")
+        return a.data_ptr()
+    raise TypeError(f"unsupported buffer type {type(a)}")
+
+
+def max_model_length() -> int:
+    return int(load().mpf_max_model_length())
+
+
+class Context:
+    """``mpf_ctx``: a device and the stream the library launches on."""
+
+    def __init__(self, device: int = 0, stream: Optional[int] = None):
+        lib = load()
+        h = ctypes.c_void_p()
+        _check(lib.mpf_ctx_create(int(device), stream, ctypes.byref(h)), "mpf_ctx_create")
+        self.handle = h
+        self.device = int(device)
+
+    @property
+    def stream(self) -> int:
+        return int(load().mpf_ctx_stream(self.handle) or 0)
+
+    def torch_stream(self):
+        import torch
+        return torch.cuda.ExternalStream(self.stream, device=torch.device("cuda", self.device))
+
+    def sync(self):
+        _check(load().mpf_sync(self.handle), "mpf_sync")
+
+    def close(self):
+        if getattr(self, "handle", None):
+            load().mpf_ctx_destroy(self.handle)
+            self.handle = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+
+class Profile:
+    """``mpf_profile`` built from a profile record (``synth.Profile`` or any
+    object with ``M, K, cost, bias, tbm, tec, tjb_fixed, tjb_by_len, scale,
+    base``)."""
+
+    def __init__(self, ctx: Context, prof):
+        lib = load()
+        cost = np.ascontiguousarray(prof.cost, dtype=np.uint8)
+        K, M = cost.shape
+        lut = getattr(prof, "tjb_by_len", None)
+        lut = None if lut is None else np.ascontiguousarray(lut, dtype=np.uint8)
+        h = ctypes.c_void_p()
+        _check(lib.mpf_profile_create(
+            ctx.handle, int(M), int(K), cost.ctypes.data, int(prof.bias), int(prof.tbm),
+            int(prof.tec), int(prof.tjb_fixed), None if lut is None else lut.ctypes.data,
+            0 if lut is None else int(lut.size), float(prof.scale), int(prof.base),
+            ctypes.byref(h)), "mpf_profile_create")
+        self.handle = h
+        self.ctx = ctx
+        self.M = int(M)
+
+    def set_config(self, filter: int, lanes: int, words: int):
+        _check(load().mpf_profile_set_config(self.handle, int(filter), int(lanes), int(words)),
+               "mpf_profile_set_config")
+
+    def get_config(self, filter: int):
+        a, b = ctypes.c_int(), ctypes.c_int()
+        _check(load().mpf_profile_get_config(self.handle, int(filter), ctypes.byref(a),
+                                             ctypes.byref(b)), "mpf_profile_get_config")
+        return a.value, b.value
+
+    def close(self):
+        if getattr(self, "handle", None):
+            load().mpf_profile_destroy(self.handle)
+            self.handle = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+
+class Database:
+    """``mpf_db``: residues resident in device memory."""
+
+    def __init__(self, ctx: Context, residues, offsets, lengths):
+        lib = load()
+        residues = np.ascontiguousarray(residues, dtype=np.uint8)
+        offsets = np.ascontiguousarray(offsets, dtype=np.uint64)
+        lengths = np.ascontiguousarray(lengths, dtype=np.uint32)
+        if offsets.size != lengths.size:
+            raise ValueError("offsets and lengths differ in size")
+        h = ctypes.c_void_p()
+        _check(lib.mpf_db_upload(ctx.handle, residues.ctypes.data if residues.size else None,
+                                 int(residues.size), offsets.ctypes.data if offsets.size else None,
+                                 lengths.ctypes.data if lengths.size else None, int(lengths.size),
+                                 ctypes.byref(h)), "mpf_db_upload")
+        self.handle = h
+        self.ctx = ctx
+
+    @property
+    def n_seqs(self) -> int:
+        return int(load().mpf_db_n_seqs(self.handle))
+
+    @property
+    def n_residues(self) -> int:
+        return int(load().mpf_db_n_residues(self.handle))
+
+    def close(self):
+        if getattr(self, "handle", None):
+            load().mpf_db_destroy(self.handle)
+            self.handle = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+
+def _scan1(fn_name, ctx, prof, db, raw, flag, nat):
+    _check(getattr(load(), fn_name)(ctx.handle, prof.handle, db.handle, _ptr(raw), _ptr(flag),
+                                    _ptr(nat)), fn_name)
+
+
+def msv_scan(ctx: Context, prof: Profile, db: Database, raw, overflow, nat=None):
+    """``mpf_msv_scan`` into caller buffers (host numpy or device tensors)."""
+    _scan1("mpf_msv_scan", ctx, prof, db, raw, overflow, nat)
+
+
+def ssv_scan(ctx: Context, prof: Profile, db: Database, raw, overflow, nat=None):
+    """``mpf_ssv_scan`` into caller buffers (host numpy or device tensors)."""
+    _scan1("mpf_ssv_scan", ctx, prof, db, raw, overflow, nat)
+
+
+def _handles(profs: Sequence[Profile]):
+    arr = (ctypes.c_void_p * len(profs))(*[p.handle.value for p in profs])
+    return arr
+
+
+def scan_batch(ctx: Context, filter: int, profs: Sequence[Profile], db: Database, raw, overflow,
+               nat=None):
+    """``mpf_scan_batch``: outputs are [n_q][n_seqs]."""
+    arr = _handles(profs)
+    _check(load().mpf_scan_batch(ctx.handle, int(filter), arr, len(profs), db.handle, _ptr(raw),
+                                 _ptr(overflow), _ptr(nat)), "mpf_scan_batch")
+
+
+class Plan:
+    """``mpf_plan``: a reusable (optionally graph-captured) batch launch."""
+
+    def __init__(self, ctx: Context, filter: int, profs: Sequence[Profile], db: Database, raw,
+                 overflow, nat=None):
+        self._arr = _handles(profs)
+        self._keep = (list(profs), db, raw, overflow, nat)
+        h = ctypes.c_void_p()
+        _check(load().mpf_plan_create(ctx.handle, int(filter), self._arr, len(profs), db.handle,
+                                      _ptr(raw), _ptr(overflow), _ptr(nat), ctypes.byref(h)),
+               "mpf_plan_create")
+        self.handle = h
+        self.ctx = ctx
+
+    def launch(self):
+        _check(load().mpf_plan_launch(self.handle), "mpf_plan_launch")
+
+    def capture_graph(self):
+        _check(load().mpf_plan_capture_graph(self.handle), "mpf_plan_capture_graph")
+
+    @property
+    def kernel_launches(self) -> int:
+        return int(load().mpf_plan_kernel_launches(self.handle))
+
+    def close(self):
+        if getattr(self, "handle", None):
+            load().mpf_plan_destroy(self.handle)
+            self.handle = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass

@@ -1,0 +1,258 @@
+"""GPU parity: the CUDA scans through the C ABI against the scalar oracle.
+
+Scores, overflow flags and nat scores must be bit-identical (integer work,
+and a nat score computed by the same IEEE float operations).  Inputs are the
+seeded synthetic workloads plus adversarial profiles and databases.
+"""
+import numpy as np
+import pytest
+
+torch = pytest.importorskip("torch")
+
+import oracle
+from paper_1707_09683_gb300 import build, mpf, synth
+
+pytestmark = pytest.mark.gpu
+
+FILTERS = ((mpf.MSV, oracle.MSV), (mpf.SSV, oracle.SSV))
+
+
+@pytest.fixture(scope="module")
+def ctx():
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    build.build()
+    oracle.build()
+    c = mpf.Context(0)
+    yield c
+    c.sync()
+
+
+def run_gpu(ctx, filt, prof, db, on_device=True):
+    n = db.n_seqs
+    if on_device:
+        dev = torch.device("cuda", 0)
+        raw = torch.empty(n, dtype=torch.uint8, device=dev)
+        flag = torch.empty(n, dtype=torch.uint8, device=dev)
+        nat = torch.empty(n, dtype=torch.float32, device=dev)
+    else:
+        raw = np.empty(n, np.uint8)
+        flag = np.empty(n, np.uint8)
+        nat = np.empty(n, np.float32)
+    (mpf.msv_scan if filt == mpf.MSV else mpf.ssv_scan)(ctx, prof, db, raw, flag, nat)
+    ctx.sync()
+    if on_device:
+        return raw.cpu().numpy(), flag.cpu().numpy(), nat.cpu().numpy()
+    return raw, flag, nat
+
+
+def assert_same(got, exp, what=""):
+    graw, gflag, gnat = got
+    eraw, eflag, enat = exp
+    bad = np.flatnonzero((graw != eraw) | (gflag != eflag))
+    assert bad.size == 0, f"{what}: {bad.size} raw/flag mismatches, first at {bad[:5]}: " \
+        f"gpu {graw[bad[:5]]}/{gflag[bad[:5]]} oracle {eraw[bad[:5]]}/{eflag[bad[:5]]}"
+    badn = np.flatnonzero(gnat.view(np.uint32) != enat.view(np.uint32))
+    assert badn.size == 0, f"{what}: nat mismatch at {badn[:5]}: {gnat[badn[:5]]} vs {enat[badn[:5]]}"
+
+
+def check_profile(ctx, p, db, ddb=None, filters=FILTERS, index=None, configs=None):
+    prof = mpf.Profile(ctx, p)
+    ddb = ddb or mpf.Database(ctx, db.residues, db.offsets, db.lengths)
+    for gf, of in filters:
+        exp = oracle.scan(of, p, db.residues, db.offsets, db.lengths, index=index, nthreads=8)
+        for cfg in (configs or [None]):
+            if cfg is not None:
+                prof.set_config(gf, *cfg)
+            got = run_gpu(ctx, gf, prof, ddb)
+            if index is not None:
+                got = tuple(a[index.astype(np.int64)] for a in got)
+            assert_same(got, exp, f"filter {gf} M={p.M} cfg={cfg}")
+    prof.close()
+
+
+# ------------------------------------------------------------- workloads ---
+
+def test_plain_workload_m100_full(ctx):
+    """The M = 100, 10,000-sequence workload, every sequence."""
+    wl = synth.make_workload(0)
+    check_profile(ctx, wl.profiles[0], wl.db)
+
+
+def test_model_length_sweep_small_db(ctx):
+    """Every model length of the sweep workload on its first 3,000 sequences
+    (tiles of every lane-group size, ragged model tails)."""
+    wl = synth.make_workload(1, n_seqs=3000)
+    ddb = mpf.Database(ctx, wl.db.residues, wl.db.offsets, wl.db.lengths)
+    for p in wl.profiles:
+        check_profile(ctx, p, wl.db, ddb)
+
+
+def test_planted_overflow_batch_sample(ctx):
+    """Uneven-batch workload shape with planted segments: overflow flags."""
+    wl = synth.make_workload(2, n_seqs=4000, n_queries=6)
+    ddb = mpf.Database(ctx, wl.db.residues, wl.db.offsets, wl.db.lengths)
+    n_flag = 0
+    for p in wl.profiles:
+        prof = mpf.Profile(ctx, p)
+        for gf, of in FILTERS:
+            exp = oracle.scan(of, p, wl.db.residues, wl.db.offsets, wl.db.lengths, nthreads=8)
+            got = run_gpu(ctx, gf, prof, ddb)
+            assert_same(got, exp, f"planted M={p.M} filter {gf}")
+            n_flag += int(exp[1].sum())
+    assert n_flag > 0, "the planted workload must exercise overflow"
+
+
+# ----------------------------------------------------------- adversarial ---
+
+@pytest.mark.parametrize("seed", range(4))
+def test_adversarial_profiles(ctx, seed):
+    """Uniform random cost bytes, free special bytes (including begin scores
+    that hit the 255 cap), residue codes 0..31, lengths 0..300."""
+    rng = np.random.default_rng(500 + seed)
+    db = synth.random_database(700, 300, rng, alphabet=32)
+    ddb = mpf.Database(ctx, db.residues, db.offsets, db.lengths)
+    for M in (1, 2, 3, 7, 33, 64, 65, 130, 257, 600, 1111):
+        K = int(rng.integers(1, 33))
+        p = synth.random_profile(M, K, rng, cost_hi=int(rng.choice([40, 255])),
+                                 bias=int(rng.choice([0, 12, 60, 130, 254, 255])),
+                                 base=int(rng.choice([60, 190, 250])),
+                                 with_lut=bool(rng.integers(2)))
+        check_profile(ctx, p, db, ddb)
+
+
+def test_strong_profiles_hit_j_and_overflow(ctx):
+    """Low costs: long hits, chained J transitions, MSV and SSV overflow."""
+    rng = np.random.default_rng(77)
+    db = synth.random_database(500, 400, rng, alphabet=20, min_len=1)
+    ddb = mpf.Database(ctx, db.residues, db.offsets, db.lengths)
+    seen_flag = seen_j = 0
+    for M in (5, 40, 150, 500):
+        for bias in (8, 20, 40):
+            p = synth.random_profile(M, 20, rng, cost_hi=bias + 6, bias=bias, base=190,
+                                     tbm=20, tec=3, tjb=10)
+            check_profile(ctx, p, db, ddb)
+            r, f, _ = oracle.msv(p, db.residues, db.offsets, db.lengths, nthreads=8)
+            seen_flag += int(f.sum())
+            seen_j += int(((f == 0) & (r > 190)).sum())
+    assert seen_flag > 0 and seen_j > 0
+
+
+def test_every_kernel_configuration(ctx):
+    """Each (lanes, words) pair that covers M scores identically."""
+    rng = np.random.default_rng(3)
+    db = synth.random_database(300, 200, rng, alphabet=21)
+    ddb = mpf.Database(ctx, db.residues, db.offsets, db.lengths)
+    for M in (24, 90, 300):
+        p = synth.make_profile(M, rng)
+        cfgs = [(lg, w) for lg in (1, 2, 4, 8, 16, 32) for w in range(4, 49, 4)
+                if 2 * lg * w >= M and 2 * lg * w < M + 2 * lg * 16]
+        check_profile(ctx, p, db, ddb, configs=cfgs)
+
+
+def test_edge_databases(ctx):
+    rng = np.random.default_rng(5)
+    p = synth.make_profile(50, rng)
+    # all empty, single residue, one long sequence, many tiny ones
+    cases = [
+        synth.Database(np.zeros(0, np.uint8), np.zeros(3, np.uint64), np.zeros(3, np.uint32)),
+        synth.Database(np.array([4], np.uint8), np.zeros(1, np.uint64), np.ones(1, np.uint32)),
+        synth.make_database(1, 20000, 20000, 20000, rng),
+        synth.make_database(5000, 3, 1, 8, rng),
+    ]
+    for db in cases:
+        check_profile(ctx, p, db)
+
+
+def test_saturated_bias_and_empty_sequences(ctx):
+    """bias = 255 puts the MSV overflow threshold at 0: every non-empty
+    sequence overflows at its first row, an empty one never does; padding
+    rows after a sequence's end must not count as rows."""
+    rng = np.random.default_rng(9)
+    lengths = np.array([0, 1, 2, 3, 0, 5, 0, 40, 0, 1], np.uint32)
+    offsets = np.zeros(lengths.size, np.uint64)
+    offsets[1:] = np.cumsum(lengths[:-1])
+    db = synth.Database(rng.integers(0, 20, int(lengths.sum())).astype(np.uint8), offsets, lengths)
+    for bias in (255, 254, 200):
+        for M in (3, 70):
+            p = synth.random_profile(M, 20, rng, bias=bias, base=190)
+            check_profile(ctx, p, db)
+
+
+def test_host_and_device_outputs_agree(ctx):
+    wl = synth.make_workload(0, n_seqs=2000)
+    p = wl.profiles[0]
+    prof = mpf.Profile(ctx, p)
+    ddb = mpf.Database(ctx, wl.db.residues, wl.db.offsets, wl.db.lengths)
+    for gf, _ in FILTERS:
+        a = run_gpu(ctx, gf, prof, ddb, on_device=True)
+        b = run_gpu(ctx, gf, prof, ddb, on_device=False)
+        assert_same(a, b, "host vs device outputs")
+
+
+# ------------------------------------------------------- batch and plans ---
+
+def test_batch_and_graph_equal_single_scans(ctx):
+    wl = synth.make_workload(2, n_seqs=3000, n_queries=10)
+    ddb = mpf.Database(ctx, wl.db.residues, wl.db.offsets, wl.db.lengths)
+    profs = [mpf.Profile(ctx, p) for p in wl.profiles]
+    n, q = ddb.n_seqs, len(profs)
+    dev = torch.device("cuda", 0)
+    for gf, of in FILTERS:
+        single = [run_gpu(ctx, gf, pr, ddb) for pr in profs]
+        raw = np.empty(q * n, np.uint8)
+        flag = np.empty(q * n, np.uint8)
+        nat = np.empty(q * n, np.float32)
+        mpf.scan_batch(ctx, gf, profs, ddb, raw, flag, nat)
+        draw = torch.empty(q * n, dtype=torch.uint8, device=dev)
+        dflag = torch.empty(q * n, dtype=torch.uint8, device=dev)
+        dnat = torch.empty(q * n, dtype=torch.float32, device=dev)
+        plan = mpf.Plan(ctx, gf, profs, ddb, draw, dflag, dnat)
+        assert plan.kernel_launches >= 1
+        plan.launch()
+        ctx.sync()
+        eager = (draw.cpu().numpy(), dflag.cpu().numpy(), dnat.cpu().numpy())
+        draw.zero_(), dflag.zero_(), dnat.zero_()
+        torch.cuda.synchronize()
+        plan.capture_graph()
+        for _ in range(2):
+            plan.launch()
+        ctx.sync()
+        graph = (draw.cpu().numpy(), dflag.cpu().numpy(), dnat.cpu().numpy())
+        plan.close()
+        for i in range(q):
+            sl = slice(i * n, (i + 1) * n)
+            exp = oracle.scan(of, wl.profiles[i], wl.db.residues, wl.db.offsets, wl.db.lengths,
+                              nthreads=8)
+            assert_same(single[i], exp, f"single q{i}")
+            assert_same((raw[sl], flag[sl], nat[sl]), exp, f"batch q{i}")
+            assert_same(tuple(a[sl] for a in eager), exp, f"plan q{i}")
+            assert_same(tuple(a[sl] for a in graph), exp, f"graph q{i}")
+
+
+# ------------------------------------------------------------ arguments ---
+
+def test_invalid_arguments(ctx):
+    rng = np.random.default_rng(1)
+    bad = synth.Database(np.array([1, 2, 40], np.uint8), np.zeros(1, np.uint64),
+                         np.full(1, 3, np.uint32))
+    with pytest.raises(mpf.MpfError) as e:
+        mpf.Database(ctx, bad.residues, bad.offsets, bad.lengths)
+    assert e.value.status == mpf.MPF_EINVAL
+    out_of_range = synth.Database(np.array([1, 2], np.uint8), np.array([1], np.uint64),
+                                  np.full(1, 5, np.uint32))
+    with pytest.raises(mpf.MpfError):
+        mpf.Database(ctx, out_of_range.residues, out_of_range.offsets, out_of_range.lengths)
+    big = synth.random_profile(mpf.max_model_length() + 1, 20, rng)
+    with pytest.raises(mpf.MpfError) as e:
+        mpf.Profile(ctx, big)
+    assert e.value.status == mpf.MPF_EUNSUPPORTED
+    p = mpf.Profile(ctx, synth.make_profile(100, rng))
+    with pytest.raises(mpf.MpfError):
+        p.set_config(mpf.MSV, 1, 8)        # 16 cells < M
+    with pytest.raises(mpf.MpfError):
+        p.set_config(mpf.MSV, 3, 8)        # not a built lane count
+    p.set_config(mpf.MSV, 4, 16)
+    assert p.get_config(mpf.MSV) == (4, 16)
+    p.set_config(mpf.MSV, 0, 0)
+    assert p.get_config(mpf.MSV) != (4, 16)
