@@ -184,6 +184,35 @@ int mpf_plan_capture_graph(mpf_plan *plan);
 int mpf_plan_kernel_launches(const mpf_plan *plan);
 void mpf_plan_destroy(mpf_plan *plan);
 
+/*
+ * Allocation-free scan.  The paper has no counterpart: this entry point exists
+ * for callers that cannot allocate device memory when they score, such as
+ * code recording a CUDA graph under a capture mode that forbids allocation,
+ * services that run under a fixed device-memory budget, or hosts whose device
+ * allocator is owned by another framework.  It scores like mpf_msv_scan /
+ * mpf_ssv_scan (filter = MPF_MSV or MPF_SSV) but calls no cudaMalloc, cudaFree
+ * or other allocating routine: its query descriptor, work counter, status word
+ * and striped cost table live in one file-scope device array of
+ * 512 + 224 KiB = 229,888 bytes that every GPU loading the library holds until
+ * the process exits.
+ *   raw, overflow: device pointers, n_seqs bytes each; nat: device pointer of
+ *     n_seqs floats or NULL.  Host pointers are rejected (MPF_EINVAL).
+ *   Asynchronous on the context stream, like a scan into device outputs.
+ *   A profile whose table image for the chosen kernel configuration exceeds
+ *     224 KiB is rejected with MPF_EUNSUPPORTED (none of the built
+ *     configurations does; the largest needs 202,832 bytes).
+ *   The first call on a device looks up the array's device address (once per
+ *     device, with that device current); make that first call before any
+ *     stream capture.
+ *   All calls share the one array and each call overwrites it (the counter
+ *     and status word are cleared on the stream): calls ordered on one stream
+ *     are safe, calls whose kernels overlap on the GPU (other streams or
+ *     contexts on the same device) race and give wrong results.
+ * Errors: MPF_EINVAL, MPF_EUNSUPPORTED, MPF_ECUDA.
+ */
+int mpf_scan_noalloc(mpf_ctx *ctx, int filter, const mpf_profile *prof, const mpf_db *db,
+                     uint8_t *raw, uint8_t *overflow, float *nat);
+
 #ifdef __cplusplus
 }
 #endif

@@ -71,6 +71,7 @@ def load(path: str = LIB_PATH):
         "mpf_plan_capture_graph": (i32, [vp]),
         "mpf_plan_kernel_launches": (i32, [vp]),
         "mpf_plan_destroy": (None, [vp]),
+        "mpf_scan_noalloc": (i32, [vp, i32, vp, vp, vp, vp, vp]),
     }
     for name, (res, args) in sig.items():
         fn = getattr(lib, name)
@@ -287,3 +288,11 @@ class Plan:
             self.close()
         except Exception:
             pass
+
+
+def scan_noalloc(ctx: Context, filter: int, prof: Profile, db: Database, raw, overflow, nat=None):
+    """``mpf_scan_noalloc``: a scan into device buffers that allocates no
+    device memory (scratch lives in a fixed device array inside the library;
+    calls overlapping on the GPU race)."""
+    _check(load().mpf_scan_noalloc(ctx.handle, int(filter), prof.handle, db.handle, _ptr(raw),
+                                   _ptr(overflow), _ptr(nat)), "mpf_scan_noalloc")
