@@ -271,20 +271,29 @@ def run_mpf(args):
             b.synchronize()
             per_kernel[f].append((i, a.elapsed_time(b)))
 
-    # Roofline of the dominant kernel (the filter with more plain kernel time).
+    # Roofline of the dominant kernel: the (filter, query) launch with the
+    # largest total device time in the plain form.
     tot = {f: sum(ms for _, ms in per_kernel[f]) for f, _ in filters}
-    dom = max(tot, key=tot.get)
-    n_l = len(per_kernel[dom])
-    cells_dom = sum(wl.profiles[i].M * res for i, _ in per_kernel[dom])
-    achieved = cells_dom / (tot[dom] * 1e-3) / 1e9      # GCUPS over its launches
+    by_launch = {}
+    for f, _ in filters:
+        for i, ms in per_kernel[f]:
+            by_launch.setdefault((f, i), []).append(ms)
+    dom_f, dom_i = max(by_launch, key=lambda k: sum(by_launch[k]))
+    durs = by_launch[(dom_f, dom_i)]
+    avg_ms = sum(durs) / len(durs)
+    dom_m = wl.profiles[dom_i].M
+    achieved = dom_m * res / (avg_ms * 1e-3) / 1e9      # GCUPS of one launch
+    lanes, words = profs[dom_i].get_config(mpf.MSV if dom_f == "msv" else mpf.SSV)
     sm_mhz = clocks.get("sm_mhz") or 2070.0
     nsm = torch.cuda.get_device_properties(dev).multi_processor_count
-    peak = nsm * INT_LANES_PER_SM_CLK * CELLS_PER_LANE_OP / OPS_PER_CELL[dom] * sm_mhz * 1e6 / 1e9
+    peak = nsm * INT_LANES_PER_SM_CLK * CELLS_PER_LANE_OP / OPS_PER_CELL[dom_f] * sm_mhz * 1e6 / 1e9
     roofline = {"bound": "alu", "achieved": achieved, "peak": peak, "unit": "GCUPS",
-                "frac": achieved / peak, "traffic": None, "kernel": f"scan_kernel ({dom})",
-                "launches_averaged": n_l,
+                "frac": achieved / peak, "traffic": None,
+                "kernel": f"scan_kernel<{lanes},{words},{'MSV' if dom_f == 'msv' else 'SSV'}> M={dom_m}",
+                "launches_averaged": len(durs), "avg_launch_ms": avg_ms,
+                "algorithmic_cells_per_launch": dom_m * res,
                 "peak_basis": f"{nsm} SMs x {INT_LANES_PER_SM_CLK} int lanes/clk x "
-                              f"{CELLS_PER_LANE_OP} cells/op / {OPS_PER_CELL[dom]} ops/cell x "
+                              f"{CELLS_PER_LANE_OP} cells/op / {OPS_PER_CELL[dom_f]} ops/cell x "
                               f"{sm_mhz:.0f} MHz (median SM clock in the timed region)"}
 
     gcups_batched = 2 * cells_per_filter * world / (ms_batched * 1e-3) / 1e9
@@ -353,6 +362,36 @@ def run_mpf(args):
         dist.destroy_process_group()
 
 
+def run_profile_case(args):
+    """Small case for ncu: the 500,000-sequence database (larger than L2) and
+    one query of M = args.profile_m; one warm-up and one measured plain launch
+    per filter (kernel launches 0-1 warm-up, 2 = MSV, 3 = SSV)."""
+    import torch
+    from paper_1707_09683_gb300 import build, mpf, synth
+    build.build()
+    wl = synth.make_workload(1)
+    rng = np.random.default_rng(0)
+    prof_rec = next((p for p in wl.profiles if p.M == args.profile_m), None) or \
+        synth.make_profile(args.profile_m, rng)
+    ctx = mpf.Context(0)
+    db = mpf.Database(ctx, wl.db.residues, wl.db.offsets, wl.db.lengths)
+    prof = mpf.Profile(ctx, prof_rec)
+    n = db.n_seqs
+    dev = torch.device("cuda", 0)
+    outs = [torch.empty(n, dtype=torch.uint8, device=dev), torch.empty(n, dtype=torch.uint8, device=dev),
+            torch.empty(n, dtype=torch.float32, device=dev)]
+    plans = [mpf.Plan(ctx, f, [prof], db, *outs) for f in (mpf.MSV, mpf.SSV)]
+    for rep in range(2):
+        for pl in plans:
+            pl.launch()
+        ctx.sync()
+    for pl in plans:
+        pl.close()
+    print(json.dumps({"profile_case": wl.name, "M": prof_rec.M, "n_seqs": n,
+                      "residues": db.n_residues, "config_msv": prof.get_config(mpf.MSV),
+                      "config_ssv": prof.get_config(mpf.SSV)}))
+
+
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
@@ -364,8 +403,12 @@ def main():
     ap.add_argument("--cpu-sample", type=int, default=6000)
     ap.add_argument("--ref-sample", type=int, default=3000)
     ap.add_argument("--no-cpu", action="store_true")
+    ap.add_argument("--profile-case", action="store_true")
+    ap.add_argument("--profile-m", type=int, default=2405)
     args = ap.parse_args()
-    if args.impl == "reference":
+    if args.profile_case:
+        run_profile_case(args)
+    elif args.impl == "reference":
         run_reference(args)
     else:
         run_mpf(args)
