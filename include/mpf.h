@@ -96,8 +96,8 @@ int mpf_sync(mpf_ctx *ctx);
  *           base bytes of the recurrences above
  *   tjb_b:  the N/C/J loop byte used when tjb_by_len is NULL
  *   tjb_by_len: nullable host pointer of n_tjb bytes: tjb for sequence length
- *           L is tjb_by_len[min(L, n_tjb - 1)] ("sc_B initialised from Len",
- *           Alg. 2)
+ *           L is tjb_by_len[min(L, n_tjb - 1)] (Alg. 2 derives the begin score
+ *           of each sequence from its length)
  *   scale_b: units per nat of the nat score (finite, > 0)
  * The profile keeps copies of cost and tjb_by_len.
  * Errors: MPF_EINVAL, MPF_EUNSUPPORTED (M too large), MPF_ENOMEM, MPF_ECUDA.
