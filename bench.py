@@ -327,6 +327,12 @@ def run_mpf(args):
     e2e_s = max_over_ranks(e2e_s, world)
     e2e_gcups = 2 * cells_per_filter * world / e2e_s / 1e9
 
+    # Serving: continuous batching of arriving queries (model lengths drawn as
+    # in the serving workload) against the resident database, per offered load.
+    serving = None
+    if world == 1 and not args.no_serve:
+        serving = run_serving(wl.db, args.serve_rates, args.serve_requests, local)
+
     cpu = None
     if rank == 0 and world == 1 and not args.no_cpu:
         cpu, _ = cpu_baseline(wl, args.cpu_sample)
@@ -351,6 +357,7 @@ def run_mpf(args):
                     "d2h_bytes_per_step": int(d2h), "s_per_step": e2e_s,
                     "path": "mpf_profile_create from host bytes + mpf_scan_batch (MSV, SSV) into "
                             "host buffers + mpf_profile_destroy; database resident"},
+            "serving": serving,
             "gpu_launches": launches_per_step * args.steps,
             "clocks": clocks,
         }
@@ -360,6 +367,34 @@ def run_mpf(args):
     if world > 1:
         import torch.distributed as dist
         dist.destroy_process_group()
+
+
+def run_serving(db_record, rates, n_requests, device, seed=3):
+    """p50/p99 latency and GCUPS of the continuous-batching server per offered
+    load (Poisson arrivals); queries drawn like the serving workload (M
+    log-uniform in [50, 2000])."""
+    from paper_1707_09683_gb300 import synth
+    from paper_1707_09683_gb300.serve import Request, ScanServer
+    import math
+    rng = np.random.default_rng(seed)
+    Ms = [int(round(math.exp(v))) for v in rng.uniform(math.log(50), math.log(2000), n_requests)]
+    profiles = [synth.make_profile(m, rng) for m in Ms]
+    server = ScanServer(db_record, device=device, n_streams=4, max_batch=8, max_queue=4 * n_requests)
+    warm = [Request(-1 - i, profiles[i], arrival=0.0) for i in range(min(4, n_requests))]
+    server.run(warm)
+    out = []
+    for rate in rates:
+        arr = synth.poisson_arrivals(rate, n_requests, seed)
+        reqs = [Request(i, profiles[i], arrival=float(arr[i] - arr[0])) for i in range(n_requests)]
+        st = server.run(reqs, offered_rate=rate)
+        out.append(st.as_dict())
+        log(f"serving {rate:6.1f} q/s: p50 {st.p50_ms:8.1f} ms p99 {st.p99_ms:8.1f} ms "
+            f"{st.gcups:9.1f} GCUPS batch {st.mean_batch:.1f}")
+    fp = server.footprint_bytes
+    server.close()
+    return {"unit": "ms / GCUPS", "requests_per_rate": n_requests, "filters": ["ssv", "msv"],
+            "query_M": "log-uniform [50, 2000]", "streams": 4, "max_batch": 8,
+            "output_arena_bytes": fp, "by_rate": out}
 
 
 def run_profile_case(args):
@@ -403,6 +438,9 @@ def main():
     ap.add_argument("--cpu-sample", type=int, default=6000)
     ap.add_argument("--ref-sample", type=int, default=3000)
     ap.add_argument("--no-cpu", action="store_true")
+    ap.add_argument("--no-serve", action="store_true")
+    ap.add_argument("--serve-rates", type=float, nargs="+", default=[10, 50, 100, 200, 500])
+    ap.add_argument("--serve-requests", type=int, default=24)
     ap.add_argument("--profile-case", action="store_true")
     ap.add_argument("--profile-m", type=int, default=2405)
     args = ap.parse_args()

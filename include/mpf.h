@@ -29,8 +29,12 @@
  *     MPF_ECUDA the context should be destroyed.
  *   - Inputs are copied; the caller keeps ownership of its buffers.  Handles
  *     are owned by the caller and released with the matching *_destroy, which
- *     accepts NULL.  A profile or database must be used with the context it
- *     was created in and destroyed before that context.
+ *     accepts NULL.  A profile or database may be used with any context on
+ *     the device it was created on (contexts are streams: several contexts
+ *     can scan one resident database concurrently); it must be destroyed
+ *     before the context it was created in, and only after the scans that
+ *     use it have completed (scans queued on its own context's stream are
+ *     ordered before the release automatically).
  *   - Output buffers are caller-allocated and may be host or device memory
  *     (detected per pointer).  With device outputs a scan is asynchronous on
  *     the context stream; call mpf_sync() (or synchronise that stream) before

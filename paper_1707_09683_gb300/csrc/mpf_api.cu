@@ -49,6 +49,9 @@ struct mpf_ctx {
   cudaStream_t fork[8] = {};
   int n_fork = 0;
   cudaStream_t capture = nullptr;
+  // Side stream for uploads that other streams must see complete (tables,
+  // length tables): allocated and copied on it, then synchronised.
+  cudaStream_t util = nullptr;
   // One-shot plans whose kernels may still be running.
   std::vector<mpf_plan *> pending;
 };
@@ -186,12 +189,15 @@ int get_table(const mpf_profile *p, int lanes, int words, DevTable *out) {
     const int16_t s = (int16_t)m;
     memcpy(&img[g.smax_off + 2 * x], &s, 2);
   }
-  DeviceGuard dg(p->ctx->device);
+  mpf_ctx *ctx = p->ctx;
+  DeviceGuard dg(ctx->device);
   uint4 *d = nullptr;
-  MPF_CUDA(cudaMalloc(&d, g.table_bytes));
-  cudaError_t e = cudaMemcpy(d, img.data(), g.table_bytes, cudaMemcpyHostToDevice);
+  MPF_CUDA(cudaMallocAsync((void **)&d, g.table_bytes, ctx->util));
+  cudaError_t e = cudaMemcpyAsync(d, img.data(), g.table_bytes, cudaMemcpyHostToDevice, ctx->util);
+  if (e == cudaSuccess) e = cudaStreamSynchronize(ctx->util);
   if (e != cudaSuccess) {
-    cudaFree(d);
+    (void)cudaGetLastError();
+    cudaFreeAsync(d, ctx->util);
     return MPF_ECUDA;
   }
   DevTable t;
@@ -249,9 +255,10 @@ void plan_free(mpf_plan *pl) {
   if (!pl) return;
   DeviceGuard dg(pl->ctx->device);
   if (pl->graph) cudaGraphExecDestroy(pl->graph);
+  // Ordered after the plan's last launch, which joins back into this stream.
   for (auto &g : pl->groups) {
-    cudaFree(g.d_queries);
-    cudaFree(g.d_counter);
+    if (g.d_queries) cudaFreeAsync(g.d_queries, pl->ctx->stream);
+    if (g.d_counter) cudaFreeAsync(g.d_counter, pl->ctx->stream);
   }
   for (auto e : pl->events) cudaEventDestroy(e);
   (void)cudaGetLastError();
@@ -286,7 +293,7 @@ int plan_create(mpf_ctx *ctx, int filter, const mpf_profile *const *profs, int n
                 const mpf_db *db, uint8_t *raw, uint8_t *flag, float *nat, mpf_plan **out) {
   if (!ctx || !profs || n_q < 1 || !db || !raw || !flag || !out) return MPF_EINVAL;
   if (filter != MPF_MSV && filter != MPF_SSV) return MPF_EINVAL;
-  if (db->ctx != ctx) return MPF_EINVAL;
+  if (db->ctx->device != ctx->device) return MPF_EINVAL;
   mpf_plan *pl = new (std::nothrow) mpf_plan;
   if (!pl) return MPF_ENOMEM;
   pl->ctx = ctx;
@@ -294,7 +301,7 @@ int plan_create(mpf_ctx *ctx, int filter, const mpf_profile *const *profs, int n
   std::map<std::tuple<int, int, int>, std::vector<QueryDesc>> byconf;
   for (int i = 0; i < n_q; ++i) {
     const mpf_profile *p = profs[i];
-    if (!p || p->ctx != ctx) {
+    if (!p || p->ctx->device != ctx->device) {
       plan_free(pl);
       return MPF_EINVAL;
     }
@@ -343,14 +350,14 @@ int plan_create(mpf_ctx *ctx, int filter, const mpf_profile *const *profs, int n
       return rc;
     }
     g.n_queries = (uint32_t)kv.second.size();
-    cudaError_t e = cudaMalloc(&g.d_queries, sizeof(QueryDesc) * kv.second.size());
-    if (e == cudaSuccess) e = cudaMalloc(&g.d_counter, sizeof(uint32_t));
+    cudaError_t e = cudaMallocAsync((void **)&g.d_queries, sizeof(QueryDesc) * kv.second.size(), ctx->stream);
+    if (e == cudaSuccess) e = cudaMallocAsync((void **)&g.d_counter, sizeof(uint32_t), ctx->stream);
     if (e == cudaSuccess)
       e = cudaMemcpyAsync(g.d_queries, kv.second.data(), sizeof(QueryDesc) * kv.second.size(),
                           cudaMemcpyHostToDevice, ctx->stream);
     if (e != cudaSuccess) {
-      cudaFree(g.d_queries);
-      cudaFree(g.d_counter);
+      if (g.d_queries) cudaFreeAsync(g.d_queries, ctx->stream);
+      if (g.d_counter) cudaFreeAsync(g.d_counter, ctx->stream);
       (void)cudaGetLastError();
       plan_free(pl);
       return e == cudaErrorMemoryAllocation ? MPF_ENOMEM : MPF_ECUDA;
@@ -517,6 +524,7 @@ int mpf_ctx_create(int device, void *cuda_stream, mpf_ctx **out) {
       ctx->own_stream = (e == cudaSuccess);
     }
   }
+  if (e == cudaSuccess) e = cudaStreamCreateWithFlags(&ctx->util, cudaStreamNonBlocking);
   if (e == cudaSuccess) e = cudaMalloc(&ctx->d_status, sizeof(int));
   if (e == cudaSuccess) e = cudaMemset(ctx->d_status, 0, sizeof(int));
   if (e != cudaSuccess) {
@@ -539,6 +547,10 @@ void mpf_ctx_destroy(mpf_ctx *ctx) {
   cudaFree(ctx->d_out);
   for (int i = 0; i < ctx->n_fork; ++i) cudaStreamDestroy(ctx->fork[i]);
   if (ctx->capture) cudaStreamDestroy(ctx->capture);
+  if (ctx->util) {
+    cudaStreamSynchronize(ctx->util);
+    cudaStreamDestroy(ctx->util);
+  }
   if (ctx->own_stream) cudaStreamDestroy(ctx->stream);
   (void)cudaGetLastError();
   delete ctx;
@@ -582,11 +594,12 @@ int mpf_profile_create(mpf_ctx *ctx, int M, int K, const uint8_t *cost, uint8_t 
   if (tjb_by_len) {
     p->tjb_min = *std::min_element(tjb_by_len, tjb_by_len + n_tjb);
     DeviceGuard dg(ctx->device);
-    cudaError_t e = cudaMalloc(&p->d_tjb, n_tjb);
-    if (e == cudaSuccess) e = cudaMemcpy(p->d_tjb, tjb_by_len, n_tjb, cudaMemcpyHostToDevice);
+    cudaError_t e = cudaMallocAsync((void **)&p->d_tjb, n_tjb, ctx->util);
+    if (e == cudaSuccess) e = cudaMemcpyAsync(p->d_tjb, tjb_by_len, n_tjb, cudaMemcpyHostToDevice, ctx->util);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(ctx->util);
     if (e != cudaSuccess) {
       (void)cudaGetLastError();
-      cudaFree(p->d_tjb);
+      if (p->d_tjb) cudaFreeAsync(p->d_tjb, ctx->util);
       delete p;
       return e == cudaErrorMemoryAllocation ? MPF_ENOMEM : MPF_ECUDA;
     }
@@ -605,8 +618,9 @@ int mpf_profile_create(mpf_ctx *ctx, int M, int K, const uint8_t *cost, uint8_t 
 void mpf_profile_destroy(mpf_profile *p) {
   if (!p) return;
   DeviceGuard dg(p->ctx->device);
-  for (auto &kv : p->tables) cudaFree(kv.second.ptr);
-  cudaFree(p->d_tjb);
+  // Ordered after the scans queued on the profile's context stream.
+  for (auto &kv : p->tables) cudaFreeAsync(kv.second.ptr, p->ctx->stream);
+  if (p->d_tjb) cudaFreeAsync(p->d_tjb, p->ctx->stream);
   (void)cudaGetLastError();
   delete p;
 }
@@ -835,7 +849,7 @@ extern "C" int mpf_scan_noalloc(mpf_ctx *ctx, int filter, const mpf_profile *pro
                                 const mpf_db *db, uint8_t *raw, uint8_t *overflow, float *nat) {
   if (!ctx || !prof || !db || !raw || !overflow) return MPF_EINVAL;
   if (filter != MPF_MSV && filter != MPF_SSV) return MPF_EINVAL;
-  if (prof->ctx != ctx || db->ctx != ctx) return MPF_EINVAL;
+  if (prof->ctx->device != ctx->device || db->ctx->device != ctx->device) return MPF_EINVAL;
   if (ctx->device < 0 || ctx->device >= kNoAllocMaxDevices) return MPF_EUNSUPPORTED;
   DeviceGuard dg(ctx->device);
   if (!is_device_ptr(raw) || !is_device_ptr(overflow) || (nat && !is_device_ptr(nat)))

@@ -113,12 +113,27 @@ def max_model_length() -> int:
 
 
 class Context:
-    """``mpf_ctx``: a device and the stream the library launches on."""
+    """``mpf_ctx``: a device and the stream the library launches on.
 
-    def __init__(self, device: int = 0, stream: Optional[int] = None):
+    Without an explicit ``stream`` the context launches on a new
+    ``torch.cuda.Stream`` that this object keeps alive, so torch (its events,
+    its pinned-memory bookkeeping) never sees a stream the library destroyed.
+    """
+
+    def __init__(self, device: int = 0, stream=None):
         lib = load()
+        self._torch_stream = None
+        if stream is None:
+            import torch
+            self._torch_stream = torch.cuda.Stream(device=torch.device("cuda", int(device)))
+            handle = self._torch_stream.cuda_stream
+        elif hasattr(stream, "cuda_stream"):
+            self._torch_stream = stream
+            handle = stream.cuda_stream
+        else:
+            handle = int(stream)
         h = ctypes.c_void_p()
-        _check(lib.mpf_ctx_create(int(device), stream, ctypes.byref(h)), "mpf_ctx_create")
+        _check(lib.mpf_ctx_create(int(device), handle or None, ctypes.byref(h)), "mpf_ctx_create")
         self.handle = h
         self.device = int(device)
 
@@ -127,6 +142,8 @@ class Context:
         return int(load().mpf_ctx_stream(self.handle) or 0)
 
     def torch_stream(self):
+        if self._torch_stream is not None:
+            return self._torch_stream
         import torch
         return torch.cuda.ExternalStream(self.stream, device=torch.device("cuda", self.device))
 

@@ -1,0 +1,40 @@
+"""The autotuner times built configurations on the device, keeps the
+fastest, and the tuned profile still scores exactly like the oracle."""
+import numpy as np
+import pytest
+
+torch = pytest.importorskip("torch")
+
+import oracle
+from paper_1707_09683_gb300 import autotune, build, mpf, synth
+
+pytestmark = pytest.mark.gpu
+
+
+def test_autotune_picks_a_candidate_and_keeps_parity(tmp_path):
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    build.build()
+    wl = synth.make_workload(1, n_seqs=20000)
+    ctx = mpf.Context(0)
+    db = mpf.Database(ctx, wl.db.residues, wl.db.offsets, wl.db.lengths)
+    cache = str(tmp_path / "tune.json")
+    tuner = autotune.Autotuner(ctx, db, cache_path=cache, reps=2)
+    for rec in (wl.profiles[1], wl.profiles[3]):          # M = 100, 400
+        prof = mpf.Profile(ctx, rec)
+        for filt, of in ((mpf.SSV, oracle.SSV), (mpf.MSV, oracle.MSV)):
+            cfg = tuner.tune(prof, filt)
+            assert cfg in autotune.candidates(rec.M)
+            assert prof.get_config(filt) == cfg
+            times = tuner.timings[tuner.key(filt, rec.M)]
+            assert min(times.values()) == times[f"{cfg[0]}x{cfg[1]}"]
+            n = db.n_seqs
+            raw, flag = np.empty(n, np.uint8), np.empty(n, np.uint8)
+            (mpf.ssv_scan if filt == mpf.SSV else mpf.msv_scan)(ctx, prof, db, raw, flag)
+            exp = oracle.scan(of, rec, wl.db.residues, wl.db.offsets, wl.db.lengths,
+                              index=np.arange(0, n, 7, dtype=np.uint64), nthreads=8)
+            assert np.array_equal(raw[::7], exp[0]) and np.array_equal(flag[::7], exp[1])
+        prof.close()
+    tuner.save()
+    again = autotune.Autotuner(ctx, db, cache_path=cache)
+    assert again.table == tuner.table
