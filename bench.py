@@ -198,6 +198,10 @@ def run_mpf(args):
     stream = ctx.torch_stream()
     db = mpf.Database(ctx, wl.db.residues, wl.db.offsets, wl.db.lengths)
     profs = [mpf.Profile(ctx, p) for p in wl.profiles]
+    arith = {"auto": mpf.ARITH_AUTO, "i16": mpf.ARITH_I16, "f16": mpf.ARITH_F16}[args.arith]
+    for pr in profs:
+        for code in (mpf.MSV, mpf.SSV):
+            pr.set_arith(code, arith)
     n, q = db.n_seqs, len(profs)
     res = db.n_residues
     cells_per_filter = sum(p.M for p in wl.profiles) * res
@@ -346,6 +350,7 @@ def run_mpf(args):
             "config": {"workload": wl.name, "queries": [p.M for p in wl.profiles],
                        "n_seqs": n, "residues": res, "filters": ["msv", "ssv"],
                        "form": "batched persistent plan per filter, CUDA-graph replay",
+                       "cell_arith": args.arith,
                        "l2": "database (%.0f MB) larger than L2; no flush" % (res / 1e6),
                        "cells_per_step": 2 * cells_per_filter},
             "plain": {"value": gcups_plain, "unit": "GCUPS", "ms_per_step": ms_plain,
@@ -438,6 +443,7 @@ def main():
     ap.add_argument("--cpu-sample", type=int, default=6000)
     ap.add_argument("--ref-sample", type=int, default=3000)
     ap.add_argument("--no-cpu", action="store_true")
+    ap.add_argument("--arith", default="auto", choices=["auto", "i16", "f16"])
     ap.add_argument("--no-serve", action="store_true")
     ap.add_argument("--serve-rates", type=float, nargs="+", default=[10, 50, 100, 200, 500])
     ap.add_argument("--serve-requests", type=int, default=24)

@@ -124,6 +124,17 @@ int mpf_profile_set_config(mpf_profile *prof, int filter, int lanes, int words);
 int mpf_profile_get_config(const mpf_profile *prof, int filter, int *lanes, int *words);
 
 /*
+ * Cell arithmetic of a profile's scans for one filter.  Both give identical
+ * results (the recurrences stay exact): MPF_ARITH_I16 updates two 16-bit
+ * integer cells per DPX instruction on the integer pipe, MPF_ARITH_F16 holds
+ * the same integers as half-precision values and updates them with a fused
+ * add-and-clamp on the FMA pipe.  MPF_ARITH_AUTO (default) picks per filter.
+ * Errors: MPF_EINVAL.
+ */
+enum { MPF_ARITH_AUTO = 0, MPF_ARITH_I16 = 1, MPF_ARITH_F16 = 2 };
+int mpf_profile_set_arith(mpf_profile *prof, int filter, int arith);
+
+/*
  * Upload a database of digital sequences (host pointers).
  *   residues: n_residues codes, each < 32
  *   offsets, lengths: n_seqs entries; sequence s is

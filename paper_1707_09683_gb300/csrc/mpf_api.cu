@@ -71,7 +71,8 @@ struct mpf_profile {
   uint32_t n_tjb = 0;
   int tjb_min = 0;
   int cfg_lanes[2] = {0, 0}, cfg_words[2] = {0, 0};
-  mutable std::map<std::pair<int, int>, DevTable> tables;
+  int arith[2] = {MPF_ARITH_AUTO, MPF_ARITH_AUTO};
+  mutable std::map<std::tuple<int, int, int>, DevTable> tables;
   mutable std::mutex mu;
 };
 
@@ -152,24 +153,29 @@ bool msv_fast_ok(const mpf_profile *p) {
   return p->bias < 255 && xb < 255 - p->bias;
 }
 
-// Build (or fetch) the striped shared-memory image of a profile.
-int get_table(const mpf_profile *p, int lanes, int words, DevTable *out) {
-  std::lock_guard<std::mutex> lk(p->mu);
-  auto key = std::make_pair(lanes, words);
-  auto it = p->tables.find(key);
-  if (it != p->tables.end()) {
-    *out = it->second;
-    return MPF_OK;
-  }
-  const TableGeom g = table_geom(lanes, words);
-  std::vector<uint8_t> img(g.table_bytes, 0);
-  const int M = p->M;
+// IEEE half bits of an integer that half represents exactly (|v| <= 2048,
+// or the padding score -16384).
+uint16_t half_bits(int v) {
+  if (v == 0) return 0;
+  const uint16_t sign = v < 0 ? 0x8000 : 0;
+  unsigned a = (unsigned)(v < 0 ? -v : v);
+  int e = 31 - __builtin_clz(a);                        // a in [2^e, 2^(e+1))
+  const unsigned m = e <= 10 ? (a << (10 - e)) - 1024u : (a >> (e - 10)) - 1024u;
+  return (uint16_t)(sign | ((unsigned)(e + 15) << 10) | (m & 0x3ffu));
+}
+
+// Fill the striped shared-memory image of a profile for (lanes, words) in
+// table format fmt: 16-bit scores s = bias - cost per (copy, residue row,
+// word quad, lane, word, half), then 33 int16 per-code best scores.
+void fill_table_image(const mpf_profile *p, const TableGeom &g, int fmt, uint8_t *img) {
+  memset(img, 0, g.table_bytes);
+  const int M = p->M, lanes = g.lanes, words = g.words;
   // Signed score of node k (0-based) for residue code x; padding nodes and
   // the padding code score kNegInf.
-  auto score = [&](int x, int k) -> int16_t {
-    if (x >= 32 || k >= M) return (int16_t)kNegInf;
+  auto score = [&](int x, int k) -> int {
+    if (x >= 32 || k >= M) return kNegInf;
     const int c = x < p->K ? (int)p->cost[(size_t)x * M + k] : 255;
-    return (int16_t)(p->bias - c);
+    return p->bias - c;
   };
   for (int c = 0; c < g.copies; ++c)
     for (int x = 0; x < kTableRows; ++x)
@@ -179,16 +185,31 @@ int get_table(const mpf_profile *p, int lanes, int words, DevTable *out) {
             const int k = (2 * l + h) * words + q;   // striped cell of (lane, half, word)
             const size_t off = (size_t)c * g.copy_bytes + (size_t)x * g.row_bytes +
                                ((size_t)(q / 4) * lanes + l) * 16 + (q % 4) * 4 + h * 2;
-            const int16_t s = score(x, k);
-            memcpy(&img[off], &s, 2);
+            const int sv = score(x, k);
+            const uint16_t bits = fmt == TABLE_F16 ? half_bits(sv) : (uint16_t)(int16_t)sv;
+            memcpy(&img[off], &bits, 2);
           }
   for (int x = 0; x < kTableRows; ++x) {
     int m = kNegInf;
     if (x < 32)
-      for (int k = 0; k < M; ++k) m = std::max(m, (int)score(x, k));
-    const int16_t s = (int16_t)m;
-    memcpy(&img[g.smax_off + 2 * x], &s, 2);
+      for (int k = 0; k < M; ++k) m = std::max(m, score(x, k));
+    const int16_t sv = (int16_t)m;
+    memcpy(&img[g.smax_off + 2 * x], &sv, 2);
   }
+}
+
+// Build (or fetch) the device copy of a profile's table image.
+int get_table(const mpf_profile *p, int lanes, int words, int fmt, DevTable *out) {
+  std::lock_guard<std::mutex> lk(p->mu);
+  auto key = std::make_tuple(lanes, words, fmt);
+  auto it = p->tables.find(key);
+  if (it != p->tables.end()) {
+    *out = it->second;
+    return MPF_OK;
+  }
+  const TableGeom g = table_geom(lanes, words);
+  std::vector<uint8_t> img(g.table_bytes, 0);
+  fill_table_image(p, g, fmt, img.data());
   mpf_ctx *ctx = p->ctx;
   DeviceGuard dg(ctx->device);
   uint4 *d = nullptr;
@@ -221,9 +242,13 @@ int ensure_out_scratch(mpf_ctx *ctx, size_t bytes) {
   return MPF_OK;
 }
 
+// Kernel mode of a profile for a filter.  Automatic arithmetic: fp16 cells
+// (FMA pipe) for both filters.
 int kernel_mode(const mpf_profile *p, int filter) {
-  if (filter == MPF_SSV) return MODE_SSV;
-  return msv_fast_ok(p) ? MODE_MSV_FAST : MODE_MSV_DIRECT;
+  const bool f16 = p->arith[filter] != MPF_ARITH_I16;
+  if (filter == MPF_SSV) return f16 ? MODE_SSV_F16 : MODE_SSV;
+  if (!msv_fast_ok(p)) return MODE_MSV_DIRECT;
+  return f16 ? MODE_MSV_FAST_F16 : MODE_MSV_FAST;
 }
 
 }  // namespace
@@ -311,8 +336,9 @@ int plan_create(mpf_ctx *ctx, int filter, const mpf_profile *const *profs, int n
       plan_free(pl);
       return MPF_EUNSUPPORTED;
     }
+    const int mode = kernel_mode(p, filter);
     DevTable t;
-    int rc = get_table(p, lanes, words, &t);
+    int rc = get_table(p, lanes, words, table_format(mode), &t);
     if (rc) {
       plan_free(pl);
       return rc;
@@ -336,7 +362,7 @@ int plan_create(mpf_ctx *ctx, int filter, const mpf_profile *const *profs, int n
     q.raw = raw + off;
     q.flag = flag + off;
     q.nat = nat ? nat + off : nullptr;
-    byconf[std::make_tuple(lanes, words, kernel_mode(p, filter))].push_back(q);
+    byconf[std::make_tuple(lanes, words, mode)].push_back(q);
   }
   DeviceGuard dg(ctx->device);
   for (auto &kv : byconf) {
@@ -639,6 +665,13 @@ int mpf_profile_set_config(mpf_profile *p, int filter, int lanes, int words) {
   return MPF_OK;
 }
 
+int mpf_profile_set_arith(mpf_profile *p, int filter, int arith) {
+  if (!p || (filter != MPF_MSV && filter != MPF_SSV)) return MPF_EINVAL;
+  if (arith != MPF_ARITH_AUTO && arith != MPF_ARITH_I16 && arith != MPF_ARITH_F16) return MPF_EINVAL;
+  p->arith[filter] = arith;
+  return MPF_OK;
+}
+
 int mpf_profile_get_config(const mpf_profile *p, int filter, int *lanes, int *words) {
   if (!p || !lanes || !words || (filter != MPF_MSV && filter != MPF_SSV)) return MPF_EINVAL;
   if (p->cfg_lanes[filter]) {
@@ -880,30 +913,7 @@ extern "C" int mpf_scan_noalloc(mpf_ctx *ctx, int filter, const mpf_profile *pro
   uint8_t *scratch = g_noalloc_dev[ctx->device];
 
   // Striped table image (same layout the kernel stages into shared memory).
-  memset(g_noalloc_image, 0, g.table_bytes);
-  const int M = prof->M;
-  auto score = [&](int x, int k) -> int16_t {
-    if (x >= 32 || k >= M) return (int16_t)kNegInf;
-    const int c = x < prof->K ? (int)prof->cost[(size_t)x * M + k] : 255;
-    return (int16_t)(prof->bias - c);
-  };
-  for (int c = 0; c < g.copies; ++c)
-    for (int x = 0; x < kTableRows; ++x)
-      for (int l = 0; l < lanes; ++l)
-        for (int q = 0; q < words; ++q)
-          for (int h = 0; h < 2; ++h) {
-            const size_t off = (size_t)c * g.copy_bytes + (size_t)x * g.row_bytes +
-                               ((size_t)(q / 4) * lanes + l) * 16 + (q % 4) * 4 + h * 2;
-            const int16_t sv = score(x, (2 * l + h) * words + q);
-            memcpy(&g_noalloc_image[off], &sv, 2);
-          }
-  for (int x = 0; x < kTableRows; ++x) {
-    int m = kNegInf;
-    if (x < 32)
-      for (int k = 0; k < M; ++k) m = std::max(m, (int)score(x, k));
-    const int16_t sv = (int16_t)m;
-    memcpy(&g_noalloc_image[g.smax_off + 2 * x], &sv, 2);
-  }
+  fill_table_image(prof, g, table_format(mode), g_noalloc_image);
 
   QueryDesc q;
   memset(&q, 0, sizeof(q));

@@ -8,6 +8,8 @@ namespace mpf {
     if (mode == MODE_SSV) return scan_kernel<8, W, MODE_SSV>;             \
     if (mode == MODE_MSV_FAST) return scan_kernel<8, W, MODE_MSV_FAST>;   \
     if (mode == MODE_MSV_DIRECT) return scan_kernel<8, W, MODE_MSV_DIRECT>; \
+    if (mode == MODE_SSV_F16) return scan_kernel<8, W, MODE_SSV_F16>; \
+    if (mode == MODE_MSV_FAST_F16) return scan_kernel<8, W, MODE_MSV_FAST_F16>; \
     return nullptr;
 
 KernelFn kernel_lg8(int words, int mode) {

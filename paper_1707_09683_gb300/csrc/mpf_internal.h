@@ -15,10 +15,19 @@ constexpr int kBlockThreads = 512;
 constexpr int kMaxWords = 48;
 
 enum Mode : int {
-  MODE_SSV = 0,         // Alg. 7
-  MODE_MSV_FAST = 1,    // Alg. 2, begin score held constant between J changes
-  MODE_MSV_DIRECT = 2,  // Alg. 2, J/B update after every row
+  MODE_SSV = 0,           // Alg. 7, 16-bit integer cells (DPX)
+  MODE_MSV_FAST = 1,      // Alg. 2, begin score held constant between J changes
+  MODE_MSV_DIRECT = 2,    // Alg. 2, J/B update after every row
+  MODE_SSV_F16 = 3,       // MODE_SSV with cells as fp16 integers (FMA pipe)
+  MODE_MSV_FAST_F16 = 4,  // MODE_MSV_FAST with cells as fp16 integers
 };
+constexpr int kNumModes = 5;
+
+// Score-table formats: signed 16-bit integers, or the same integers as fp16.
+enum TableFormat : int { TABLE_I16 = 0, TABLE_F16 = 1 };
+inline int table_format(int mode) {
+  return (mode == MODE_SSV_F16 || mode == MODE_MSV_FAST_F16) ? TABLE_F16 : TABLE_I16;
+}
 
 // One profile in one kernel layout (lives in device memory).
 struct QueryDesc {

@@ -31,11 +31,25 @@
 // xJ passes base, so each lane keeps a running maximum and the group reduces
 // it (Alg. 6) only on rows where some lane crosses the threshold at which xJ
 // would pass base or the score would overflow.  After the first such row
-// the group reduces every row (exact mode) until the sequence ends.
+// the group reduces every row (exact mode) until the sequence ends.  A row
+// can raise the running maximum by at most `bias`, so a warp runs four rows
+// without any per-row test whenever no lane is within 4 * bias of T.
+//
+// The F16 modes hold the same integers as IEEE half values and update a cell
+// pair with one fused add-and-clamp-at-zero (HFMA2.RELU, v * 1 + s), which
+// issues on the FMA pipe instead of the integer ALU pipe that the DPX
+// instructions use.  Every value a scored cell takes before its sequence
+// has reached the overflow threshold is an integer of magnitude below 2048,
+// which half precision represents exactly; later values only need to stay
+// above the threshold, and rounding is monotone.  Running maxima compare the
+// half bit patterns of non-negative values as unsigned integers.
 #pragma once
+#include <cuda_fp16.h>
 #include <cuda_runtime.h>
 #include <limits.h>
 #include <stdint.h>
+
+#include <type_traits>
 
 #include "mpf_internal.h"
 
@@ -65,12 +79,44 @@ __device__ __forceinline__ float nat_score(int num, float scale) {
   return __fsub_rn(__fdiv_rn(__int2float_rn(num), scale), 3.0f);
 }
 
+// Order-preserving key of a cell value: the integer itself, or the bit
+// pattern of a non-negative half.
+template <bool F16>
+__device__ __forceinline__ int value_key(int v) {
+  if (!F16) return v;
+  return (int)__half_as_ushort(__int2half_rn(v));
+}
+
+template <bool F16>
+__device__ __forceinline__ int key_value(int k) {
+  if (!F16) return k;
+  if (k >= 0x7c00) return 1 << 20;   // +inf: far above every threshold
+  return __half2int_rn(__ushort_as_half((unsigned short)k));
+}
+
+__device__ __forceinline__ uint32_t hfma2_relu_u32(uint32_t a, uint32_t b, uint32_t c) {
+  const __half2 r = __hfma2_relu(*reinterpret_cast<const __half2 *>(&a),
+                                 *reinterpret_cast<const __half2 *>(&b),
+                                 *reinterpret_cast<const __half2 *>(&c));
+  return *reinterpret_cast<const uint32_t *>(&r);
+}
+
+__device__ __forceinline__ uint32_t pack2_half(int v) {
+  const uint32_t h = (uint32_t)__half_as_ushort(__int2half_rn(v));
+  return (h << 16) | h;
+}
+
 template <int LG, int H, int MODE>
 __global__ void __launch_bounds__(kBlockThreads, 1) scan_kernel(ScanParams p) {
   static_assert(H % 4 == 0 && H >= 4 && H <= kMaxWords, "words per lane");
   static_assert(LG == 1 || LG == 2 || LG == 4 || LG == 8 || LG == 16 || LG == 32, "lanes");
   constexpr int NC = LG >= 8 ? 1 : 8 / LG;
   constexpr int G = 32 / LG;
+  constexpr bool kF16 = (MODE == MODE_SSV_F16 || MODE == MODE_MSV_FAST_F16);
+  constexpr bool kSSV = (MODE == MODE_SSV || MODE == MODE_SSV_F16);
+  constexpr bool kFast = (MODE == MODE_MSV_FAST || MODE == MODE_MSV_FAST_F16);
+  constexpr bool kDirect = (MODE == MODE_MSV_DIRECT);
+  const uint32_t one2 = 0x3c003c00u;   // (1.0, 1.0) as half2
   extern __shared__ __align__(16) uint8_t smem[];
   __shared__ uint32_t s_item, s_next;
 
@@ -135,19 +181,23 @@ __global__ void __launch_bounds__(kBlockThreads, 1) scan_kernel(ScanParams p) {
       int xJ = 0;
       int b = min(sat8(base - (t + tbm)), cap);
       uint32_t b2 = pack2(b);
-      int T = min(base + tec - b, cap - b - 1);
+      const int T = min(base + tec - b, cap - b - 1);
+      const int Tk = value_key<kF16>(max(T, 0));          // threshold as a key
+      const int Tnear = T - 4 * max(bias, 0);              // no trigger possible in 4 rows below it
+      const int Tnear_k = value_key<kF16>(max(Tnear, 0));
       bool done = false, exact = false;
 
-      // Lane state: H words of two 16-bit cells and a running maximum.
+      // Lane state: H words of two 16-bit cells and a running maximum (key).
       uint32_t v[H];
 #pragma unroll
       for (int q = 0; q < H; ++q) v[q] = 0u;
       uint32_t vacc = 0u;
       uint32_t cur = __ldg(p.residues + (nsteps > 0 ? wptr : p.pad_word));
 
-      for (int step = 0; step < wsteps; ++step) {
-        // Prefetch the next residue word; past the end a group reads padding.
-        const uint32_t nxt = __ldg(p.residues + (step + 1 < nsteps ? wptr + (uint32_t)step + 1u : p.pad_word));
+      // Four rows of one residue word.  CHECK: test every row for the MSV
+      // threshold (only needed when some lane is near it, or in exact mode).
+      auto four_rows = [&](const int step, auto check_tag) {
+        constexpr bool CHECK = decltype(check_tag)::value;
 #pragma unroll
         for (int rr = 0; rr < 4; ++rr) {
           // Rows past the end of a sequence read padding codes: their cells
@@ -172,20 +222,22 @@ __global__ void __launch_bounds__(kBlockThreads, 1) scan_kernel(ScanParams p) {
             for (int i = 3; i >= 0; --i) {
               const int q = 4 * j + i;
               const uint32_t prev = (q == 0) ? mpv : v[q - 1];
-              if (MODE == MODE_MSV_DIRECT)
+              if (kF16)
+                v[q] = hfma2_relu_u32(prev, one2, sc[i]);
+              else if (kDirect)
                 v[q] = __viaddmax_s16x2(__vimax_s16x2_relu(prev, b2), sc[i], 0u);
               else
                 v[q] = __viaddmax_s16x2(prev, sc[i], 0u);
             }
-            if (MODE == MODE_MSV_DIRECT) {
-              rmax = __vimax3_s16x2(rmax, v[4 * j + 3], v[4 * j + 2]);
-              rmax = __vimax3_s16x2(rmax, v[4 * j + 1], v[4 * j]);
+            if (kDirect) {
+              rmax = __vimax3_u16x2(rmax, v[4 * j + 3], v[4 * j + 2]);
+              rmax = __vimax3_u16x2(rmax, v[4 * j + 1], v[4 * j]);
             } else {
-              vacc = __vimax3_s16x2(vacc, v[4 * j + 3], v[4 * j + 2]);
-              vacc = __vimax3_s16x2(vacc, v[4 * j + 1], v[4 * j]);
+              vacc = __vimax3_u16x2(vacc, v[4 * j + 3], v[4 * j + 2]);
+              vacc = __vimax3_u16x2(vacc, v[4 * j + 1], v[4 * j]);
             }
           }
-          if (MODE == MODE_MSV_DIRECT) {
+          if (kDirect) {
             // xE of this row (Alg. 6), then the J and B special states.
             const int xE = group_max<LG>(half_max(rmax));
             if (real && !done) {
@@ -197,11 +249,11 @@ __global__ void __launch_bounds__(kBlockThreads, 1) scan_kernel(ScanParams p) {
                 b2 = pack2(b);
               }
             }
-          } else if (MODE == MODE_MSV_FAST) {
-            const bool trig = real && !done && half_max(vacc) > T;
+          } else if (kFast && CHECK) {
+            const bool trig = real && !done && (exact || half_max(vacc) > Tk);
             if (__any_sync(kFull, trig)) {
-              const int mm = group_max<LG>(half_max(vacc));
-              if (real && !done && mm > T) {
+              const int mm = key_value<kF16>(group_max<LG>(half_max(vacc)));
+              if (real && !done && (exact || mm > T)) {
                 const int xE = b + mm;
                 if (xE >= cap) {
                   done = true;
@@ -209,25 +261,39 @@ __global__ void __launch_bounds__(kBlockThreads, 1) scan_kernel(ScanParams p) {
                   xJ = exact ? max(xJ, xE - tec) : max(0, xE - tec);
                   const int bn = min(sat8(max(base, xJ) - (t + tbm)), cap);
                   if (bn > b) {
-                    const uint32_t nd = pack2(b - bn);
 #pragma unroll
-                    for (int q = 0; q < H; ++q) v[q] = __viaddmax_s16x2(v[q], nd, 0u);
+                    for (int q = 0; q < H; ++q)
+                      v[q] = kF16 ? hfma2_relu_u32(v[q], one2, pack2_half(b - bn))
+                                  : __viaddmax_s16x2(v[q], pack2(b - bn), 0u);
                   }
                   b = bn;
                   exact = true;
-                  T = -1;
                 }
               }
               if (exact) vacc = 0u;
             }
           }
         }
+      };
+
+      for (int step = 0; step < wsteps; ++step) {
+        // Prefetch the next residue word; past the end a group reads padding.
+        const uint32_t nxt = __ldg(p.residues + (step + 1 < nsteps ? wptr + (uint32_t)step + 1u : p.pad_word));
+        if (kFast) {
+          const bool near = active && !done && (exact || Tnear < 0 || half_max(vacc) > Tnear_k);
+          if (__any_sync(kFull, near))
+            four_rows(step, std::true_type{});
+          else
+            four_rows(step, std::false_type{});
+        } else {
+          four_rows(step, std::false_type{});
+        }
         cur = nxt;
       }
 
       // ---- finalise the G sequences -------------------------------------
-      const int V = group_max<LG>(half_max(vacc));
-      if (MODE == MODE_MSV_FAST) {
+      const int V = key_value<kF16>(group_max<LG>(half_max(vacc)));
+      if (kFast) {
         // A sequence whose cells never rose above the begin score: its best
         // row maximum is the best single-cell score of its residues.
         const bool rescue = active && !done && !exact && V == 0 && len > 0;
@@ -257,7 +323,7 @@ __global__ void __launch_bounds__(kBlockThreads, 1) scan_kernel(ScanParams p) {
           out_flag[orig] = flag;
           if (out_nat) out_nat[orig] = flag ? __int_as_float(0x7f800000) : nat_score(raw - t - base, scale);
         }
-      } else if (MODE == MODE_MSV_DIRECT) {
+      } else if (kDirect) {
         if (active && gl == 0) {
           const int raw = done ? 255 : xJ;
           out_raw[orig] = (uint8_t)raw;

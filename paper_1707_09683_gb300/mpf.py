@@ -20,6 +20,7 @@ LIB_PATH = os.path.join(_HERE, "libmpf.so")
 
 MPF_OK, MPF_EINVAL, MPF_ENOMEM, MPF_ECUDA, MPF_ETIMEOUT, MPF_EUNSUPPORTED = range(6)
 MSV, SSV = 0, 1
+ARITH_AUTO, ARITH_I16, ARITH_F16 = 0, 1, 2
 
 
 class MpfLibraryMissing(RuntimeError):
@@ -59,6 +60,7 @@ def load(path: str = LIB_PATH):
         "mpf_profile_destroy": (None, [vp]),
         "mpf_profile_set_config": (i32, [vp, i32, i32, i32]),
         "mpf_profile_get_config": (i32, [vp, i32, ctypes.POINTER(i32), ctypes.POINTER(i32)]),
+        "mpf_profile_set_arith": (i32, [vp, i32, i32]),
         "mpf_db_upload": (i32, [vp, vp, u64, vp, vp, u64, ctypes.POINTER(vp)]),
         "mpf_db_destroy": (None, [vp]),
         "mpf_db_n_seqs": (u64, [vp]),
@@ -186,6 +188,10 @@ class Profile:
     def set_config(self, filter: int, lanes: int, words: int):
         _check(load().mpf_profile_set_config(self.handle, int(filter), int(lanes), int(words)),
                "mpf_profile_set_config")
+
+    def set_arith(self, filter: int, arith: int):
+        _check(load().mpf_profile_set_arith(self.handle, int(filter), int(arith)),
+               "mpf_profile_set_arith")
 
     def get_config(self, filter: int):
         a, b = ctypes.c_int(), ctypes.c_int()

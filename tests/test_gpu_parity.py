@@ -56,8 +56,11 @@ def assert_same(got, exp, what=""):
     assert badn.size == 0, f"{what}: nat mismatch at {badn[:5]}: {gnat[badn[:5]]} vs {enat[badn[:5]]}"
 
 
-def check_profile(ctx, p, db, ddb=None, filters=FILTERS, index=None, configs=None):
+def check_profile(ctx, p, db, ddb=None, filters=FILTERS, index=None, configs=None, arith=None):
     prof = mpf.Profile(ctx, p)
+    if arith is not None:
+        for gf, _ in filters:
+            prof.set_arith(gf, arith)
     ddb = ddb or mpf.Database(ctx, db.residues, db.offsets, db.lengths)
     for gf, of in filters:
         exp = oracle.scan(of, p, db.residues, db.offsets, db.lengths, index=index, nthreads=8)
@@ -119,6 +122,29 @@ def test_adversarial_profiles(ctx, seed):
                                  base=int(rng.choice([60, 190, 250])),
                                  with_lut=bool(rng.integers(2)))
         check_profile(ctx, p, db, ddb)
+
+
+@pytest.mark.parametrize("arith", [mpf.ARITH_I16, mpf.ARITH_F16])
+def test_both_cell_arithmetics(ctx, arith):
+    """Integer (DPX) and half-precision (HFMA2) cells give the same scores:
+    adversarial bytes, strong profiles (J reuse, overflow far past 255) and
+    long sequences whose cells would leave the exact half range after
+    saturation."""
+    rng = np.random.default_rng(900 + arith)
+    db = synth.random_database(400, 600, rng, alphabet=32)
+    long_db = synth.make_database(40, 8000, 4000, 12000, rng)
+    ddb = mpf.Database(ctx, db.residues, db.offsets, db.lengths)
+    lddb = mpf.Database(ctx, long_db.residues, long_db.offsets, long_db.lengths)
+    for M in (1, 9, 64, 250, 700, 2405):
+        p = synth.random_profile(M, int(rng.integers(1, 33)), rng,
+                                 cost_hi=int(rng.choice([30, 255])),
+                                 bias=int(rng.choice([5, 40, 130, 255])),
+                                 base=int(rng.choice([120, 190, 250])), with_lut=True)
+        check_profile(ctx, p, db, ddb, arith=arith)
+        strong = synth.random_profile(M, 20, rng, cost_hi=24, bias=20, base=190, tbm=10, tec=3, tjb=8)
+        check_profile(ctx, strong, long_db, lddb, arith=arith)
+    for M in (100, 800):
+        check_profile(ctx, synth.make_profile(M, rng), long_db, lddb, arith=arith)
 
 
 def test_strong_profiles_hit_j_and_overflow(ctx):
