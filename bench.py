@@ -188,7 +188,7 @@ def run_mpf(args):
     dev = torch.device("cuda", local)
 
     t0 = time.time()
-    wl = synth.make_workload(args.workload, n_seqs=args.n_seqs)
+    wl = synth.make_workload(args.workload, n_seqs=args.n_seqs, n_queries=args.n_queries)
     if world > 1:   # weak scaling: every rank scores its own database of the same shape
         wl.db = synth.make_database(wl.db.n_seqs, wl.meta["mean"], *wl.meta["clip"],
                                     np.random.default_rng(1000 + rank))
@@ -202,6 +202,17 @@ def run_mpf(args):
     for pr in profs:
         for code in (mpf.MSV, mpf.SSV):
             pr.set_arith(code, arith)
+    # Kernel configurations (lanes per sequence, words per lane) from the
+    # autotuner, each candidate timed on the whole database.
+    tuned = {}
+    if args.tune and len({p.M for p in wl.profiles}) <= 16:
+        from paper_1707_09683_gb300 import autotune
+        t_tune = time.time()
+        tuner = autotune.Autotuner(ctx, db, reps=1)
+        for pr in profs:
+            for name, code in (("msv", mpf.MSV), ("ssv", mpf.SSV)):
+                tuned.setdefault(name, {})[pr.M] = list(tuner.tune(pr, code))
+        log(f"[rank {rank}] autotuned {len(profs)} queries in {time.time() - t_tune:.1f} s: {tuned}")
     n, q = db.n_seqs, len(profs)
     res = db.n_residues
     cells_per_filter = sum(p.M for p in wl.profiles) * res
@@ -351,6 +362,7 @@ def run_mpf(args):
                        "n_seqs": n, "residues": res, "filters": ["msv", "ssv"],
                        "form": "batched persistent plan per filter, CUDA-graph replay",
                        "cell_arith": args.arith,
+                       "kernel_configs": tuned or "default",
                        "l2": "database (%.0f MB) larger than L2; no flush" % (res / 1e6),
                        "cells_per_step": 2 * cells_per_filter},
             "plain": {"value": gcups_plain, "unit": "GCUPS", "ms_per_step": ms_plain,
@@ -440,6 +452,8 @@ def main():
     ap.add_argument("--impl", default="mpf", choices=["mpf", "reference"])
     ap.add_argument("--workload", type=int, default=1)
     ap.add_argument("--n-seqs", type=int, default=None)
+    ap.add_argument("--n-queries", type=int, default=None)
+    ap.add_argument("--no-tune", dest="tune", action="store_false")
     ap.add_argument("--cpu-sample", type=int, default=6000)
     ap.add_argument("--ref-sample", type=int, default=3000)
     ap.add_argument("--no-cpu", action="store_true")

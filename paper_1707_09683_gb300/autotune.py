@@ -35,7 +35,7 @@ M_MIN = 20
 M_MAX = {"msv": 2450, "ssv": 1000}
 
 LANES = (1, 2, 4, 8, 16, 32)
-WORDS = tuple(range(4, 49, 4))
+WORDS = tuple(sorted(set(range(4, 49, 4)) | set(range(6, 48, 4))))   # %4 == 2: two-word tail
 
 
 @dataclass(frozen=True)
@@ -70,7 +70,7 @@ def paper_policy(m: int, filt: str, switch: bool = True) -> PaperChoice:
 
 def covering_words(m: int, lanes: int) -> int:
     w = -(-m // (2 * lanes))
-    return max(4, -(-w // 4) * 4)
+    return max(4, -(-w // 2) * 2)
 
 
 def paper_point(m: int, filt: str) -> Optional[Tuple[int, int]]:
@@ -87,14 +87,18 @@ def paper_point(m: int, filt: str) -> Optional[Tuple[int, int]]:
     return None
 
 
-def candidates(m: int, max_waste: float = 0.45) -> List[Tuple[int, int]]:
-    """Built configurations that cover m with at most max_waste padding."""
+def candidates(m: int, max_waste: float = 0.3, min_words: int = 8) -> List[Tuple[int, int]]:
+    """Built configurations that cover m with at most max_waste padding and
+    at least min_words registers per lane (fewer leaves the per-row work of
+    a lane dominated by the shift and residue handling)."""
     out = []
     for lanes in LANES:
         for w in WORDS:
             cells = 2 * lanes * w
-            if cells >= m and (cells - m) / cells <= max_waste:
+            if cells >= m and (cells - m) / cells <= max_waste and w >= min_words:
                 out.append((lanes, w))
+    if not out:      # tiny models: the smallest covering configuration
+        out.append((1, covering_words(m, 1)))
     pp = paper_point(m, "msv")
     if pp and pp not in out:
         out.append(pp)
@@ -123,7 +127,10 @@ class Autotuner:
     def _time(self, prof, filt, lanes, words, outs) -> float:
         import torch
         from . import mpf
-        prof.set_config(filt, lanes, words)
+        try:
+            prof.set_config(filt, lanes, words)
+        except mpf.MpfError:      # no kernel built for this pair in this arithmetic
+            return float("inf")
         plan = mpf.Plan(self.ctx, filt, [prof], self.db, *outs)
         stream = self.ctx.torch_stream()
         plan.launch()

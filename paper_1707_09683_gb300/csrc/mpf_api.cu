@@ -123,20 +123,21 @@ bool is_device_ptr(const void *p) {
 
 const int kLanes[6] = {1, 2, 4, 8, 16, 32};
 
-bool words_built(int w) { return w >= 4 && w <= kMaxWords && w % 4 == 0; }
+bool words_built(int w) { return w >= 4 && w <= kMaxWords && (w % 4 == 0 || w % 4 == 2); }
 
 int smem_need(int lanes, int words) { return (int)table_geom(lanes, words).table_bytes; }
 
-// Default (lanes, words): the fewest lanes per sequence whose rows need at
-// most 40 words (48 for whole-warp groups) and whose table fits on chip.
-void default_config(const mpf_ctx *ctx, int M, int *lanes, int *words) {
+// Default (lanes, words) for a kernel mode: the fewest lanes per sequence
+// whose rows need at most 40 words (48 for whole-warp groups), using the
+// smallest built word count that covers M and whose table fits on chip.
+void default_config(const mpf_ctx *ctx, int M, int mode, int *lanes, int *words) {
   for (int i = 0; i < 6; ++i) {
     const int lg = kLanes[i];
     int w = (M + 2 * lg - 1) / (2 * lg);
-    w = (w + 3) / 4 * 4;
-    if (w < 4) w = 4;
+    w = std::max(4, (w + 1) / 2 * 2);
+    if (!kernel_for(lg, w, mode)) w = (w + 3) / 4 * 4;
     const int wmax = lg == 32 ? kMaxWords : 40;
-    if (w <= wmax && smem_need(lg, w) <= ctx->max_smem) {
+    if (w <= wmax && kernel_for(lg, w, mode) && smem_need(lg, w) <= ctx->max_smem) {
       *lanes = lg;
       *words = w;
       return;
@@ -177,18 +178,27 @@ void fill_table_image(const mpf_profile *p, const TableGeom &g, int fmt, uint8_t
     const int c = x < p->K ? (int)p->cost[(size_t)x * M + k] : 255;
     return p->bias - c;
   };
-  for (int c = 0; c < g.copies; ++c)
-    for (int x = 0; x < kTableRows; ++x)
-      for (int l = 0; l < lanes; ++l)
-        for (int q = 0; q < words; ++q)
-          for (int h = 0; h < 2; ++h) {
-            const int k = (2 * l + h) * words + q;   // striped cell of (lane, half, word)
-            const size_t off = (size_t)c * g.copy_bytes + (size_t)x * g.row_bytes +
-                               ((size_t)(q / 4) * lanes + l) * 16 + (q % 4) * 4 + h * 2;
-            const int sv = score(x, k);
-            const uint16_t bits = fmt == TABLE_F16 ? half_bits(sv) : (uint16_t)(int16_t)sv;
-            memcpy(&img[off], &bits, 2);
+  auto put = [&](size_t off, int x, int k) {
+    const int sv = score(x, k);
+    const uint16_t bits = fmt == TABLE_F16 ? half_bits(sv) : (uint16_t)(int16_t)sv;
+    memcpy(&img[off], &bits, 2);
+  };
+  const int qw = 4 * g.quads;   // words held in the quad region
+  for (int x = 0; x < kTableRows; ++x)
+    for (int l = 0; l < lanes; ++l)
+      for (int q = 0; q < words; ++q)
+        for (int h = 0; h < 2; ++h) {
+          const int k = (2 * l + h) * words + q;   // striped cell of (lane, half, word)
+          if (q < qw) {
+            for (int c = 0; c < g.copies; ++c)
+              put((size_t)c * g.copy_bytes + (size_t)x * g.row_bytes +
+                      ((size_t)(q / 4) * lanes + l) * 16 + (q % 4) * 4 + h * 2, x, k);
+          } else {
+            for (int c = 0; c < g.tail_copies; ++c)
+              put(g.tail_off + (size_t)x * g.tail_row_bytes + ((size_t)c * lanes + l) * 8 +
+                      (q - qw) * 4 + h * 2, x, k);
           }
+        }
   for (int x = 0; x < kTableRows; ++x) {
     int m = kNegInf;
     if (x < 32)
@@ -330,13 +340,13 @@ int plan_create(mpf_ctx *ctx, int filter, const mpf_profile *const *profs, int n
       plan_free(pl);
       return MPF_EINVAL;
     }
+    const int mode = kernel_mode(p, filter);
     int lanes = p->cfg_lanes[filter], words = p->cfg_words[filter];
-    if (!lanes) default_config(ctx, p->M, &lanes, &words);
-    if (!lanes) {
+    if (!lanes) default_config(ctx, p->M, mode, &lanes, &words);
+    if (!lanes || !kernel_for(lanes, words, mode)) {
       plan_free(pl);
       return MPF_EUNSUPPORTED;
     }
-    const int mode = kernel_mode(p, filter);
     DevTable t;
     int rc = get_table(p, lanes, words, table_format(mode), &t);
     if (rc) {
@@ -350,6 +360,8 @@ int plan_create(mpf_ctx *ctx, int filter, const mpf_profile *const *profs, int n
     q.row_bytes = t.geom.row_bytes;
     q.copy_bytes = t.geom.copy_bytes;
     q.smax_off = t.geom.smax_off;
+    q.tail_off = t.geom.tail_off;
+    q.tail_row_bytes = t.geom.tail_row_bytes;
     q.bias = p->bias;
     q.tbm = p->tbm;
     q.tec = p->tec;
@@ -632,7 +644,7 @@ int mpf_profile_create(mpf_ctx *ctx, int M, int K, const uint8_t *cost, uint8_t 
     p->n_tjb = n_tjb;
   }
   int lanes = 0, words = 0;
-  default_config(ctx, M, &lanes, &words);
+  default_config(ctx, M, kernel_mode(p, MPF_MSV), &lanes, &words);
   if (!lanes) {
     mpf_profile_destroy(p);
     return MPF_EUNSUPPORTED;
@@ -657,7 +669,7 @@ int mpf_profile_set_config(mpf_profile *p, int filter, int lanes, int words) {
     p->cfg_lanes[filter] = p->cfg_words[filter] = 0;
     return MPF_OK;
   }
-  if (!kernel_for(lanes, words, MODE_SSV) || !words_built(words)) return MPF_EINVAL;
+  if (!words_built(words) || !kernel_for(lanes, words, kernel_mode(p, filter))) return MPF_EINVAL;
   if (2 * lanes * words < p->M) return MPF_EINVAL;
   if (smem_need(lanes, words) > p->ctx->max_smem) return MPF_EUNSUPPORTED;
   p->cfg_lanes[filter] = lanes;
@@ -669,6 +681,10 @@ int mpf_profile_set_arith(mpf_profile *p, int filter, int arith) {
   if (!p || (filter != MPF_MSV && filter != MPF_SSV)) return MPF_EINVAL;
   if (arith != MPF_ARITH_AUTO && arith != MPF_ARITH_I16 && arith != MPF_ARITH_F16) return MPF_EINVAL;
   p->arith[filter] = arith;
+  // A configured (lanes, words) pair without a kernel in the new arithmetic
+  // falls back to the default configuration.
+  if (p->cfg_lanes[filter] && !kernel_for(p->cfg_lanes[filter], p->cfg_words[filter], kernel_mode(p, filter)))
+    p->cfg_lanes[filter] = p->cfg_words[filter] = 0;
   return MPF_OK;
 }
 
@@ -678,7 +694,7 @@ int mpf_profile_get_config(const mpf_profile *p, int filter, int *lanes, int *wo
     *lanes = p->cfg_lanes[filter];
     *words = p->cfg_words[filter];
   } else {
-    default_config(p->ctx, p->M, lanes, words);
+    default_config(p->ctx, p->M, kernel_mode(p, filter), lanes, words);
   }
   return MPF_OK;
 }
@@ -889,12 +905,12 @@ extern "C" int mpf_scan_noalloc(mpf_ctx *ctx, int filter, const mpf_profile *pro
     return MPF_EINVAL;
   if (db->n_seqs == 0) return MPF_OK;
 
+  const int mode = kernel_mode(prof, filter);
   int lanes = prof->cfg_lanes[filter], words = prof->cfg_words[filter];
-  if (!lanes) default_config(ctx, prof->M, &lanes, &words);
+  if (!lanes) default_config(ctx, prof->M, mode, &lanes, &words);
   if (!lanes) return MPF_EUNSUPPORTED;
   const TableGeom g = table_geom(lanes, words);
   if (g.table_bytes > kNoAllocTableMax) return MPF_EUNSUPPORTED;   // beyond the scratch size
-  const int mode = kernel_mode(prof, filter);
   KernelFn fn = kernel_for(lanes, words, mode);
   if (!fn) return MPF_EINVAL;
 
@@ -922,6 +938,8 @@ extern "C" int mpf_scan_noalloc(mpf_ctx *ctx, int filter, const mpf_profile *pro
   q.row_bytes = g.row_bytes;
   q.copy_bytes = g.copy_bytes;
   q.smax_off = g.smax_off;
+  q.tail_off = g.tail_off;
+  q.tail_row_bytes = g.tail_row_bytes;
   q.bias = prof->bias;
   q.tbm = prof->tbm;
   q.tec = prof->tec;

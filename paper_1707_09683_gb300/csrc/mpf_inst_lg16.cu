@@ -12,6 +12,15 @@ namespace mpf {
     if (mode == MODE_MSV_FAST_F16) return scan_kernel<16, W, MODE_MSV_FAST_F16>; \
     return nullptr;
 
+// Word counts with a two-word tail: the half-precision modes and the
+// per-row MSV fallback.
+#define MPF_WORDS_CASE_TAIL(W)                                          \
+  case W:                                                               \
+    if (mode == MODE_MSV_DIRECT) return scan_kernel<16, W, MODE_MSV_DIRECT>;     \
+    if (mode == MODE_SSV_F16) return scan_kernel<16, W, MODE_SSV_F16>;           \
+    if (mode == MODE_MSV_FAST_F16) return scan_kernel<16, W, MODE_MSV_FAST_F16>; \
+    return nullptr;
+
 KernelFn kernel_lg16(int words, int mode) {
   switch (words) {
     MPF_WORDS_CASE(4)
@@ -26,6 +35,17 @@ KernelFn kernel_lg16(int words, int mode) {
     MPF_WORDS_CASE(40)
     MPF_WORDS_CASE(44)
     MPF_WORDS_CASE(48)
+    MPF_WORDS_CASE_TAIL(6)
+    MPF_WORDS_CASE_TAIL(10)
+    MPF_WORDS_CASE_TAIL(14)
+    MPF_WORDS_CASE_TAIL(18)
+    MPF_WORDS_CASE_TAIL(22)
+    MPF_WORDS_CASE_TAIL(26)
+    MPF_WORDS_CASE_TAIL(30)
+    MPF_WORDS_CASE_TAIL(34)
+    MPF_WORDS_CASE_TAIL(38)
+    MPF_WORDS_CASE_TAIL(42)
+    MPF_WORDS_CASE_TAIL(46)
     default:
       return nullptr;
   }

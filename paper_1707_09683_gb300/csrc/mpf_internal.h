@@ -36,6 +36,8 @@ struct QueryDesc {
   uint32_t row_bytes;     // stride between residue rows
   uint32_t copy_bytes;    // stride between bank-offset copies
   uint32_t smax_off;      // byte offset of 33 int16 per-code maximum scores
+  uint32_t tail_off;      // byte offset of the two-word tail region (words % 4 == 2)
+  uint32_t tail_row_bytes;
   int bias, tbm, tec, base, tjb_fixed;
   float scale;
   const uint8_t *tjb;     // per-length tjb (nullable)
@@ -71,22 +73,40 @@ KernelFn kernel_lg8(int words, int mode);
 KernelFn kernel_lg16(int words, int mode);
 KernelFn kernel_lg32(int words, int mode);
 
-// Shared-memory table geometry of a (lanes, words) layout.
+// Shared-memory table geometry of a (lanes, words) layout.  Words 4q..4q+3
+// of a lane are one 16-byte chunk of the quad region; when words % 4 == 2 the
+// last two words of every lane are 8-byte chunks of a separate tail region.
+//
+// Quad region: for each residue row, the quads of the group's lanes are
+// adjacent 16-byte chunks, so 8 lanes of one group (one phase of a 128-bit
+// shared load) hit 8 distinct 16-byte bank groups.  Groups of fewer than 8
+// lanes share a phase with other groups (other residues): the region then
+// holds 8 / lanes copies with 128-byte aligned rows and bases offset by
+// lanes * 16 bytes, and group g reads copy g mod copies.
+// Tail region: a 64-bit load runs in phases of 16 lanes; each residue row is
+// 128 bytes (256 for 32-lane groups) holding 16 / lanes copies of the
+// group's 8-byte chunks side by side, and group g reads copy g mod copies.
 struct TableGeom {
-  int lanes, words, copies;
-  uint32_t row_bytes, copy_bytes, smax_off, table_bytes;
+  int lanes, words, copies, quads, tail_words, tail_copies;
+  uint32_t row_bytes, copy_bytes, tail_off, tail_row_bytes, smax_off, table_bytes;
 };
 
 inline TableGeom table_geom(int lanes, int words) {
   TableGeom g;
   g.lanes = lanes;
   g.words = words;
+  g.quads = words / 4;
+  g.tail_words = words % 4;
   g.copies = lanes >= 8 ? 1 : 8 / lanes;
-  uint32_t row = (uint32_t)words * (uint32_t)lanes * 4u;
+  uint32_t row = (uint32_t)g.quads * (uint32_t)lanes * 16u;
   if (g.copies > 1) row = (row + 127u) & ~127u;
   g.row_bytes = row;
   g.copy_bytes = (uint32_t)kTableRows * row + (g.copies > 1 ? (uint32_t)lanes * 16u : 0u);
-  g.smax_off = (uint32_t)g.copies * g.copy_bytes;
+  g.tail_off = (uint32_t)g.copies * g.copy_bytes;
+  g.tail_off = (g.tail_off + 127u) & ~127u;
+  g.tail_copies = lanes >= 16 ? 1 : 16 / lanes;
+  g.tail_row_bytes = g.tail_words ? (uint32_t)(lanes >= 16 ? lanes * 8 : 128) : 0u;
+  g.smax_off = g.tail_off + (uint32_t)kTableRows * g.tail_row_bytes;
   g.table_bytes = g.smax_off + 80u;   // 33 int16 rounded up to 16 bytes
   return g;
 }

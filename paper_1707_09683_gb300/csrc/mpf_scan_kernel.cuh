@@ -108,7 +108,10 @@ __device__ __forceinline__ uint32_t pack2_half(int v) {
 
 template <int LG, int H, int MODE>
 __global__ void __launch_bounds__(kBlockThreads, 1) scan_kernel(ScanParams p) {
-  static_assert(H % 4 == 0 && H >= 4 && H <= kMaxWords, "words per lane");
+  static_assert((H % 4 == 0 || H % 4 == 2) && H >= 4 && H <= kMaxWords, "words per lane");
+  constexpr int Q = H / 4;               // full 4-word chunks per lane and row
+  constexpr bool kTail = (H % 4) == 2;   // two more words from the tail region
+  constexpr int NT = LG >= 16 ? 1 : 16 / LG;
   static_assert(LG == 1 || LG == 2 || LG == 4 || LG == 8 || LG == 16 || LG == 32, "lanes");
   constexpr int NC = LG >= 8 ? 1 : 8 / LG;
   constexpr int G = 32 / LG;
@@ -155,6 +158,8 @@ __global__ void __launch_bounds__(kBlockThreads, 1) scan_kernel(ScanParams p) {
     float *out_nat = qd->nat;
     const uint8_t *tbl_lane = smem + (grp % NC) * qd->copy_bytes + gl * 16;
     const uint32_t row_bytes = qd->row_bytes;
+    const uint8_t *tail_lane = smem + qd->tail_off + ((grp % NT) * LG + gl) * 8;
+    const uint32_t tail_row_bytes = qd->tail_row_bytes;
     const int16_t *smax = reinterpret_cast<const int16_t *>(smem + qd->smax_off);
 
     for (;;) {
@@ -214,8 +219,27 @@ __global__ void __launch_bounds__(kBlockThreads, 1) scan_kernel(ScanParams p) {
           }
           const uint32_t mpv = __byte_perm(up, wl, 0x5432);
           uint32_t rmax = 0u;
+          if (kTail) {   // words 4Q+1 and 4Q (highest first: in-place update)
+            const uint2 t2 = *reinterpret_cast<const uint2 *>(tail_lane + x * tail_row_bytes);
+            const uint32_t tsc[2] = {t2.x, t2.y};
 #pragma unroll
-          for (int j = H / 4 - 1; j >= 0; --j) {
+            for (int i = 1; i >= 0; --i) {
+              const int q = 4 * Q + i;
+              const uint32_t prev = (q == 0) ? mpv : v[q - 1];
+              if (kF16)
+                v[q] = hfma2_relu_u32(prev, one2, tsc[i]);
+              else if (kDirect)
+                v[q] = __viaddmax_s16x2(__vimax_s16x2_relu(prev, b2), tsc[i], 0u);
+              else
+                v[q] = __viaddmax_s16x2(prev, tsc[i], 0u);
+            }
+            if (kDirect)
+              rmax = __vimax3_u16x2(rmax, v[4 * Q + 1], v[4 * Q]);
+            else
+              vacc = __vimax3_u16x2(vacc, v[4 * Q + 1], v[4 * Q]);
+          }
+#pragma unroll
+          for (int j = Q - 1; j >= 0; --j) {
             const uint4 s4 = *reinterpret_cast<const uint4 *>(rowp + j * LG * 16);
             const uint32_t sc[4] = {s4.x, s4.y, s4.z, s4.w};
 #pragma unroll

@@ -171,7 +171,7 @@ def test_every_kernel_configuration(ctx):
     ddb = mpf.Database(ctx, db.residues, db.offsets, db.lengths)
     for M in (24, 90, 300):
         p = synth.make_profile(M, rng)
-        cfgs = [(lg, w) for lg in (1, 2, 4, 8, 16, 32) for w in range(4, 49, 4)
+        cfgs = [(lg, w) for lg in (1, 2, 4, 8, 16, 32) for w in range(4, 49, 2)
                 if 2 * lg * w >= M and 2 * lg * w < M + 2 * lg * 16]
         check_profile(ctx, p, db, ddb, configs=cfgs)
 

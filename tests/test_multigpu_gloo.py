@@ -1,0 +1,83 @@
+"""The N > 1 path on CPU: two gloo ranks shard a database, score their
+shards (with the oracle standing in for the GPU scan), gather the outputs,
+and must reproduce the single-process result exactly; the bench's
+max-over-ranks timing reduction is checked the same way."""
+import os
+import socket
+
+import numpy as np
+import pytest
+import torch
+import torch.distributed as dist
+import torch.multiprocessing as mp
+
+from paper_1707_09683_gb300 import shard, synth
+
+
+def _free_port():
+    s = socket.socket()
+    s.bind(("127.0.0.1", 0))
+    port = s.getsockname()[1]
+    s.close()
+    return port
+
+
+def _worker(rank, world, port, result_q):
+    os.environ["MASTER_ADDR"] = "127.0.0.1"
+    os.environ["MASTER_PORT"] = str(port)
+    dist.init_process_group("gloo", rank=rank, world_size=world)
+    try:
+        import oracle
+        import bench
+        wl = synth.make_workload(0, n_seqs=900)
+        p = wl.profiles[0]
+        res, off, ln, (lo, hi) = shard.local_database(wl.db, rank, world)
+        outs = []
+        for f in (oracle.MSV, oracle.SSV):
+            r, fl, nat = oracle.scan(f, p, res, off, ln)
+            outs += [torch.from_numpy(r), torch.from_numpy(fl), torch.from_numpy(nat)]
+        bounds = shard.shard_bounds(wl.db.lengths, world)
+        full = shard.gather_outputs(outs, bounds, rank, world)
+        slowest = bench.max_over_ranks(1.5 + rank, world)
+        result_q.put((rank, [t.numpy() for t in full], slowest, (lo, hi)))
+    finally:
+        dist.destroy_process_group()
+
+
+def test_sharded_scan_gathers_to_the_single_process_result():
+    import oracle
+    oracle.build()
+    world = 2
+    ctx = mp.get_context("spawn")
+    q = ctx.Queue()
+    port = _free_port()
+    procs = [ctx.Process(target=_worker, args=(r, world, port, q)) for r in range(world)]
+    for pr in procs:
+        pr.start()
+    got = [q.get(timeout=120) for _ in range(world)]
+    for pr in procs:
+        pr.join(timeout=60)
+        assert pr.exitcode == 0
+    wl = synth.make_workload(0, n_seqs=900)
+    p = wl.profiles[0]
+    ref = []
+    for f in (oracle.MSV, oracle.SSV):
+        ref += list(oracle.scan(f, p, wl.db.residues, wl.db.offsets, wl.db.lengths))
+    for rank, full, slowest, (lo, hi) in got:
+        assert slowest == 2.5                      # max over ranks of 1.5 + rank
+        for a, b in zip(full, ref):
+            assert np.array_equal(a.view(np.uint8), b.view(np.uint8))
+    spans = sorted(b for _, _, _, b in got)
+    assert spans[0][0] == 0 and spans[-1][1] == 900 and spans[0][1] == spans[1][0]
+
+
+def test_shard_bounds_balance_and_cover():
+    rng = np.random.default_rng(2)
+    lengths = rng.integers(0, 5000, size=10_001).astype(np.uint32)
+    for world in (1, 2, 3, 8):
+        b = shard.shard_bounds(lengths, world)
+        assert b[0][0] == 0 and b[-1][1] == lengths.size
+        assert all(b[i][1] == b[i + 1][0] for i in range(world - 1))
+        tot = [int(lengths[lo:hi].sum()) for lo, hi in b]
+        assert max(tot) - min(tot) <= 2 * int(lengths.max())
+    assert shard.shard_bounds(np.zeros(0, np.uint32), 4) == [(0, 0)] * 4
