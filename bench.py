@@ -306,6 +306,11 @@ def run_mpf(args):
                 "frac": achieved / peak, "traffic": None,
                 "kernel": f"scan_kernel<{lanes},{words},{'MSV' if dom_f == 'msv' else 'SSV'}> M={dom_m}",
                 "launches_averaged": len(durs), "avg_launch_ms": avg_ms,
+                "smem_ceiling": {
+                    "peak": nsm * 128 / 2 * sm_mhz * 1e6 * dom_m / (2 * lanes * words) / 1e9,
+                    "frac": achieved / (nsm * 128 / 2 * sm_mhz * 1e6 * dom_m / (2 * lanes * words) / 1e9),
+                    "basis": "128 B/clk/SM of shared memory / 2 B of score table per padded cell "
+                             "x model cells / padded cells (the ceiling of the 16-bit table)"},
                 "algorithmic_cells_per_launch": dom_m * res,
                 "peak_basis": f"{nsm} SMs x {INT_LANES_PER_SM_CLK} int lanes/clk x "
                               f"{CELLS_PER_LANE_OP} cells/op / {OPS_PER_CELL[dom_f]} ops/cell x "
@@ -327,6 +332,11 @@ def run_mpf(args):
 
     def step_e2e():
         ps = [mpf.Profile(ctx, p) for p in wl.profiles]
+        for pr in ps:
+            for name, code in filters:
+                pr.set_arith(code, arith)
+                if tuned:
+                    pr.set_config(code, *tuned[name][pr.M])
         for _, code in filters:
             mpf.scan_batch(ctx, code, ps, db, raw_h, flag_h, nat_h)
         for p in ps:
