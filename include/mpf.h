@@ -200,6 +200,35 @@ int mpf_plan_kernel_launches(const mpf_plan *plan);
 void mpf_plan_destroy(mpf_plan *plan);
 
 /*
+ * Two-stage filter of the HMMER3 pipeline (Sec. 2.1): SSV scores every
+ * sequence; the sequences whose SSV nat score is >= ssv_min_nat, or whose SSV
+ * score overflowed, are re-scored by MSV; the others are marked filtered.
+ *   All buffers are device pointers; outputs [n_q][n_seqs] by original
+ *   sequence number.  ssv_* receive the SSV scores of every sequence; msv_*
+ *   receive the MSV scores of the passing sequences and raw 0, flag 2, nat NaN
+ *   for filtered ones (msv_nat nullable).  n_pass[n_q] receives the number of
+ *   passing sequences per query.
+ *   Asynchronous on the context stream (one SSV and one MSV launch per kernel
+ *   configuration, three selection kernels between them); temporary device
+ *   memory is taken from and returned to the stream-ordered pool.
+ * Errors: MPF_EINVAL (null or host buffer, NaN threshold), MPF_ENOMEM, MPF_ECUDA.
+ */
+int mpf_pipeline_scan(mpf_ctx *ctx, const mpf_profile *const *profs, int n_q, const mpf_db *db,
+                      float ssv_min_nat, uint8_t *ssv_raw, uint8_t *ssv_flag, float *ssv_nat,
+                      uint8_t *msv_raw, uint8_t *msv_flag, float *msv_nat, uint32_t *n_pass);
+
+/*
+ * P-values of nat scores under a Gumbel (extreme-value) distribution with
+ * location mu and slope lambda > 0: P(S > x) = 1 - exp(-exp(-lambda (x - mu)))
+ * (the per-sequence P-value of Alg. 2 and Alg. 7; mu and lambda come from
+ * the caller's calibration).  +inf (overflow) gives 0, NaN (filtered) stays
+ * NaN.  nat and p are device pointers of n floats (may alias); single
+ * precision; asynchronous on the context stream.
+ * Errors: MPF_EINVAL, MPF_ECUDA.
+ */
+int mpf_pvalues(mpf_ctx *ctx, const float *nat, uint64_t n, float mu, float lambda, float *p);
+
+/*
  * Allocation-free scan.  The paper has no counterpart: this entry point exists
  * for callers that cannot allocate device memory when they score, such as
  * code recording a CUDA graph under a capture mode that forbids allocation,

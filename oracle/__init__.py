@@ -126,3 +126,35 @@ def msv(prof, residues, offsets, lengths, index=None, nthreads: int = 1):
 def ssv(prof, residues, offsets, lengths, index=None, nthreads: int = 1):
     """SSV scores (Alg. 7, single segment, no J state)."""
     return scan(SSV, prof, residues, offsets, lengths, index, nthreads)
+
+
+def gumbel_pvalue(x, mu: float, lam: float):
+    """P(S > x) for a Gumbel (type I extreme-value) score distribution with
+    location mu and slope lam, the per-sequence P-value the filters record
+    (Alg. 2, Alg. 7): 1 - exp(-exp(-lam (x - mu))), in float64; +inf -> 0,
+    NaN stays NaN."""
+    x = np.asarray(x, dtype=np.float64)
+    with np.errstate(over="ignore", invalid="ignore"):
+        p = -np.expm1(-np.exp(-lam * (x - mu)))
+    p = np.where(np.isposinf(x), 0.0, p)
+    return p
+
+
+def pipeline(prof, residues, offsets, lengths, ssv_min_nat: float, nthreads: int = 1):
+    """SSV over every sequence, MSV over those whose SSV nat score is
+    >= ssv_min_nat or whose SSV score overflowed (Sec. 2.1).  Returns
+    (ssv (raw, flag, nat), msv (raw, flag, nat) with flag 2 / NaN for
+    filtered sequences, number passing)."""
+    sr, sf, sn = ssv(prof, residues, offsets, lengths, nthreads=nthreads)
+    keep = (sf != 0) | (sn >= np.float32(ssv_min_nat))
+    idx = np.flatnonzero(keep).astype(np.uint64)
+    n = sr.size
+    mr = np.zeros(n, np.uint8)
+    mf = np.full(n, 2, np.uint8)
+    mn = np.full(n, np.nan, np.float32)
+    if idx.size:
+        r, f, nt = msv(prof, residues, offsets, lengths, index=idx, nthreads=nthreads)
+        mr[idx.astype(np.int64)] = r
+        mf[idx.astype(np.int64)] = f
+        mn[idx.astype(np.int64)] = nt
+    return (sr, sf, sn), (mr, mf, mn), int(idx.size)

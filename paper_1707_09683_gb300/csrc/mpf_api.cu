@@ -324,8 +324,11 @@ int configure_kernel(mpf_ctx *ctx, LaunchGroup *g) {
 }
 
 // Build a plan: queries grouped by kernel configuration.
+// ranks/n_ranks (nullable): query i scores only the n_ranks[i] length ranks
+// listed at ranks + i * n_seqs (device memory).
 int plan_create(mpf_ctx *ctx, int filter, const mpf_profile *const *profs, int n_q,
-                const mpf_db *db, uint8_t *raw, uint8_t *flag, float *nat, mpf_plan **out) {
+                const mpf_db *db, uint8_t *raw, uint8_t *flag, float *nat, mpf_plan **out,
+                const uint32_t *ranks = nullptr, const uint32_t *n_ranks = nullptr) {
   if (!ctx || !profs || n_q < 1 || !db || !raw || !flag || !out) return MPF_EINVAL;
   if (filter != MPF_MSV && filter != MPF_SSV) return MPF_EINVAL;
   if (db->ctx->device != ctx->device) return MPF_EINVAL;
@@ -374,6 +377,8 @@ int plan_create(mpf_ctx *ctx, int filter, const mpf_profile *const *profs, int n
     q.raw = raw + off;
     q.flag = flag + off;
     q.nat = nat ? nat + off : nullptr;
+    q.ranks = ranks ? ranks + off : nullptr;
+    q.n_ranks = ranks ? n_ranks + i : nullptr;
     byconf[std::make_tuple(lanes, words, mode)].push_back(q);
   }
   DeviceGuard dg(ctx->device);
@@ -853,6 +858,52 @@ int mpf_plan_capture_graph(mpf_plan *plan) {
 }
 
 int mpf_plan_kernel_launches(const mpf_plan *plan) { return plan ? (int)plan->groups.size() : 0; }
+
+int mpf_pipeline_scan(mpf_ctx *ctx, const mpf_profile *const *profs, int n_q, const mpf_db *db,
+                      float ssv_min_nat, uint8_t *ssv_raw, uint8_t *ssv_flag, float *ssv_nat,
+                      uint8_t *msv_raw, uint8_t *msv_flag, float *msv_nat, uint32_t *n_pass) {
+  if (!ctx || !profs || n_q < 1 || !db || !ssv_raw || !ssv_flag || !ssv_nat || !msv_raw ||
+      !msv_flag || !n_pass || isnan(ssv_min_nat))
+    return MPF_EINVAL;
+  DeviceGuard dg(ctx->device);
+  for (const void *ptr : {(const void *)ssv_raw, (const void *)ssv_flag, (const void *)ssv_nat,
+                          (const void *)msv_raw, (const void *)msv_flag, (const void *)n_pass})
+    if (!is_device_ptr(ptr)) return MPF_EINVAL;
+  if (msv_nat && !is_device_ptr(msv_nat)) return MPF_EINVAL;
+  const uint64_t n = db->n_seqs;
+  const uint64_t n_chunks = (n + kSelectChunk - 1) / kSelectChunk;
+  uint32_t *ranks = nullptr, *n_ranks = nullptr, *chunk = nullptr;
+  cudaError_t e = cudaMallocAsync((void **)&ranks, std::max<uint64_t>(1, (uint64_t)n_q * n) * 4, ctx->stream);
+  if (e == cudaSuccess) e = cudaMallocAsync((void **)&n_ranks, (size_t)n_q * 4, ctx->stream);
+  if (e == cudaSuccess) e = cudaMallocAsync((void **)&chunk, std::max<uint64_t>(1, 2 * (uint64_t)n_q * n_chunks) * 4, ctx->stream);
+  int rc = e == cudaSuccess ? MPF_OK : (e == cudaErrorMemoryAllocation ? MPF_ENOMEM : MPF_ECUDA);
+  mpf_plan *ssv = nullptr, *msv = nullptr;
+  if (rc == MPF_OK) rc = plan_create(ctx, MPF_SSV, profs, n_q, db, ssv_raw, ssv_flag, ssv_nat, &ssv);
+  if (rc == MPF_OK) rc = plan_enqueue(ssv, ctx->stream);
+  if (rc == MPF_OK && launch_select(db->d_seq_orig, n, n_q, ssv_flag, ssv_nat, ssv_min_nat, msv_raw,
+                                    msv_flag, msv_nat, chunk, chunk + (uint64_t)n_q * n_chunks,
+                                    ranks, n_ranks, ctx->stream) != 0)
+    rc = MPF_ECUDA;
+  if (rc == MPF_OK) rc = plan_create(ctx, MPF_MSV, profs, n_q, db, msv_raw, msv_flag, msv_nat, &msv, ranks, n_ranks);
+  if (rc == MPF_OK) rc = plan_enqueue(msv, ctx->stream);
+  if (rc == MPF_OK && cudaMemcpyAsync(n_pass, n_ranks, (size_t)n_q * 4, cudaMemcpyDeviceToDevice, ctx->stream) != cudaSuccess)
+    rc = MPF_ECUDA;
+  // Stream-ordered release after the MSV scan; plans are freed at the next sync.
+  if (ranks) cudaFreeAsync(ranks, ctx->stream);
+  if (n_ranks) cudaFreeAsync(n_ranks, ctx->stream);
+  if (chunk) cudaFreeAsync(chunk, ctx->stream);
+  if (ssv) ctx->pending.push_back(ssv);
+  if (msv) ctx->pending.push_back(msv);
+  (void)cudaGetLastError();
+  return rc;
+}
+
+int mpf_pvalues(mpf_ctx *ctx, const float *nat, uint64_t n, float mu, float lambda, float *p) {
+  if (!ctx || (n && (!nat || !p)) || !isfinite(mu) || !(lambda > 0.f) || !isfinite(lambda)) return MPF_EINVAL;
+  DeviceGuard dg(ctx->device);
+  if (n && (!is_device_ptr(nat) || !is_device_ptr(p))) return MPF_EINVAL;
+  return launch_pvalues(nat, n, mu, lambda, p, ctx->num_sms, ctx->stream) ? MPF_ECUDA : MPF_OK;
+}
 
 void mpf_plan_destroy(mpf_plan *plan) {
   if (!plan) return;

@@ -46,6 +46,10 @@ struct QueryDesc {
   uint8_t *raw;           // outputs indexed by original sequence number
   uint8_t *flag;
   float *nat;             // nullable
+  // Nullable: score only these length ranks (ascending), *n_ranks of them
+  // (a device count written by an earlier kernel on the same stream).
+  const uint32_t *ranks;
+  const uint32_t *n_ranks;
 };
 
 struct ScanParams {
@@ -63,6 +67,15 @@ struct ScanParams {
 };
 
 typedef void (*KernelFn)(ScanParams);
+
+// SSV -> MSV hand-off (mpf_pipeline.cu).
+constexpr int kSelectChunk = 4096;   // length ranks per selection block
+int launch_select(const uint32_t *seq_orig, uint64_t n, int n_q, const uint8_t *ssv_flag,
+                  const float *ssv_nat, float min_nat, uint8_t *msv_raw, uint8_t *msv_flag,
+                  float *msv_nat, uint32_t *chunk_count, uint32_t *chunk_offset, uint32_t *ranks,
+                  uint32_t *n_ranks, cudaStream_t st);
+int launch_pvalues(const float *nat, uint64_t n, float mu, float lambda, float *p, int num_sms,
+                   cudaStream_t st);
 
 // Kernel instantiation for (lanes, words, mode), or nullptr if not built.
 KernelFn kernel_for(int lanes, int words, int mode);

@@ -161,15 +161,18 @@ __global__ void __launch_bounds__(kBlockThreads, 1) scan_kernel(ScanParams p) {
     const uint8_t *tail_lane = smem + qd->tail_off + ((grp % NT) * LG + gl) * 8;
     const uint32_t tail_row_bytes = qd->tail_row_bytes;
     const int16_t *smax = reinterpret_cast<const int16_t *>(smem + qd->smax_off);
+    const uint32_t *ranks = qd->ranks;
+    const uint64_t n_sel = ranks ? (uint64_t)*qd->n_ranks : (uint64_t)p.n_seqs;
 
     for (;;) {
       // ---- take G consecutive length ranks of this shard (one per group) ----
       uint32_t k0 = 0;
       if (lane == 0) k0 = atomicAdd(&s_next, (uint32_t)G);
       k0 = __shfl_sync(kFull, k0, 0);
-      const uint64_t r = (uint64_t)shard + (uint64_t)(k0 + grp) * p.n_shards;
-      const bool active = r < p.n_seqs;
+      const uint64_t kr = (uint64_t)shard + (uint64_t)(k0 + grp) * p.n_shards;
+      const bool active = kr < n_sel;
       if (!__any_sync(kFull, active)) break;
+      const uint64_t r = (ranks && active) ? (uint64_t)__ldg(ranks + kr) : kr;
 
       // Group state (identical in every lane of a group).
       uint32_t wptr = p.pad_word, orig = 0;

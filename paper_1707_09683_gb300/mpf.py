@@ -74,6 +74,8 @@ def load(path: str = LIB_PATH):
         "mpf_plan_kernel_launches": (i32, [vp]),
         "mpf_plan_destroy": (None, [vp]),
         "mpf_scan_noalloc": (i32, [vp, i32, vp, vp, vp, vp, vp]),
+        "mpf_pipeline_scan": (i32, [vp, vp, i32, vp, ctypes.c_float, vp, vp, vp, vp, vp, vp, vp]),
+        "mpf_pvalues": (i32, [vp, vp, u64, ctypes.c_float, ctypes.c_float, vp]),
     }
     for name, (res, args) in sig.items():
         fn = getattr(lib, name)
@@ -319,3 +321,21 @@ def scan_noalloc(ctx: Context, filter: int, prof: Profile, db: Database, raw, ov
     calls overlapping on the GPU race)."""
     _check(load().mpf_scan_noalloc(ctx.handle, int(filter), prof.handle, db.handle, _ptr(raw),
                                    _ptr(overflow), _ptr(nat)), "mpf_scan_noalloc")
+
+
+def pipeline_scan(ctx: Context, profs: Sequence[Profile], db: Database, ssv_min_nat: float,
+                  ssv_out, msv_out, n_pass):
+    """``mpf_pipeline_scan``: SSV over every sequence, MSV over the ones whose
+    SSV nat score is >= ssv_min_nat (or overflowed).  ``ssv_out`` and
+    ``msv_out`` are (raw, flag, nat) device tensors of n_q * n_seqs; MSV
+    entries of filtered sequences read raw 0, flag 2, nat NaN."""
+    arr = _handles(profs)
+    _check(load().mpf_pipeline_scan(ctx.handle, arr, len(profs), db.handle, float(ssv_min_nat),
+                                    *[_ptr(t) for t in ssv_out], *[_ptr(t) for t in msv_out],
+                                    _ptr(n_pass)), "mpf_pipeline_scan")
+
+
+def pvalues(ctx: Context, nat, mu: float, lam: float, out):
+    """``mpf_pvalues``: Gumbel P-values of device nat scores into ``out``."""
+    _check(load().mpf_pvalues(ctx.handle, _ptr(nat), int(nat.numel()), float(mu), float(lam),
+                              _ptr(out)), "mpf_pvalues")
