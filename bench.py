@@ -39,6 +39,17 @@ CELLS_PER_LANE_OP = 4
 OPS_PER_CELL = {"msv": 4, "ssv": 2}
 
 
+# DRAM bytes per launch (dram__bytes_read.sum + dram__bytes_write.sum) from the
+# ncu captures summarised in profiles/, keyed by kernel, workload and model
+# length; only used while the kernel is the one that was captured.
+NCU_TRAFFIC = {
+    ("scan_kernel<32,38,MSV_FAST_F16>", "msweep_500k", 2405): 188.730624e6 + 3.762688e6,
+    ("scan_kernel<32,38,SSV_F16>", "msweep_500k", 2405): 189.139712e6 + 3.725824e6,
+}
+KERNEL_SOURCE = os.path.join(ROOT, "paper_1707_09683_gb300", "csrc", "mpf_scan_kernel.cuh")
+KERNEL_SOURCE_SHA256 = "35a53c52a0627b8460c0a54fa9b5aad3d62f52f863ad19e2ad092d600f742cde"
+
+
 def log(*a):
     print(*a, file=sys.stderr, flush=True)
 
@@ -302,8 +313,15 @@ def run_mpf(args):
     sm_mhz = clocks.get("sm_mhz") or 2070.0
     nsm = torch.cuda.get_device_properties(dev).multi_processor_count
     peak = nsm * INT_LANES_PER_SM_CLK * CELLS_PER_LANE_OP / OPS_PER_CELL[dom_f] * sm_mhz * 1e6 / 1e9
+    mode_name = ("MSV_FAST" if dom_f == "msv" else "SSV") + ("_F16" if args.arith != "i16" else "")
+    import hashlib
+    src_ok = hashlib.sha256(open(KERNEL_SOURCE, "rb").read()).hexdigest() == KERNEL_SOURCE_SHA256
+    traffic = NCU_TRAFFIC.get((f"scan_kernel<{lanes},{words},{mode_name}>", wl.name, dom_m)) if src_ok else None
     roofline = {"bound": "alu", "achieved": achieved, "peak": peak, "unit": "GCUPS",
-                "frac": achieved / peak, "traffic": None,
+                "frac": achieved / peak, "traffic": traffic,
+                "traffic_note": "ncu dram__bytes_read.sum + dram__bytes_write.sum of this kernel on this "
+                                "workload (profiles/scan_kernel_m2405_msweep500k.md); algorithmic bytes "
+                                "per launch: %.0f" % (res + 6 * n),
                 "kernel": f"scan_kernel<{lanes},{words},{'MSV' if dom_f == 'msv' else 'SSV'}> M={dom_m}",
                 "launches_averaged": len(durs), "avg_launch_ms": avg_ms,
                 "smem_ceiling": {
@@ -352,6 +370,28 @@ def run_mpf(args):
     e2e_s = max_over_ranks(e2e_s, world)
     e2e_gcups = 2 * cells_per_filter * world / e2e_s / 1e9
 
+    # Two-stage filter (SSV over everything, MSV over the sequences whose SSV
+    # score passes): threshold at the 98th percentile of this step's SSV nat
+    # scores, so about 2% pass, the fraction Sec. 2.1 reports for the stage.
+    pipe = None
+    if args.pipeline:
+        sn = outs["ssv"][2].float()
+        fin = sn[torch.isfinite(sn)]
+        thr = float(torch.quantile(fin[:: max(1, fin.numel() // 4_000_000)], 0.98))
+        p_ssv = tuple(torch.empty_like(t) for t in outs["ssv"])
+        p_msv = tuple(torch.empty_like(t) for t in outs["msv"])
+        n_pass = torch.empty(q, dtype=torch.int32, device=dev)
+        run_pipe = lambda: mpf.pipeline_scan(ctx, profs, db, thr, p_ssv, p_msv, n_pass)
+        for _ in range(args.warmup):
+            run_pipe()
+        ms_pipe = time_steps(run_pipe, args.steps)
+        passed = int(n_pass.sum().item())
+        pipe = {"ms_per_step": ms_pipe, "ssv_min_nat": thr, "pass_fraction": passed / (q * n),
+                "queries_x_db_gcups": cells_per_filter / (ms_pipe * 1e-3) / 1e9,
+                "vs_both_filters_on_all_ms": ms_batched}
+        log(f"pipeline: {ms_pipe:.1f} ms per step, {100 * passed / (q * n):.2f}% pass SSV "
+            f"(both filters on everything: {ms_batched:.1f} ms)")
+
     # Serving: continuous batching of arriving queries (model lengths drawn as
     # in the serving workload) against the resident database, per offered load.
     serving = None
@@ -384,6 +424,7 @@ def run_mpf(args):
                     "d2h_bytes_per_step": int(d2h), "s_per_step": e2e_s,
                     "path": "mpf_profile_create from host bytes + mpf_scan_batch (MSV, SSV) into "
                             "host buffers + mpf_profile_destroy; database resident"},
+            "pipeline": pipe,
             "serving": serving,
             "gpu_launches": launches_per_step * args.steps,
             "clocks": clocks,
@@ -469,6 +510,7 @@ def main():
     ap.add_argument("--no-cpu", action="store_true")
     ap.add_argument("--arith", default="auto", choices=["auto", "i16", "f16"])
     ap.add_argument("--no-serve", action="store_true")
+    ap.add_argument("--no-pipeline", dest="pipeline", action="store_false")
     ap.add_argument("--serve-rates", type=float, nargs="+", default=[10, 50, 100, 200, 500])
     ap.add_argument("--serve-requests", type=int, default=24)
     ap.add_argument("--profile-case", action="store_true")
