@@ -19,6 +19,7 @@ import numpy as np
 
 _HERE = os.path.dirname(os.path.abspath(__file__))
 _SRC = os.path.join(_HERE, "mpf_oracle.c")
+_VIT_SRC = os.path.join(_HERE, "mpf_vit_oracle.c")
 _BUILD = os.path.join(_HERE, "_build")
 _LIB_PATH = os.path.join(_BUILD, "libmpf_oracle.so")
 _lib = None
@@ -27,11 +28,12 @@ MSV = 0
 SSV = 1
 
 
-def compile_source(src: str, out: str) -> str:
-    """Compile an oracle C source file into the shared library ``out``."""
+def compile_source(src, out: str) -> str:
+    """Compile oracle C source file(s) into the shared library ``out``."""
+    srcs = [src] if isinstance(src, str) else list(src)
     tmp = out + f".{os.getpid()}.tmp"
     cmd = ["gcc", "-O2", "-std=c11", "-fPIC", "-shared", "-pthread",
-           "-ffp-contract=off", "-fno-fast-math", "-o", tmp, src, "-lm"]
+           "-ffp-contract=off", "-fno-fast-math", "-o", tmp, *srcs, "-lm"]
     subprocess.run(cmd, check=True)
     os.replace(tmp, out)
     return out
@@ -40,10 +42,10 @@ def compile_source(src: str, out: str) -> str:
 def build(force: bool = False) -> str:
     """Compile the oracle into a shared library and return its path."""
     if (not force and os.path.exists(_LIB_PATH)
-            and os.path.getmtime(_LIB_PATH) >= os.path.getmtime(_SRC)):
+            and os.path.getmtime(_LIB_PATH) >= max(os.path.getmtime(_SRC), os.path.getmtime(_VIT_SRC))):
         return _LIB_PATH
     os.makedirs(_BUILD, exist_ok=True)
-    return compile_source(_SRC, _LIB_PATH)
+    return compile_source([_SRC, _VIT_SRC], _LIB_PATH)
 
 
 def load_library(path: str):
@@ -58,6 +60,14 @@ def load_library(path: str):
         ctypes.POINTER(ctypes.c_uint64), ctypes.c_uint64,
         u8p, u8p, ctypes.POINTER(ctypes.c_float), ctypes.c_int]
     lib.oracle_scan.restype = ctypes.c_int
+    if hasattr(lib, "oracle_viterbi"):
+        i16p = ctypes.POINTER(ctypes.c_int16)
+        lib.oracle_viterbi.argtypes = [
+            ctypes.c_int, ctypes.c_int, i16p, i16p, i16p, ctypes.c_int, ctypes.c_float,
+            u8p, ctypes.POINTER(ctypes.c_uint64), ctypes.POINTER(ctypes.c_uint32),
+            ctypes.POINTER(ctypes.c_uint64), ctypes.c_uint64,
+            i16p, u8p, ctypes.POINTER(ctypes.c_float), ctypes.c_int]
+        lib.oracle_viterbi.restype = ctypes.c_int
     return lib
 
 
@@ -158,3 +168,42 @@ def pipeline(prof, residues, offsets, lengths, ssv_min_nat: float, nthreads: int
         mf[idx.astype(np.int64)] = f
         mn[idx.astype(np.int64)] = nt
     return (sr, sf, sn), (mr, mf, mn), int(idx.size)
+
+
+VIT_TRANSITIONS = ("BM", "MM", "IM", "DM", "MI", "II", "MD", "DD")
+VIT_SPECIALS = ("NN", "NB", "EC", "CC", "CT", "EJ", "JJ", "JB")
+
+
+def viterbi(vprof, residues, offsets, lengths, index=None, nthreads: int = 1):
+    """P7Viterbi filter scores (Eq. 1 with the Plan-7 special states, 16-bit
+    saturating word arithmetic).  ``vprof`` has ``M, K, msc (K x M int16),
+    trans (8 x M int16, order VIT_TRANSITIONS), special (8 int16, order
+    VIT_SPECIALS), base, scale``.  Returns (score int16, flag uint8, nat float32)."""
+    lib = _load()
+    msc = np.ascontiguousarray(vprof.msc, dtype=np.int16)
+    trans = np.ascontiguousarray(vprof.trans, dtype=np.int16)
+    special = np.ascontiguousarray(vprof.special, dtype=np.int16)
+    K, M = msc.shape
+    assert trans.shape == (8, M) and special.shape == (8,)
+    residues = np.ascontiguousarray(residues, dtype=np.uint8)
+    offsets = np.ascontiguousarray(offsets, dtype=np.uint64)
+    lengths = np.ascontiguousarray(lengths, dtype=np.uint32)
+    if index is not None:
+        index = np.ascontiguousarray(index, dtype=np.uint64)
+        n = int(index.size)
+    else:
+        n = int(lengths.size)
+    score = np.zeros(n, np.int16)
+    flag = np.zeros(n, np.uint8)
+    nat = np.zeros(n, np.float32)
+    if residues.size == 0:
+        residues = np.zeros(1, np.uint8)
+    i16 = ctypes.c_int16
+    rc = lib.oracle_viterbi(int(M), int(K), _ptr(msc, i16), _ptr(trans, i16), _ptr(special, i16),
+                            int(vprof.base), float(vprof.scale), _ptr(residues, ctypes.c_uint8),
+                            _ptr(offsets, ctypes.c_uint64), _ptr(lengths, ctypes.c_uint32),
+                            _ptr(index, ctypes.c_uint64), n, _ptr(score, i16),
+                            _ptr(flag, ctypes.c_uint8), _ptr(nat, ctypes.c_float), int(nthreads))
+    if rc != 0:
+        raise RuntimeError(f"oracle_viterbi failed with status {rc}")
+    return score, flag, nat

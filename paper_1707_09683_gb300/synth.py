@@ -269,3 +269,70 @@ def random_database(n: int, max_len: int, rng: np.random.Generator, alphabet: in
         np.cumsum(lengths[:-1], dtype=np.uint64, out=offsets[1:])
     residues = rng.integers(0, alphabet, size=int(lengths.sum()), dtype=np.int64).astype(np.uint8)
     return Database(residues=residues, offsets=offsets, lengths=lengths)
+
+
+# ----------------------------------------------------------------------------
+# Viterbi filter profiles (Eq. 1): match emissions, the seven node transitions
+# and the special states in the HMMER3 16-bit word convention
+# (scale 500 / ln 2 words per nat, base 12000).
+
+VIT_SCALE = 500.0 / math.log(2.0)
+VIT_BASE = 12000
+NEG16 = -32768
+
+
+@dataclass
+class VitProfile:
+    M: int
+    K: int
+    msc: np.ndarray        # K x M int16 match scores
+    trans: np.ndarray      # 8 x M int16: BM, MM, IM, DM, MI, II, MD, DD (node k at k-1)
+    special: np.ndarray    # 8 int16: NN, NB, EC, CC, CT, EJ, JJ, JB
+    base: int
+    scale: float
+
+
+def _words(p, scale=VIT_SCALE):
+    with np.errstate(divide="ignore"):
+        w = round_half_away(np.where(p > 0, scale * np.log(np.maximum(p, 1e-300)), -1e9))
+    return np.clip(w, NEG16, 32767).astype(np.int16)
+
+
+def make_vit_profile(M: int, rng: np.random.Generator, L: int = 350,
+                     concentration: float = 20.0) -> VitProfile:
+    """Match emissions as in make_profile; per-node transitions drawn from
+    Dirichlets around a typical Plan-7 model (M->M 0.96, M->I 0.02, M->D 0.02,
+    I->M/I->I and D->M/D->D 0.5/0.5); uniform local entry 2 / (M (M + 1)); the
+    N, C and J loops and moves configured for sequence length L, multi-hit
+    (E->C = E->J = 1/2)."""
+    emit = rng.dirichlet(concentration * BACKGROUND, size=M)
+    msc = _words(emit / BACKGROUND[None, :]).T.copy()
+    tm = rng.dirichlet([96.0, 2.0, 2.0], size=M)     # from M_k: MM, MI, MD
+    ti = rng.dirichlet([5.0, 5.0], size=M)            # from I_k: IM, II
+    td = rng.dirichlet([5.0, 5.0], size=M)            # from D_k: DM, DD
+    trans = np.full((8, M), NEG16, dtype=np.int16)
+    trans[0] = _words(np.full(M, 2.0 / (M * (M + 1.0))))
+    if M > 1:
+        trans[1, 1:] = _words(tm[:-1, 0])    # M_{k-1} -> M_k
+        trans[2, 1:] = _words(ti[:-1, 0])    # I_{k-1} -> M_k
+        trans[3, 1:] = _words(td[:-1, 0])    # D_{k-1} -> M_k
+        trans[4, :-1] = _words(tm[:-1, 1])   # M_k -> I_k
+        trans[5, :-1] = _words(ti[:-1, 1])   # I_k -> I_k
+        trans[6, 1:] = _words(tm[:-1, 2])    # M_{k-1} -> D_k
+    if M > 2:
+        trans[7, 2:] = _words(td[1:-1, 1])   # D_{k-1} -> D_k
+    loop = L / (L + 3.0)
+    move = 3.0 / (L + 3.0)
+    special = _words(np.array([loop, move, 0.5, loop, move, 0.5, loop, move]))
+    return VitProfile(M=M, K=20, msc=msc, trans=trans, special=special, base=VIT_BASE,
+                      scale=float(np.float32(VIT_SCALE)))
+
+
+def random_vit_profile(M: int, K: int, rng: np.random.Generator, lo: int = -32768,
+                       hi: int = 32767, base=None) -> VitProfile:
+    """Adversarial Viterbi profile: uniform int16 scores in [lo, hi]."""
+    def u(shape):
+        return rng.integers(lo, hi + 1, size=shape, dtype=np.int64).astype(np.int16)
+    return VitProfile(M=M, K=K, msc=u((K, M)), trans=u((8, M)), special=u(8),
+                      base=int(rng.integers(-32768, 32768)) if base is None else int(base),
+                      scale=float(np.float32(VIT_SCALE)))
