@@ -1,5 +1,6 @@
 /*
  * mpf.h -- C ABI of the GB300 MSV/SSV protein-profile scan library (libmpf.so).
+ *          (The P7Viterbi filter that follows them is declared further down.)
  *
  * The library scores every sequence of a protein database against Plan-7
  * profiles with the two byte-quantised heuristic filters of the HMMER3
@@ -227,6 +228,71 @@ int mpf_pipeline_scan(mpf_ctx *ctx, const mpf_profile *const *profs, int n_q, co
  * Errors: MPF_EINVAL, MPF_ECUDA.
  */
 int mpf_pvalues(mpf_ctx *ctx, const float *nat, uint64_t n, float mu, float lambda, float *p);
+
+/*
+ * P7Viterbi filter: the gapped Viterbi recurrence of Eq. 1 (Sec. 2.1), the
+ * third filter of the HMMER3 pipeline, in 16-bit saturating word arithmetic:
+ *
+ *   sat(v) = min(32767, max(-32768, v)); -32768 stands for minus infinity;
+ *   primed values are the previous row; M'[0] = I'[0] = D'[0] = -32768.
+ *   row 0:  M = I = D = -32768; xN = base; xB = sat(xN + NB); xJ = xC = -32768
+ *   residue x:
+ *     M[k] = sat(max(sat(M'[k-1] + MM[k]), sat(I'[k-1] + IM[k]),
+ *                    sat(D'[k-1] + DM[k]), sat(xB + BM[k])) + msc[x][k])
+ *     I[k] = max(sat(M'[k] + MI[k]), sat(I'[k] + II[k]))   for k < M; I[M] = -32768
+ *     D[k] = max(sat(M[k-1] + MD[k]), sat(D[k-1] + DD[k])) for k > 1; D[1] = -32768
+ *     xE = max over k of max(M[k], D[k]); xE >= 32767 -> overflow (stop)
+ *     xN = sat(xN + NN);  xC = max(sat(xC + CC), sat(xE + EC));
+ *     xJ = max(sat(xJ + JJ), sat(xE + EJ));  xB = max(sat(xN + NB), sat(xJ + JB))
+ *   score = sat(xC + CT); nat = (score - base) / scale - 3 (float; +inf on overflow)
+ *
+ * Insert states emit with score 0 and every match and delete state may exit
+ * to E with score 0 (local alignment).
+ */
+typedef struct mpf_vprofile mpf_vprofile;
+
+/*
+ * Create a Viterbi profile.  Host inputs, copied.
+ *   M: 1 <= M <= mpf_max_model_length(); K: 1 <= K <= 32 residue codes
+ *   msc: K*M int16, row-major [x][k-1] match scores; codes K..31 score -32768
+ *   trans: 8*M int16, rows BM, MM, IM, DM, MI, II, MD, DD, column k-1 holds
+ *          the transition into (BM, MM, IM, DM: M_k; MD, DD: D_k) or out of
+ *          (MI, II: I_k) node k
+ *   special: 8 int16 NN, NB, EC, CC, CT, EJ, JJ, JB
+ *   base: the score offset, -32768..32767; scale: units per nat (finite, > 0)
+ * Errors: MPF_EINVAL, MPF_EUNSUPPORTED (M too large), MPF_ENOMEM, MPF_ECUDA.
+ */
+int mpf_vit_profile_create(mpf_ctx *ctx, int M, int K, const int16_t *msc, const int16_t *trans,
+                           const int16_t *special, int base, float scale, mpf_vprofile **out);
+/* Waits for the creating context's stream, then frees the profile. */
+void mpf_vit_profile_destroy(mpf_vprofile *vprof);
+
+/*
+ * Score every database sequence against n_q Viterbi profiles.
+ *   score [n_q][n_seqs] int16, overflow [n_q][n_seqs] bytes (0 or 1), nat
+ *   [n_q][n_seqs] floats or NULL, by original sequence number; host or device
+ *   buffers, as for the byte scans (one kernel launch for all queries).
+ * Errors: MPF_EINVAL, MPF_EUNSUPPORTED, MPF_ENOMEM, MPF_ECUDA.
+ */
+int mpf_viterbi_scan(mpf_ctx *ctx, const mpf_vprofile *const *vprofs, int n_q, const mpf_db *db,
+                     int16_t *score, uint8_t *overflow, float *nat);
+
+/*
+ * Third stage of the pipeline (Sec. 2.1): re-score with the Viterbi filter
+ * the sequences that passed MSV.  msv_flag / msv_nat are the MSV outputs of
+ * mpf_pipeline_scan (or of an MSV scan), [n_q][n_seqs] device buffers; a
+ * sequence passes when its MSV flag is 1 (overflow) or its MSV nat score is
+ * >= msv_min_nat (flag 2, filtered by SSV, never passes).  Passing sequences
+ * receive their Viterbi score, flag and nat; the others score -32768, flag 2,
+ * nat NaN.  n_pass[n_q] receives the number of passing sequences per query.
+ * All buffers are device pointers (nat nullable); asynchronous on the context
+ * stream; temporary device memory comes from the stream-ordered pool.
+ * Errors: MPF_EINVAL (null or host buffer, NaN threshold), MPF_EUNSUPPORTED,
+ * MPF_ENOMEM, MPF_ECUDA.
+ */
+int mpf_viterbi_rescore(mpf_ctx *ctx, const mpf_vprofile *const *vprofs, int n_q, const mpf_db *db,
+                        const uint8_t *msv_flag, const float *msv_nat, float msv_min_nat,
+                        int16_t *score, uint8_t *overflow, float *nat, uint32_t *n_pass);
 
 /*
  * Allocation-free scan.  The paper has no counterpart: this entry point exists

@@ -1,9 +1,10 @@
-"""Scalar MSV/SSV oracle (test infrastructure).
+"""Scalar MSV/SSV and P7Viterbi oracle (test infrastructure).
 
 This package is the checker, not the product: only the test suite,
 ``__graft_entry__.smoke()`` and the CPU-baseline leg of ``bench.py`` use it.
 It wraps ``mpf_oracle.c`` (plain C, one scalar loop per cell, every byte
-saturation of Alg. 2 / Alg. 7 written out) through ctypes.  It imports
+saturation of Alg. 2 / Alg. 7 written out) and ``mpf_vit_oracle.c`` (the same
+for the 16-bit Viterbi recurrence of Eq. 1) through ctypes.  It imports
 nothing from the CUDA library and the library imports nothing from here.
 
 ``build()`` compiles the C file with gcc into ``oracle/_build/``;
@@ -207,3 +208,26 @@ def viterbi(vprof, residues, offsets, lengths, index=None, nthreads: int = 1):
     if rc != 0:
         raise RuntimeError(f"oracle_viterbi failed with status {rc}")
     return score, flag, nat
+
+
+def viterbi_stage(vprof, residues, offsets, lengths, msv_flag, msv_nat, msv_min_nat: float,
+                  nthreads: int = 1):
+    """Third pipeline stage (Sec. 2.1): Viterbi over the sequences whose MSV
+    flag is 1 (overflow) or whose MSV nat score is >= msv_min_nat; flag 2
+    (filtered by SSV, nat NaN) never passes.  Returns (score, flag, nat) with
+    score -32768, flag 2, nat NaN for the others, and the number passing."""
+    msv_flag = np.asarray(msv_flag)
+    msv_nat = np.asarray(msv_nat, dtype=np.float32)
+    with np.errstate(invalid="ignore"):
+        keep = (msv_flag == 1) | (msv_nat >= np.float32(msv_min_nat))
+    idx = np.flatnonzero(keep).astype(np.uint64)
+    n = msv_flag.size
+    vs = np.full(n, -32768, np.int16)
+    vf = np.full(n, 2, np.uint8)
+    vn = np.full(n, np.nan, np.float32)
+    if idx.size:
+        s, f, nt = viterbi(vprof, residues, offsets, lengths, index=idx, nthreads=nthreads)
+        vs[idx.astype(np.int64)] = s
+        vf[idx.astype(np.int64)] = f
+        vn[idx.astype(np.int64)] = nt
+    return (vs, vf, vn), int(idx.size)

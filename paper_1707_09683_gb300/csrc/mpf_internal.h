@@ -68,14 +68,51 @@ struct ScanParams {
 
 typedef void (*KernelFn)(ScanParams);
 
-// SSV -> MSV hand-off (mpf_pipeline.cu).
+// Stage-to-stage hand-off (mpf_pipeline.cu): SSV -> MSV (raw_bytes 1) and
+// MSV -> Viterbi (raw_bytes 2).
 constexpr int kSelectChunk = 4096;   // length ranks per selection block
-int launch_select(const uint32_t *seq_orig, uint64_t n, int n_q, const uint8_t *ssv_flag,
-                  const float *ssv_nat, float min_nat, uint8_t *msv_raw, uint8_t *msv_flag,
-                  float *msv_nat, uint32_t *chunk_count, uint32_t *chunk_offset, uint32_t *ranks,
-                  uint32_t *n_ranks, cudaStream_t st);
+int launch_select(const uint32_t *seq_orig, uint64_t n, int n_q, const uint8_t *in_flag,
+                  const float *in_nat, float min_nat, void *out_raw, int raw_bytes,
+                  uint8_t *out_flag, float *out_nat, uint32_t *chunk_count,
+                  uint32_t *chunk_offset, uint32_t *ranks, uint32_t *n_ranks, cudaStream_t st);
 int launch_pvalues(const float *nat, uint64_t n, float mu, float lambda, float *p, int num_sms,
                    cudaStream_t st);
+
+// P7Viterbi filter (mpf_viterbi.cu).  Tables are int16 in device memory,
+// node k (0-based) at column k of rows Mpad long; -32768 is minus infinity.
+constexpr int kVitThreads = 256;
+constexpr int kVitRows = 32;         // msc rows: residue codes 0..31
+constexpr int kVitTrans = 8;         // BM, MM, IM, DM, MI, II, MD, DD
+constexpr int kVitSpecial = 8;       // NN, NB, EC, CC, CT, EJ, JJ, JB
+
+// One query of a Viterbi launch (lives in device memory).
+struct VitQuery {
+  const int16_t *msc;         // kVitRows x Mpad match scores (codes >= K: -32768)
+  const int16_t *trans;       // kVitTrans x Mpad
+  int sp[kVitSpecial];
+  int M, Mpad;                // nodes; row length, a multiple of 32
+  int base;
+  float scale;
+  int16_t *score;             // outputs indexed by original sequence number
+  uint8_t *flag;
+  float *nat;                 // nullable
+  const uint32_t *ranks;      // nullable: score only these length ranks (ascending),
+  const uint32_t *n_ranks;    //   *n_ranks of them
+};
+
+struct VitParams {
+  const uint32_t *residues;   // database words (4 codes each)
+  const uint32_t *seq_word;   // per length rank
+  const uint32_t *seq_len;
+  const uint32_t *seq_orig;
+  uint32_t n_seqs;
+  uint32_t n_queries;
+  int max_Mpad;               // largest Mpad of the queries (sets shared memory)
+  const VitQuery *queries;
+  uint32_t *counters;         // one per query, zero before the launch
+};
+int launch_viterbi(const VitParams &p, int num_sms, cudaStream_t st);
+size_t viterbi_smem_bytes(int Mpad);
 
 // Kernel instantiation for (lanes, words, mode), or nullptr if not built.
 KernelFn kernel_for(int lanes, int words, int mode);

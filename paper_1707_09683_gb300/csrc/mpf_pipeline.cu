@@ -1,11 +1,14 @@
-// mpf_pipeline.cu -- the SSV -> MSV hand-off and P-values (Sec. 2.1).
+// mpf_pipeline.cu -- filter-to-filter hand-off and P-values (Sec. 2.1).
 //
-// In the HMMER3 pipeline SSV scores every sequence and only the sequences
-// whose SSV score passes a threshold are re-scored by MSV.  Between the two
-// scans these kernels compact, per query, the length ranks of the passing
-// sequences into an ascending list (stable, so the MSV scan keeps its
-// length-homogeneous lock-step batches) and mark every other sequence as
-// filtered in the MSV outputs.  A separate element-wise kernel turns nat
+// In the HMMER3 pipeline SSV scores every sequence, only the sequences whose
+// SSV score passes a threshold are re-scored by MSV, and only the MSV
+// survivors by the Viterbi filter.  Between two stages these kernels compact,
+// per query, the length ranks of the passing sequences into an ascending list
+// (stable, so the next scan keeps its length-homogeneous batches) and mark
+// every other sequence as filtered in the next stage's outputs.  A sequence
+// passes when the earlier stage flagged it as overflowed (flag 1) or its nat
+// score is >= the threshold; a sequence the earlier stage itself filtered
+// (flag 2, nat NaN) never passes.  A separate element-wise kernel turns nat
 // scores into Gumbel P-values.
 #include <cuda_runtime.h>
 #include <math.h>
@@ -25,11 +28,13 @@ struct SelectParams {
   const uint32_t *seq_orig;   // per length rank: original sequence number
   uint64_t n;                 // sequences
   uint32_t n_chunks;          // ceil(n / kSelectChunk)
-  const uint8_t *ssv_flag;    // [q][n] by original number
-  const float *ssv_nat;       // [q][n]
-  float min_nat;              // a sequence passes if its SSV nat >= min_nat or it overflowed
-  uint8_t *msv_raw, *msv_flag;
-  float *msv_nat;             // nullable
+  const uint8_t *in_flag;     // [q][n] by original number: earlier stage
+  const float *in_nat;        // [q][n]
+  float min_nat;              // a sequence passes if its nat >= min_nat or it overflowed
+  void *out_raw;              // next stage's outputs: raw scores of raw_bytes each
+  int raw_bytes;              // 1 (byte filters, filtered = 0) or 2 (Viterbi, filtered = -32768)
+  uint8_t *out_flag;
+  float *out_nat;             // nullable
   uint32_t *chunk_count;      // [q][n_chunks]
   uint32_t *chunk_offset;     // [q][n_chunks]
   uint32_t *ranks;            // [q][n] passing ranks, ascending
@@ -37,12 +42,12 @@ struct SelectParams {
 };
 
 __device__ __forceinline__ bool passes(const SelectParams &p, uint64_t idx) {
-  return p.ssv_flag[idx] != 0 || p.ssv_nat[idx] >= p.min_nat;
+  return p.in_flag[idx] == 1 || p.in_nat[idx] >= p.min_nat;
 }
 
 // Pass 1: count the passing sequences of one chunk of ranks of one query and
-// mark every sequence of the chunk as filtered (raw 0, flag 2, nat NaN); the
-// MSV scan overwrites the passing ones.
+// mark every sequence of the chunk as filtered (raw 0 or -32768, flag 2, nat
+// NaN); the next scan overwrites the passing ones.
 __global__ void __launch_bounds__(kSelThreads) select_count(SelectParams p) {
   const uint32_t q = blockIdx.y;
   const uint64_t lo = (uint64_t)blockIdx.x * kSelectChunk;
@@ -51,9 +56,12 @@ __global__ void __launch_bounds__(kSelThreads) select_count(SelectParams p) {
   for (uint64_t r = lo + threadIdx.x; r < hi; r += blockDim.x) {
     const uint64_t idx = (uint64_t)q * p.n + p.seq_orig[r];
     c += passes(p, idx) ? 1u : 0u;
-    p.msv_raw[idx] = 0;
-    p.msv_flag[idx] = 2;
-    if (p.msv_nat) p.msv_nat[idx] = __int_as_float(0x7fc00000);
+    if (p.raw_bytes == 2)
+      static_cast<int16_t *>(p.out_raw)[idx] = (int16_t)-32768;
+    else
+      static_cast<uint8_t *>(p.out_raw)[idx] = 0;
+    p.out_flag[idx] = 2;
+    if (p.out_nat) p.out_nat[idx] = __int_as_float(0x7fc00000);
   }
   __shared__ uint32_t warp_sum[kSelThreads / 32];
   for (int off = 16; off >= 1; off >>= 1) c += __shfl_xor_sync(0xffffffffu, c, off);
@@ -154,20 +162,21 @@ __global__ void pvalue_kernel(const float *nat, uint64_t n, float mu, float lamb
 
 }  // namespace
 
-int launch_select(const uint32_t *seq_orig, uint64_t n, int n_q, const uint8_t *ssv_flag,
-                  const float *ssv_nat, float min_nat, uint8_t *msv_raw, uint8_t *msv_flag,
-                  float *msv_nat, uint32_t *chunk_count, uint32_t *chunk_offset, uint32_t *ranks,
-                  uint32_t *n_ranks, cudaStream_t st) {
+int launch_select(const uint32_t *seq_orig, uint64_t n, int n_q, const uint8_t *in_flag,
+                  const float *in_nat, float min_nat, void *out_raw, int raw_bytes,
+                  uint8_t *out_flag, float *out_nat, uint32_t *chunk_count,
+                  uint32_t *chunk_offset, uint32_t *ranks, uint32_t *n_ranks, cudaStream_t st) {
   SelectParams p;
   p.seq_orig = seq_orig;
   p.n = n;
   p.n_chunks = (uint32_t)((n + kSelectChunk - 1) / kSelectChunk);
-  p.ssv_flag = ssv_flag;
-  p.ssv_nat = ssv_nat;
+  p.in_flag = in_flag;
+  p.in_nat = in_nat;
   p.min_nat = min_nat;
-  p.msv_raw = msv_raw;
-  p.msv_flag = msv_flag;
-  p.msv_nat = msv_nat;
+  p.out_raw = out_raw;
+  p.raw_bytes = raw_bytes;
+  p.out_flag = out_flag;
+  p.out_nat = out_nat;
   p.chunk_count = chunk_count;
   p.chunk_offset = chunk_offset;
   p.ranks = ranks;

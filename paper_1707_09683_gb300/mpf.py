@@ -76,6 +76,11 @@ def load(path: str = LIB_PATH):
         "mpf_scan_noalloc": (i32, [vp, i32, vp, vp, vp, vp, vp]),
         "mpf_pipeline_scan": (i32, [vp, vp, i32, vp, ctypes.c_float, vp, vp, vp, vp, vp, vp, vp]),
         "mpf_pvalues": (i32, [vp, vp, u64, ctypes.c_float, ctypes.c_float, vp]),
+        "mpf_vit_profile_create": (i32, [vp, i32, i32, vp, vp, vp, i32, ctypes.c_float,
+                                         ctypes.POINTER(vp)]),
+        "mpf_vit_profile_destroy": (None, [vp]),
+        "mpf_viterbi_scan": (i32, [vp, vp, i32, vp, vp, vp, vp]),
+        "mpf_viterbi_rescore": (i32, [vp, vp, i32, vp, vp, vp, ctypes.c_float, vp, vp, vp, vp]),
     }
     for name, (res, args) in sig.items():
         fn = getattr(lib, name)
@@ -339,3 +344,57 @@ def pvalues(ctx: Context, nat, mu: float, lam: float, out):
     """``mpf_pvalues``: Gumbel P-values of device nat scores into ``out``."""
     _check(load().mpf_pvalues(ctx.handle, _ptr(nat), int(nat.numel()), float(mu), float(lam),
                               _ptr(out)), "mpf_pvalues")
+
+
+class VitProfile:
+    """``mpf_vprofile`` built from a Viterbi profile record (``synth.VitProfile``
+    or any object with ``M, K, msc, trans, special, base, scale``)."""
+
+    def __init__(self, ctx: Context, vprof):
+        lib = load()
+        msc = np.ascontiguousarray(vprof.msc, dtype=np.int16)
+        trans = np.ascontiguousarray(vprof.trans, dtype=np.int16)
+        special = np.ascontiguousarray(vprof.special, dtype=np.int16)
+        K, M = msc.shape
+        if trans.shape != (8, M) or special.shape != (8,):
+            raise ValueError("trans must be 8 x M and special 8 values")
+        h = ctypes.c_void_p()
+        _check(lib.mpf_vit_profile_create(ctx.handle, int(M), int(K), msc.ctypes.data,
+                                          trans.ctypes.data, special.ctypes.data, int(vprof.base),
+                                          float(vprof.scale), ctypes.byref(h)),
+               "mpf_vit_profile_create")
+        self.handle = h
+        self.ctx = ctx
+        self.M = int(M)
+
+    def close(self):
+        if getattr(self, "handle", None):
+            load().mpf_vit_profile_destroy(self.handle)
+            self.handle = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+
+def viterbi_scan(ctx: Context, vprofs: Sequence[VitProfile], db: Database, score, overflow,
+                 nat=None):
+    """``mpf_viterbi_scan``: int16 scores, overflow bytes and nat scores,
+    [n_q][n_seqs] (host numpy or device tensors)."""
+    arr = _handles(vprofs)
+    _check(load().mpf_viterbi_scan(ctx.handle, arr, len(vprofs), db.handle, _ptr(score),
+                                   _ptr(overflow), _ptr(nat)), "mpf_viterbi_scan")
+
+
+def viterbi_rescore(ctx: Context, vprofs: Sequence[VitProfile], db: Database, msv_flag, msv_nat,
+                    msv_min_nat: float, score, overflow, nat, n_pass):
+    """``mpf_viterbi_rescore``: Viterbi over the sequences whose MSV flag is 1
+    or MSV nat >= msv_min_nat; the others read score -32768, flag 2, nat NaN.
+    Device tensors."""
+    arr = _handles(vprofs)
+    _check(load().mpf_viterbi_rescore(ctx.handle, arr, len(vprofs), db.handle, _ptr(msv_flag),
+                                      _ptr(msv_nat), float(msv_min_nat), _ptr(score),
+                                      _ptr(overflow), _ptr(nat), _ptr(n_pass)),
+           "mpf_viterbi_rescore")

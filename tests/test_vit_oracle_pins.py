@@ -213,3 +213,20 @@ def test_generated_profiles_and_codes_at_or_above_K():
     for _ in range(30):
         seq = rng.integers(0, 32, size=int(rng.integers(0, 40)))
         assert one(pk, seq) == one(pw, seq)
+
+
+def test_stage_selection_rule():
+    """MSV -> Viterbi hand-off (Sec. 2.1): overflowed MSV scores pass whatever
+    their nat, SSV-filtered entries (flag 2, NaN) never pass, the threshold
+    is inclusive, and unselected entries read -32768 / 2 / NaN."""
+    rng = np.random.default_rng(5)
+    p = synth.make_vit_profile(20, rng)
+    db = synth.random_database(6, 30, rng, alphabet=20, min_len=1)
+    flag = np.array([0, 0, 1, 2, 0, 1], np.uint8)
+    nat = np.array([1.0, 0.999, -50.0, np.nan, 2.0, np.inf], np.float32)
+    (s, f, n), npass = oracle.viterbi_stage(p, db.residues, db.offsets, db.lengths, flag, nat, 1.0)
+    sel = np.array([True, False, True, False, True, True])
+    assert npass == 4
+    full = oracle.viterbi(p, db.residues, db.offsets, db.lengths)
+    assert np.array_equal(s[sel], full[0][sel]) and np.array_equal(f[sel], full[1][sel])
+    assert np.all(s[~sel] == -32768) and np.all(f[~sel] == 2) and np.all(np.isnan(n[~sel]))
