@@ -1042,8 +1042,9 @@ extern "C" int mpf_scan_noalloc(mpf_ctx *ctx, int filter, const mpf_profile *pro
 struct mpf_vprofile {
   mpf_ctx *ctx = nullptr;
   int M = 0, K = 0, Mpad = 0;
-  int16_t *d_msc = nullptr;     // kVitRows x Mpad
-  int16_t *d_trans = nullptr;   // kVitTrans x Mpad
+  bool fast = false;            // every transition and special score <= 0
+  int16_t *d_msc = nullptr;     // kVitRows x Mpad (striped when fast)
+  int16_t *d_trans = nullptr;   // kVitTrans x Mpad (striped when fast)
   int sp[kVitSpecial] = {};
   int base = 0;
   float scale = 1.f;
@@ -1051,33 +1052,39 @@ struct mpf_vprofile {
 
 namespace {
 
-// Launch one Viterbi kernel over n_q queries.  ranks / n_ranks (nullable) are
-// [n_q][n_seqs] and [n_q] device arrays of selected length ranks.
+// Launch the Viterbi kernels over n_q queries (one launch per kernel kind
+// present).  ranks / n_ranks (nullable) are [n_q][n_seqs] and [n_q] device
+// arrays of selected length ranks.
 int viterbi_enqueue(mpf_ctx *ctx, const mpf_vprofile *const *vps, int n_q, const mpf_db *db,
                     int16_t *score, uint8_t *flag, float *nat, const uint32_t *ranks,
                     const uint32_t *n_ranks) {
   const uint64_t n = db->n_seqs;
-  std::vector<VitQuery> qs((size_t)n_q);
-  int max_Mpad = 32;
-  for (int q = 0; q < n_q; ++q) {
-    const mpf_vprofile *v = vps[q];
-    VitQuery &d = qs[(size_t)q];
-    memset(&d, 0, sizeof(d));
-    d.msc = v->d_msc;
-    d.trans = v->d_trans;
-    for (int i = 0; i < kVitSpecial; ++i) d.sp[i] = v->sp[i];
-    d.M = v->M;
-    d.Mpad = v->Mpad;
-    d.base = v->base;
-    d.scale = v->scale;
-    d.score = score + (uint64_t)q * n;
-    d.flag = flag + (uint64_t)q * n;
-    d.nat = nat ? nat + (uint64_t)q * n : nullptr;
-    d.ranks = ranks ? ranks + (uint64_t)q * n : nullptr;
-    d.n_ranks = n_ranks ? n_ranks + q : nullptr;
-    max_Mpad = std::max(max_Mpad, v->Mpad);
+  std::vector<VitQuery> qs;
+  qs.reserve((size_t)n_q);
+  int max_Mpad[2] = {32, 32}, count[2] = {0, 0};
+  for (int pass = 0; pass < 2; ++pass) {   // general queries first, then fast ones
+    for (int q = 0; q < n_q; ++q) {
+      const mpf_vprofile *v = vps[q];
+      if ((int)v->fast != pass) continue;
+      VitQuery d;
+      memset(&d, 0, sizeof(d));
+      d.msc = v->d_msc;
+      d.trans = v->d_trans;
+      for (int i = 0; i < kVitSpecial; ++i) d.sp[i] = v->sp[i];
+      d.M = v->M;
+      d.Mpad = v->Mpad;
+      d.base = v->base;
+      d.scale = v->scale;
+      d.score = score + (uint64_t)q * n;
+      d.flag = flag + (uint64_t)q * n;
+      d.nat = nat ? nat + (uint64_t)q * n : nullptr;
+      d.ranks = ranks ? ranks + (uint64_t)q * n : nullptr;
+      d.n_ranks = n_ranks ? n_ranks + q : nullptr;
+      qs.push_back(d);
+      max_Mpad[pass] = std::max(max_Mpad[pass], v->Mpad);
+      ++count[pass];
+    }
   }
-  if (viterbi_smem_bytes(max_Mpad) > (size_t)ctx->max_smem) return MPF_EUNSUPPORTED;
   const size_t desc_bytes = sizeof(VitQuery) * (size_t)n_q;
   uint8_t *dev = nullptr;
   MPF_CUDA(cudaMallocAsync((void **)&dev, desc_bytes + 4 * (size_t)n_q, ctx->stream));
@@ -1085,18 +1092,22 @@ int viterbi_enqueue(mpf_ctx *ctx, const mpf_vprofile *const *vps, int n_q, const
   uint32_t *counters = reinterpret_cast<uint32_t *>(dev + desc_bytes);
   if (e == cudaSuccess) e = cudaMemsetAsync(counters, 0, 4 * (size_t)n_q, ctx->stream);
   int rc = e == cudaSuccess ? MPF_OK : MPF_ECUDA;
-  if (rc == MPF_OK) {
+  int first = 0;
+  for (int pass = 0; pass < 2 && rc == MPF_OK; ++pass) {
+    if (!count[pass]) continue;
     VitParams p;
     p.residues = db->d_words;
     p.seq_word = db->d_seq_word;
     p.seq_len = db->d_seq_len;
     p.seq_orig = db->d_seq_orig;
     p.n_seqs = (uint32_t)n;
-    p.n_queries = (uint32_t)n_q;
-    p.max_Mpad = max_Mpad;
-    p.queries = reinterpret_cast<const VitQuery *>(dev);
-    p.counters = counters;
-    if (launch_viterbi(p, ctx->num_sms, ctx->stream) != 0) rc = MPF_ECUDA;
+    p.n_queries = (uint32_t)count[pass];
+    p.max_Mpad = max_Mpad[pass];
+    p.queries = reinterpret_cast<const VitQuery *>(dev) + first;
+    p.counters = counters + first;
+    const int lr = launch_viterbi(p, pass == 1, ctx->max_smem, ctx->num_sms, ctx->stream);
+    if (lr) rc = lr == 2 ? MPF_EUNSUPPORTED : MPF_ECUDA;
+    first += count[pass];
   }
   cudaFreeAsync(dev, ctx->stream);
   (void)cudaGetLastError();
@@ -1121,16 +1132,30 @@ int mpf_vit_profile_create(mpf_ctx *ctx, int M, int K, const int16_t *msc, const
   if (!ctx || !msc || !trans || !special || M < 1 || K < 1 || K > kVitRows) return MPF_EINVAL;
   if (base < -32768 || base > 32767 || !isfinite(scale) || !(scale > 0.f)) return MPF_EINVAL;
   if (M > mpf_max_model_length()) return MPF_EUNSUPPORTED;
-  const int Mpad = (M + 31) & ~31;
-  if (viterbi_smem_bytes(Mpad) > (size_t)ctx->max_smem) return MPF_EUNSUPPORTED;
+  const int Mpad = (M + 31) & ~31, Q = Mpad / 32;
+  bool fast = true;
+  for (size_t i = 0; i < (size_t)kVitTrans * M; ++i) fast = fast && trans[i] <= 0;
+  for (int i = 0; i < kVitSpecial; ++i) fast = fast && special[i] <= 0;
+  const size_t need = fast ? viterbi_fast_smem_bytes(Mpad, 1) : viterbi_smem_bytes(Mpad);
+  if (need > (size_t)ctx->max_smem) return MPF_EUNSUPPORTED;
   std::vector<int16_t> hm((size_t)kVitRows * Mpad, (int16_t)-32768);
   std::vector<int16_t> ht((size_t)kVitTrans * Mpad, (int16_t)-32768);
-  for (int x = 0; x < K; ++x)
-    memcpy(&hm[(size_t)x * Mpad], msc + (size_t)x * M, sizeof(int16_t) * (size_t)M);
-  for (int t = 0; t < kVitTrans; ++t)
-    memcpy(&ht[(size_t)t * Mpad], trans + (size_t)t * M, sizeof(int16_t) * (size_t)M);
+  if (fast) {
+    // Striped: node k = l*Q + j in slot j*32 + l; transitions 8 per slot.
+    for (int k = 0; k < M; ++k) {
+      const size_t slot = (size_t)(k % Q) * 32 + (size_t)(k / Q);
+      for (int x = 0; x < K; ++x) hm[(size_t)x * Mpad + slot] = msc[(size_t)x * M + k];
+      for (int t = 0; t < kVitTrans; ++t) ht[slot * kVitTrans + t] = trans[(size_t)t * M + k];
+    }
+  } else {
+    for (int x = 0; x < K; ++x)
+      memcpy(&hm[(size_t)x * Mpad], msc + (size_t)x * M, sizeof(int16_t) * (size_t)M);
+    for (int t = 0; t < kVitTrans; ++t)
+      memcpy(&ht[(size_t)t * Mpad], trans + (size_t)t * M, sizeof(int16_t) * (size_t)M);
+  }
   mpf_vprofile *v = new (std::nothrow) mpf_vprofile;
   if (!v) return MPF_ENOMEM;
+  v->fast = fast;
   v->ctx = ctx;
   v->M = M;
   v->K = K;

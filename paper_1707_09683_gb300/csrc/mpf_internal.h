@@ -78,8 +78,9 @@ int launch_select(const uint32_t *seq_orig, uint64_t n, int n_q, const uint8_t *
 int launch_pvalues(const float *nat, uint64_t n, float mu, float lambda, float *p, int num_sms,
                    cudaStream_t st);
 
-// P7Viterbi filter (mpf_viterbi.cu).  Tables are int16 in device memory,
-// node k (0-based) at column k of rows Mpad long; -32768 is minus infinity.
+// P7Viterbi filter (mpf_viterbi.cu).  Tables are int16 in device memory;
+// -32768 is minus infinity.  General layout: node k (0-based) at column k of
+// rows Mpad long.
 constexpr int kVitThreads = 256;
 constexpr int kVitRows = 32;         // msc rows: residue codes 0..31
 constexpr int kVitTrans = 8;         // BM, MM, IM, DM, MI, II, MD, DD
@@ -111,8 +112,12 @@ struct VitParams {
   const VitQuery *queries;
   uint32_t *counters;         // one per query, zero before the launch
 };
-int launch_viterbi(const VitParams &p, int num_sms, cudaStream_t st);
+// fast: every transition and special score <= 0; tables in the striped
+// layout (msc [32][Q][32] int16, trans [Q][32] x 8 int16 with Q = Mpad / 32).
+// Returns 0, 1 on a CUDA error, 2 if the rows do not fit in shared memory.
+int launch_viterbi(const VitParams &p, bool fast, int max_smem, int num_sms, cudaStream_t st);
 size_t viterbi_smem_bytes(int Mpad);
+size_t viterbi_fast_smem_bytes(int Mpad, int warps);
 
 // Kernel instantiation for (lanes, words, mode), or nullptr if not built.
 KernelFn kernel_for(int lanes, int words, int mode);

@@ -1,8 +1,11 @@
 // mpf_viterbi.cu -- the P7Viterbi filter (Eq. 1 of Sec. 2.1) for sm_103a.
 //
-// One warp scores one sequence.  The DP row (M, I, D scores of every node)
-// lives in the warp's slice of shared memory as 16-bit words and is swept in
-// chunks of 32 consecutive nodes, node k handled by lane k mod 32:
+// One warp scores one sequence; all arithmetic is the 16-bit saturating word
+// arithmetic of the Viterbi filter, carried in 32-bit registers.  Two kernels:
+//
+// viterbi_kernel (any profile).  The DP row (M, I, D of every node) lives in
+// the warp's slice of shared memory and is swept in chunks of 32 consecutive
+// nodes, node k handled by lane k mod 32:
 //   * the diagonal terms of Eq. 1 (node k-1 of the previous row) come from the
 //     neighbouring lane by one shuffle, and from the previous chunk's last
 //     lane across a chunk boundary;
@@ -12,8 +15,27 @@
 //     predecessor, these maps compose, and a 5-step warp scan gives every lane
 //     its node's value from the chunk's carry-in;
 //   * E is a warp max, then the N, C, J, B special states are scalar.
-// All arithmetic is the 16-bit saturating word arithmetic of the Viterbi
-// filter, computed in 32-bit registers with explicit clamps.
+//
+// viterbi_fast_kernel (every transition and special score <= 0, as for any
+// profile of log-probabilities).  Then no sum can pass the upper bound
+// except M[k] itself, whose saturation at 32767 is the overflow, so every
+// sat() reduces to max(., -32768) and a chain of them to one DPX
+// add-then-max per term; and D[k] <= max of the M of earlier nodes, so E is
+// the maximum of M alone.  Lane l owns a contiguous segment of Q = ceil(M/32)
+// nodes (Farrar's striped order: node l*Q + j sits in slot j*32 + l, so
+// every shared access of a warp is one contiguous line):
+//   pass 1  each lane sweeps its segment, computing M and I and a local
+//           delete chain that assumes minus infinity enters the segment;
+//   carry   the delete score entering each segment is an exclusive warp scan
+//           of the segments' maps d -> max(A, d + B) (B = sum of tDD over the
+//           segment, a per-query constant);
+//   pass 2  each lane raises its local delete chain by the entering score
+//           only while that raises anything (the "lazy F" idea of the SIMD
+//           Viterbi of HMMER3): once the carried value falls below the local
+//           chain it can never win again.
+// The transition table is staged once per query into shared memory and read
+// by all warps of a block; match scores are read from global memory in the
+// same striped order.
 #include <cuda_runtime.h>
 #include <math.h>
 #include <stdint.h>
@@ -153,21 +175,191 @@ __global__ void __launch_bounds__(kVitThreads) viterbi_kernel(VitParams p) {
   }
 }
 
+// ------------------------------------------------------------ fast kernel
+
+constexpr int kNeg = -32768;
+
+__device__ __forceinline__ int lo16(uint32_t w) { return (int)(int16_t)(w & 0xffffu); }
+__device__ __forceinline__ int hi16(uint32_t w) { return ((int)w) >> 16; }
+// max(a + b, c), one DPX instruction.
+__device__ __forceinline__ int addmax(int a, int b, int c) { return __viaddmax_s32(a, b, c); }
+
+// Shared memory: the query's transitions, Qmax*32 uint4 (8 int16 per node:
+// BM|MM, IM|DM, MI|II, MD|DD), then per warp Qmax*32 uint2 of DP state
+// (M|I, D) in slot j*32 + lane.
+__global__ void __launch_bounds__(kVitThreads) viterbi_fast_kernel(VitParams p) {
+  extern __shared__ __align__(16) uint4 fsm[];
+  const int lane = threadIdx.x & 31;
+  const int warp = threadIdx.x >> 5;
+  const int Qmax = p.max_Mpad >> 5;
+  uint4 *tr = fsm;
+  uint2 *st = reinterpret_cast<uint2 *>(fsm + (size_t)Qmax * 32) + (size_t)warp * Qmax * 32;
+  int16_t *st_d = reinterpret_cast<int16_t *>(st) + 2;       // D of slot s at st_d[4 s]
+  const int16_t *tr_dd = reinterpret_cast<const int16_t *>(tr) + 7;   // tDD of slot s at tr_dd[8 s]
+
+  for (uint32_t qi = 0; qi < p.n_queries; ++qi) {
+    const VitQuery Q = p.queries[qi];
+    const int nq = Q.Mpad >> 5;
+    __syncthreads();   // every warp is done with the previous query's table
+    const uint4 *gtr = reinterpret_cast<const uint4 *>(Q.trans);
+    for (int i = threadIdx.x; i < nq * 32; i += blockDim.x) tr[i] = __ldg(gtr + i);
+    __syncthreads();
+
+    // Per-lane constants of the query.
+    const int nv = min(max(Q.M - lane * nq, 0), nq);   // real nodes in this lane's segment
+    int tMD0 = kNeg, tDD0 = 0, Bl = 0;
+    if (nv > 0) {
+      tMD0 = lo16(tr[lane].w);
+      tDD0 = hi16(tr[lane].w);
+    }
+    for (int j = 0; j < nv; ++j) Bl += hi16(tr[j * 32 + lane].w);
+    const int Bsuf = Bl - tDD0;
+    int P = Bl;   // inclusive prefix over lanes
+#pragma unroll
+    for (int off = 1; off < 32; off <<= 1) {
+      const int y = __shfl_up_sync(kAll, P, off);
+      if (lane >= off) P += y;
+    }
+    int Wn[5];    // sum of B over lanes (lane - 2^r, lane], or a sentinel
+#pragma unroll
+    for (int r = 0; r < 5; ++r) {
+      const int y = __shfl_up_sync(kAll, P, 1 << r);
+      Wn[r] = lane >= (1 << r) ? P - y : -(1 << 29);
+    }
+    const int tNN = Q.sp[0], tNB = Q.sp[1], tEC = Q.sp[2], tCC = Q.sp[3];
+    const int tCT = Q.sp[4], tEJ = Q.sp[5], tJJ = Q.sp[6], tJB = Q.sp[7];
+    const uint64_t n_sel = Q.ranks ? (uint64_t)*Q.n_ranks : (uint64_t)p.n_seqs;
+
+    for (;;) {
+      uint32_t q = 0;
+      if (lane == 0) q = atomicAdd(p.counters + qi, 1u);
+      q = __shfl_sync(kAll, q, 0);
+      if ((uint64_t)q >= n_sel) break;
+      const uint32_t r = Q.ranks ? __ldg(Q.ranks + q) : q;
+      const uint32_t w0 = __ldg(p.seq_word + r);
+      const int len = (int)__ldg(p.seq_len + r);
+      const uint32_t orig = __ldg(p.seq_orig + r);
+
+      const uint2 neg2 = make_uint2(0x80008000u, 0x8000u);
+      for (int j = 0; j < nq; ++j) st[j * 32 + lane] = neg2;
+      int xN = Q.base, xJ = kNeg, xC = kNeg;
+      int xB = addmax(xN, tNB, kNeg);
+      int pM0 = kNeg, pI0 = kNeg, pD0 = kNeg;   // previous row, node before the segment
+      bool ovf = false;
+      uint32_t word = 0;
+      for (int i = 0; i < len; ++i) {
+        if ((i & 3) == 0) word = __ldg(p.residues + w0 + (uint32_t)(i >> 2));
+        const int x = (int)((word >> (8 * (i & 3))) & 0xffu);
+        const int16_t *erow = Q.msc + (size_t)x * nq * 32 + lane;
+
+        // Pass 1: M, I and the segment-local delete chain.
+        int dM = pM0, dI = pI0, dD = pD0, mprev = kNeg, d = kNeg, mx = kNeg;
+        int Mn = kNeg, In = kNeg;
+#pragma unroll 4
+        for (int j = 0; j < nv; ++j) {
+          const uint2 s = st[j * 32 + lane];
+          const uint4 t = tr[j * 32 + lane];
+          const int e = __ldg(erow + j * 32);
+          const int Mo = lo16(s.x), Io = hi16(s.x), Do = lo16(s.y);
+          int best = addmax(dM, hi16(t.x), kNeg);      // M' + tMM
+          best = addmax(dI, lo16(t.y), best);           // I' + tIM
+          best = addmax(dD, hi16(t.y), best);           // D' + tDM
+          best = addmax(xB, lo16(t.x), best);           // xB + tBM
+          Mn = addmax(best, e, kNeg);
+          In = addmax(Io, hi16(t.z), addmax(Mo, lo16(t.z), kNeg));
+          d = addmax(d, hi16(t.w), addmax(mprev, lo16(t.w), kNeg));
+          mx = max(mx, Mn);
+          st[j * 32 + lane] = make_uint2(__byte_perm((uint32_t)Mn, (uint32_t)In, 0x5410), (uint32_t)d);
+          dM = Mo;
+          dI = Io;
+          dD = Do;
+          mprev = Mn;
+        }
+        const int xE = __reduce_max_sync(kAll, mx);
+        if (xE >= 32767) {
+          ovf = true;
+          break;
+        }
+
+        // Delete score entering each segment: exclusive scan of the maps.
+        int Mlp = __shfl_up_sync(kAll, Mn, 1);
+        int Ilp = __shfl_up_sync(kAll, In, 1);
+        if (lane == 0) Mlp = Ilp = kNeg;
+        int A = addmax(Mlp, tMD0 + Bsuf, d);
+#pragma unroll
+        for (int r = 0; r < 5; ++r) A = addmax(__shfl_up_sync(kAll, A, 1 << r), Wn[r], A);
+        int carry = __shfl_up_sync(kAll, A, 1);
+        if (lane == 0) carry = kNeg;
+
+        // Pass 2: raise the local chain while the carried score wins.
+        int X = max(carry + tDD0, Mlp + tMD0);
+        int Dlast = d;
+        for (int j = 0; j < nv; ++j) {
+          const int sl = j * 32 + lane;
+          if (X <= (int)st_d[4 * sl]) break;
+          st_d[4 * sl] = (int16_t)X;
+          if (j == nv - 1) {
+            Dlast = X;
+            break;
+          }
+          X += (int)tr_dd[8 * (sl + 32)];
+        }
+        int Dlp = __shfl_up_sync(kAll, Dlast, 1);
+        if (lane == 0) Dlp = kNeg;
+        pM0 = Mlp;
+        pI0 = Ilp;
+        pD0 = Dlp;
+
+        xN = addmax(xN, tNN, kNeg);
+        xC = addmax(xC, tCC, addmax(xE, tEC, kNeg));
+        xJ = addmax(xJ, tJJ, addmax(xE, tEJ, kNeg));
+        xB = addmax(xN, tNB, addmax(xJ, tJB, kNeg));
+      }
+      if (lane == 0) {
+        if (ovf) {
+          Q.score[orig] = 32767;
+          Q.flag[orig] = 1;
+          if (Q.nat) Q.nat[orig] = __int_as_float(0x7f800000);
+        } else {
+          const int sc = addmax(xC, tCT, kNeg);
+          Q.score[orig] = (int16_t)sc;
+          Q.flag[orig] = 0;
+          if (Q.nat) Q.nat[orig] = __fsub_rn(__fdiv_rn(__int2float_rn(sc - Q.base), Q.scale), 3.0f);
+        }
+      }
+      __syncwarp();
+    }
+  }
+}
+
 }  // namespace
+
+size_t viterbi_fast_smem_bytes(int Mpad, int warps) {
+  return (size_t)(Mpad >> 5) * 32 * (16 + 8 * (size_t)warps);
+}
 
 size_t viterbi_smem_bytes(int Mpad) { return (size_t)(kVitThreads / 32) * 3 * (size_t)Mpad * sizeof(int16_t); }
 
-int launch_viterbi(const VitParams &p, int num_sms, cudaStream_t st) {
+int launch_viterbi(const VitParams &p, bool fast, int max_smem, int num_sms, cudaStream_t st) {
   if (p.n_queries == 0) return 0;
-  const size_t smem = viterbi_smem_bytes(p.max_Mpad);
-  if (cudaFuncSetAttribute((const void *)viterbi_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                           (int)smem) != cudaSuccess)
+  const void *fn = fast ? (const void *)viterbi_fast_kernel : (const void *)viterbi_kernel;
+  int warps = kVitThreads / 32;
+  size_t smem = viterbi_smem_bytes(p.max_Mpad);
+  if (fast) {
+    while (warps > 1 && viterbi_fast_smem_bytes(p.max_Mpad, warps) > (size_t)max_smem) --warps;
+    smem = viterbi_fast_smem_bytes(p.max_Mpad, warps);
+  }
+  if (smem > (size_t)max_smem) return 2;
+  if (cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem) != cudaSuccess)
     return 1;
   int per_sm = 0;
-  if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, (const void *)viterbi_kernel, kVitThreads,
-                                                    smem) != cudaSuccess || per_sm < 1)
+  if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, fn, warps * 32, smem) != cudaSuccess ||
+      per_sm < 1)
     return 1;
-  viterbi_kernel<<<num_sms * per_sm, kVitThreads, smem, st>>>(p);
+  if (fast)
+    viterbi_fast_kernel<<<num_sms * per_sm, warps * 32, smem, st>>>(p);
+  else
+    viterbi_kernel<<<num_sms * per_sm, warps * 32, smem, st>>>(p);
   return cudaGetLastError() == cudaSuccess ? 0 : 1;
 }
 

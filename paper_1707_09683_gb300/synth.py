@@ -329,10 +329,13 @@ def make_vit_profile(M: int, rng: np.random.Generator, L: int = 350,
 
 
 def random_vit_profile(M: int, K: int, rng: np.random.Generator, lo: int = -32768,
-                       hi: int = 32767, base=None) -> VitProfile:
-    """Adversarial Viterbi profile: uniform int16 scores in [lo, hi]."""
-    def u(shape):
-        return rng.integers(lo, hi + 1, size=shape, dtype=np.int64).astype(np.int16)
-    return VitProfile(M=M, K=K, msc=u((K, M)), trans=u((8, M)), special=u(8),
+                       hi: int = 32767, base=None, moves_hi=None) -> VitProfile:
+    """Adversarial Viterbi profile: uniform int16 scores in [lo, hi]; with
+    ``moves_hi`` the transition and special scores are drawn from
+    [lo, moves_hi] instead (moves_hi=0: log-probability-like signs)."""
+    def u(shape, top=hi):
+        return rng.integers(lo, top + 1, size=shape, dtype=np.int64).astype(np.int16)
+    mh = hi if moves_hi is None else min(hi, moves_hi)
+    return VitProfile(M=M, K=K, msc=u((K, M)), trans=u((8, M), mh), special=u(8, mh),
                       base=int(rng.integers(-32768, 32768)) if base is None else int(base),
                       scale=float(np.float32(VIT_SCALE)))

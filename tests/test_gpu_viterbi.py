@@ -101,11 +101,29 @@ def test_adversarial_profiles(ctx, seed):
         assert got[1].any()   # positive scores overflow
 
 
+@pytest.mark.parametrize("seed", range(6))
+def test_adversarial_nonpositive_moves(ctx, seed):
+    """Transition and special scores <= 0 (the fast kernel) with arbitrary
+    match scores: saturation at -32768, overflow from positive matches."""
+    rng = np.random.default_rng(300 + seed)
+    M = int(rng.integers(1, 700))
+    K = int(rng.integers(1, 33))
+    lo, hi = [(-32768, 32767), (-3000, 3000), (-300, 300), (-32768, 0),
+              (-600, 4000), (-20, 32767)][seed]
+    v = synth.random_vit_profile(M, K, rng, lo=lo, hi=hi, moves_hi=0)
+    db = synth.random_database(700, 150, rng, alphabet=32)
+    got = _run(ctx, [v], db)
+    if seed == 5:
+        assert got[1].any()
+
+
 def test_multi_query_launch(ctx):
     rng = np.random.default_rng(9)
     wl = synth.make_workload(0, n_seqs=800)
     vprofs = [synth.make_vit_profile(M, rng) for M in (45, 700, 1, 128, 333)]
-    vprofs.append(synth.random_vit_profile(90, 20, rng, lo=-400, hi=60))
+    vprofs.append(synth.random_vit_profile(90, 20, rng, lo=-400, hi=60))        # general kernel
+    vprofs.append(synth.random_vit_profile(1500, 20, rng, lo=-400, hi=60))
+    vprofs.append(synth.random_vit_profile(70, 20, rng, lo=-900, hi=400, moves_hi=0))
     _run(ctx, vprofs, wl.db)
 
 
