@@ -392,6 +392,12 @@ def run_mpf(args):
         log(f"pipeline: {ms_pipe:.1f} ms per step, {100 * passed / (q * n):.2f}% pass SSV "
             f"(both filters on everything: {ms_batched:.1f} ms)")
 
+    # Third stage: the P7Viterbi filter (Eq. 1) over the sequences whose MSV
+    # score passed (one Viterbi profile per query, same model lengths).
+    vit = None
+    if args.pipeline and args.viterbi:
+        vit = run_viterbi_stage(args, ctx, db, wl, profs, p_msv, thr, run_pipe, time_steps, clocks, dev)
+
     # Serving: continuous batching of arriving queries (model lengths drawn as
     # in the serving workload) against the resident database, per offered load.
     serving = None
@@ -425,6 +431,7 @@ def run_mpf(args):
                     "path": "mpf_profile_create from host bytes + mpf_scan_batch (MSV, SSV) into "
                             "host buffers + mpf_profile_destroy; database resident"},
             "pipeline": pipe,
+            "viterbi": vit,
             "serving": serving,
             "gpu_launches": launches_per_step * args.steps,
             "clocks": clocks,
@@ -435,6 +442,52 @@ def run_mpf(args):
     if world > 1:
         import torch.distributed as dist
         dist.destroy_process_group()
+
+
+# DPX operations per cell of the saturating Viterbi recurrence once every
+# sat() is a single add-then-max (moves <= 0): 4 for the best predecessor of
+# M, 1 for the emission, 2 for I, 2 for D, 1 for the E maximum.
+VIT_OPS_PER_CELL = 10
+
+
+def run_viterbi_stage(args, ctx, db, wl, profs, p_msv, thr, run_pipe, time_steps, clocks, dev):
+    import torch
+    from paper_1707_09683_gb300 import mpf, synth
+    n, q = db.n_seqs, len(profs)
+    vrecs = [synth.make_vit_profile(p.M, np.random.default_rng(500 + i))
+             for i, p in enumerate(wl.profiles)]
+    vps = [mpf.VitProfile(ctx, v) for v in vrecs]
+    v_out = (torch.empty(q * n, dtype=torch.int16, device=dev),
+             torch.empty(q * n, dtype=torch.uint8, device=dev),
+             torch.empty(q * n, dtype=torch.float32, device=dev))
+    n_v = torch.empty(q, dtype=torch.int32, device=dev)
+    run_vit = lambda: mpf.viterbi_rescore(ctx, vps, db, p_msv[1], p_msv[2], thr, *v_out, n_v)
+    for _ in range(args.warmup):
+        run_vit()
+    ms_vit = time_steps(run_vit, args.steps)
+    ms_three = time_steps(lambda: (run_pipe(), run_vit()), args.steps)
+    lens = torch.from_numpy(wl.db.lengths.astype(np.int64)).to(dev)
+    sel = (v_out[1].view(q, n) != 2)
+    cells = float(sum(int(lens[sel[i]].sum().item()) * wl.profiles[i].M for i in range(q)))
+    passed = int(n_v.sum().item())
+    gcups = cells / (ms_vit * 1e-3) / 1e9
+    nsm = torch.cuda.get_device_properties(dev).multi_processor_count
+    sm_mhz = clocks.get("sm_mhz") or 2070.0
+    peak = nsm * INT_LANES_PER_SM_CLK / VIT_OPS_PER_CELL * sm_mhz * 1e6 / 1e9
+    for v in vps:
+        v.close()
+    log(f"viterbi: {ms_vit:.2f} ms per step over {passed} (query, sequence) pairs, "
+        f"{gcups:.1f} GCUPS; three stages {ms_three:.1f} ms")
+    return {"metric": "Viterbi GCUPS over the MSV survivors", "value": gcups, "unit": "GCUPS",
+            "ms_per_step": ms_vit, "msv_min_nat": thr, "pairs_scored": passed,
+            "pass_fraction": passed / (q * n), "cells_per_step": cells,
+            "three_stage_ms_per_step": ms_three,
+            "kernel": "viterbi_fast_kernel (all moves <= 0)",
+            "roofline": {"bound": "alu", "achieved": gcups, "peak": peak, "unit": "GCUPS",
+                         "frac": gcups / peak, "traffic": None,
+                         "timed": "mpf_viterbi_rescore per step (3 selection kernels + 1 Viterbi kernel)",
+                         "peak_basis": f"{nsm} SMs x {INT_LANES_PER_SM_CLK} DPX lanes/clk / "
+                                       f"{VIT_OPS_PER_CELL} ops per cell x {sm_mhz:.0f} MHz"}}
 
 
 def run_serving(db_record, rates, n_requests, device, seed=3):
@@ -495,6 +548,28 @@ def run_profile_case(args):
                       "config_ssv": prof.get_config(mpf.SSV)}))
 
 
+def run_profile_viterbi(args):
+    """Small case for ncu: the first args.profile_vit_seqs sequences of the
+    500,000-sequence database against one Viterbi profile of M =
+    args.profile_m; one warm-up and one measured scan (kernel launches 0, 1)."""
+    import torch
+    from paper_1707_09683_gb300 import build, mpf, synth
+    build.build()
+    wl = synth.make_workload(1)
+    k = min(args.profile_vit_seqs, wl.db.n_seqs)
+    ctx = mpf.Context(0)
+    db = mpf.Database(ctx, wl.db.residues, wl.db.offsets[:k], wl.db.lengths[:k])
+    vp = mpf.VitProfile(ctx, synth.make_vit_profile(args.profile_m, np.random.default_rng(0)))
+    dev = torch.device("cuda", 0)
+    outs = (torch.empty(k, dtype=torch.int16, device=dev), torch.empty(k, dtype=torch.uint8, device=dev),
+            torch.empty(k, dtype=torch.float32, device=dev))
+    for rep in range(2):
+        mpf.viterbi_scan(ctx, [vp], db, *outs)
+        ctx.sync()
+    print(json.dumps({"profile_case": "viterbi", "M": args.profile_m, "n_seqs": k,
+                      "residues": db.n_residues}))
+
+
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
@@ -511,12 +586,17 @@ def main():
     ap.add_argument("--arith", default="auto", choices=["auto", "i16", "f16"])
     ap.add_argument("--no-serve", action="store_true")
     ap.add_argument("--no-pipeline", dest="pipeline", action="store_false")
+    ap.add_argument("--no-viterbi", dest="viterbi", action="store_false")
     ap.add_argument("--serve-rates", type=float, nargs="+", default=[10, 50, 100, 200, 500])
     ap.add_argument("--serve-requests", type=int, default=24)
     ap.add_argument("--profile-case", action="store_true")
     ap.add_argument("--profile-m", type=int, default=2405)
+    ap.add_argument("--profile-viterbi", action="store_true")
+    ap.add_argument("--profile-vit-seqs", type=int, default=20000)
     args = ap.parse_args()
-    if args.profile_case:
+    if args.profile_viterbi:
+        run_profile_viterbi(args)
+    elif args.profile_case:
         run_profile_case(args)
     elif args.impl == "reference":
         run_reference(args)

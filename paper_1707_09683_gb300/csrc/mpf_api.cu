@@ -84,6 +84,7 @@ struct mpf_db {
   uint32_t *d_seq_len = nullptr;
   uint32_t *d_seq_orig = nullptr;
   uint32_t pad_word = 0;
+  int n_codes = 0;                  // distinct residue codes present
 };
 
 // ---------------------------------------------------------------- helpers --
@@ -717,8 +718,11 @@ int mpf_db_upload(mpf_ctx *ctx, const uint8_t *residues, uint64_t n_residues,
     if (offsets[s] > n_residues || lengths[s] > n_residues - offsets[s]) return MPF_EINVAL;
     chunks += (lengths[s] + 15u) / 16u;
   }
-  for (uint64_t i = 0; i < n_residues; ++i)
+  uint32_t seen = 0;
+  for (uint64_t i = 0; i < n_residues; ++i) {
     if (residues[i] >= 32) return MPF_EINVAL;
+    seen |= 1u << residues[i];
+  }
   chunks += 1;  // the kernel prefetches one word past a sequence
   if (chunks * 4 >= (1ull << 32)) return MPF_EUNSUPPORTED;
   // Length ranks: longest first, ties by sequence number.
@@ -757,6 +761,7 @@ int mpf_db_upload(mpf_ctx *ctx, const uint8_t *residues, uint64_t n_residues,
   db->n_residues = 0;
   for (uint64_t s = 0; s < n_seqs; ++s) db->n_residues += lengths[s];
   db->pad_word = 0;
+  db->n_codes = __builtin_popcount(seen);
   const size_t ns = std::max<uint64_t>(n_seqs, 1);
   cudaError_t e = cudaMalloc(&db->d_words, chunks * 16);
   if (e == cudaSuccess) e = cudaMalloc(&db->d_seq_word, ns * 4);
@@ -1052,38 +1057,44 @@ struct mpf_vprofile {
 
 namespace {
 
-// Launch the Viterbi kernels over n_q queries (one launch per kernel kind
-// present).  ranks / n_ranks (nullable) are [n_q][n_seqs] and [n_q] device
-// arrays of selected length ranks.
+// Launch the Viterbi kernels over n_q queries: the general kernel for the
+// profiles with a positive move, the fast kernel for the others, one launch
+// per group of queries that share the fast kernel's launch shape (queries of
+// one launch are scored one after the other by every block).  ranks /
+// n_ranks (nullable) are [n_q][n_seqs] and [n_q] device arrays of selected
+// length ranks.
 int viterbi_enqueue(mpf_ctx *ctx, const mpf_vprofile *const *vps, int n_q, const mpf_db *db,
                     int16_t *score, uint8_t *flag, float *nat, const uint32_t *ranks,
                     const uint32_t *n_ranks) {
   const uint64_t n = db->n_seqs;
+  // Order: general queries first (key -1), then fast ones by launch shape and length.
+  std::vector<std::tuple<int, int, int>> order;   // (key, Mpad, query)
+  for (int q = 0; q < n_q; ++q) {
+    const mpf_vprofile *v = vps[q];
+    const int key = v->fast ? viterbi_fast_shape_key(v->Mpad, db->n_codes, ctx->max_smem) : -1;
+    order.emplace_back(key, v->Mpad, q);
+  }
+  std::stable_sort(order.begin(), order.end());
   std::vector<VitQuery> qs;
   qs.reserve((size_t)n_q);
-  int max_Mpad[2] = {32, 32}, count[2] = {0, 0};
-  for (int pass = 0; pass < 2; ++pass) {   // general queries first, then fast ones
-    for (int q = 0; q < n_q; ++q) {
-      const mpf_vprofile *v = vps[q];
-      if ((int)v->fast != pass) continue;
-      VitQuery d;
-      memset(&d, 0, sizeof(d));
-      d.msc = v->d_msc;
-      d.trans = v->d_trans;
-      for (int i = 0; i < kVitSpecial; ++i) d.sp[i] = v->sp[i];
-      d.M = v->M;
-      d.Mpad = v->Mpad;
-      d.base = v->base;
-      d.scale = v->scale;
-      d.score = score + (uint64_t)q * n;
-      d.flag = flag + (uint64_t)q * n;
-      d.nat = nat ? nat + (uint64_t)q * n : nullptr;
-      d.ranks = ranks ? ranks + (uint64_t)q * n : nullptr;
-      d.n_ranks = n_ranks ? n_ranks + q : nullptr;
-      qs.push_back(d);
-      max_Mpad[pass] = std::max(max_Mpad[pass], v->Mpad);
-      ++count[pass];
-    }
+  for (const auto &o : order) {
+    const int q = std::get<2>(o);
+    const mpf_vprofile *v = vps[q];
+    VitQuery d;
+    memset(&d, 0, sizeof(d));
+    d.msc = v->d_msc;
+    d.trans = v->d_trans;
+    for (int i = 0; i < kVitSpecial; ++i) d.sp[i] = v->sp[i];
+    d.M = v->M;
+    d.Mpad = v->Mpad;
+    d.base = v->base;
+    d.scale = v->scale;
+    d.score = score + (uint64_t)q * n;
+    d.flag = flag + (uint64_t)q * n;
+    d.nat = nat ? nat + (uint64_t)q * n : nullptr;
+    d.ranks = ranks ? ranks + (uint64_t)q * n : nullptr;
+    d.n_ranks = n_ranks ? n_ranks + q : nullptr;
+    qs.push_back(d);
   }
   const size_t desc_bytes = sizeof(VitQuery) * (size_t)n_q;
   uint8_t *dev = nullptr;
@@ -1092,22 +1103,62 @@ int viterbi_enqueue(mpf_ctx *ctx, const mpf_vprofile *const *vps, int n_q, const
   uint32_t *counters = reinterpret_cast<uint32_t *>(dev + desc_bytes);
   if (e == cudaSuccess) e = cudaMemsetAsync(counters, 0, 4 * (size_t)n_q, ctx->stream);
   int rc = e == cudaSuccess ? MPF_OK : MPF_ECUDA;
-  int first = 0;
-  for (int pass = 0; pass < 2 && rc == MPF_OK; ++pass) {
-    if (!count[pass]) continue;
+  // Groups run concurrently on the context's fork streams, so that one
+  // group's tail overlaps the others' work.
+  std::vector<std::pair<int, int>> groups;
+  for (int first = 0; first < n_q;) {
+    int last = first;
+    while (last < n_q && std::get<0>(order[(size_t)last]) == std::get<0>(order[(size_t)first])) ++last;
+    groups.emplace_back(first, last);
+    first = last;
+  }
+  const bool fork = groups.size() > 1;
+  std::vector<cudaEvent_t> evs;
+  if (fork && rc == MPF_OK) {
+    while (ctx->n_fork < 8 && (size_t)ctx->n_fork < groups.size()) {
+      if (cudaStreamCreateWithFlags(&ctx->fork[ctx->n_fork], cudaStreamNonBlocking) != cudaSuccess) break;
+      ++ctx->n_fork;
+    }
+    for (size_t i = 0; i <= groups.size() && rc == MPF_OK; ++i) {
+      cudaEvent_t ev;
+      if (cudaEventCreateWithFlags(&ev, cudaEventDisableTiming) != cudaSuccess) rc = MPF_ECUDA;
+      else evs.push_back(ev);
+    }
+    if (ctx->n_fork < 1) rc = MPF_ECUDA;
+    if (rc == MPF_OK && cudaEventRecord(evs.back(), ctx->stream) != cudaSuccess) rc = MPF_ECUDA;
+  }
+  for (size_t gi = 0; gi < groups.size() && rc == MPF_OK; ++gi) {
+    const int first = groups[gi].first, last = groups[gi].second;
+    const int key = std::get<0>(order[(size_t)first]);
+    int max_Mpad = 32;
+    for (int i = first; i < last; ++i) max_Mpad = std::max(max_Mpad, std::get<1>(order[(size_t)i]));
+    cudaStream_t st = ctx->stream;
+    if (fork) {
+      st = ctx->fork[gi % (size_t)ctx->n_fork];
+      if (cudaStreamWaitEvent(st, evs.back(), 0) != cudaSuccess) {
+        rc = MPF_ECUDA;
+        break;
+      }
+    }
     VitParams p;
     p.residues = db->d_words;
     p.seq_word = db->d_seq_word;
     p.seq_len = db->d_seq_len;
     p.seq_orig = db->d_seq_orig;
     p.n_seqs = (uint32_t)n;
-    p.n_queries = (uint32_t)count[pass];
-    p.max_Mpad = max_Mpad[pass];
+    p.n_queries = (uint32_t)(last - first);
+    p.max_Mpad = max_Mpad;
     p.queries = reinterpret_cast<const VitQuery *>(dev) + first;
     p.counters = counters + first;
-    const int lr = launch_viterbi(p, pass == 1, ctx->max_smem, ctx->num_sms, ctx->stream);
+    const int lr = launch_viterbi(p, key >= 0, db->n_codes, ctx->max_smem, ctx->num_sms, st);
     if (lr) rc = lr == 2 ? MPF_EUNSUPPORTED : MPF_ECUDA;
-    first += count[pass];
+    if (fork && cudaEventRecord(evs[gi], st) != cudaSuccess) rc = MPF_ECUDA;
+  }
+  if (fork) {
+    // Join every fork stream that may have work queued, then release the events.
+    for (size_t gi = 0; gi < groups.size() && gi + 1 < evs.size(); ++gi)
+      if (cudaStreamWaitEvent(ctx->stream, evs[gi], 0) != cudaSuccess) rc = MPF_ECUDA;
+    for (cudaEvent_t ev : evs) cudaEventDestroy(ev);
   }
   cudaFreeAsync(dev, ctx->stream);
   (void)cudaGetLastError();

@@ -82,6 +82,7 @@ int launch_pvalues(const float *nat, uint64_t n, float mu, float lambda, float *
 // -32768 is minus infinity.  General layout: node k (0-based) at column k of
 // rows Mpad long.
 constexpr int kVitThreads = 256;
+constexpr int kVitFastMaxThreads = 512;
 constexpr int kVitRows = 32;         // msc rows: residue codes 0..31
 constexpr int kVitTrans = 8;         // BM, MM, IM, DM, MI, II, MD, DD
 constexpr int kVitSpecial = 8;       // NN, NB, EC, CC, CT, EJ, JJ, JB
@@ -114,10 +115,14 @@ struct VitParams {
 };
 // fast: every transition and special score <= 0; tables in the striped
 // layout (msc [32][Q][32] int16, trans [Q][32] x 8 int16 with Q = Mpad / 32).
+// n_codes: distinct residue codes in the database (sizes the L1 share).
 // Returns 0, 1 on a CUDA error, 2 if the rows do not fit in shared memory.
-int launch_viterbi(const VitParams &p, bool fast, int max_smem, int num_sms, cudaStream_t st);
+int launch_viterbi(const VitParams &p, bool fast, int n_codes, int max_smem, int num_sms,
+                   cudaStream_t st);
 size_t viterbi_smem_bytes(int Mpad);
 size_t viterbi_fast_smem_bytes(int Mpad, int warps);
+// Launch shape of the fast kernel for one model length (equal keys share a launch).
+int viterbi_fast_shape_key(int Mpad, int n_codes, int max_smem);
 
 // Kernel instantiation for (lanes, words, mode), or nullptr if not built.
 KernelFn kernel_for(int lanes, int words, int mode);

@@ -40,6 +40,8 @@
 #include <math.h>
 #include <stdint.h>
 
+#include <algorithm>
+
 #include "mpf_internal.h"
 
 namespace mpf {
@@ -185,17 +187,16 @@ __device__ __forceinline__ int hi16(uint32_t w) { return ((int)w) >> 16; }
 __device__ __forceinline__ int addmax(int a, int b, int c) { return __viaddmax_s32(a, b, c); }
 
 // Shared memory: the query's transitions, Qmax*32 uint4 (8 int16 per node:
-// BM|MM, IM|DM, MI|II, MD|DD), then per warp Qmax*32 uint2 of DP state
-// (M|I, D) in slot j*32 + lane.
-__global__ void __launch_bounds__(kVitThreads) viterbi_fast_kernel(VitParams p) {
+// BM|MM, IM|DM, MI|II, MD|DD), then per warp Qmax*32 words of M|I and
+// Qmax*32 int16 of D, slot j*32 + lane.
+__global__ void __launch_bounds__(kVitFastMaxThreads) viterbi_fast_kernel(VitParams p) {
   extern __shared__ __align__(16) uint4 fsm[];
   const int lane = threadIdx.x & 31;
   const int warp = threadIdx.x >> 5;
   const int Qmax = p.max_Mpad >> 5;
   uint4 *tr = fsm;
-  uint2 *st = reinterpret_cast<uint2 *>(fsm + (size_t)Qmax * 32) + (size_t)warp * Qmax * 32;
-  int16_t *st_d = reinterpret_cast<int16_t *>(st) + 2;       // D of slot s at st_d[4 s]
-  const int16_t *tr_dd = reinterpret_cast<const int16_t *>(tr) + 7;   // tDD of slot s at tr_dd[8 s]
+  uint32_t *sMI = reinterpret_cast<uint32_t *>(fsm + (size_t)Qmax * 32) + (size_t)warp * Qmax * 32 * 3 / 2;
+  int16_t *sD = reinterpret_cast<int16_t *>(sMI + (size_t)Qmax * 32);
 
   for (uint32_t qi = 0; qi < p.n_queries; ++qi) {
     const VitQuery Q = p.queries[qi];
@@ -240,11 +241,16 @@ __global__ void __launch_bounds__(kVitThreads) viterbi_fast_kernel(VitParams p) 
       const int len = (int)__ldg(p.seq_len + r);
       const uint32_t orig = __ldg(p.seq_orig + r);
 
-      const uint2 neg2 = make_uint2(0x80008000u, 0x8000u);
-      for (int j = 0; j < nq; ++j) st[j * 32 + lane] = neg2;
+      for (int j = 0; j < nq; ++j) {
+        sMI[j * 32 + lane] = 0x80008000u;
+        sD[j * 32 + lane] = (int16_t)kNeg;
+      }
       int xN = Q.base, xJ = kNeg, xC = kNeg;
       int xB = addmax(xN, tNB, kNeg);
-      int pM0 = kNeg, pI0 = kNeg, pD0 = kNeg;   // previous row, node before the segment
+      // Previous row: M, I and true D of the node before the segment, and the
+      // delete score carried into the segment (X0m + tDD of node 0 is its
+      // value at node 0; row 0 carries minus infinity).
+      int pM0 = kNeg, pI0 = kNeg, pD0 = kNeg, X0m = kNeg - tDD0;
       bool ovf = false;
       uint32_t word = 0;
       for (int i = 0; i < len; ++i) {
@@ -252,24 +258,32 @@ __global__ void __launch_bounds__(kVitThreads) viterbi_fast_kernel(VitParams p) 
         const int x = (int)((word >> (8 * (i & 3))) & 0xffu);
         const int16_t *erow = Q.msc + (size_t)x * nq * 32 + lane;
 
-        // Pass 1: M, I and the segment-local delete chain.
-        int dM = pM0, dI = pI0, dD = pD0, mprev = kNeg, d = kNeg, mx = kNeg;
+        // Sweep the segment: the previous row's delete chain is completed on
+        // the fly (D' = max(local D', carried chain)), then M, I and this
+        // row's segment-local delete chain.
+        int dM = pM0, dI = pI0, dD = pD0, X = X0m, mprev = kNeg, d = kNeg, mx = kNeg;
         int Mn = kNeg, In = kNeg;
 #pragma unroll 4
         for (int j = 0; j < nv; ++j) {
-          const uint2 s = st[j * 32 + lane];
-          const uint4 t = tr[j * 32 + lane];
+          const int sl = j * 32 + lane;
+          const uint32_t mi = sMI[sl];
+          const int Dl = sD[sl];
+          const uint4 t = tr[sl];
           const int e = __ldg(erow + j * 32);
-          const int Mo = lo16(s.x), Io = hi16(s.x), Do = lo16(s.y);
+          const int tDD = hi16(t.w);
+          const int Mo = lo16(mi), Io = hi16(mi);
+          X += tDD;
+          const int Do = max(Dl, X);
           int best = addmax(dM, hi16(t.x), kNeg);      // M' + tMM
           best = addmax(dI, lo16(t.y), best);           // I' + tIM
           best = addmax(dD, hi16(t.y), best);           // D' + tDM
           best = addmax(xB, lo16(t.x), best);           // xB + tBM
           Mn = addmax(best, e, kNeg);
           In = addmax(Io, hi16(t.z), addmax(Mo, lo16(t.z), kNeg));
-          d = addmax(d, hi16(t.w), addmax(mprev, lo16(t.w), kNeg));
+          d = addmax(d, tDD, addmax(mprev, lo16(t.w), kNeg));
           mx = max(mx, Mn);
-          st[j * 32 + lane] = make_uint2(__byte_perm((uint32_t)Mn, (uint32_t)In, 0x5410), (uint32_t)d);
+          sMI[sl] = __byte_perm((uint32_t)Mn, (uint32_t)In, 0x5410);
+          sD[sl] = (int16_t)d;
           dM = Mo;
           dI = Io;
           dD = Do;
@@ -281,7 +295,8 @@ __global__ void __launch_bounds__(kVitThreads) viterbi_fast_kernel(VitParams p) 
           break;
         }
 
-        // Delete score entering each segment: exclusive scan of the maps.
+        // True delete score at the end of every segment: inclusive scan of
+        // the segments' maps d -> max(A, d + B).
         int Mlp = __shfl_up_sync(kAll, Mn, 1);
         int Ilp = __shfl_up_sync(kAll, In, 1);
         if (lane == 0) Mlp = Ilp = kNeg;
@@ -290,25 +305,10 @@ __global__ void __launch_bounds__(kVitThreads) viterbi_fast_kernel(VitParams p) 
         for (int r = 0; r < 5; ++r) A = addmax(__shfl_up_sync(kAll, A, 1 << r), Wn[r], A);
         int carry = __shfl_up_sync(kAll, A, 1);
         if (lane == 0) carry = kNeg;
-
-        // Pass 2: raise the local chain while the carried score wins.
-        int X = max(carry + tDD0, Mlp + tMD0);
-        int Dlast = d;
-        for (int j = 0; j < nv; ++j) {
-          const int sl = j * 32 + lane;
-          if (X <= (int)st_d[4 * sl]) break;
-          st_d[4 * sl] = (int16_t)X;
-          if (j == nv - 1) {
-            Dlast = X;
-            break;
-          }
-          X += (int)tr_dd[8 * (sl + 32)];
-        }
-        int Dlp = __shfl_up_sync(kAll, Dlast, 1);
-        if (lane == 0) Dlp = kNeg;
         pM0 = Mlp;
         pI0 = Ilp;
-        pD0 = Dlp;
+        pD0 = carry;
+        X0m = max(carry + tDD0, Mlp + tMD0) - tDD0;
 
         xN = addmax(xN, tNN, kNeg);
         xC = addmax(xC, tCC, addmax(xE, tEC, kNeg));
@@ -335,31 +335,94 @@ __global__ void __launch_bounds__(kVitThreads) viterbi_fast_kernel(VitParams p) 
 }  // namespace
 
 size_t viterbi_fast_smem_bytes(int Mpad, int warps) {
-  return (size_t)(Mpad >> 5) * 32 * (16 + 8 * (size_t)warps);
+  return (size_t)(Mpad >> 5) * 32 * (16 + 6 * (size_t)warps);
 }
 
 size_t viterbi_smem_bytes(int Mpad) { return (size_t)(kVitThreads / 32) * 3 * (size_t)Mpad * sizeof(int16_t); }
 
-int launch_viterbi(const VitParams &p, bool fast, int max_smem, int num_sms, cudaStream_t st) {
-  if (p.n_queries == 0) return 0;
-  const void *fn = fast ? (const void *)viterbi_fast_kernel : (const void *)viterbi_kernel;
-  int warps = kVitThreads / 32;
-  size_t smem = viterbi_smem_bytes(p.max_Mpad);
-  if (fast) {
-    while (warps > 1 && viterbi_fast_smem_bytes(p.max_Mpad, warps) > (size_t)max_smem) --warps;
-    smem = viterbi_fast_smem_bytes(p.max_Mpad, warps);
+namespace {
+
+// Launch shape of the fast kernel: warps per block, resident blocks per SM
+// and the shared-memory carveout.  Each warp reads the match-score rows of
+// its residues from global memory, so the L1 left beside shared memory
+// should hold the rows of the codes the database uses (n_codes x Mpad x 2
+// bytes, at most 124 KB); among the carveouts that leave that much L1, take
+// the one that keeps the most warps resident.
+struct FastShape {
+  int warps = 1, blocks = 1;
+  size_t smem = 0;
+  int carve_pct = 100;
+};
+
+FastShape fast_shape(int Mpad, int n_codes, int max_smem_block) {
+  constexpr size_t kKB = 1024, kUnified = 256 * kKB, kCarveMax = 228 * kKB;
+  static int regs = 0;
+  if (!regs) {
+    cudaFuncAttributes a;
+    regs = cudaFuncGetAttributes(&a, (const void *)viterbi_fast_kernel) == cudaSuccess ? a.numRegs : 128;
   }
-  if (smem > (size_t)max_smem) return 2;
-  if (cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem) != cudaSuccess)
+  const int warp_regs = ((regs + 7) / 8) * 8 * 32;
+  const size_t ws = std::min((size_t)std::max(n_codes, 1) * 2 * (size_t)Mpad, 124 * kKB);
+  static const int carves_kb[] = {228, 196, 164, 132, 100};   // supported carveouts
+  FastShape best;
+  for (int c : carves_kb) {
+    const size_t C = (size_t)c * kKB;
+    if (kUnified - C < ws && c != 100) continue;
+    FastShape s;
+    s.warps = 0;
+    for (int w = kVitFastMaxThreads / 32; w >= 1; --w) {
+      const size_t sm = viterbi_fast_smem_bytes(Mpad, w);
+      if (sm > (size_t)max_smem_block || sm + kKB > C) continue;
+      int b = (int)(C / (sm + kKB));
+      b = std::min(b, 65536 / (warp_regs * w));
+      b = std::min(b, 64 / w);
+      if (b < 1) continue;
+      if (w * b > s.warps * s.blocks || (w * b == s.warps * s.blocks && b > s.blocks)) {
+        s.warps = w;
+        s.blocks = b;
+        s.smem = sm;
+      }
+    }
+    if (s.warps == 0) continue;
+    // The driver takes the smallest supported carveout at or above the
+    // preference: ask for just under C.
+    s.carve_pct = (int)std::min<size_t>(100, ((C - kKB) * 100) / kCarveMax);
+    return s;
+  }
+  best.warps = 0;
+  return best;
+}
+
+}  // namespace
+
+int viterbi_fast_shape_key(int Mpad, int n_codes, int max_smem) {
+  const FastShape s = fast_shape(Mpad, n_codes, max_smem);
+  return s.warps * 10000 + s.blocks * 100 + s.carve_pct;
+}
+
+int launch_viterbi(const VitParams &p, bool fast, int n_codes, int max_smem, int num_sms,
+                   cudaStream_t st) {
+  if (p.n_queries == 0) return 0;
+  if (!fast) {
+    const size_t smem = viterbi_smem_bytes(p.max_Mpad);
+    if (smem > (size_t)max_smem) return 2;
+    if (cudaFuncSetAttribute((const void *)viterbi_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                             (int)smem) != cudaSuccess)
+      return 1;
+    int per_sm = 0;
+    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, (const void *)viterbi_kernel, kVitThreads,
+                                                      smem) != cudaSuccess || per_sm < 1)
+      return 1;
+    viterbi_kernel<<<num_sms * per_sm, kVitThreads, smem, st>>>(p);
+    return cudaGetLastError() == cudaSuccess ? 0 : 1;
+  }
+  const FastShape s = fast_shape(p.max_Mpad, n_codes, max_smem);
+  if (s.warps == 0) return 2;
+  const void *fn = (const void *)viterbi_fast_kernel;
+  if (cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)s.smem) != cudaSuccess ||
+      cudaFuncSetAttribute(fn, cudaFuncAttributePreferredSharedMemoryCarveout, s.carve_pct) != cudaSuccess)
     return 1;
-  int per_sm = 0;
-  if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, fn, warps * 32, smem) != cudaSuccess ||
-      per_sm < 1)
-    return 1;
-  if (fast)
-    viterbi_fast_kernel<<<num_sms * per_sm, warps * 32, smem, st>>>(p);
-  else
-    viterbi_kernel<<<num_sms * per_sm, warps * 32, smem, st>>>(p);
+  viterbi_fast_kernel<<<num_sms * s.blocks, s.warps * 32, s.smem, st>>>(p);
   return cudaGetLastError() == cudaSuccess ? 0 : 1;
 }
 
