@@ -187,16 +187,17 @@ __device__ __forceinline__ int hi16(uint32_t w) { return ((int)w) >> 16; }
 __device__ __forceinline__ int addmax(int a, int b, int c) { return __viaddmax_s32(a, b, c); }
 
 // Shared memory: the query's transitions, Qmax*32 uint4 (8 int16 per node:
-// BM|MM, IM|DM, MI|II, MD|DD), then per warp Qmax*32 words of M|I and
-// Qmax*32 int16 of D, slot j*32 + lane.
+// BM|MM, IM|DM, MI|II, MD|DD), then per warp three arrays of Qmax*32 int16
+// (M, I, D), slot j*32 + lane (sign-extending 16-bit loads, no unpacking).
 __global__ void __launch_bounds__(kVitFastMaxThreads) viterbi_fast_kernel(VitParams p) {
   extern __shared__ __align__(16) uint4 fsm[];
   const int lane = threadIdx.x & 31;
   const int warp = threadIdx.x >> 5;
   const int Qmax = p.max_Mpad >> 5;
   uint4 *tr = fsm;
-  uint32_t *sMI = reinterpret_cast<uint32_t *>(fsm + (size_t)Qmax * 32) + (size_t)warp * Qmax * 32 * 3 / 2;
-  int16_t *sD = reinterpret_cast<int16_t *>(sMI + (size_t)Qmax * 32);
+  int16_t *sM = reinterpret_cast<int16_t *>(fsm + (size_t)Qmax * 32) + (size_t)warp * Qmax * 32 * 3;
+  int16_t *sI = sM + (size_t)Qmax * 32;
+  int16_t *sD = sI + (size_t)Qmax * 32;
 
   for (uint32_t qi = 0; qi < p.n_queries; ++qi) {
     const VitQuery Q = p.queries[qi];
@@ -241,10 +242,7 @@ __global__ void __launch_bounds__(kVitFastMaxThreads) viterbi_fast_kernel(VitPar
       const int len = (int)__ldg(p.seq_len + r);
       const uint32_t orig = __ldg(p.seq_orig + r);
 
-      for (int j = 0; j < nq; ++j) {
-        sMI[j * 32 + lane] = 0x80008000u;
-        sD[j * 32 + lane] = (int16_t)kNeg;
-      }
+      for (int j = 0; j < nq; ++j) sM[j * 32 + lane] = sI[j * 32 + lane] = sD[j * 32 + lane] = (int16_t)kNeg;
       int xN = Q.base, xJ = kNeg, xC = kNeg;
       int xB = addmax(xN, tNB, kNeg);
       // Previous row: M, I and true D of the node before the segment, and the
@@ -266,12 +264,10 @@ __global__ void __launch_bounds__(kVitFastMaxThreads) viterbi_fast_kernel(VitPar
 #pragma unroll 4
         for (int j = 0; j < nv; ++j) {
           const int sl = j * 32 + lane;
-          const uint32_t mi = sMI[sl];
-          const int Dl = sD[sl];
+          const int Mo = sM[sl], Io = sI[sl], Dl = sD[sl];
           const uint4 t = tr[sl];
           const int e = __ldg(erow + j * 32);
           const int tDD = hi16(t.w);
-          const int Mo = lo16(mi), Io = hi16(mi);
           X += tDD;
           const int Do = max(Dl, X);
           int best = addmax(dM, hi16(t.x), kNeg);      // M' + tMM
@@ -282,7 +278,8 @@ __global__ void __launch_bounds__(kVitFastMaxThreads) viterbi_fast_kernel(VitPar
           In = addmax(Io, hi16(t.z), addmax(Mo, lo16(t.z), kNeg));
           d = addmax(d, tDD, addmax(mprev, lo16(t.w), kNeg));
           mx = max(mx, Mn);
-          sMI[sl] = __byte_perm((uint32_t)Mn, (uint32_t)In, 0x5410);
+          sM[sl] = (int16_t)Mn;
+          sI[sl] = (int16_t)In;
           sD[sl] = (int16_t)d;
           dM = Mo;
           dI = Io;
