@@ -398,6 +398,12 @@ def run_mpf(args):
     if args.pipeline and args.viterbi:
         vit = run_viterbi_stage(args, ctx, db, wl, profs, p_msv, thr, run_pipe, time_steps, clocks, dev)
 
+    # Models longer than the striped kernels hold (§8(f)-3): one query of
+    # args.long_m nodes against the whole database, both filters.
+    long_model = None
+    if args.long_m and world == 1:
+        long_model = run_long_model(args, ctx, db, wl, time_steps, clocks, dev)
+
     # Serving: continuous batching of arriving queries (model lengths drawn as
     # in the serving workload) against the resident database, per offered load.
     serving = None
@@ -432,6 +438,7 @@ def run_mpf(args):
                             "host buffers + mpf_profile_destroy; database resident"},
             "pipeline": pipe,
             "viterbi": vit,
+            "long_model": long_model,
             "serving": serving,
             "gpu_launches": launches_per_step * args.steps,
             "clocks": clocks,
@@ -488,6 +495,33 @@ def run_viterbi_stage(args, ctx, db, wl, profs, p_msv, thr, run_pipe, time_steps
                          "timed": "mpf_viterbi_rescore per step (3 selection kernels + 1 Viterbi kernel)",
                          "peak_basis": f"{nsm} SMs x {INT_LANES_PER_SM_CLK} DPX lanes/clk / "
                                        f"{VIT_OPS_PER_CELL} ops per cell x {sm_mhz:.0f} MHz"}}
+
+
+def run_long_model(args, ctx, db, wl, time_steps, clocks, dev):
+    import torch
+    from paper_1707_09683_gb300 import mpf, synth
+    rec = synth.make_profile(args.long_m, np.random.default_rng(900))
+    prof = mpf.Profile(ctx, rec)
+    n, res = db.n_seqs, db.n_residues
+    outs = (torch.empty(n, dtype=torch.uint8, device=dev), torch.empty(n, dtype=torch.uint8, device=dev),
+            torch.empty(n, dtype=torch.float32, device=dev))
+    nsm = torch.cuda.get_device_properties(dev).multi_processor_count
+    sm_mhz = clocks.get("sm_mhz") or 2070.0
+    out = {"M": args.long_m, "config": list(prof.get_config(mpf.MSV)), "n_seqs": n,
+           "cells_per_launch": args.long_m * res, "kernel": "long_kernel (lane segments, costs from HBM/L2)"}
+    steps = max(1, min(args.steps, 3))
+    for name, code in (("msv", mpf.MSV), ("ssv", mpf.SSV)):
+        pl = mpf.Plan(ctx, code, [prof], db, *outs)
+        pl.launch()
+        ms = time_steps(pl.launch, steps)
+        pl.close()
+        g = args.long_m * res / (ms * 1e-3) / 1e9
+        peak = nsm * INT_LANES_PER_SM_CLK * CELLS_PER_LANE_OP / OPS_PER_CELL[name] * sm_mhz * 1e6 / 1e9
+        out[name] = {"gcups": g, "ms_per_launch": ms, "roofline_frac": g / peak, "peak": peak}
+        log(f"long model M={args.long_m}: {name} {g:.1f} GCUPS ({ms:.1f} ms per launch)")
+    prof.close()
+    out["roofline_basis"] = "integer-SIMD roofline of the striped kernels (same formula as roofline.peak)"
+    return out
 
 
 def run_serving(db_record, rates, n_requests, device, seed=3):
@@ -587,6 +621,8 @@ def main():
     ap.add_argument("--no-serve", action="store_true")
     ap.add_argument("--no-pipeline", dest="pipeline", action="store_false")
     ap.add_argument("--no-viterbi", dest="viterbi", action="store_false")
+    ap.add_argument("--long-m", type=int, default=5000,
+                    help="model length of the long-model measurement (0: skip)")
     ap.add_argument("--serve-rates", type=float, nargs="+", default=[10, 50, 100, 200, 500])
     ap.add_argument("--serve-requests", type=int, default=24)
     ap.add_argument("--profile-case", action="store_true")

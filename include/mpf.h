@@ -68,8 +68,16 @@ enum {
 
 enum { MPF_MSV = 0, MPF_SSV = 1 };
 
-/* Largest model length M a profile may have (set by shared memory per SM). */
+/* Largest model length M a byte-filter profile may have (100,000). */
 int mpf_max_model_length(void);
+
+/* Largest model length the striped shared-memory scan kernels hold (3,072).
+ * Longer byte-filter profiles are scored by the long-model kernel: one warp
+ * per sequence, each lane a contiguous segment of nodes, the cost bytes read
+ * from device memory (the paper's tables end at M = 2405; models beyond the
+ * on-chip table are the large-model case of its Sec. 6).  It is also the
+ * largest Viterbi profile. */
+int mpf_max_striped_length(void);
 
 /* Message for a status code (static string, never NULL). */
 const char *mpf_strerror(int status);
@@ -104,7 +112,9 @@ int mpf_sync(mpf_ctx *ctx);
  *           L is tjb_by_len[min(L, n_tjb - 1)] (Alg. 2 derives the begin score
  *           of each sequence from its length)
  *   scale_b: units per nat of the nat score (finite, > 0)
- * The profile keeps copies of cost and tjb_by_len.
+ * The profile keeps copies of cost and tjb_by_len.  Results are the same
+ * exact recurrences whichever kernel runs (striped up to
+ * mpf_max_striped_length(), long-model above).
  * Errors: MPF_EINVAL, MPF_EUNSUPPORTED (M too large), MPF_ENOMEM, MPF_ECUDA.
  */
 int mpf_profile_create(mpf_ctx *ctx, int M, int K, const uint8_t *cost, uint8_t bias_b,
@@ -118,8 +128,10 @@ void mpf_profile_destroy(mpf_profile *prof);
  * words of two 16-bit cells (4 <= words <= 48, multiple of 4), so the striped
  * model holds 2 * lanes * words >= M cells (Sec. 3.1: S = 32 / lanes
  * sequences per warp, W = 2 * lanes cells per row step, H = words).
- * set: MPF_EINVAL if the pair is not built or does not cover M.
- * get: writes the pair the next scan will use (tuned default if never set).
+ * set: MPF_EINVAL if the pair is not built or does not cover M, or if the
+ *      profile is longer than mpf_max_striped_length() (one configuration).
+ * get: writes the pair the next scan will use (tuned default if never set);
+ *      lanes 32, words 0 for the long-model kernel.
  */
 int mpf_profile_set_config(mpf_profile *prof, int filter, int lanes, int words);
 int mpf_profile_get_config(const mpf_profile *prof, int filter, int *lanes, int *words);
@@ -253,7 +265,7 @@ typedef struct mpf_vprofile mpf_vprofile;
 
 /*
  * Create a Viterbi profile.  Host inputs, copied.
- *   M: 1 <= M <= mpf_max_model_length(); K: 1 <= K <= 32 residue codes
+ *   M: 1 <= M <= mpf_max_striped_length(); K: 1 <= K <= 32 residue codes
  *   msc: K*M int16, row-major [x][k-1] match scores; codes K..31 score -32768
  *   trans: 8*M int16, rows BM, MM, IM, DM, MI, II, MD, DD, column k-1 holds
  *          the transition into (BM, MM, IM, DM: M_k; MD, DD: D_k) or out of
@@ -310,7 +322,8 @@ int mpf_viterbi_rescore(mpf_ctx *ctx, const mpf_vprofile *const *vprofs, int n_q
  *   Asynchronous on the context stream, like a scan into device outputs.
  *   A profile whose table image for the chosen kernel configuration exceeds
  *     224 KiB is rejected with MPF_EUNSUPPORTED (none of the built
- *     configurations does; the largest needs 202,832 bytes).
+ *     configurations does; the largest needs 202,832 bytes), and so is a
+ *     profile longer than mpf_max_striped_length().
  *   The first call on a device looks up the array's device address (once per
  *     device, with that device current); make that first call before any
  *     stream capture.

@@ -72,6 +72,7 @@ struct mpf_profile {
   int tjb_min = 0;
   int cfg_lanes[2] = {0, 0}, cfg_words[2] = {0, 0};
   int arith[2] = {MPF_ARITH_AUTO, MPF_ARITH_AUTO};
+  int seg_words = 0;            // > 0: longer than the striped kernels hold (long-model kernel)
   mutable std::map<std::tuple<int, int, int>, DevTable> tables;
   mutable std::mutex mu;
 };
@@ -240,6 +241,43 @@ int get_table(const mpf_profile *p, int lanes, int words, int fmt, DevTable *out
   return MPF_OK;
 }
 
+// Device copy of a long profile's cost bytes in the long-model kernel's order:
+// residue row x, word w of lane l at (x * seg_words + w) * 32 + l, four nodes
+// (l * 4 * seg_words + 4w .. +3) per word; codes >= K and nodes past M cost 255.
+int get_long_table(const mpf_profile *p, const uint8_t **out) {
+  std::lock_guard<std::mutex> lk(p->mu);
+  auto key = std::make_tuple(32, 0, 2);
+  auto it = p->tables.find(key);
+  if (it != p->tables.end()) {
+    *out = reinterpret_cast<const uint8_t *>(it->second.ptr);
+    return MPF_OK;
+  }
+  const int sw = p->seg_words, Q = 4 * sw, M = p->M;
+  const size_t row = (size_t)sw * 32 * 4;
+  std::vector<uint8_t> img(32 * row, 255);
+  for (int x = 0; x < p->K; ++x)
+    for (int k = 0; k < M; ++k) {
+      const int l = k / Q, j = k % Q;
+      img[(size_t)x * row + ((size_t)(j / 4) * 32 + l) * 4 + (j % 4)] = p->cost[(size_t)x * M + k];
+    }
+  mpf_ctx *ctx = p->ctx;
+  DeviceGuard dg(ctx->device);
+  uint4 *d = nullptr;
+  MPF_CUDA(cudaMallocAsync((void **)&d, img.size(), ctx->util));
+  cudaError_t e = cudaMemcpyAsync(d, img.data(), img.size(), cudaMemcpyHostToDevice, ctx->util);
+  if (e == cudaSuccess) e = cudaStreamSynchronize(ctx->util);
+  if (e != cudaSuccess) {
+    (void)cudaGetLastError();
+    cudaFreeAsync(d, ctx->util);
+    return MPF_ECUDA;
+  }
+  DevTable t;
+  t.ptr = d;
+  p->tables[key] = t;
+  *out = reinterpret_cast<const uint8_t *>(d);
+  return MPF_OK;
+}
+
 int ensure_out_scratch(mpf_ctx *ctx, size_t bytes) {
   if (ctx->d_out_bytes >= bytes) return MPF_OK;
   if (ctx->d_out) {
@@ -256,6 +294,7 @@ int ensure_out_scratch(mpf_ctx *ctx, size_t bytes) {
 // Kernel mode of a profile for a filter.  Automatic arithmetic: fp16 cells
 // (FMA pipe) for both filters.
 int kernel_mode(const mpf_profile *p, int filter) {
+  if (p->seg_words) return filter == MPF_MSV ? MODE_LONG_MSV : MODE_LONG_SSV;
   const bool f16 = p->arith[filter] != MPF_ARITH_I16;
   if (filter == MPF_SSV) return f16 ? MODE_SSV_F16 : MODE_SSV;
   if (!msv_fast_ok(p)) return MODE_MSV_DIRECT;
@@ -271,6 +310,9 @@ struct LaunchGroup {
   int lanes = 0, words = 0, mode = 0;
   uint32_t smem = 0;
   int grid = 0;
+  int threads = kBlockThreads;
+  uint32_t long_words = 0;       // long-model kernel: largest seg_words of the group
+  int n_codes = 32;              // distinct residue codes of the database
   uint32_t n_shards = 0;
   QueryDesc *d_queries = nullptr;
   uint32_t n_queries = 0;
@@ -310,6 +352,58 @@ int free_pending(mpf_ctx *ctx) {
 }
 
 int configure_kernel(mpf_ctx *ctx, LaunchGroup *g) {
+  if (g->mode == MODE_LONG_MSV || g->mode == MODE_LONG_SSV) {
+    // Each warp reads the cost rows of its residues from device memory, so
+    // when the rows of the codes the database uses (n_codes x 128 x
+    // seg_words bytes) fit in the L1 of the smallest carveout (156 KB, with
+    // margin: 124 KB), take among the shared-memory carveouts that leave that
+    // much L1 the one that keeps the most warps resident; when they cannot
+    // fit, just keep the most warps resident (blocks of up to
+    // kLongThreads / 32 warps).
+    // The DP row is kept as 16-bit pairs unless that leaves fewer than four
+    // warps per SM; then as bytes (half the shared memory per warp).
+    const bool bytes = 4 * long_smem_per_warp((int)g->long_words, false) > 228 * 1024;
+    g->fn = long_kernel_for(g->mode, bytes);
+    const size_t per_warp = long_smem_per_warp((int)g->long_words, bytes);
+    constexpr size_t kKB = 1024;
+    size_t ws = (size_t)std::max(g->n_codes, 1) * 128 * g->long_words;
+    if (ws > 124 * kKB) ws = 0;
+    static const int carves_kb[] = {228, 196, 164, 132, 100};
+    int best_w = 0, best_b = 0, carve = 0;
+    for (int c : carves_kb) {
+      const size_t C = (size_t)c * kKB;
+      if (256 * kKB - C < ws) continue;
+      for (int w = kLongThreads / 32; w >= 1; --w) {
+        const size_t sm = per_warp * (size_t)w;
+        if (sm > (size_t)ctx->max_smem || sm + kKB > C) continue;
+        const int b = std::min((int)(C / (sm + kKB)), 64 / w);
+        if (w * b > best_w * best_b) {
+          best_w = w;
+          best_b = b;
+        }
+      }
+      if (best_w) {
+        carve = c;
+        break;
+      }
+    }
+    if (!best_w) return MPF_EUNSUPPORTED;
+    g->threads = best_w * 32;
+    g->smem = (uint32_t)(per_warp * (size_t)best_w);
+    MPF_CUDA(cudaFuncSetAttribute((const void *)g->fn, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                  (int)g->smem));
+    // The driver takes the smallest supported carveout at or above the
+    // preference: ask for just under the chosen one.
+    MPF_CUDA(cudaFuncSetAttribute((const void *)g->fn, cudaFuncAttributePreferredSharedMemoryCarveout,
+                                  (int)std::min<size_t>(100, (((size_t)carve - 1) * 100) / 228)));
+    int per_sm = 0;
+    MPF_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, (const void *)g->fn, g->threads,
+                                                           g->smem));
+    if (per_sm < 1) return MPF_EUNSUPPORTED;
+    g->grid = ctx->num_sms * std::min(per_sm, best_b);
+    g->n_shards = (uint32_t)g->grid;
+    return MPF_OK;
+  }
   g->fn = kernel_for(g->lanes, g->words, g->mode);
   if (!g->fn) return MPF_EINVAL;
   g->smem = (uint32_t)smem_need(g->lanes, g->words);
@@ -345,27 +439,42 @@ int plan_create(mpf_ctx *ctx, int filter, const mpf_profile *const *profs, int n
       return MPF_EINVAL;
     }
     const int mode = kernel_mode(p, filter);
-    int lanes = p->cfg_lanes[filter], words = p->cfg_words[filter];
-    if (!lanes) default_config(ctx, p->M, mode, &lanes, &words);
-    if (!lanes || !kernel_for(lanes, words, mode)) {
-      plan_free(pl);
-      return MPF_EUNSUPPORTED;
-    }
-    DevTable t;
-    int rc = get_table(p, lanes, words, table_format(mode), &t);
-    if (rc) {
-      plan_free(pl);
-      return rc;
-    }
     QueryDesc q;
     memset(&q, 0, sizeof(q));
-    q.table = t.ptr;
-    q.table_bytes = t.geom.table_bytes;
-    q.row_bytes = t.geom.row_bytes;
-    q.copy_bytes = t.geom.copy_bytes;
-    q.smax_off = t.geom.smax_off;
-    q.tail_off = t.geom.tail_off;
-    q.tail_row_bytes = t.geom.tail_row_bytes;
+    int lanes = 32, words = 0;
+    if (p->seg_words) {
+      const uint8_t *lt = nullptr;
+      int rc = get_long_table(p, &lt);
+      if (rc) {
+        plan_free(pl);
+        return rc;
+      }
+      q.table = reinterpret_cast<const uint4 *>(lt);
+      q.M = (uint32_t)p->M;
+      q.seg_words = (uint32_t)p->seg_words;
+    } else {
+      lanes = p->cfg_lanes[filter];
+      words = p->cfg_words[filter];
+      if (!lanes) default_config(ctx, p->M, mode, &lanes, &words);
+      if (!lanes || !kernel_for(lanes, words, mode)) {
+        plan_free(pl);
+        return MPF_EUNSUPPORTED;
+      }
+      DevTable t;
+      int rc = get_table(p, lanes, words, table_format(mode), &t);
+      if (rc) {
+        plan_free(pl);
+        return rc;
+      }
+      q.table = t.ptr;
+      q.table_bytes = t.geom.table_bytes;
+      q.row_bytes = t.geom.row_bytes;
+      q.copy_bytes = t.geom.copy_bytes;
+      q.smax_off = t.geom.smax_off;
+      q.tail_off = t.geom.tail_off;
+      q.tail_row_bytes = t.geom.tail_row_bytes;
+      q.M = (uint32_t)p->M;
+    }
     q.bias = p->bias;
     q.tbm = p->tbm;
     q.tec = p->tec;
@@ -388,6 +497,8 @@ int plan_create(mpf_ctx *ctx, int filter, const mpf_profile *const *profs, int n
     g.lanes = std::get<0>(kv.first);
     g.words = std::get<1>(kv.first);
     g.mode = std::get<2>(kv.first);
+    for (const QueryDesc &qd : kv.second) g.long_words = std::max(g.long_words, qd.seg_words);
+    g.n_codes = db->n_codes;
     int rc = configure_kernel(ctx, &g);
     if (rc) {
       plan_free(pl);
@@ -445,8 +556,9 @@ int enqueue_group(const mpf_db *db, mpf_ctx *ctx, LaunchGroup &g, cudaStream_t s
   sp.n_shards = g.n_shards;
   sp.item_counter = g.d_counter;
   sp.status = ctx->d_status;
+  sp.long_words = g.long_words;
   const int grid = (int)std::min<uint64_t>((uint64_t)g.grid, (uint64_t)g.n_queries * g.n_shards);
-  g.fn<<<grid, kBlockThreads, g.smem, st>>>(sp);
+  g.fn<<<grid, g.threads, g.smem, st>>>(sp);
   MPF_CUDA(cudaGetLastError());
   return MPF_OK;
 }
@@ -530,7 +642,9 @@ int run_scan(mpf_ctx *ctx, int filter, const mpf_profile *const *profs, int n_q,
 
 extern "C" {
 
-int mpf_max_model_length(void) { return 2 * 32 * kMaxWords; }
+int mpf_max_model_length(void) { return kMaxLongM; }
+
+int mpf_max_striped_length(void) { return kStripedMaxM; }
 
 const char *mpf_strerror(int status) {
   switch (status) {
@@ -649,6 +763,17 @@ int mpf_profile_create(mpf_ctx *ctx, int M, int K, const uint8_t *cost, uint8_t 
     }
     p->n_tjb = n_tjb;
   }
+  if (M > kStripedMaxM) {
+    // Longer than the striped table holds: the long-model kernel, lane
+    // segments of 4 * seg_words nodes, one warp's DP row in shared memory.
+    p->seg_words = ((M + 31) / 32 + 3) / 4;
+    if (long_smem_per_warp(p->seg_words, true) > (size_t)ctx->max_smem) {
+      mpf_profile_destroy(p);
+      return MPF_EUNSUPPORTED;
+    }
+    *out = p;
+    return MPF_OK;
+  }
   int lanes = 0, words = 0;
   default_config(ctx, M, kernel_mode(p, MPF_MSV), &lanes, &words);
   if (!lanes) {
@@ -675,6 +800,7 @@ int mpf_profile_set_config(mpf_profile *p, int filter, int lanes, int words) {
     p->cfg_lanes[filter] = p->cfg_words[filter] = 0;
     return MPF_OK;
   }
+  if (p->seg_words) return MPF_EINVAL;   // long models have one configuration
   if (!words_built(words) || !kernel_for(lanes, words, kernel_mode(p, filter))) return MPF_EINVAL;
   if (2 * lanes * words < p->M) return MPF_EINVAL;
   if (smem_need(lanes, words) > p->ctx->max_smem) return MPF_EUNSUPPORTED;
@@ -696,7 +822,10 @@ int mpf_profile_set_arith(mpf_profile *p, int filter, int arith) {
 
 int mpf_profile_get_config(const mpf_profile *p, int filter, int *lanes, int *words) {
   if (!p || !lanes || !words || (filter != MPF_MSV && filter != MPF_SSV)) return MPF_EINVAL;
-  if (p->cfg_lanes[filter]) {
+  if (p->seg_words) {
+    *lanes = 32;
+    *words = 0;
+  } else if (p->cfg_lanes[filter]) {
     *lanes = p->cfg_lanes[filter];
     *words = p->cfg_words[filter];
   } else {
@@ -961,6 +1090,7 @@ extern "C" int mpf_scan_noalloc(mpf_ctx *ctx, int filter, const mpf_profile *pro
     return MPF_EINVAL;
   if (db->n_seqs == 0) return MPF_OK;
 
+  if (prof->seg_words) return MPF_EUNSUPPORTED;   // long models need the table in device memory
   const int mode = kernel_mode(prof, filter);
   int lanes = prof->cfg_lanes[filter], words = prof->cfg_words[filter];
   if (!lanes) default_config(ctx, prof->M, mode, &lanes, &words);
@@ -1182,7 +1312,7 @@ int mpf_vit_profile_create(mpf_ctx *ctx, int M, int K, const int16_t *msc, const
   *out = nullptr;
   if (!ctx || !msc || !trans || !special || M < 1 || K < 1 || K > kVitRows) return MPF_EINVAL;
   if (base < -32768 || base > 32767 || !isfinite(scale) || !(scale > 0.f)) return MPF_EINVAL;
-  if (M > mpf_max_model_length()) return MPF_EUNSUPPORTED;
+  if (M > kStripedMaxM) return MPF_EUNSUPPORTED;
   const int Mpad = (M + 31) & ~31, Q = Mpad / 32;
   bool fast = true;
   for (size_t i = 0; i < (size_t)kVitTrans * M; ++i) fast = fast && trans[i] <= 0;

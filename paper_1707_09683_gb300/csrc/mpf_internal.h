@@ -13,6 +13,9 @@ constexpr int kTableRows = 33;           // codes 0..31 plus padding
 constexpr int kNegInf = -16384;          // score of padding rows and nodes > M
 constexpr int kBlockThreads = 512;
 constexpr int kMaxWords = 48;
+constexpr int kStripedMaxM = 2 * 32 * kMaxWords;   // longest model of the striped kernels
+constexpr int kMaxLongM = 100000;                  // longest model of the long-model kernel
+constexpr int kLongThreads = 256;
 
 enum Mode : int {
   MODE_SSV = 0,           // Alg. 7, 16-bit integer cells (DPX)
@@ -20,8 +23,10 @@ enum Mode : int {
   MODE_MSV_DIRECT = 2,    // Alg. 2, J/B update after every row
   MODE_SSV_F16 = 3,       // MODE_SSV with cells as fp16 integers (FMA pipe)
   MODE_MSV_FAST_F16 = 4,  // MODE_MSV_FAST with cells as fp16 integers
+  MODE_LONG_MSV = 5,      // models beyond kStripedMaxM: long_kernel<MSV>
+  MODE_LONG_SSV = 6,      // long_kernel<SSV>
 };
-constexpr int kNumModes = 5;
+constexpr int kNumModes = 5;   // modes of the striped scan kernel
 
 // Score-table formats: signed 16-bit integers, or the same integers as fp16.
 enum TableFormat : int { TABLE_I16 = 0, TABLE_F16 = 1 };
@@ -42,7 +47,8 @@ struct QueryDesc {
   float scale;
   const uint8_t *tjb;     // per-length tjb (nullable)
   uint32_t n_tjb;
-  uint32_t pad0;
+  uint32_t M;             // model length (long-model kernel)
+  uint32_t seg_words;     // long-model kernel: cost words (4 nodes) per lane segment
   uint8_t *raw;           // outputs indexed by original sequence number
   uint8_t *flag;
   float *nat;             // nullable
@@ -64,9 +70,15 @@ struct ScanParams {
   uint32_t n_shards;          // work item i = (query i / n_shards, shard i % n_shards)
   uint32_t *item_counter;     // zero before the launch
   int *status;                // nonzero: error reported by a kernel
+  uint32_t long_words;        // long-model kernel: largest seg_words of its queries
 };
 
 typedef void (*KernelFn)(ScanParams);
+
+// Long-model kernel (mpf_long_kernel.cu): MODE_LONG_MSV or MODE_LONG_SSV,
+// DP row as 16-bit pairs or (bytes) as bytes.
+KernelFn long_kernel_for(int mode, bool bytes);
+size_t long_smem_per_warp(int seg_words, bool bytes);
 
 // Stage-to-stage hand-off (mpf_pipeline.cu): SSV -> MSV (raw_bytes 1) and
 // MSV -> Viterbi (raw_bytes 2).

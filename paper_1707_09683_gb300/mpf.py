@@ -49,6 +49,7 @@ def load(path: str = LIB_PATH):
     i32, u32, u64 = ctypes.c_int, ctypes.c_uint32, ctypes.c_uint64
     sig = {
         "mpf_max_model_length": (i32, []),
+        "mpf_max_striped_length": (i32, []),
         "mpf_strerror": (ctypes.c_char_p, [i32]),
         "mpf_ctx_create": (i32, [i32, vp, ctypes.POINTER(vp)]),
         "mpf_ctx_destroy": (None, [vp]),
@@ -121,16 +122,31 @@ def max_model_length() -> int:
     return int(load().mpf_max_model_length())
 
 
+def max_striped_length() -> int:
+    return int(load().mpf_max_striped_length())
+
+
+# Handles a context owns, destroyed in this order before the context itself.
+_CHILD_ORDER = ("mpf_plan_destroy", "mpf_vit_profile_destroy", "mpf_profile_destroy",
+                "mpf_db_destroy")
+
+
 class Context:
     """``mpf_ctx``: a device and the stream the library launches on.
 
     Without an explicit ``stream`` the context launches on a new
     ``torch.cuda.Stream`` that this object keeps alive, so torch (its events,
     its pinned-memory bookkeeping) never sees a stream the library destroyed.
+
+    The context records the handles created in it (profiles, databases,
+    plans); closing it destroys the ones still live first, so the C rule
+    "destroy children before their context" holds whatever order Python
+    finalises objects in (reference cycles, interpreter exit).
     """
 
     def __init__(self, device: int = 0, stream=None):
         lib = load()
+        self._live = {}
         self._torch_stream = None
         if stream is None:
             import torch
@@ -159,9 +175,22 @@ class Context:
     def sync(self):
         _check(load().mpf_sync(self.handle), "mpf_sync")
 
+    def _own(self, handle, destroy: str):
+        self._live[int(handle.value)] = destroy
+
+    def _release(self, handle) -> bool:
+        """True if ``handle`` was still live (the caller destroys it now)."""
+        return self._live.pop(int(handle.value), None) is not None
+
     def close(self):
         if getattr(self, "handle", None):
-            load().mpf_ctx_destroy(self.handle)
+            lib = load()
+            live = getattr(self, "_live", {})
+            for fn in _CHILD_ORDER:
+                for h in [h for h, d in live.items() if d == fn]:
+                    del live[h]
+                    getattr(lib, fn)(ctypes.c_void_p(h))
+            lib.mpf_ctx_destroy(self.handle)
             self.handle = None
 
     def __del__(self):
@@ -191,6 +220,7 @@ class Profile:
         self.handle = h
         self.ctx = ctx
         self.M = int(M)
+        ctx._own(h, "mpf_profile_destroy")
 
     def set_config(self, filter: int, lanes: int, words: int):
         _check(load().mpf_profile_set_config(self.handle, int(filter), int(lanes), int(words)),
@@ -208,7 +238,8 @@ class Profile:
 
     def close(self):
         if getattr(self, "handle", None):
-            load().mpf_profile_destroy(self.handle)
+            if self.ctx._release(self.handle):
+                load().mpf_profile_destroy(self.handle)
             self.handle = None
 
     def __del__(self):
@@ -235,6 +266,7 @@ class Database:
                                  ctypes.byref(h)), "mpf_db_upload")
         self.handle = h
         self.ctx = ctx
+        ctx._own(h, "mpf_db_destroy")
 
     @property
     def n_seqs(self) -> int:
@@ -246,7 +278,8 @@ class Database:
 
     def close(self):
         if getattr(self, "handle", None):
-            load().mpf_db_destroy(self.handle)
+            if self.ctx._release(self.handle):
+                load().mpf_db_destroy(self.handle)
             self.handle = None
 
     def __del__(self):
@@ -297,6 +330,7 @@ class Plan:
                "mpf_plan_create")
         self.handle = h
         self.ctx = ctx
+        ctx._own(h, "mpf_plan_destroy")
 
     def launch(self):
         _check(load().mpf_plan_launch(self.handle), "mpf_plan_launch")
@@ -310,7 +344,8 @@ class Plan:
 
     def close(self):
         if getattr(self, "handle", None):
-            load().mpf_plan_destroy(self.handle)
+            if self.ctx._release(self.handle):
+                load().mpf_plan_destroy(self.handle)
             self.handle = None
 
     def __del__(self):
@@ -366,10 +401,12 @@ class VitProfile:
         self.handle = h
         self.ctx = ctx
         self.M = int(M)
+        ctx._own(h, "mpf_vit_profile_destroy")
 
     def close(self):
         if getattr(self, "handle", None):
-            load().mpf_vit_profile_destroy(self.handle)
+            if self.ctx._release(self.handle):
+                load().mpf_vit_profile_destroy(self.handle)
             self.handle = None
 
     def __del__(self):

@@ -49,7 +49,8 @@ def test_status_strings_and_limits(lib):
     assert mpf.strerror(mpf.MPF_OK) == "ok"
     assert mpf.strerror(mpf.MPF_EINVAL) == "invalid argument"
     assert mpf.strerror(99) == "unknown status"
-    assert mpf.max_model_length() == 3072
+    assert mpf.max_model_length() == 100000
+    assert mpf.max_striped_length() == 3072
 
 
 def test_null_arguments_are_rejected_without_a_device(lib):

@@ -84,7 +84,7 @@ def test_long_model(ctx):
 def test_largest_model(ctx):
     rng = np.random.default_rng(8)
     db = synth.random_database(40, 300, rng, alphabet=20)
-    _run(ctx, [synth.make_vit_profile(mpf.max_model_length(), rng)], db)
+    _run(ctx, [synth.make_vit_profile(mpf.max_striped_length(), rng)], db)
 
 
 @pytest.mark.parametrize("seed", range(6))
