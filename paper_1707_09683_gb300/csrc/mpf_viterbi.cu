@@ -186,18 +186,51 @@ __device__ __forceinline__ int hi16(uint32_t w) { return ((int)w) >> 16; }
 // max(a + b, c), one DPX instruction.
 __device__ __forceinline__ int addmax(int a, int b, int c) { return __viaddmax_s32(a, b, c); }
 
+// One node of a lane's sweep (fast kernel): the previous row's M, I and
+// segment-local D of this node arrive in Mo, Io, Dl; the node's new M, I and
+// local D leave in Mn, In, d.  dM, dI, dD hold the previous row's values of
+// the node before (true D), X the carried delete chain, mprev this row's M of
+// the node before.
+struct FastCell {
+  int dM, dI, dD, X, mprev, d, mx, Mn, In;
+  __device__ __forceinline__ void step(const uint4 t, int e, int Mo, int Io, int Dl, int xB) {
+    const int tDD = hi16(t.w);
+    X += tDD;
+    const int Do = max(Dl, X);
+    int best = addmax(dM, hi16(t.x), kNeg);      // M' + tMM
+    best = addmax(dI, lo16(t.y), best);           // I' + tIM
+    best = addmax(dD, hi16(t.y), best);           // D' + tDM
+    best = addmax(xB, lo16(t.x), best);           // xB + tBM
+    Mn = addmax(best, e, kNeg);
+    In = addmax(Io, hi16(t.z), addmax(Mo, lo16(t.z), kNeg));
+    d = addmax(d, tDD, addmax(mprev, lo16(t.w), kNeg));
+    mx = max(mx, Mn);
+    dM = Mo;
+    dI = Io;
+    dD = Do;
+    mprev = Mn;
+  }
+};
+
 // Shared memory: the query's transitions, Qmax*32 uint4 (8 int16 per node:
-// BM|MM, IM|DM, MI|II, MD|DD), then per warp three arrays of Qmax*32 int16
-// (M, I, D), slot j*32 + lane (sign-extending 16-bit loads, no unpacking).
-__global__ void __launch_bounds__(kVitFastMaxThreads) viterbi_fast_kernel(VitParams p) {
+// BM|MM, IM|DM, MI|II, MD|DD), then per warp three arrays of (Qmax - R)*32
+// int16 (M, I, D of nodes R.. of every segment), slot (j - R)*32 + lane
+// (sign-extending 16-bit loads, no unpacking).  The first R nodes of each
+// lane's segment live in registers, which leaves more shared memory per SM
+// for warps on long models.
+template <int R>
+__global__ void __launch_bounds__(R ? kVitFastRegThreads : kVitFastMaxThreads)
+    viterbi_fast_kernel(VitParams p) {
   extern __shared__ __align__(16) uint4 fsm[];
   const int lane = threadIdx.x & 31;
   const int warp = threadIdx.x >> 5;
   const int Qmax = p.max_Mpad >> 5;
+  const int Smax = max(Qmax - R, 0);
   uint4 *tr = fsm;
-  int16_t *sM = reinterpret_cast<int16_t *>(fsm + (size_t)Qmax * 32) + (size_t)warp * Qmax * 32 * 3;
-  int16_t *sI = sM + (size_t)Qmax * 32;
-  int16_t *sD = sI + (size_t)Qmax * 32;
+  int16_t *sM = reinterpret_cast<int16_t *>(fsm + (size_t)Qmax * 32) + (size_t)warp * Smax * 32 * 3;
+  int16_t *sI = sM + (size_t)Smax * 32;
+  int16_t *sD = sI + (size_t)Smax * 32;
+  int rM[R > 0 ? R : 1], rI[R > 0 ? R : 1], rD[R > 0 ? R : 1];
 
   for (uint32_t qi = 0; qi < p.n_queries; ++qi) {
     const VitQuery Q = p.queries[qi];
@@ -242,7 +275,9 @@ __global__ void __launch_bounds__(kVitFastMaxThreads) viterbi_fast_kernel(VitPar
       const int len = (int)__ldg(p.seq_len + r);
       const uint32_t orig = __ldg(p.seq_orig + r);
 
-      for (int j = 0; j < nq; ++j) sM[j * 32 + lane] = sI[j * 32 + lane] = sD[j * 32 + lane] = (int16_t)kNeg;
+#pragma unroll
+      for (int j = 0; j < R; ++j) rM[j] = rI[j] = rD[j] = kNeg;
+      for (int j = 0; j < nq - R; ++j) sM[j * 32 + lane] = sI[j * 32 + lane] = sD[j * 32 + lane] = (int16_t)kNeg;
       int xN = Q.base, xJ = kNeg, xC = kNeg;
       int xB = addmax(xN, tNB, kNeg);
       // Previous row: M, I and true D of the node before the segment, and the
@@ -259,34 +294,25 @@ __global__ void __launch_bounds__(kVitFastMaxThreads) viterbi_fast_kernel(VitPar
         // Sweep the segment: the previous row's delete chain is completed on
         // the fly (D' = max(local D', carried chain)), then M, I and this
         // row's segment-local delete chain.
-        int dM = pM0, dI = pI0, dD = pD0, X = X0m, mprev = kNeg, d = kNeg, mx = kNeg;
-        int Mn = kNeg, In = kNeg;
-#pragma unroll 4
-        for (int j = 0; j < nv; ++j) {
-          const int sl = j * 32 + lane;
-          const int Mo = sM[sl], Io = sI[sl], Dl = sD[sl];
-          const uint4 t = tr[sl];
-          const int e = __ldg(erow + j * 32);
-          const int tDD = hi16(t.w);
-          X += tDD;
-          const int Do = max(Dl, X);
-          int best = addmax(dM, hi16(t.x), kNeg);      // M' + tMM
-          best = addmax(dI, lo16(t.y), best);           // I' + tIM
-          best = addmax(dD, hi16(t.y), best);           // D' + tDM
-          best = addmax(xB, lo16(t.x), best);           // xB + tBM
-          Mn = addmax(best, e, kNeg);
-          In = addmax(Io, hi16(t.z), addmax(Mo, lo16(t.z), kNeg));
-          d = addmax(d, tDD, addmax(mprev, lo16(t.w), kNeg));
-          mx = max(mx, Mn);
-          sM[sl] = (int16_t)Mn;
-          sI[sl] = (int16_t)In;
-          sD[sl] = (int16_t)d;
-          dM = Mo;
-          dI = Io;
-          dD = Do;
-          mprev = Mn;
+        FastCell c{pM0, pI0, pD0, X0m, kNeg, kNeg, kNeg, kNeg, kNeg};
+#pragma unroll
+        for (int j = 0; j < R; ++j) {
+          if (j < nv) {
+            c.step(tr[j * 32 + lane], __ldg(erow + j * 32), rM[j], rI[j], rD[j], xB);
+            rM[j] = c.Mn;
+            rI[j] = c.In;
+            rD[j] = c.d;
+          }
         }
-        const int xE = __reduce_max_sync(kAll, mx);
+#pragma unroll 4
+        for (int j = R; j < nv; ++j) {
+          const int sl = (j - R) * 32 + lane;
+          c.step(tr[j * 32 + lane], __ldg(erow + j * 32), sM[sl], sI[sl], sD[sl], xB);
+          sM[sl] = (int16_t)c.Mn;
+          sI[sl] = (int16_t)c.In;
+          sD[sl] = (int16_t)c.d;
+        }
+        const int xE = __reduce_max_sync(kAll, c.mx);
         if (xE >= 32767) {
           ovf = true;
           break;
@@ -294,10 +320,10 @@ __global__ void __launch_bounds__(kVitFastMaxThreads) viterbi_fast_kernel(VitPar
 
         // True delete score at the end of every segment: inclusive scan of
         // the segments' maps d -> max(A, d + B).
-        int Mlp = __shfl_up_sync(kAll, Mn, 1);
-        int Ilp = __shfl_up_sync(kAll, In, 1);
+        int Mlp = __shfl_up_sync(kAll, c.Mn, 1);
+        int Ilp = __shfl_up_sync(kAll, c.In, 1);
         if (lane == 0) Mlp = Ilp = kNeg;
-        int A = addmax(Mlp, tMD0 + Bsuf, d);
+        int A = addmax(Mlp, tMD0 + Bsuf, c.d);
 #pragma unroll
         for (int r = 0; r < 5; ++r) A = addmax(__shfl_up_sync(kAll, A, 1 << r), Wn[r], A);
         int carry = __shfl_up_sync(kAll, A, 1);
@@ -339,62 +365,86 @@ size_t viterbi_smem_bytes(int Mpad) { return (size_t)(kVitThreads / 32) * 3 * (s
 
 namespace {
 
-// Launch shape of the fast kernel: warps per block, resident blocks per SM
-// and the shared-memory carveout.  Each warp reads the match-score rows of
-// its residues from global memory, so the L1 left beside shared memory
-// should hold the rows of the codes the database uses (n_codes x Mpad x 2
-// bytes, at most 124 KB); among the carveouts that leave that much L1, take
-// the one that keeps the most warps resident.
+// Shared memory of a fast-kernel block: transitions + per warp the DP rows
+// of the nodes past the register-resident prefix R.
+size_t fast_smem(int Mpad, int warps, int R) {
+  const size_t q = (size_t)(Mpad >> 5);
+  const size_t s = q > (size_t)R ? q - (size_t)R : 0;
+  return q * 32 * 16 + (size_t)warps * s * 32 * 6;
+}
+
+typedef void (*VitKernelFn)(VitParams);
+
+VitKernelFn fast_kernel_for(int R) {
+  return R ? viterbi_fast_kernel<kVitRegPrefix> : viterbi_fast_kernel<0>;
+}
+
+// Launch shape of the fast kernel: register prefix (0 or kVitRegPrefix
+// nodes), warps per block, resident blocks per SM and the shared-memory
+// carveout.  Each warp reads the match-score rows of its residues from
+// global memory, so the L1 left beside shared memory should hold the rows
+// of the codes the database uses (n_codes x Mpad x 2 bytes, at most 124 KB);
+// among the carveouts that leave that much L1, take the shape that keeps
+// the most warps resident (registers permitting).  The register-prefix
+// variant runs fewer cells per warp-instruction (measured: 284 against 375
+// GCUPS at M = 2405), so it is taken only when the plain kernel would keep
+// four warps or fewer per SM (M = 3072: 350 against 299).
 struct FastShape {
-  int warps = 1, blocks = 1;
+  int R = 0, warps = 0, blocks = 1;
   size_t smem = 0;
   int carve_pct = 100;
 };
 
 FastShape fast_shape(int Mpad, int n_codes, int max_smem_block) {
   constexpr size_t kKB = 1024, kUnified = 256 * kKB, kCarveMax = 228 * kKB;
-  static int regs = 0;
-  if (!regs) {
-    cudaFuncAttributes a;
-    regs = cudaFuncGetAttributes(&a, (const void *)viterbi_fast_kernel) == cudaSuccess ? a.numRegs : 128;
-  }
-  const int warp_regs = ((regs + 7) / 8) * 8 * 32;
+  static int regs[2] = {0, 0};
+  const int Rs[2] = {0, kVitRegPrefix};
+  const int max_threads[2] = {kVitFastMaxThreads, kVitFastRegThreads};
+  for (int v = 0; v < 2; ++v)
+    if (!regs[v]) {
+      cudaFuncAttributes a;
+      regs[v] = cudaFuncGetAttributes(&a, (const void *)fast_kernel_for(Rs[v])) == cudaSuccess ? a.numRegs : 255;
+    }
   const size_t ws = std::min((size_t)std::max(n_codes, 1) * 2 * (size_t)Mpad, 124 * kKB);
   static const int carves_kb[] = {228, 196, 164, 132, 100};   // supported carveouts
-  FastShape best;
   for (int c : carves_kb) {
     const size_t C = (size_t)c * kKB;
     if (kUnified - C < ws && c != 100) continue;
-    FastShape s;
-    s.warps = 0;
-    for (int w = kVitFastMaxThreads / 32; w >= 1; --w) {
-      const size_t sm = viterbi_fast_smem_bytes(Mpad, w);
-      if (sm > (size_t)max_smem_block || sm + kKB > C) continue;
-      int b = (int)(C / (sm + kKB));
-      b = std::min(b, 65536 / (warp_regs * w));
-      b = std::min(b, 64 / w);
-      if (b < 1) continue;
-      if (w * b > s.warps * s.blocks || (w * b == s.warps * s.blocks && b > s.blocks)) {
-        s.warps = w;
-        s.blocks = b;
-        s.smem = sm;
+    FastShape best;
+    for (int v = 0; v < 2; ++v) {
+      if (Rs[v] && (Mpad >> 5) <= Rs[v]) continue;   // a prefix only for segments longer than it
+      if (Rs[v] && best.warps * best.blocks > 4) continue;
+      const int warp_regs = ((regs[v] + 7) / 8) * 8 * 32;
+      for (int w = max_threads[v] / 32; w >= 1; --w) {
+        const size_t sm = fast_smem(Mpad, w, Rs[v]);
+        if (sm > (size_t)max_smem_block || sm + kKB > C) continue;
+        int b = (int)(C / (sm + kKB));
+        b = std::min(b, 65536 / (warp_regs * w));
+        b = std::min(b, 64 / w);
+        if (b < 1) continue;
+        if (w * b > best.warps * best.blocks ||
+            (w * b == best.warps * best.blocks && Rs[v] == best.R && b > best.blocks)) {
+          best.R = Rs[v];
+          best.warps = w;
+          best.blocks = b;
+          best.smem = sm;
+        }
       }
     }
-    if (s.warps == 0) continue;
+    if (best.warps == 0) continue;
     // The driver takes the smallest supported carveout at or above the
     // preference: ask for just under C.
-    s.carve_pct = (int)std::min<size_t>(100, ((C - kKB) * 100) / kCarveMax);
-    return s;
+    best.carve_pct = (int)std::min<size_t>(100, ((C - kKB) * 100) / kCarveMax);
+    return best;
   }
-  best.warps = 0;
-  return best;
+  return FastShape();
 }
 
 }  // namespace
 
 int viterbi_fast_shape_key(int Mpad, int n_codes, int max_smem) {
   const FastShape s = fast_shape(Mpad, n_codes, max_smem);
-  return s.warps * 10000 + s.blocks * 100 + s.carve_pct;
+  return s.R * 1000000 + s.warps * 10000 + s.blocks * 100 + s.carve_pct;
 }
 
 int launch_viterbi(const VitParams &p, bool fast, int n_codes, int max_smem, int num_sms,
@@ -415,11 +465,12 @@ int launch_viterbi(const VitParams &p, bool fast, int n_codes, int max_smem, int
   }
   const FastShape s = fast_shape(p.max_Mpad, n_codes, max_smem);
   if (s.warps == 0) return 2;
-  const void *fn = (const void *)viterbi_fast_kernel;
+  const VitKernelFn k = fast_kernel_for(s.R);
+  const void *fn = (const void *)k;
   if (cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)s.smem) != cudaSuccess ||
       cudaFuncSetAttribute(fn, cudaFuncAttributePreferredSharedMemoryCarveout, s.carve_pct) != cudaSuccess)
     return 1;
-  viterbi_fast_kernel<<<num_sms * s.blocks, s.warps * 32, s.smem, st>>>(p);
+  k<<<num_sms * s.blocks, s.warps * 32, s.smem, st>>>(p);
   return cudaGetLastError() == cudaSuccess ? 0 : 1;
 }
 

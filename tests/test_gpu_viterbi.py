@@ -117,6 +117,16 @@ def test_adversarial_nonpositive_moves(ctx, seed):
         assert got[1].any()
 
 
+@pytest.mark.parametrize("M", [1100, 2100, 3000])
+def test_register_prefix_lengths(ctx, M):
+    """Models long enough for the fast kernel to keep the first nodes of each
+    lane segment in registers: realistic and adversarial (moves <= 0)."""
+    rng = np.random.default_rng(400 + M)
+    db = synth.random_database(160, 220, rng, alphabet=32)
+    _run(ctx, [synth.make_vit_profile(M, rng),
+               synth.random_vit_profile(M - 7, 29, rng, lo=-2500, hi=2500, moves_hi=0)], db)
+
+
 def test_multi_query_launch(ctx):
     rng = np.random.default_rng(9)
     wl = synth.make_workload(0, n_seqs=800)
