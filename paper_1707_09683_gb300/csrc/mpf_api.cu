@@ -1199,12 +1199,23 @@ int viterbi_enqueue(mpf_ctx *ctx, const mpf_vprofile *const *vps, int n_q, const
   const uint64_t n = db->n_seqs;
   // Order: general queries first (key -1), then fast ones by launch shape and length.
   std::vector<std::tuple<int, int, int>> order;   // (key, Mpad, query)
+  std::map<int, int> group_max;                    // key -> longest model of the group
   for (int q = 0; q < n_q; ++q) {
     const mpf_vprofile *v = vps[q];
     const int key = v->fast ? viterbi_fast_shape_key(v->Mpad, db->n_codes, ctx->max_smem) : -1;
     order.emplace_back(key, v->Mpad, q);
+    group_max[key] = std::max(group_max[key], v->Mpad);
   }
-  std::stable_sort(order.begin(), order.end());
+  // Groups with the longest models first (the launches are persistent and
+  // fill the GPU in launch order, so the short-model groups finish last and
+  // the final tail is short); within a group, longest models first.
+  std::stable_sort(order.begin(), order.end(), [&](const std::tuple<int, int, int> &a,
+                                                   const std::tuple<int, int, int> &b) {
+    const int ga = group_max[std::get<0>(a)], gb = group_max[std::get<0>(b)];
+    if (ga != gb) return ga > gb;
+    if (std::get<0>(a) != std::get<0>(b)) return std::get<0>(a) < std::get<0>(b);
+    return std::get<1>(a) > std::get<1>(b);
+  });
   std::vector<VitQuery> qs;
   qs.reserve((size_t)n_q);
   for (const auto &o : order) {
