@@ -41,6 +41,7 @@
 #include <stdint.h>
 
 #include <algorithm>
+#include <array>
 
 #include "mpf_internal.h"
 
@@ -401,17 +402,22 @@ struct FastShape {
 
 FastShape fast_shape(int Mpad, int n_codes, int max_smem_block) {
   constexpr size_t kKB = 1024, kUnified = 256 * kKB, kCarveMax = 228 * kKB;
-  static int regs_tab[3] = {0, 0, 0};   // <0,4>, <0,8>, <kVitRegPrefix,8>
+  // Registers per thread of the three variants, looked up once (thread-safe
+  // static initialisation).
+  static const std::array<int, 3> regs_tab = [] {
+    std::array<int, 3> t{};
+    const VitKernelFn fns[3] = {viterbi_fast_kernel<0, 4>, viterbi_fast_kernel<0, 8>,
+                                viterbi_fast_kernel<kVitRegPrefix, 8>};
+    for (int i = 0; i < 3; ++i) {
+      cudaFuncAttributes a;
+      t[i] = cudaFuncGetAttributes(&a, (const void *)fns[i]) == cudaSuccess ? a.numRegs : 255;
+    }
+    return t;
+  }();
   const int Rs[2] = {0, kVitRegPrefix};
   const int max_threads[2] = {kVitFastMaxThreads, kVitFastRegThreads};
   const int Q = Mpad >> 5;
   const int vi[2] = {Q >= 32 ? 1 : 0, 2};
-  for (int v = 0; v < 2; ++v)
-    if (!regs_tab[vi[v]]) {
-      cudaFuncAttributes a;
-      regs_tab[vi[v]] = cudaFuncGetAttributes(&a, (const void *)fast_kernel_for(Rs[v], Q)) == cudaSuccess
-                            ? a.numRegs : 255;
-    }
   const int regs[2] = {regs_tab[vi[0]], regs_tab[vi[1]]};
   const size_t ws = std::min((size_t)std::max(n_codes, 1) * 2 * (size_t)Mpad, 124 * kKB);
   static const int carves_kb[] = {228, 196, 164, 132, 100};   // supported carveouts

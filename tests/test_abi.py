@@ -66,3 +66,19 @@ def test_null_arguments_are_rejected_without_a_device(lib):
     lib.mpf_profile_destroy(None)
     lib.mpf_db_destroy(None)
     lib.mpf_plan_destroy(None)
+
+
+def test_stage_and_viterbi_calls_reject_null_arguments_without_a_device(lib):
+    h = ctypes.c_void_p()
+    i16 = (ctypes.c_int16 * 8)()
+    assert lib.mpf_vit_profile_create(None, 10, 20, i16, i16, i16, 12000, 721.0,
+                                      ctypes.byref(h)) == mpf.MPF_EINVAL
+    assert lib.mpf_vit_profile_create(None, 10, 20, i16, i16, i16, 12000, 721.0, None) == mpf.MPF_EINVAL
+    assert lib.mpf_viterbi_scan(None, None, 1, None, None, None, None) == mpf.MPF_EINVAL
+    assert lib.mpf_viterbi_rescore(None, None, 1, None, None, None, 0.0, None, None, None,
+                                   None) == mpf.MPF_EINVAL
+    assert lib.mpf_pipeline_scan(None, None, 1, None, 0.0, None, None, None, None, None, None,
+                                 None) == mpf.MPF_EINVAL
+    assert lib.mpf_pvalues(None, None, 0, 0.0, 1.0, None) == mpf.MPF_EINVAL
+    assert lib.mpf_scan_noalloc(None, 0, None, None, None, None, None) == mpf.MPF_EINVAL
+    lib.mpf_vit_profile_destroy(None)

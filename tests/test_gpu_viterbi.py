@@ -242,3 +242,31 @@ def test_three_stage_pipeline(ctx):
         sl = slice(i * n, (i + 1) * n)
         assert int(gp[i]) == npass
         _check((gs[sl], gf[sl], gn[sl]), want, i)
+
+
+def test_invalid_arguments(ctx):
+    rng = np.random.default_rng(14)
+    too_long = synth.make_vit_profile(mpf.max_striped_length() + 1, rng)
+    with pytest.raises(mpf.MpfError) as e:
+        mpf.VitProfile(ctx, too_long)
+    assert e.value.status == mpf.MPF_EUNSUPPORTED
+    bad_scale = synth.make_vit_profile(20, rng)
+    bad_scale.scale = 0.0
+    with pytest.raises(mpf.MpfError) as e:
+        mpf.VitProfile(ctx, bad_scale)
+    assert e.value.status == mpf.MPF_EINVAL
+    dbh = synth.random_database(20, 30, rng)
+    db = mpf.Database(ctx, dbh.residues, dbh.offsets, dbh.lengths)
+    vp = mpf.VitProfile(ctx, synth.make_vit_profile(30, rng))
+    n = db.n_seqs
+    host_flag = np.zeros(n, np.uint8)
+    host_nat = np.zeros(n, np.float32)
+    s, f, x = _dev(n, torch.int16), _dev(n, torch.uint8), _dev(n, torch.float32)
+    with pytest.raises(mpf.MpfError) as e:      # stage inputs must be device buffers
+        mpf.viterbi_rescore(ctx, [vp], db, host_flag, host_nat, 0.0, s, f, x, _dev(1, torch.int32))
+    assert e.value.status == mpf.MPF_EINVAL
+    with pytest.raises(mpf.MpfError) as e:      # NaN threshold
+        mpf.viterbi_rescore(ctx, [vp], db, f, x, float("nan"), s, f, x, _dev(1, torch.int32))
+    assert e.value.status == mpf.MPF_EINVAL
+    vp.close()
+    db.close()
