@@ -614,8 +614,8 @@ def main():
     ap.add_argument("--n-seqs", type=int, default=None)
     ap.add_argument("--n-queries", type=int, default=None)
     ap.add_argument("--no-tune", dest="tune", action="store_false")
-    ap.add_argument("--cpu-sample", type=int, default=6000)
-    ap.add_argument("--ref-sample", type=int, default=3000)
+    ap.add_argument("--cpu-sample", type=int, default=40000)
+    ap.add_argument("--ref-sample", type=int, default=12000)
     ap.add_argument("--no-cpu", action="store_true")
     ap.add_argument("--arith", default="auto", choices=["auto", "i16", "f16"])
     ap.add_argument("--no-serve", action="store_true")
