@@ -95,8 +95,6 @@ int launch_pvalues(const float *nat, uint64_t n, float mu, float lambda, float *
 // rows Mpad long.
 constexpr int kVitThreads = 256;
 constexpr int kVitFastMaxThreads = 512;
-constexpr int kVitRegPrefix = 32;        // fast kernel: nodes per lane held in registers (long models)
-constexpr int kVitFastRegThreads = 384;  // block limit of that variant (registers)
 constexpr int kVitRows = 32;         // msc rows: residue codes 0..31
 constexpr int kVitTrans = 8;         // BM, MM, IM, DM, MI, II, MD, DD
 constexpr int kVitSpecial = 8;       // NN, NB, EC, CC, CT, EJ, JJ, JB

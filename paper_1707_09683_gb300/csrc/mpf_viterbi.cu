@@ -194,10 +194,24 @@ __device__ __forceinline__ int addmax(int a, int b, int c) { return __viaddmax_s
 // the node before.
 struct FastCell {
   int dM, dI, dD, X, mprev, d, mx, Mn, In;
+  int mop, Dlp;   // recomputed previous-row chain: M' of the node before (in the segment), local D'
   __device__ __forceinline__ void step(const uint4 t, int e, int Mo, int Io, int Dl, int xB) {
     const int tDD = hi16(t.w);
     X += tDD;
     const int Do = max(Dl, X);
+    cell(t, tDD, e, Mo, Io, Do, xB);
+  }
+  // The same node when the previous row's local delete chain is not stored:
+  // it is recomputed here from the previous row's M (2 DPX operations).
+  __device__ __forceinline__ void step_nd(const uint4 t, int e, int Mo, int Io, int xB) {
+    const int tDD = hi16(t.w);
+    X += tDD;
+    Dlp = addmax(Dlp, tDD, addmax(mop, lo16(t.w), kNeg));
+    mop = Mo;
+    const int Do = max(Dlp, X);
+    cell(t, tDD, e, Mo, Io, Do, xB);
+  }
+  __device__ __forceinline__ void cell(const uint4 t, int tDD, int e, int Mo, int Io, int Do, int xB) {
     int best = addmax(dM, hi16(t.x), kNeg);      // M' + tMM
     best = addmax(dI, lo16(t.y), best);           // I' + tIM
     best = addmax(dD, hi16(t.y), best);           // D' + tDM
@@ -214,24 +228,22 @@ struct FastCell {
 };
 
 // Shared memory: the query's transitions, Qmax*32 uint4 (8 int16 per node:
-// BM|MM, IM|DM, MI|II, MD|DD), then per warp three arrays of (Qmax - R)*32
-// int16 (M, I, D of nodes R.. of every segment), slot (j - R)*32 + lane
-// (sign-extending 16-bit loads, no unpacking).  The first R nodes of each
-// lane's segment live in registers, which leaves more shared memory per SM
-// for warps on long models.
-template <int R, int U>
-__global__ void __launch_bounds__(R ? kVitFastRegThreads : kVitFastMaxThreads, 1)
-    viterbi_fast_kernel(VitParams p) {
+// BM|MM, IM|DM, MI|II, MD|DD), then per warp three arrays of Qmax*32 int16
+// (M, I, D), slot j*32 + lane (sign-extending 16-bit loads, no unpacking).
+// With ND the D array is not kept: the next row recomputes the local delete
+// chain from the stored M row (4 bytes of state per node instead of 6, two
+// more DPX operations per node), so more warps fit on long models.  U is the
+// unroll depth of the node loop.
+template <int U, bool ND>
+__global__ void __launch_bounds__(kVitFastMaxThreads, 1) viterbi_fast_kernel(VitParams p) {
   extern __shared__ __align__(16) uint4 fsm[];
   const int lane = threadIdx.x & 31;
   const int warp = threadIdx.x >> 5;
   const int Qmax = p.max_Mpad >> 5;
-  const int Smax = max(Qmax - R, 0);
   uint4 *tr = fsm;
-  int16_t *sM = reinterpret_cast<int16_t *>(fsm + (size_t)Qmax * 32) + (size_t)warp * Smax * 32 * 3;
-  int16_t *sI = sM + (size_t)Smax * 32;
-  int16_t *sD = sI + (size_t)Smax * 32;
-  int rM[R > 0 ? R : 1], rI[R > 0 ? R : 1], rD[R > 0 ? R : 1];
+  int16_t *sM = reinterpret_cast<int16_t *>(fsm + (size_t)Qmax * 32) + (size_t)warp * Qmax * 32 * (ND ? 2 : 3);
+  int16_t *sI = sM + (size_t)Qmax * 32;
+  int16_t *sD = sI + (size_t)Qmax * 32;   // unused with ND
 
   for (uint32_t qi = 0; qi < p.n_queries; ++qi) {
     const VitQuery Q = p.queries[qi];
@@ -276,9 +288,10 @@ __global__ void __launch_bounds__(R ? kVitFastRegThreads : kVitFastMaxThreads, 1
       const int len = (int)__ldg(p.seq_len + r);
       const uint32_t orig = __ldg(p.seq_orig + r);
 
-#pragma unroll
-      for (int j = 0; j < R; ++j) rM[j] = rI[j] = rD[j] = kNeg;
-      for (int j = 0; j < nq - R; ++j) sM[j * 32 + lane] = sI[j * 32 + lane] = sD[j * 32 + lane] = (int16_t)kNeg;
+      for (int j = 0; j < nq; ++j) {
+        sM[j * 32 + lane] = sI[j * 32 + lane] = (int16_t)kNeg;
+        if (!ND) sD[j * 32 + lane] = (int16_t)kNeg;
+      }
       int xN = Q.base, xJ = kNeg, xC = kNeg;
       int xB = addmax(xN, tNB, kNeg);
       // Previous row: M, I and true D of the node before the segment, and the
@@ -295,23 +308,18 @@ __global__ void __launch_bounds__(R ? kVitFastRegThreads : kVitFastMaxThreads, 1
         // Sweep the segment: the previous row's delete chain is completed on
         // the fly (D' = max(local D', carried chain)), then M, I and this
         // row's segment-local delete chain.
-        FastCell c{pM0, pI0, pD0, X0m, kNeg, kNeg, kNeg, kNeg, kNeg};
-#pragma unroll
-        for (int j = 0; j < R; ++j) {
-          if (j < nv) {
-            c.step(tr[j * 32 + lane], __ldg(erow + j * 32), rM[j], rI[j], rD[j], xB);
-            rM[j] = c.Mn;
-            rI[j] = c.In;
-            rD[j] = c.d;
-          }
-        }
+        FastCell c{pM0, pI0, pD0, X0m, kNeg, kNeg, kNeg, kNeg, kNeg, kNeg, kNeg};
 #pragma unroll U
-        for (int j = R; j < nv; ++j) {
-          const int sl = (j - R) * 32 + lane;
-          c.step(tr[j * 32 + lane], __ldg(erow + j * 32), sM[sl], sI[sl], sD[sl], xB);
+        for (int j = 0; j < nv; ++j) {
+          const int sl = j * 32 + lane;
+          if (ND) {
+            c.step_nd(tr[sl], __ldg(erow + j * 32), sM[sl], sI[sl], xB);
+          } else {
+            c.step(tr[sl], __ldg(erow + j * 32), sM[sl], sI[sl], sD[sl], xB);
+            sD[sl] = (int16_t)c.d;
+          }
           sM[sl] = (int16_t)c.Mn;
           sI[sl] = (int16_t)c.In;
-          sD[sl] = (int16_t)c.d;
         }
         const int xE = __reduce_max_sync(kAll, c.mx);
         if (xE >= 32767) {
@@ -367,58 +375,56 @@ size_t viterbi_smem_bytes(int Mpad) { return (size_t)(kVitThreads / 32) * 3 * (s
 namespace {
 
 // Shared memory of a fast-kernel block: transitions + per warp the DP rows
-// of the nodes past the register-resident prefix R.
-size_t fast_smem(int Mpad, int warps, int R) {
+// (M, I and D, or M and I with ND).
+size_t fast_smem(int Mpad, int warps, bool nd) {
   const size_t q = (size_t)(Mpad >> 5);
-  const size_t s = q > (size_t)R ? q - (size_t)R : 0;
-  return q * 32 * 16 + (size_t)warps * s * 32 * 6;
+  return q * 32 * 16 + (size_t)warps * q * 32 * (nd ? 4 : 6);
 }
 
 typedef void (*VitKernelFn)(VitParams);
 
-// Variants: register prefix R and the unroll depth of the shared-memory node
-// loop (8 for segments of 32 nodes or more, which measured 5-10% faster
-// there; 4 below, where the deeper unroll measured slower).
-VitKernelFn fast_kernel_for(int R, int Q) {
-  if (R) return viterbi_fast_kernel<kVitRegPrefix, 8>;
-  return Q >= 32 ? viterbi_fast_kernel<0, 8> : viterbi_fast_kernel<0, 4>;
+// Variants: the unroll depth of the node loop (8 for segments of 32 nodes or
+// more, which measured 5-10% faster there; 4 below, where the deeper unroll
+// measured slower) and whether the D row is stored.
+VitKernelFn fast_kernel_for(int Q, bool nd) {
+  if (nd) return viterbi_fast_kernel<8, true>;
+  return Q >= 32 ? viterbi_fast_kernel<8, false> : viterbi_fast_kernel<4, false>;
 }
 
-// Launch shape of the fast kernel: register prefix (0 or kVitRegPrefix
-// nodes), warps per block, resident blocks per SM and the shared-memory
-// carveout.  Each warp reads the match-score rows of its residues from
-// global memory, so the L1 left beside shared memory should hold the rows
-// of the codes the database uses (n_codes x Mpad x 2 bytes, at most 124 KB);
-// among the carveouts that leave that much L1, take the shape that keeps
-// the most warps resident (registers permitting).  The register-prefix
-// variant runs fewer cells per warp-instruction (measured: 284 against 375
-// GCUPS at M = 2405), so it is taken only when the plain kernel would keep
-// four warps or fewer per SM (M = 3072: 350 against 299).
+// Launch shape of the fast kernel: variant, warps per block, resident blocks
+// per SM and the shared-memory carveout.  Each warp reads the match-score
+// rows of its residues from global memory, so the L1 left beside shared
+// memory should hold the rows of the codes the database uses (n_codes x Mpad
+// x 2 bytes, at most 124 KB); among the carveouts that leave that much L1,
+// take the shape that keeps the most warps resident (registers permitting).
+// The variant without a stored D row trades two DPX operations per cell for
+// a third less shared memory per warp; it is taken where the plain kernel
+// keeps five warps or fewer per SM (measured, one query against 10,000
+// sequences: M = 2800 510 against 435 GCUPS, M = 3072 513 against 377; at
+// M = 2000-2405, with 6-11 plain warps, it measured 6-13% slower).
 struct FastShape {
-  int R = 0, warps = 0, blocks = 1;
+  bool nd = false;
+  int warps = 0, blocks = 1;
   size_t smem = 0;
   int carve_pct = 100;
 };
 
 FastShape fast_shape(int Mpad, int n_codes, int max_smem_block) {
   constexpr size_t kKB = 1024, kUnified = 256 * kKB, kCarveMax = 228 * kKB;
-  // Registers per thread of the three variants, looked up once (thread-safe
+  const int Q = Mpad >> 5;
+  // Registers per thread of every instantiation, looked up once (thread-safe
   // static initialisation).
   static const std::array<int, 3> regs_tab = [] {
     std::array<int, 3> t{};
-    const VitKernelFn fns[3] = {viterbi_fast_kernel<0, 4>, viterbi_fast_kernel<0, 8>,
-                                viterbi_fast_kernel<kVitRegPrefix, 8>};
+    const VitKernelFn fns[3] = {viterbi_fast_kernel<4, false>, viterbi_fast_kernel<8, false>,
+                                viterbi_fast_kernel<8, true>};
     for (int i = 0; i < 3; ++i) {
       cudaFuncAttributes a;
       t[i] = cudaFuncGetAttributes(&a, (const void *)fns[i]) == cudaSuccess ? a.numRegs : 255;
     }
     return t;
   }();
-  const int Rs[2] = {0, kVitRegPrefix};
-  const int max_threads[2] = {kVitFastMaxThreads, kVitFastRegThreads};
-  const int Q = Mpad >> 5;
-  const int vi[2] = {Q >= 32 ? 1 : 0, 2};
-  const int regs[2] = {regs_tab[vi[0]], regs_tab[vi[1]]};
+  const int regs[2] = {regs_tab[Q >= 32 ? 1 : 0], regs_tab[2]};
   const size_t ws = std::min((size_t)std::max(n_codes, 1) * 2 * (size_t)Mpad, 124 * kKB);
   static const int carves_kb[] = {228, 196, 164, 132, 100};   // supported carveouts
   for (int c : carves_kb) {
@@ -426,24 +432,25 @@ FastShape fast_shape(int Mpad, int n_codes, int max_smem_block) {
     if (kUnified - C < ws && c != 100) continue;
     FastShape best;
     for (int v = 0; v < 2; ++v) {
-      if (Rs[v] && (Mpad >> 5) <= Rs[v]) continue;   // a prefix only for segments longer than it
-      if (Rs[v] && best.warps * best.blocks > 4) continue;
+      const bool nd = v == 1;
+      if (nd && best.warps * best.blocks > 5) continue;
       const int warp_regs = ((regs[v] + 7) / 8) * 8 * 32;
-      for (int w = max_threads[v] / 32; w >= 1; --w) {
-        const size_t sm = fast_smem(Mpad, w, Rs[v]);
+      FastShape cand;
+      for (int w = kVitFastMaxThreads / 32; w >= 1; --w) {
+        const size_t sm = fast_smem(Mpad, w, nd);
         if (sm > (size_t)max_smem_block || sm + kKB > C) continue;
         int b = (int)(C / (sm + kKB));
         b = std::min(b, 65536 / (warp_regs * w));
         b = std::min(b, 64 / w);
         if (b < 1) continue;
-        if (w * b > best.warps * best.blocks ||
-            (w * b == best.warps * best.blocks && Rs[v] == best.R && b > best.blocks)) {
-          best.R = Rs[v];
-          best.warps = w;
-          best.blocks = b;
-          best.smem = sm;
+        if (w * b > cand.warps * cand.blocks || (w * b == cand.warps * cand.blocks && b > cand.blocks)) {
+          cand.nd = nd;
+          cand.warps = w;
+          cand.blocks = b;
+          cand.smem = sm;
         }
       }
+      if (cand.warps * cand.blocks > best.warps * best.blocks) best = cand;
     }
     if (best.warps == 0) continue;
     // The driver takes the smallest supported carveout at or above the
@@ -458,7 +465,7 @@ FastShape fast_shape(int Mpad, int n_codes, int max_smem_block) {
 
 int viterbi_fast_shape_key(int Mpad, int n_codes, int max_smem) {
   const FastShape s = fast_shape(Mpad, n_codes, max_smem);
-  return s.R * 1000000 + s.warps * 10000 + s.blocks * 100 + s.carve_pct;
+  return (s.nd ? 1000000 : 0) + s.warps * 10000 + s.blocks * 100 + s.carve_pct;
 }
 
 int launch_viterbi(const VitParams &p, bool fast, int n_codes, int max_smem, int num_sms,
@@ -479,7 +486,7 @@ int launch_viterbi(const VitParams &p, bool fast, int n_codes, int max_smem, int
   }
   const FastShape s = fast_shape(p.max_Mpad, n_codes, max_smem);
   if (s.warps == 0) return 2;
-  const VitKernelFn k = fast_kernel_for(s.R, p.max_Mpad >> 5);
+  const VitKernelFn k = fast_kernel_for(p.max_Mpad >> 5, s.nd);
   const void *fn = (const void *)k;
   if (cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)s.smem) != cudaSuccess ||
       cudaFuncSetAttribute(fn, cudaFuncAttributePreferredSharedMemoryCarveout, s.carve_pct) != cudaSuccess)

@@ -117,10 +117,12 @@ def test_adversarial_nonpositive_moves(ctx, seed):
         assert got[1].any()
 
 
-@pytest.mark.parametrize("M", [1100, 2100, 3000])
-def test_register_prefix_lengths(ctx, M):
-    """Models long enough for the fast kernel to keep the first nodes of each
-    lane segment in registers: realistic and adversarial (moves <= 0)."""
+@pytest.mark.parametrize("M", [1100, 2100, 2600, 3000])
+def test_long_segment_variants(ctx, M):
+    """Model lengths that select the fast kernel's long-segment variants
+    (deeper unrolling; the recomputed D row near M = 2,400-2,900; the
+    register-resident prefix near 3,000): realistic and adversarial (moves
+    <= 0)."""
     rng = np.random.default_rng(400 + M)
     db = synth.random_database(160, 220, rng, alphabet=32)
     _run(ctx, [synth.make_vit_profile(M, rng),
