@@ -1,8 +1,12 @@
-// mpf_api.cu -- host side of the C ABI declared in include/mpf.h.
+// mpf_api.cu -- host side of the C ABI declared in include/mpf.h: contexts,
+// byte-filter profiles, the resident database, scans, plans, the SSV -> MSV
+// pipeline and P-values (the allocation-free entry point is in
+// mpf_noalloc.cu, the Viterbi calls in mpf_vit_api.cu).
 //
 // Owns device memory and streams, lays the database out in HBM, builds the
 // striped cost tables, chooses kernel configurations and launches the scan
-// kernel.  Every step of the scan itself runs in mpf_scan_kernel.cuh.
+// kernels.  Every step of a scan itself runs in the kernels
+// (mpf_scan_kernel.cuh, mpf_long_kernel.cu, mpf_pipeline.cu).
 #include <cuda_runtime.h>
 #include <math.h>
 #include <string.h>
@@ -17,9 +21,11 @@
 #include <vector>
 
 #include "../../include/mpf.h"
+#include "mpf_handles.h"
 #include "mpf_internal.h"
 
 using namespace mpf;
+using namespace mpf::host;
 
 namespace mpf {
 KernelFn kernel_for(int lanes, int words, int mode) {
@@ -35,93 +41,10 @@ KernelFn kernel_for(int lanes, int words, int mode) {
 }
 }  // namespace mpf
 
-struct mpf_ctx {
-  int device = 0;
-  cudaStream_t stream = nullptr;
-  bool own_stream = false;
-  int num_sms = 0;
-  int max_smem = 0;
-  int *d_status = nullptr;
-  // Scratch for host-pointer outputs (grown on demand).
-  void *d_out = nullptr;
-  size_t d_out_bytes = 0;
-  // Streams for overlapping launch groups and for graph capture.
-  cudaStream_t fork[8] = {};
-  int n_fork = 0;
-  cudaStream_t capture = nullptr;
-  // Side stream for uploads that other streams must see complete (tables,
-  // length tables): allocated and copied on it, then synchronised.
-  cudaStream_t util = nullptr;
-  // One-shot plans whose kernels may still be running.
-  std::vector<mpf_plan *> pending;
-};
-
-struct DevTable {
-  uint4 *ptr = nullptr;
-  TableGeom geom{};
-};
-
-struct mpf_profile {
-  mpf_ctx *ctx = nullptr;
-  int M = 0, K = 0;
-  std::vector<uint8_t> cost;  // K x M
-  int bias = 0, tbm = 0, tec = 0, tjb_fixed = 0, base = 0;
-  float scale = 1.f;
-  uint8_t *d_tjb = nullptr;
-  uint32_t n_tjb = 0;
-  int tjb_min = 0;
-  int cfg_lanes[2] = {0, 0}, cfg_words[2] = {0, 0};
-  int arith[2] = {MPF_ARITH_AUTO, MPF_ARITH_AUTO};
-  int seg_words = 0;            // > 0: longer than the striped kernels hold (long-model kernel)
-  mutable std::map<std::tuple<int, int, int>, DevTable> tables;
-  mutable std::mutex mu;
-};
-
-struct mpf_db {
-  mpf_ctx *ctx = nullptr;
-  uint64_t n_seqs = 0, n_residues = 0;
-  uint32_t *d_words = nullptr;      // residue words, sequences 16-byte aligned
-  uint32_t *d_seq_word = nullptr;   // per length rank
-  uint32_t *d_seq_len = nullptr;
-  uint32_t *d_seq_orig = nullptr;
-  uint32_t pad_word = 0;
-  int n_codes = 0;                  // distinct residue codes present
-};
-
 // ---------------------------------------------------------------- helpers --
 
-#define MPF_CUDA(call)                        \
-  do {                                        \
-    cudaError_t e_ = (call);                  \
-    if (e_ != cudaSuccess) {                  \
-      (void)cudaGetLastError();               \
-      return e_ == cudaErrorMemoryAllocation ? MPF_ENOMEM : MPF_ECUDA; \
-    }                                         \
-  } while (0)
-
-namespace {
-
-struct DeviceGuard {
-  int prev = -1;
-  explicit DeviceGuard(int dev) {
-    if (cudaGetDevice(&prev) != cudaSuccess) prev = -1;
-    if (prev != dev) cudaSetDevice(dev);
-  }
-  ~DeviceGuard() {
-    int cur = -1;
-    if (prev >= 0 && cudaGetDevice(&cur) == cudaSuccess && cur != prev) cudaSetDevice(prev);
-  }
-};
-
-bool is_device_ptr(const void *p) {
-  if (!p) return false;
-  cudaPointerAttributes a;
-  if (cudaPointerGetAttributes(&a, p) != cudaSuccess) {
-    (void)cudaGetLastError();
-    return false;
-  }
-  return a.type == cudaMemoryTypeDevice || a.type == cudaMemoryTypeManaged;
-}
+namespace mpf {
+namespace host {
 
 const int kLanes[6] = {1, 2, 4, 8, 16, 32};
 
@@ -301,7 +224,8 @@ int kernel_mode(const mpf_profile *p, int filter) {
   return f16 ? MODE_MSV_FAST_F16 : MODE_MSV_FAST;
 }
 
-}  // namespace
+}  // namespace host
+}  // namespace mpf
 
 // One launch of the scan kernel over a set of queries sharing a kernel
 // configuration.  Device arrays are owned by the group.
@@ -1046,395 +970,6 @@ void mpf_plan_destroy(mpf_plan *plan) {
     cudaStreamSynchronize(plan->ctx->stream);
   }
   plan_free(plan);
-}
-
-}  // extern "C"
-
-// ====================================================== allocation-free scan
-//
-// mpf_scan_noalloc serves callers that must not allocate device memory at
-// call time: code running inside a CUDA stream capture that forbids
-// allocation, processes under a fixed memory budget, or hosts whose
-// allocator belongs to someone else.  Everything the scan kernel needs
-// beyond its inputs and outputs -- the query descriptor, the work-item
-// counter, the status word and the striped cost table -- lives in the
-// file-scope device array below instead of memory from cudaMalloc.
-namespace {
-
-constexpr size_t kNoAllocHeader = 512;                 // descriptor, counter, status
-constexpr size_t kNoAllocTableMax = 224u * 1024u;      // largest staged table image
-constexpr size_t kNoAllocBytes = kNoAllocHeader + kNoAllocTableMax;
-
-// Device scratch (one copy per GPU that loads the library, kept until exit).
-// In host code this name is a host-side stand-in, never a device address:
-// the address comes from cudaGetSymbolAddress below.
-static __device__ __align__(256) uint8_t g_noalloc_scratch[kNoAllocBytes];
-
-// Host staging of the table image (pageable; a copy from it returns only
-// after the driver has taken the bytes, so the next call may refill it).
-static uint8_t g_noalloc_image[kNoAllocTableMax];
-static std::mutex g_noalloc_mu;
-constexpr int kNoAllocMaxDevices = 64;
-static uint8_t *g_noalloc_dev[kNoAllocMaxDevices];   // scratch address per device
-
-}  // namespace
-
-extern "C" int mpf_scan_noalloc(mpf_ctx *ctx, int filter, const mpf_profile *prof,
-                                const mpf_db *db, uint8_t *raw, uint8_t *overflow, float *nat) {
-  if (!ctx || !prof || !db || !raw || !overflow) return MPF_EINVAL;
-  if (filter != MPF_MSV && filter != MPF_SSV) return MPF_EINVAL;
-  if (prof->ctx->device != ctx->device || db->ctx->device != ctx->device) return MPF_EINVAL;
-  if (ctx->device < 0 || ctx->device >= kNoAllocMaxDevices) return MPF_EUNSUPPORTED;
-  DeviceGuard dg(ctx->device);
-  if (!is_device_ptr(raw) || !is_device_ptr(overflow) || (nat && !is_device_ptr(nat)))
-    return MPF_EINVAL;
-  if (db->n_seqs == 0) return MPF_OK;
-
-  if (prof->seg_words) return MPF_EUNSUPPORTED;   // long models need the table in device memory
-  const int mode = kernel_mode(prof, filter);
-  int lanes = prof->cfg_lanes[filter], words = prof->cfg_words[filter];
-  if (!lanes) default_config(ctx, prof->M, mode, &lanes, &words);
-  if (!lanes) return MPF_EUNSUPPORTED;
-  const TableGeom g = table_geom(lanes, words);
-  if (g.table_bytes > kNoAllocTableMax) return MPF_EUNSUPPORTED;   // beyond the scratch size
-  KernelFn fn = kernel_for(lanes, words, mode);
-  if (!fn) return MPF_EINVAL;
-
-  std::lock_guard<std::mutex> lk(g_noalloc_mu);
-  // Set-up, once per device with that device current (the first call on a
-  // device does it; make that first call outside any stream capture).
-  if (!g_noalloc_dev[ctx->device]) {
-    void *addr = nullptr;
-    cudaError_t e = cudaGetSymbolAddress(&addr, g_noalloc_scratch);
-    if (e != cudaSuccess || !addr) {
-      (void)cudaGetLastError();
-      return MPF_ECUDA;
-    }
-    g_noalloc_dev[ctx->device] = (uint8_t *)addr;
-  }
-  uint8_t *scratch = g_noalloc_dev[ctx->device];
-
-  // Striped table image (same layout the kernel stages into shared memory).
-  fill_table_image(prof, g, table_format(mode), g_noalloc_image);
-
-  QueryDesc q;
-  memset(&q, 0, sizeof(q));
-  q.table = reinterpret_cast<const uint4 *>(scratch + kNoAllocHeader);
-  q.table_bytes = g.table_bytes;
-  q.row_bytes = g.row_bytes;
-  q.copy_bytes = g.copy_bytes;
-  q.smax_off = g.smax_off;
-  q.tail_off = g.tail_off;
-  q.tail_row_bytes = g.tail_row_bytes;
-  q.bias = prof->bias;
-  q.tbm = prof->tbm;
-  q.tec = prof->tec;
-  q.base = prof->base;
-  q.tjb_fixed = prof->tjb_fixed;
-  q.scale = prof->scale;
-  q.tjb = prof->d_tjb;
-  q.n_tjb = prof->n_tjb;
-  q.raw = raw;
-  q.flag = overflow;
-  q.nat = nat;
-  static_assert(sizeof(QueryDesc) + 16 <= 256, "descriptor fits the scratch header");
-  uint32_t *counter = reinterpret_cast<uint32_t *>(scratch + 256);
-  int *status = reinterpret_cast<int *>(scratch + 260);
-
-  const int smem = (int)g.table_bytes;
-  MPF_CUDA(cudaFuncSetAttribute((const void *)fn, cudaFuncAttributeMaxDynamicSharedMemorySize, smem));
-  int per_sm = 0;
-  MPF_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, (const void *)fn, kBlockThreads, smem));
-  if (per_sm < 1) return MPF_EUNSUPPORTED;
-  const uint32_t n_shards = (uint32_t)(ctx->num_sms * per_sm);
-
-  // Every call reuses the same scratch: the table, descriptor, counter and
-  // status are rewritten (the counter and status cleared) on the stream.
-  MPF_CUDA(cudaMemcpyAsync(scratch + kNoAllocHeader, g_noalloc_image, g.table_bytes,
-                           cudaMemcpyHostToDevice, ctx->stream));
-  MPF_CUDA(cudaMemcpyAsync(scratch, &q, sizeof(q), cudaMemcpyHostToDevice, ctx->stream));
-  MPF_CUDA(cudaMemsetAsync(scratch + 256, 0, 8, ctx->stream));
-
-  ScanParams sp;
-  sp.residues = db->d_words;
-  sp.seq_word = db->d_seq_word;
-  sp.seq_len = db->d_seq_len;
-  sp.seq_orig = db->d_seq_orig;
-  sp.n_seqs = (uint32_t)db->n_seqs;
-  sp.pad_word = db->pad_word;
-  sp.queries = reinterpret_cast<const QueryDesc *>(scratch);
-  sp.n_queries = 1;
-  sp.n_shards = n_shards;
-  sp.item_counter = counter;
-  sp.status = status;
-  fn<<<(int)n_shards, kBlockThreads, smem, ctx->stream>>>(sp);
-  MPF_CUDA(cudaGetLastError());
-  return MPF_OK;
-}
-
-// ============================================================ Viterbi filter
-
-struct mpf_vprofile {
-  mpf_ctx *ctx = nullptr;
-  int M = 0, K = 0, Mpad = 0;
-  bool fast = false;            // every transition and special score <= 0
-  int16_t *d_msc = nullptr;     // kVitRows x Mpad (striped when fast)
-  int16_t *d_trans = nullptr;   // kVitTrans x Mpad (striped when fast)
-  int sp[kVitSpecial] = {};
-  int base = 0;
-  float scale = 1.f;
-};
-
-namespace {
-
-// Launch the Viterbi kernels over n_q queries: the general kernel for the
-// profiles with a positive move, the fast kernel for the others, one launch
-// per group of queries that share the fast kernel's launch shape (queries of
-// one launch are scored one after the other by every block).  ranks /
-// n_ranks (nullable) are [n_q][n_seqs] and [n_q] device arrays of selected
-// length ranks.
-int viterbi_enqueue(mpf_ctx *ctx, const mpf_vprofile *const *vps, int n_q, const mpf_db *db,
-                    int16_t *score, uint8_t *flag, float *nat, const uint32_t *ranks,
-                    const uint32_t *n_ranks) {
-  const uint64_t n = db->n_seqs;
-  // Order: general queries first (key -1), then fast ones by launch shape and length.
-  std::vector<std::tuple<int, int, int>> order;   // (key, Mpad, query)
-  std::map<int, int> group_max;                    // key -> longest model of the group
-  for (int q = 0; q < n_q; ++q) {
-    const mpf_vprofile *v = vps[q];
-    const int key = v->fast ? viterbi_fast_shape_key(v->Mpad, db->n_codes, ctx->max_smem) : -1;
-    order.emplace_back(key, v->Mpad, q);
-    group_max[key] = std::max(group_max[key], v->Mpad);
-  }
-  // Groups with the longest models first (the launches are persistent and
-  // fill the GPU in launch order, so the short-model groups finish last and
-  // the final tail is short); within a group, longest models first.
-  std::stable_sort(order.begin(), order.end(), [&](const std::tuple<int, int, int> &a,
-                                                   const std::tuple<int, int, int> &b) {
-    const int ga = group_max[std::get<0>(a)], gb = group_max[std::get<0>(b)];
-    if (ga != gb) return ga > gb;
-    if (std::get<0>(a) != std::get<0>(b)) return std::get<0>(a) < std::get<0>(b);
-    return std::get<1>(a) > std::get<1>(b);
-  });
-  std::vector<VitQuery> qs;
-  qs.reserve((size_t)n_q);
-  for (const auto &o : order) {
-    const int q = std::get<2>(o);
-    const mpf_vprofile *v = vps[q];
-    VitQuery d;
-    memset(&d, 0, sizeof(d));
-    d.msc = v->d_msc;
-    d.trans = v->d_trans;
-    for (int i = 0; i < kVitSpecial; ++i) d.sp[i] = v->sp[i];
-    d.M = v->M;
-    d.Mpad = v->Mpad;
-    d.base = v->base;
-    d.scale = v->scale;
-    d.score = score + (uint64_t)q * n;
-    d.flag = flag + (uint64_t)q * n;
-    d.nat = nat ? nat + (uint64_t)q * n : nullptr;
-    d.ranks = ranks ? ranks + (uint64_t)q * n : nullptr;
-    d.n_ranks = n_ranks ? n_ranks + q : nullptr;
-    qs.push_back(d);
-  }
-  const size_t desc_bytes = sizeof(VitQuery) * (size_t)n_q;
-  uint8_t *dev = nullptr;
-  MPF_CUDA(cudaMallocAsync((void **)&dev, desc_bytes + 4 * (size_t)n_q, ctx->stream));
-  cudaError_t e = cudaMemcpyAsync(dev, qs.data(), desc_bytes, cudaMemcpyHostToDevice, ctx->stream);
-  uint32_t *counters = reinterpret_cast<uint32_t *>(dev + desc_bytes);
-  if (e == cudaSuccess) e = cudaMemsetAsync(counters, 0, 4 * (size_t)n_q, ctx->stream);
-  int rc = e == cudaSuccess ? MPF_OK : MPF_ECUDA;
-  // Groups run concurrently on the context's fork streams, so that one
-  // group's tail overlaps the others' work.
-  std::vector<std::pair<int, int>> groups;
-  for (int first = 0; first < n_q;) {
-    int last = first;
-    while (last < n_q && std::get<0>(order[(size_t)last]) == std::get<0>(order[(size_t)first])) ++last;
-    groups.emplace_back(first, last);
-    first = last;
-  }
-  const bool fork = groups.size() > 1;
-  std::vector<cudaEvent_t> evs;
-  if (fork && rc == MPF_OK) {
-    while (ctx->n_fork < 8 && (size_t)ctx->n_fork < groups.size()) {
-      if (cudaStreamCreateWithFlags(&ctx->fork[ctx->n_fork], cudaStreamNonBlocking) != cudaSuccess) break;
-      ++ctx->n_fork;
-    }
-    for (size_t i = 0; i <= groups.size() && rc == MPF_OK; ++i) {
-      cudaEvent_t ev;
-      if (cudaEventCreateWithFlags(&ev, cudaEventDisableTiming) != cudaSuccess) rc = MPF_ECUDA;
-      else evs.push_back(ev);
-    }
-    if (ctx->n_fork < 1) rc = MPF_ECUDA;
-    if (rc == MPF_OK && cudaEventRecord(evs.back(), ctx->stream) != cudaSuccess) rc = MPF_ECUDA;
-  }
-  for (size_t gi = 0; gi < groups.size() && rc == MPF_OK; ++gi) {
-    const int first = groups[gi].first, last = groups[gi].second;
-    const int key = std::get<0>(order[(size_t)first]);
-    int max_Mpad = 32;
-    for (int i = first; i < last; ++i) max_Mpad = std::max(max_Mpad, std::get<1>(order[(size_t)i]));
-    cudaStream_t st = ctx->stream;
-    if (fork) {
-      st = ctx->fork[gi % (size_t)ctx->n_fork];
-      if (cudaStreamWaitEvent(st, evs.back(), 0) != cudaSuccess) {
-        rc = MPF_ECUDA;
-        break;
-      }
-    }
-    VitParams p;
-    p.residues = db->d_words;
-    p.seq_word = db->d_seq_word;
-    p.seq_len = db->d_seq_len;
-    p.seq_orig = db->d_seq_orig;
-    p.n_seqs = (uint32_t)n;
-    p.n_queries = (uint32_t)(last - first);
-    p.max_Mpad = max_Mpad;
-    p.queries = reinterpret_cast<const VitQuery *>(dev) + first;
-    p.counters = counters + first;
-    const int lr = launch_viterbi(p, key >= 0, db->n_codes, ctx->max_smem, ctx->num_sms, st);
-    if (lr) rc = lr == 2 ? MPF_EUNSUPPORTED : MPF_ECUDA;
-    if (fork && cudaEventRecord(evs[gi], st) != cudaSuccess) rc = MPF_ECUDA;
-  }
-  if (fork) {
-    // Join every fork stream that may have work queued, then release the events.
-    for (size_t gi = 0; gi < groups.size() && gi + 1 < evs.size(); ++gi)
-      if (cudaStreamWaitEvent(ctx->stream, evs[gi], 0) != cudaSuccess) rc = MPF_ECUDA;
-    for (cudaEvent_t ev : evs) cudaEventDestroy(ev);
-  }
-  cudaFreeAsync(dev, ctx->stream);
-  (void)cudaGetLastError();
-  return rc;
-}
-
-bool vit_args_ok(mpf_ctx *ctx, const mpf_vprofile *const *vps, int n_q, const mpf_db *db) {
-  if (!ctx || !vps || n_q < 1 || !db || db->ctx->device != ctx->device) return false;
-  for (int q = 0; q < n_q; ++q)
-    if (!vps[q] || vps[q]->ctx->device != ctx->device) return false;
-  return true;
-}
-
-}  // namespace
-
-extern "C" {
-
-int mpf_vit_profile_create(mpf_ctx *ctx, int M, int K, const int16_t *msc, const int16_t *trans,
-                           const int16_t *special, int base, float scale, mpf_vprofile **out) {
-  if (!out) return MPF_EINVAL;
-  *out = nullptr;
-  if (!ctx || !msc || !trans || !special || M < 1 || K < 1 || K > kVitRows) return MPF_EINVAL;
-  if (base < -32768 || base > 32767 || !isfinite(scale) || !(scale > 0.f)) return MPF_EINVAL;
-  if (M > kStripedMaxM) return MPF_EUNSUPPORTED;
-  const int Mpad = (M + 31) & ~31, Q = Mpad / 32;
-  bool fast = true;
-  for (size_t i = 0; i < (size_t)kVitTrans * M; ++i) fast = fast && trans[i] <= 0;
-  for (int i = 0; i < kVitSpecial; ++i) fast = fast && special[i] <= 0;
-  const size_t need = fast ? viterbi_fast_smem_bytes(Mpad, 1) : viterbi_smem_bytes(Mpad);
-  if (need > (size_t)ctx->max_smem) return MPF_EUNSUPPORTED;
-  std::vector<int16_t> hm((size_t)kVitRows * Mpad, (int16_t)-32768);
-  std::vector<int16_t> ht((size_t)kVitTrans * Mpad, (int16_t)-32768);
-  if (fast) {
-    // Striped: node k = l*Q + j in slot j*32 + l; transitions 8 per slot.
-    for (int k = 0; k < M; ++k) {
-      const size_t slot = (size_t)(k % Q) * 32 + (size_t)(k / Q);
-      for (int x = 0; x < K; ++x) hm[(size_t)x * Mpad + slot] = msc[(size_t)x * M + k];
-      for (int t = 0; t < kVitTrans; ++t) ht[slot * kVitTrans + t] = trans[(size_t)t * M + k];
-    }
-  } else {
-    for (int x = 0; x < K; ++x)
-      memcpy(&hm[(size_t)x * Mpad], msc + (size_t)x * M, sizeof(int16_t) * (size_t)M);
-    for (int t = 0; t < kVitTrans; ++t)
-      memcpy(&ht[(size_t)t * Mpad], trans + (size_t)t * M, sizeof(int16_t) * (size_t)M);
-  }
-  mpf_vprofile *v = new (std::nothrow) mpf_vprofile;
-  if (!v) return MPF_ENOMEM;
-  v->fast = fast;
-  v->ctx = ctx;
-  v->M = M;
-  v->K = K;
-  v->Mpad = Mpad;
-  for (int i = 0; i < kVitSpecial; ++i) v->sp[i] = special[i];
-  v->base = base;
-  v->scale = scale;
-  DeviceGuard dg(ctx->device);
-  cudaError_t e = cudaMalloc(&v->d_msc, hm.size() * sizeof(int16_t));
-  if (e == cudaSuccess) e = cudaMalloc(&v->d_trans, ht.size() * sizeof(int16_t));
-  if (e == cudaSuccess) e = cudaMemcpy(v->d_msc, hm.data(), hm.size() * sizeof(int16_t), cudaMemcpyHostToDevice);
-  if (e == cudaSuccess) e = cudaMemcpy(v->d_trans, ht.data(), ht.size() * sizeof(int16_t), cudaMemcpyHostToDevice);
-  if (e != cudaSuccess) {
-    (void)cudaGetLastError();
-    mpf_vit_profile_destroy(v);
-    return e == cudaErrorMemoryAllocation ? MPF_ENOMEM : MPF_ECUDA;
-  }
-  *out = v;
-  return MPF_OK;
-}
-
-void mpf_vit_profile_destroy(mpf_vprofile *v) {
-  if (!v) return;
-  DeviceGuard dg(v->ctx->device);
-  cudaStreamSynchronize(v->ctx->stream);
-  cudaFree(v->d_msc);
-  cudaFree(v->d_trans);
-  (void)cudaGetLastError();
-  delete v;
-}
-
-int mpf_viterbi_scan(mpf_ctx *ctx, const mpf_vprofile *const *vps, int n_q, const mpf_db *db,
-                     int16_t *score, uint8_t *overflow, float *nat) {
-  if (!vit_args_ok(ctx, vps, n_q, db) || !score || !overflow) return MPF_EINVAL;
-  DeviceGuard dg(ctx->device);
-  const uint64_t n = (uint64_t)n_q * db->n_seqs;
-  if (db->n_seqs == 0) return MPF_OK;
-  const bool device_out = is_device_ptr(score) && is_device_ptr(overflow) && (!nat || is_device_ptr(nat));
-  if (device_out) return viterbi_enqueue(ctx, vps, n_q, db, score, overflow, nat, nullptr, nullptr);
-  int rc = ensure_out_scratch(ctx, (size_t)n * 7 + 64);
-  if (rc) return rc;
-  uint8_t *base = (uint8_t *)ctx->d_out;
-  float *k_nat = nat ? (float *)base : nullptr;
-  int16_t *k_score = reinterpret_cast<int16_t *>(base + (size_t)n * 4);
-  uint8_t *k_flag = base + (size_t)n * 6;
-  rc = viterbi_enqueue(ctx, vps, n_q, db, k_score, k_flag, k_nat, nullptr, nullptr);
-  if (rc == MPF_OK) {
-    cudaError_t e = cudaMemcpyAsync(score, k_score, n * 2, cudaMemcpyDefault, ctx->stream);
-    if (e == cudaSuccess) e = cudaMemcpyAsync(overflow, k_flag, n, cudaMemcpyDefault, ctx->stream);
-    if (e == cudaSuccess && nat) e = cudaMemcpyAsync(nat, k_nat, n * 4, cudaMemcpyDefault, ctx->stream);
-    if (e != cudaSuccess) rc = MPF_ECUDA;
-  }
-  if (cudaStreamSynchronize(ctx->stream) != cudaSuccess && rc == MPF_OK) rc = MPF_ECUDA;
-  (void)cudaGetLastError();
-  return rc;
-}
-
-int mpf_viterbi_rescore(mpf_ctx *ctx, const mpf_vprofile *const *vps, int n_q, const mpf_db *db,
-                        const uint8_t *msv_flag, const float *msv_nat, float msv_min_nat,
-                        int16_t *score, uint8_t *overflow, float *nat, uint32_t *n_pass) {
-  if (!vit_args_ok(ctx, vps, n_q, db) || !msv_flag || !msv_nat || !score || !overflow || !n_pass ||
-      isnan(msv_min_nat))
-    return MPF_EINVAL;
-  DeviceGuard dg(ctx->device);
-  for (const void *ptr : {(const void *)msv_flag, (const void *)msv_nat, (const void *)score,
-                          (const void *)overflow, (const void *)n_pass})
-    if (!is_device_ptr(ptr)) return MPF_EINVAL;
-  if (nat && !is_device_ptr(nat)) return MPF_EINVAL;
-  const uint64_t n = db->n_seqs;
-  const uint64_t n_chunks = (n + kSelectChunk - 1) / kSelectChunk;
-  uint32_t *ranks = nullptr, *n_ranks = nullptr, *chunk = nullptr;
-  cudaError_t e = cudaMallocAsync((void **)&ranks, std::max<uint64_t>(1, (uint64_t)n_q * n) * 4, ctx->stream);
-  if (e == cudaSuccess) e = cudaMallocAsync((void **)&n_ranks, (size_t)n_q * 4, ctx->stream);
-  if (e == cudaSuccess) e = cudaMallocAsync((void **)&chunk, std::max<uint64_t>(1, 2 * (uint64_t)n_q * n_chunks) * 4, ctx->stream);
-  int rc = e == cudaSuccess ? MPF_OK : (e == cudaErrorMemoryAllocation ? MPF_ENOMEM : MPF_ECUDA);
-  if (rc == MPF_OK && launch_select(db->d_seq_orig, n, n_q, msv_flag, msv_nat, msv_min_nat, score, 2,
-                                    overflow, nat, chunk, chunk + (uint64_t)n_q * n_chunks, ranks,
-                                    n_ranks, ctx->stream) != 0)
-    rc = MPF_ECUDA;
-  if (rc == MPF_OK && n > 0) rc = viterbi_enqueue(ctx, vps, n_q, db, score, overflow, nat, ranks, n_ranks);
-  if (rc == MPF_OK && cudaMemcpyAsync(n_pass, n_ranks, (size_t)n_q * 4, cudaMemcpyDeviceToDevice, ctx->stream) != cudaSuccess)
-    rc = MPF_ECUDA;
-  if (ranks) cudaFreeAsync(ranks, ctx->stream);
-  if (n_ranks) cudaFreeAsync(n_ranks, ctx->stream);
-  if (chunk) cudaFreeAsync(chunk, ctx->stream);
-  (void)cudaGetLastError();
-  return rc;
 }
 
 }  // extern "C"
