@@ -564,7 +564,8 @@ def run_profile_case(args):
     prof_rec = next((p for p in wl.profiles if p.M == args.profile_m), None) or \
         synth.make_profile(args.profile_m, rng)
     ctx = mpf.Context(0)
-    db = mpf.Database(ctx, wl.db.residues, wl.db.offsets, wl.db.lengths)
+    k = min(args.profile_seqs or wl.db.n_seqs, wl.db.n_seqs)
+    db = mpf.Database(ctx, wl.db.residues, wl.db.offsets[:k], wl.db.lengths[:k])
     prof = mpf.Profile(ctx, prof_rec)
     n = db.n_seqs
     dev = torch.device("cuda", 0)
@@ -627,6 +628,8 @@ def main():
     ap.add_argument("--serve-requests", type=int, default=24)
     ap.add_argument("--profile-case", action="store_true")
     ap.add_argument("--profile-m", type=int, default=2405)
+    ap.add_argument("--profile-seqs", type=int, default=0,
+                    help="profile case: first N sequences of the database (0: all)")
     ap.add_argument("--profile-viterbi", action="store_true")
     ap.add_argument("--profile-vit-seqs", type=int, default=20000)
     args = ap.parse_args()

@@ -287,7 +287,7 @@ int configure_kernel(mpf_ctx *ctx, LaunchGroup *g) {
     // The DP row is kept as 16-bit pairs unless that leaves fewer than four
     // warps per SM; then as bytes (half the shared memory per warp).
     const bool bytes = 4 * long_smem_per_warp((int)g->long_words, false) > 228 * 1024;
-    g->fn = long_kernel_for(g->mode, bytes);
+    g->fn = long_kernel_for(g->mode, bytes, (int)g->long_words);
     const size_t per_warp = long_smem_per_warp((int)g->long_words, bytes);
     constexpr size_t kKB = 1024;
     size_t ws = (size_t)std::max(g->n_codes, 1) * 128 * g->long_words;

@@ -77,7 +77,7 @@ typedef void (*KernelFn)(ScanParams);
 
 // Long-model kernel (mpf_long_kernel.cu): MODE_LONG_MSV or MODE_LONG_SSV,
 // DP row as 16-bit pairs or (bytes) as bytes.
-KernelFn long_kernel_for(int mode, bool bytes);
+KernelFn long_kernel_for(int mode, bool bytes, int seg_words);
 size_t long_smem_per_warp(int seg_words, bool bytes);
 
 // Stage-to-stage hand-off (mpf_pipeline.cu): SSV -> MSV (raw_bytes 1) and
