@@ -85,7 +85,7 @@ struct RowSlot<true> {
   static __device__ __forceinline__ T join(uint32_t u0, uint32_t u1) { return __byte_perm(u0, u1, 0x6420); }
 };
 
-template <bool MSV, bool B8, int U>
+template <bool MSV, bool B8, int U, bool PF>
 __global__ void __launch_bounds__(kLongThreads) long_kernel(ScanParams sp) {
   typedef RowSlot<B8> Slot;
   extern __shared__ __align__(16) uint32_t lsm[];
@@ -137,9 +137,28 @@ __global__ void __launch_bounds__(kLongThreads) long_kernel(ScanParams sp) {
       const uint32_t *row = tab + (size_t)x * sw * 32;
       if (MSV) umin2 = kU255;
       uint32_t prev = carry << 16, last = kU255;
+      // PF: a rolling window of the next four cost words, so four loads per
+      // lane stay in flight whatever the unroll depth (the cost rows come
+      // from L2 once they no longer fit in L1).
+      uint32_t q0 = 0, q1 = 0, q2 = 0, q3 = 0;
+      if (PF) {
+        q0 = nfull > 0 ? __ldg(row) : 0u;
+        q1 = nfull > 1 ? __ldg(row + 32) : 0u;
+        q2 = nfull > 2 ? __ldg(row + 64) : 0u;
+        q3 = nfull > 3 ? __ldg(row + 96) : 0u;
+      }
 #pragma unroll U
       for (int w = 0; w < nfull; ++w) {
-        const uint32_t cw = __ldg(row + (size_t)w * 32);
+        uint32_t cw;
+        if (PF) {
+          cw = q0;
+          q0 = q1;
+          q1 = q2;
+          q2 = q3;
+          q3 = w + 4 < nfull ? __ldg(row + (size_t)(w + 4) * 32) : 0u;
+        } else {
+          cw = __ldg(row + (size_t)w * 32);
+        }
         uint32_t sx, sy;
         Slot::split(st[(size_t)w * 32], sx, sy);
         const uint32_t u0 = cell_pair<MSV>(diag_pair(prev, sx), lo_cost_pair(cw), negbias2, bias2, uBb2);
@@ -199,16 +218,18 @@ __global__ void __launch_bounds__(kLongThreads) long_kernel(ScanParams sp) {
 
 }  // namespace
 
-// Unroll depth of the word loop (more cost loads in flight per warp; measured
-// on one query against 10,000-40,000 sequences): 8 for segments of at most 48
-// words (M <= 6,144; 9-16% faster than 4), 16 with byte rows (M = 40,000:
-// 35% faster), 4 in between (deeper unrolling cost a resident block there).
+// Unroll depth of the word loop and the rolling cost prefetch (measured on
+// one query against 3,000-40,000 sequences): unroll 8 for segments of at most
+// 48 words (M <= 6,144; 9-16% faster than 4), 16 with byte rows (M = 40,000:
+// 35% faster), 4 in between; the prefetch for MSV in those two bands
+// (M = 12,345: 1,597 against 1,138 GCUPS; M = 40,000: 934 against 877), not
+// for MSV at unroll 8 (mixed) nor for SSV (slower).
 KernelFn long_kernel_for(int mode, bool bytes, int seg_words) {
   const bool msv = mode == MODE_LONG_MSV;
   if (mode != MODE_LONG_MSV && mode != MODE_LONG_SSV) return nullptr;
-  if (bytes) return msv ? long_kernel<true, true, 16> : long_kernel<false, true, 16>;
-  if (seg_words <= 48) return msv ? long_kernel<true, false, 8> : long_kernel<false, false, 8>;
-  return msv ? long_kernel<true, false, 4> : long_kernel<false, false, 4>;
+  if (bytes) return msv ? long_kernel<true, true, 16, true> : long_kernel<false, true, 16, false>;
+  if (seg_words <= 48) return msv ? long_kernel<true, false, 8, false> : long_kernel<false, false, 8, false>;
+  return msv ? long_kernel<true, false, 4, true> : long_kernel<false, false, 4, false>;
 }
 
 size_t long_smem_per_warp(int seg_words, bool bytes) {
