@@ -81,3 +81,48 @@ def test_shard_bounds_balance_and_cover():
         tot = [int(lengths[lo:hi].sum()) for lo, hi in b]
         assert max(tot) - min(tot) <= 2 * int(lengths.max())
     assert shard.shard_bounds(np.zeros(0, np.uint32), 4) == [(0, 0)] * 4
+
+
+def _failing_worker(rank, world, port, result_q):
+    """Rank 1 fails before the gather (an exception between steps, none of
+    its work in flight); rank 0 must get an error from its collective within
+    the process group's timeout instead of waiting forever."""
+    import datetime
+    os.environ["MASTER_ADDR"] = "127.0.0.1"
+    os.environ["MASTER_PORT"] = str(port)
+    dist.init_process_group("gloo", rank=rank, world_size=world,
+                            timeout=datetime.timedelta(seconds=5))
+    try:
+        wl = synth.make_workload(0, n_seqs=200)
+        bounds = shard.shard_bounds(wl.db.lengths, world)
+        lo, hi = bounds[rank]
+        local = [torch.zeros(hi - lo, dtype=torch.uint8)]
+        if rank == 1:
+            result_q.put((rank, "raised"))
+            raise RuntimeError("injected rank failure")
+        try:
+            shard.gather_outputs(local, bounds, rank, world)
+            result_q.put((rank, "gathered"))
+        except Exception as e:   # the collective reports the lost peer
+            result_q.put((rank, "error: " + type(e).__name__))
+    finally:
+        try:
+            dist.destroy_process_group()
+        except Exception:
+            pass
+
+
+def test_failed_rank_surfaces_as_a_collective_error():
+    world = 2
+    ctx = mp.get_context("spawn")
+    q = ctx.Queue()
+    port = _free_port()
+    procs = [ctx.Process(target=_failing_worker, args=(r, world, port, q)) for r in range(world)]
+    for pr in procs:
+        pr.start()
+    got = dict(q.get(timeout=120) for _ in range(world))
+    for pr in procs:
+        pr.join(timeout=60)
+    assert got[1] == "raised"
+    assert got[0].startswith("error:")
+    assert procs[1].exitcode != 0
