@@ -63,7 +63,8 @@ enum {
   MPF_ENOMEM = 2,       /* host or device allocation failed                              */
   MPF_ECUDA = 3,        /* a CUDA runtime call failed                                    */
   MPF_ETIMEOUT = 4,     /* a bounded device wait gave up (status word set by a kernel)    */
-  MPF_EUNSUPPORTED = 5  /* valid request the library does not handle (e.g. M too large)  */
+  MPF_EUNSUPPORTED = 5, /* valid request the library does not handle (e.g. M too large)  */
+  MPF_EDEVICE = 6       /* a kernel's index check failed (only libmpf_debug.so checks)    */
 };
 
 enum { MPF_MSV = 0, MPF_SSV = 1 };
@@ -94,8 +95,12 @@ void mpf_ctx_destroy(mpf_ctx *ctx);
 /* The cudaStream_t the context launches on (for events and interop). */
 void *mpf_ctx_stream(mpf_ctx *ctx);
 
-/* Wait for all work queued on the context stream; returns MPF_ETIMEOUT if a
- * kernel reported a bounded wait that gave up. */
+/* Wait for all work queued on the context stream.  Returns MPF_EDEVICE if a
+ * kernel of the debug build (libmpf_debug.so) found an index outside the
+ * buffers it was given (the access was skipped, results are not valid), and
+ * reserves MPF_ETIMEOUT for a bounded device wait that gave up (the current
+ * kernels have no device-side waits).  The status stays set until the
+ * context is destroyed. */
 int mpf_sync(mpf_ctx *ctx);
 
 /*
@@ -305,6 +310,20 @@ int mpf_viterbi_scan(mpf_ctx *ctx, const mpf_vprofile *const *vprofs, int n_q, c
 int mpf_viterbi_rescore(mpf_ctx *ctx, const mpf_vprofile *const *vprofs, int n_q, const mpf_db *db,
                         const uint8_t *msv_flag, const float *msv_nat, float msv_min_nat,
                         int16_t *score, uint8_t *overflow, float *nat, uint32_t *n_pass);
+
+/*
+ * Self-test of the kernels' debug index checks (libmpf_debug.so only: the
+ * library built with -DMPF_DEBUG_CHECKS, whose kernels test every index they
+ * derive from their inputs against the buffers they were given, skip the
+ * access and record the failure in the context's status word).  Launches one
+ * block whose check fails with no access behind it; the next mpf_sync on the
+ * context returns MPF_EDEVICE, as do all later ones (the status is sticky:
+ * use a context of its own).  The paper has no counterpart: this stands in
+ * for a memory checker on a pool where none is available.
+ * Errors: MPF_EINVAL (null context), MPF_EUNSUPPORTED (release library),
+ * MPF_ECUDA.
+ */
+int mpf_debug_check_selftest(mpf_ctx *ctx);
 
 /*
  * Allocation-free scan.  The paper has no counterpart: this entry point exists

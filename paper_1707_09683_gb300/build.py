@@ -18,6 +18,11 @@ ROOT = os.path.dirname(HERE)
 CSRC = os.path.join(HERE, "csrc")
 OBJ = os.path.join(HERE, "_build")
 LIB = os.path.join(HERE, "libmpf.so")
+# Debug build: the same sources with the kernels' index checks
+# (-DMPF_DEBUG_CHECKS): a failed check sets the context's status word and
+# skips the access; mpf_sync then returns MPF_EDEVICE.
+OBJ_DEBUG = os.path.join(HERE, "_build_debug")
+LIB_DEBUG = os.path.join(HERE, "libmpf_debug.so")
 ARCH = "-gencode=arch=compute_103a,code=sm_103a"
 
 
@@ -42,14 +47,16 @@ def _newest_header() -> float:
     return max(os.path.getmtime(h) for h in hs if os.path.exists(h))
 
 
-def _compile(src: str, hdr_time: float, verbose: bool) -> str:
-    obj = os.path.join(OBJ, os.path.basename(src).replace(".cu", ".o"))
+def _compile(src: str, hdr_time: float, verbose: bool, debug: bool = False) -> str:
+    obj = os.path.join(OBJ_DEBUG if debug else OBJ, os.path.basename(src).replace(".cu", ".o"))
     if os.path.exists(obj) and os.path.getmtime(obj) >= max(os.path.getmtime(src), hdr_time):
         return obj
     cmd = [_nvcc(), ARCH, "-O3", "-lineinfo", "-std=c++17", "-Xcompiler", "-fPIC",
            "-Xcompiler", "-O2", "-I", os.path.join(ROOT, "include"), "-c", src, "-o", obj + ".tmp"]
     if verbose:
         cmd.insert(1, "-Xptxas=-v")
+    if debug:
+        cmd.insert(1, "-DMPF_DEBUG_CHECKS")
     r = subprocess.run(cmd, capture_output=True, text=True)
     if r.returncode != 0:
         raise RuntimeError(f"nvcc failed for {src}:\n{r.stdout}\n{r.stderr}")
@@ -59,27 +66,29 @@ def _compile(src: str, hdr_time: float, verbose: bool) -> str:
     return obj
 
 
-def build(verbose: bool = False, jobs: int | None = None) -> str:
-    """Compile and link libmpf.so; returns its path."""
-    os.makedirs(OBJ, exist_ok=True)
+def build(verbose: bool = False, jobs: int | None = None, debug: bool = False) -> str:
+    """Compile and link libmpf.so (libmpf_debug.so with debug=True); returns
+    its path."""
+    obj_dir, lib = (OBJ_DEBUG, LIB_DEBUG) if debug else (OBJ, LIB)
+    os.makedirs(obj_dir, exist_ok=True)
     srcs = sorted(glob.glob(os.path.join(CSRC, "*.cu")))
     hdr = _newest_header()
     jobs = jobs or min(len(srcs), os.cpu_count() or 4)
     with cf.ThreadPoolExecutor(max_workers=jobs) as ex:
-        objs = list(ex.map(lambda s: _compile(s, hdr, verbose), srcs))
+        objs = list(ex.map(lambda s: _compile(s, hdr, verbose, debug), srcs))
     newest = max(os.path.getmtime(o) for o in objs)
-    if os.path.exists(LIB) and os.path.getmtime(LIB) >= newest:
-        return LIB
+    if os.path.exists(lib) and os.path.getmtime(lib) >= newest:
+        return lib
     libdir = _cuda_lib_dir()
-    cmd = [_nvcc(), ARCH, "-shared", "-cudart", "shared", "-o", LIB + ".tmp", *objs,
+    cmd = [_nvcc(), ARCH, "-shared", "-cudart", "shared", "-o", lib + ".tmp", *objs,
            "-Xlinker", f"-rpath,{libdir}", "-L", libdir]
     r = subprocess.run(cmd, capture_output=True, text=True)
     if r.returncode != 0:
         raise RuntimeError(f"link failed:\n{r.stdout}\n{r.stderr}")
-    os.replace(LIB + ".tmp", LIB)
-    return LIB
+    os.replace(lib + ".tmp", lib)
+    return lib
 
 
 if __name__ == "__main__":
     import sys
-    print(build(verbose="-v" in sys.argv))
+    print(build(verbose="-v" in sys.argv, debug="--debug" in sys.argv))

@@ -470,6 +470,7 @@ int enqueue_group(const mpf_db *db, mpf_ctx *ctx, LaunchGroup &g, cudaStream_t s
   MPF_CUDA(cudaMemsetAsync(g.d_counter, 0, sizeof(uint32_t), st));
   ScanParams sp;
   sp.residues = db->d_words;
+  sp.n_words = db->n_words;
   sp.seq_word = db->d_seq_word;
   sp.seq_len = db->d_seq_len;
   sp.seq_orig = db->d_seq_orig;
@@ -555,7 +556,7 @@ int run_scan(mpf_ctx *ctx, int filter, const mpf_profile *const *profs, int n_q,
   if (rc == MPF_OK) {
     int st = 0;
     if (cudaMemcpy(&st, ctx->d_status, sizeof(int), cudaMemcpyDeviceToHost) != cudaSuccess) return MPF_ECUDA;
-    if (st) return MPF_ETIMEOUT;
+    if (st) return status_code(st);
   }
   return rc;
 }
@@ -578,6 +579,7 @@ const char *mpf_strerror(int status) {
     case MPF_ECUDA: return "CUDA runtime error";
     case MPF_ETIMEOUT: return "bounded device wait timed out";
     case MPF_EUNSUPPORTED: return "unsupported request";
+    case MPF_EDEVICE: return "a kernel's index check failed (debug build)";
     default: return "unknown status";
   }
 }
@@ -648,7 +650,7 @@ int mpf_sync(mpf_ctx *ctx) {
   if (rc) return rc;
   int st = 0;
   MPF_CUDA(cudaMemcpy(&st, ctx->d_status, sizeof(int), cudaMemcpyDeviceToHost));
-  return st ? MPF_ETIMEOUT : MPF_OK;
+  return status_code(st);
 }
 
 int mpf_profile_create(mpf_ctx *ctx, int M, int K, const uint8_t *cost, uint8_t bias_b,
@@ -816,6 +818,7 @@ int mpf_db_upload(mpf_ctx *ctx, const uint8_t *residues, uint64_t n_residues,
   db->pad_word = 0;
   db->n_codes = __builtin_popcount(seen);
   const size_t ns = std::max<uint64_t>(n_seqs, 1);
+  db->n_words = (uint32_t)(chunks * 4);
   cudaError_t e = cudaMalloc(&db->d_words, chunks * 16);
   if (e == cudaSuccess) e = cudaMalloc(&db->d_seq_word, ns * 4);
   if (e == cudaSuccess) e = cudaMalloc(&db->d_seq_len, ns * 4);

@@ -63,6 +63,7 @@ struct mpf_db {
   mpf_ctx *ctx = nullptr;
   uint64_t n_seqs = 0, n_residues = 0;
   uint32_t *d_words = nullptr;      // residue words, sequences 16-byte aligned
+  uint32_t n_words = 0;             // words in d_words
   uint32_t *d_seq_word = nullptr;   // per length rank
   uint32_t *d_seq_len = nullptr;
   uint32_t *d_seq_orig = nullptr;
@@ -105,6 +106,12 @@ inline bool is_device_ptr(const void *p) {
     return false;
   }
   return a.type == cudaMemoryTypeDevice || a.type == cudaMemoryTypeManaged;
+}
+
+// C status code of a nonzero device status word.
+inline int status_code(int st) {
+  if (st == 0) return MPF_OK;
+  return st == kStatusBadIndex ? MPF_EDEVICE : MPF_ETIMEOUT;
 }
 
 // Default (lanes, words) of the striped kernels for a kernel mode.

@@ -5,6 +5,28 @@
 
 namespace mpf {
 
+// Debug builds (compiled with -DMPF_DEBUG_CHECKS, libmpf_debug.so): kernels
+// test their indexes against the buffers they were given; a failed test
+// records kStatusBadIndex in the status word and the access is skipped, so
+// nothing traps.  Release builds compile the tests away.
+constexpr int kStatusBadIndex = 2;
+#ifdef __CUDACC__
+__device__ __forceinline__ void report_bad_index(int *status) {
+  if (status) atomicCAS(status, 0, kStatusBadIndex);
+}
+// Dynamic shared memory of the running block, in bytes.
+__device__ __forceinline__ uint32_t dynamic_smem_bytes() {
+  uint32_t r;
+  asm("mov.u32 %0, %%dynamic_smem_size;" : "=r"(r));
+  return r;
+}
+#endif
+#ifdef MPF_DEBUG_CHECKS
+#define MPF_DCHECK(status, cond) ((cond) || (mpf::report_bad_index(status), false))
+#else
+#define MPF_DCHECK(status, cond) true
+#endif
+
 // Residue code of padding rows.  Database sequences are padded with it to a
 // 16-byte boundary; its table row scores kNegInf at every node, so a padding
 // row leaves every score unchanged (the paper's '#' residue, Sec. 3.2).
@@ -60,6 +82,7 @@ struct QueryDesc {
 
 struct ScanParams {
   const uint32_t *residues;   // residue words (4 codes each)
+  uint32_t n_words;           // words in residues (debug index checks)
   const uint32_t *seq_word;   // per length rank: first word of the sequence
   const uint32_t *seq_len;    // per length rank: length
   const uint32_t *seq_orig;   // per length rank: original sequence number
@@ -116,6 +139,8 @@ struct VitQuery {
 
 struct VitParams {
   const uint32_t *residues;   // database words (4 codes each)
+  uint32_t n_words;           // words in residues (debug index checks)
+  int *status;                // debug index checks (nullable)
   const uint32_t *seq_word;   // per length rank
   const uint32_t *seq_len;
   const uint32_t *seq_orig;

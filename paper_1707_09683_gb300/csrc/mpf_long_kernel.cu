@@ -92,6 +92,10 @@ __global__ void __launch_bounds__(kLongThreads) long_kernel(ScanParams sp) {
   const int lane = threadIdx.x & 31;
   const int warp = threadIdx.x >> 5;
   typename Slot::T *st = reinterpret_cast<typename Slot::T *>(lsm) + (size_t)warp * sp.long_words * 32 + lane;
+  // Debug builds: the warps' DP rows must fit the block's shared memory.
+  if (!MPF_DCHECK(sp.status, (size_t)(blockDim.x >> 5) * sp.long_words * 32 * sizeof(typename Slot::T) <=
+                                 dynamic_smem_bytes()))
+    return;
 
   for (;;) {
     uint32_t it = 0;
@@ -108,10 +112,13 @@ __global__ void __launch_bounds__(kLongThreads) long_kernel(ScanParams sp) {
     }
     if (qi == sp.n_queries) break;
     const QueryDesc &qd = sp.queries[qi];
+    if (!MPF_DCHECK(sp.status, rem < sp.n_seqs && qd.seg_words <= sp.long_words)) continue;
     const uint32_t r = qd.ranks ? __ldg(qd.ranks + rem) : (uint32_t)rem;
+    if (!MPF_DCHECK(sp.status, r < sp.n_seqs)) continue;
     const uint32_t w0 = __ldg(sp.seq_word + r);
     const uint32_t len = __ldg(sp.seq_len + r);
     const uint32_t orig = __ldg(sp.seq_orig + r);
+    if (!MPF_DCHECK(sp.status, (uint64_t)w0 + ((len + 3u) >> 2) <= sp.n_words && orig < sp.n_seqs)) continue;
     const int t = qd.tjb ? (int)__ldg(qd.tjb + min(len, qd.n_tjb - 1u)) : qd.tjb_fixed;
     const int bias = qd.bias;
     const int sw = (int)qd.seg_words;
@@ -133,7 +140,8 @@ __global__ void __launch_bounds__(kLongThreads) long_kernel(ScanParams sp) {
     uint32_t word = 0;
     for (uint32_t i = 0; i < len; ++i) {
       if ((i & 3) == 0) word = __ldg(sp.residues + w0 + (i >> 2));
-      const uint32_t x = (word >> (8 * (i & 3))) & 0xffu;
+      uint32_t x = (word >> (8 * (i & 3))) & 0xffu;
+      if (!MPF_DCHECK(sp.status, x < 32u)) x = 0;
       const uint32_t *row = tab + (size_t)x * sw * 32;
       if (MSV) umin2 = kU255;
       uint32_t prev = carry << 16, last = kU255;

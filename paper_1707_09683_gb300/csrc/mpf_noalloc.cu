@@ -117,6 +117,7 @@ extern "C" int mpf_scan_noalloc(mpf_ctx *ctx, int filter, const mpf_profile *pro
 
   ScanParams sp;
   sp.residues = db->d_words;
+  sp.n_words = db->n_words;
   sp.seq_word = db->d_seq_word;
   sp.seq_len = db->d_seq_len;
   sp.seq_orig = db->d_seq_orig;

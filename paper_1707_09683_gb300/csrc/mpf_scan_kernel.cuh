@@ -138,6 +138,13 @@ __global__ void __launch_bounds__(kBlockThreads, 1) scan_kernel(ScanParams p) {
     if (item >= n_items) break;
     const uint32_t shard = item % p.n_shards;
     const QueryDesc *qd = p.queries + item / p.n_shards;
+    // Debug builds: the table must fit the block's shared memory and the
+    // selected ranks the database (the item is skipped otherwise).
+    if (!MPF_DCHECK(p.status, qd->table_bytes <= dynamic_smem_bytes() && p.pad_word < p.n_words &&
+                                  (!qd->ranks || *qd->n_ranks <= p.n_seqs))) {
+      __syncthreads();
+      continue;
+    }
 
     {  // stage the striped table (16-byte vector copies, coalesced)
       const uint32_t nvec = qd->table_bytes >> 4;
@@ -170,9 +177,10 @@ __global__ void __launch_bounds__(kBlockThreads, 1) scan_kernel(ScanParams p) {
       if (lane == 0) k0 = atomicAdd(&s_next, (uint32_t)G);
       k0 = __shfl_sync(kFull, k0, 0);
       const uint64_t kr = (uint64_t)shard + (uint64_t)(k0 + grp) * p.n_shards;
-      const bool active = kr < n_sel;
+      bool active = kr < n_sel;
       if (!__any_sync(kFull, active)) break;
       const uint64_t r = (ranks && active) ? (uint64_t)__ldg(ranks + kr) : kr;
+      if (active && !MPF_DCHECK(p.status, r < p.n_seqs)) active = false;
 
       // Group state (identical in every lane of a group).
       uint32_t wptr = p.pad_word, orig = 0;
@@ -182,6 +190,12 @@ __global__ void __launch_bounds__(kBlockThreads, 1) scan_kernel(ScanParams p) {
         len = (int)__ldg(p.seq_len + r);
         orig = __ldg(p.seq_orig + r);
         t = tjb ? (int)__ldg(tjb + min((uint32_t)len, n_tjb - 1u)) : tjb_fixed;
+        if (!MPF_DCHECK(p.status, (uint64_t)wptr + (uint64_t)((len + 3) >> 2) <= p.n_words &&
+                                      orig < p.n_seqs)) {
+          active = false;
+          wptr = p.pad_word;
+          len = 0;
+        }
       }
       const uint32_t wstart = wptr;
       const int nsteps = (len + 3) >> 2;           // residue words of this sequence
@@ -211,7 +225,8 @@ __global__ void __launch_bounds__(kBlockThreads, 1) scan_kernel(ScanParams p) {
           // Rows past the end of a sequence read padding codes: their cells
           // score kNegInf, and the special states must not see them.
           const bool real = active && (4 * step + rr) < len;
-          const uint32_t x = (cur >> (8 * rr)) & 0xffu;
+          uint32_t x = (cur >> (8 * rr)) & 0xffu;
+          if (!MPF_DCHECK(p.status, x < (uint32_t)kTableRows)) x = kPadCode;
           const uint8_t *rowp = tbl_lane + x * row_bytes;
           // Diagonal shift (Alg. 5): cell k-1 of the previous row feeds cell k.
           const uint32_t wl = v[H - 1];
@@ -330,7 +345,8 @@ __global__ void __launch_bounds__(kBlockThreads, 1) scan_kernel(ScanParams p) {
             const uint32_t word = __ldg(p.residues + wstart + (uint32_t)w);
 #pragma unroll
             for (int i = 0; i < 4; ++i)
-              if (4 * w + i < len) g = max(g, (int)smax[(word >> (8 * i)) & 0xffu]);
+              if (4 * w + i < len && MPF_DCHECK(p.status, ((word >> (8 * i)) & 0xffu) < (uint32_t)kTableRows))
+                g = max(g, (int)smax[(word >> (8 * i)) & 0xffu]);
           }
         }
         g = group_max<LG>(g);

@@ -128,6 +128,8 @@ int viterbi_enqueue(mpf_ctx *ctx, const mpf_vprofile *const *vps, int n_q, const
     }
     VitParams p;
     p.residues = db->d_words;
+    p.n_words = db->n_words;
+    p.status = ctx->d_status;
     p.seq_word = db->d_seq_word;
     p.seq_len = db->d_seq_len;
     p.seq_orig = db->d_seq_orig;

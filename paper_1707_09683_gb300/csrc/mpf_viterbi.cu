@@ -61,9 +61,12 @@ __device__ __forceinline__ void viterbi_one(const VitParams &p, const VitQuery &
   const int nch = Mpad >> 5;
   const int tNN = Q.sp[0], tNB = Q.sp[1], tEC = Q.sp[2], tCC = Q.sp[3];
   const int tCT = Q.sp[4], tEJ = Q.sp[5], tJJ = Q.sp[6], tJB = Q.sp[7];
+  if (!MPF_DCHECK(p.status, r < p.n_seqs)) return;
   const uint32_t w0 = __ldg(p.seq_word + r);
   const int len = (int)__ldg(p.seq_len + r);
   const uint32_t orig = __ldg(p.seq_orig + r);
+  if (!MPF_DCHECK(p.status, (uint64_t)w0 + (uint64_t)((len + 3) >> 2) <= p.n_words && orig < p.n_seqs))
+    return;
 
   for (int k = lane; k < Mpad; k += 32) sM[k] = sI[k] = sD[k] = (int16_t)-32768;
   __syncwarp();
@@ -73,7 +76,8 @@ __device__ __forceinline__ void viterbi_one(const VitParams &p, const VitQuery &
   uint32_t word = 0;
   for (int i = 0; i < len; ++i) {
     if ((i & 3) == 0) word = __ldg(p.residues + w0 + (uint32_t)(i >> 2));
-    const int x = (int)((word >> (8 * (i & 3))) & 0xffu);
+    int x = (int)((word >> (8 * (i & 3))) & 0xffu);
+    if (!MPF_DCHECK(p.status, x < kVitRows)) x = 0;
     const int16_t *msc_row = Q.msc + (size_t)x * Mpad;
     int coM = -32768, coI = -32768, coD = -32768;   // previous row, node before the chunk
     int cnM = -32768, cnD = -32768;                  // this row, node before the chunk
@@ -164,9 +168,11 @@ __global__ void __launch_bounds__(kVitThreads) viterbi_kernel(VitParams p) {
   int16_t *sM = vsm + (size_t)warp * 3 * p.max_Mpad;
   int16_t *sI = sM + p.max_Mpad;
   int16_t *sD = sI + p.max_Mpad;
+  if (!MPF_DCHECK(p.status, (size_t)(blockDim.x >> 5) * 3 * p.max_Mpad * 2 <= dynamic_smem_bytes())) return;
   for (uint32_t qi = 0; qi < p.n_queries; ++qi) {
     const VitQuery Q = p.queries[qi];
     const uint64_t n_sel = Q.ranks ? (uint64_t)*Q.n_ranks : (uint64_t)p.n_seqs;
+    if (!MPF_DCHECK(p.status, Q.Mpad <= p.max_Mpad && n_sel <= p.n_seqs)) continue;
     for (;;) {
       uint32_t q = 0;
       if (lane == 0) q = atomicAdd(p.counters + qi, 1u);
@@ -244,10 +250,15 @@ __global__ void __launch_bounds__(kVitFastMaxThreads, 1) viterbi_fast_kernel(Vit
   int16_t *sM = reinterpret_cast<int16_t *>(fsm + (size_t)Qmax * 32) + (size_t)warp * Qmax * 32 * (ND ? 2 : 3);
   int16_t *sI = sM + (size_t)Qmax * 32;
   int16_t *sD = sI + (size_t)Qmax * 32;   // unused with ND
+  // Debug builds: the transitions and the warps' DP rows must fit the block's
+  // shared memory.
+  if (!MPF_DCHECK(p.status, (size_t)Qmax * 32 * (16 + (blockDim.x >> 5) * (ND ? 4 : 6)) <= dynamic_smem_bytes()))
+    return;
 
   for (uint32_t qi = 0; qi < p.n_queries; ++qi) {
     const VitQuery Q = p.queries[qi];
     const int nq = Q.Mpad >> 5;
+    if (!MPF_DCHECK(p.status, Q.Mpad <= p.max_Mpad && (!Q.ranks || *Q.n_ranks <= p.n_seqs))) continue;
     __syncthreads();   // every warp is done with the previous query's table
     const uint4 *gtr = reinterpret_cast<const uint4 *>(Q.trans);
     for (int i = threadIdx.x; i < nq * 32; i += blockDim.x) tr[i] = __ldg(gtr + i);
@@ -284,9 +295,12 @@ __global__ void __launch_bounds__(kVitFastMaxThreads, 1) viterbi_fast_kernel(Vit
       q = __shfl_sync(kAll, q, 0);
       if ((uint64_t)q >= n_sel) break;
       const uint32_t r = Q.ranks ? __ldg(Q.ranks + q) : q;
+      if (!MPF_DCHECK(p.status, r < p.n_seqs)) continue;
       const uint32_t w0 = __ldg(p.seq_word + r);
       const int len = (int)__ldg(p.seq_len + r);
       const uint32_t orig = __ldg(p.seq_orig + r);
+      if (!MPF_DCHECK(p.status, (uint64_t)w0 + (uint64_t)((len + 3) >> 2) <= p.n_words && orig < p.n_seqs))
+        continue;
 
       for (int j = 0; j < nq; ++j) {
         sM[j * 32 + lane] = sI[j * 32 + lane] = (int16_t)kNeg;
@@ -302,7 +316,8 @@ __global__ void __launch_bounds__(kVitFastMaxThreads, 1) viterbi_fast_kernel(Vit
       uint32_t word = 0;
       for (int i = 0; i < len; ++i) {
         if ((i & 3) == 0) word = __ldg(p.residues + w0 + (uint32_t)(i >> 2));
-        const int x = (int)((word >> (8 * (i & 3))) & 0xffu);
+        int x = (int)((word >> (8 * (i & 3))) & 0xffu);
+        if (!MPF_DCHECK(p.status, x < kVitRows)) x = 0;
         const int16_t *erow = Q.msc + (size_t)x * nq * 32 + lane;
 
         // Sweep the segment: the previous row's delete chain is completed on

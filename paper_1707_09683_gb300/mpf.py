@@ -17,8 +17,10 @@ import numpy as np
 
 _HERE = os.path.dirname(os.path.abspath(__file__))
 LIB_PATH = os.path.join(_HERE, "libmpf.so")
+# The same library with the kernels' debug index checks (build(debug=True)).
+DEBUG_LIB_PATH = os.path.join(_HERE, "libmpf_debug.so")
 
-MPF_OK, MPF_EINVAL, MPF_ENOMEM, MPF_ECUDA, MPF_ETIMEOUT, MPF_EUNSUPPORTED = range(6)
+MPF_OK, MPF_EINVAL, MPF_ENOMEM, MPF_ECUDA, MPF_ETIMEOUT, MPF_EUNSUPPORTED, MPF_EDEVICE = range(7)
 MSV, SSV = 0, 1
 ARITH_AUTO, ARITH_I16, ARITH_F16 = 0, 1, 2
 
@@ -77,6 +79,7 @@ def load(path: str = LIB_PATH):
         "mpf_scan_noalloc": (i32, [vp, i32, vp, vp, vp, vp, vp]),
         "mpf_pipeline_scan": (i32, [vp, vp, i32, vp, ctypes.c_float, vp, vp, vp, vp, vp, vp, vp]),
         "mpf_pvalues": (i32, [vp, vp, u64, ctypes.c_float, ctypes.c_float, vp]),
+        "mpf_debug_check_selftest": (i32, [vp]),
         "mpf_vit_profile_create": (i32, [vp, i32, i32, vp, vp, vp, i32, ctypes.c_float,
                                          ctypes.POINTER(vp)]),
         "mpf_vit_profile_destroy": (None, [vp]),
@@ -435,3 +438,9 @@ def viterbi_rescore(ctx: Context, vprofs: Sequence[VitProfile], db: Database, ms
                                       _ptr(msv_nat), float(msv_min_nat), _ptr(score),
                                       _ptr(overflow), _ptr(nat), _ptr(n_pass)),
            "mpf_viterbi_rescore")
+
+
+def debug_check_selftest(ctx: Context):
+    """``mpf_debug_check_selftest``: one failing index check (debug library);
+    the next ``ctx.sync()`` raises MpfError(MPF_EDEVICE)."""
+    _check(load().mpf_debug_check_selftest(ctx.handle), "mpf_debug_check_selftest")
