@@ -80,3 +80,97 @@ def test_overflow_batch_full_database():
 def test_throughput_workload_full_database():
     wl = synth.make_workload(4, n_queries=12)
     run_and_check(wl, list(range(12)), np.random.default_rng(13))
+
+
+def test_pipeline_and_viterbi_stage_full_database():
+    """The three stages as the bench times them (workload 1 in full, SSV
+    threshold at the 98th percentile of the SSV nat scores, the same value
+    for MSV -> Viterbi); sampled sequences checked one by one."""
+    wl = synth.make_workload(1)
+    rng = np.random.default_rng(14)
+    ctx = mpf.Context(0)
+    db = mpf.Database(ctx, wl.db.residues, wl.db.offsets, wl.db.lengths)
+    profs = [mpf.Profile(ctx, p) for p in wl.profiles]
+    vrecs = [synth.make_vit_profile(p.M, np.random.default_rng(500 + i)) for i, p in enumerate(wl.profiles)]
+    vps = [mpf.VitProfile(ctx, v) for v in vrecs]
+    n, q = db.n_seqs, len(profs)
+    dev = torch.device("cuda", 0)
+    mk = lambda t: torch.empty(q * n, dtype=t, device=dev)
+    ssv_out = (mk(torch.uint8), mk(torch.uint8), mk(torch.float32))
+    msv_out = (mk(torch.uint8), mk(torch.uint8), mk(torch.float32))
+    n1 = torch.empty(q, dtype=torch.int32, device=dev)
+    # threshold from a first SSV pass, as the bench does
+    plan = mpf.Plan(ctx, mpf.SSV, profs, db, *ssv_out)
+    plan.launch()
+    ctx.sync()
+    plan.close()
+    sn = ssv_out[2]
+    fin = sn[torch.isfinite(sn)]
+    thr = float(torch.quantile(fin[:: max(1, fin.numel() // 4_000_000)], 0.98))
+    mpf.pipeline_scan(ctx, profs, db, thr, ssv_out, msv_out, n1)
+    vs, vf, vn = mk(torch.int16), mk(torch.uint8), mk(torch.float32)
+    n2 = torch.empty(q, dtype=torch.int32, device=dev)
+    mpf.viterbi_rescore(ctx, vps, db, msv_out[1], msv_out[2], thr, vs, vf, vn, n2)
+    ctx.sync()
+    sr, sf, snat = (t.cpu().numpy() for t in ssv_out)
+    mr, mf, mnat = (t.cpu().numpy() for t in msv_out)
+    gvs, gvf, gvn = vs.cpu().numpy(), vf.cpu().numpy(), vn.cpu().numpy()
+    got1, got2 = n1.cpu().numpy(), n2.cpu().numpy()
+    for i, p in enumerate(wl.profiles):
+        sl = slice(i * n, (i + 1) * n)
+        pass1 = (sf[sl] != 0) | (snat[sl] >= np.float32(thr))
+        pass2 = (mf[sl] == 1) | (mnat[sl] >= np.float32(thr))
+        assert int(got1[i]) == int(pass1.sum()) and int(got2[i]) == int(pass2.sum())
+        assert np.all(mf[sl][~pass1] == 2) and np.all(gvf[sl][~pass2] == 2)
+        idx = sample_index(wl.db, rng, n_random=150, n_edge=20)
+        er, ef, en = oracle.ssv(p, wl.db.residues, wl.db.offsets, wl.db.lengths, index=idx, nthreads=16)
+        j = idx.astype(np.int64)
+        assert np.array_equal(sr[sl][j], er) and np.array_equal(sf[sl][j], ef)
+        assert np.array_equal(snat[sl][j].view(np.uint32), en.view(np.uint32))
+        passing = np.flatnonzero(pass1)
+        take = rng.choice(passing, min(120, passing.size), replace=False).astype(np.uint64)
+        er, ef, en = oracle.msv(p, wl.db.residues, wl.db.offsets, wl.db.lengths, index=take, nthreads=16)
+        k = take.astype(np.int64)
+        assert np.array_equal(mr[sl][k], er) and np.array_equal(mf[sl][k], ef)
+        assert np.array_equal(mnat[sl][k].view(np.uint32), en.view(np.uint32))
+        passing = np.flatnonzero(pass2)
+        take = rng.choice(passing, min(60, passing.size), replace=False).astype(np.uint64)
+        es, ef, en = oracle.viterbi(vrecs[i], wl.db.residues, wl.db.offsets, wl.db.lengths, index=take,
+                                    nthreads=16)
+        k = take.astype(np.int64)
+        assert np.array_equal(gvs[sl][k], es) and np.array_equal(gvf[sl][k], ef)
+        assert np.array_equal(gvn[sl][k].view(np.uint32), en.view(np.uint32))
+    for v in vps:
+        v.close()
+    for p in profs:
+        p.close()
+    db.close()
+    ctx.close()
+
+
+def test_long_model_full_database():
+    """A 5,000-node model (the long-model kernel) against workload 1 in full,
+    as the bench measures it; sampled sequences checked one by one."""
+    wl = synth.make_workload(1)
+    rec = synth.make_profile(5000, np.random.default_rng(900))
+    ctx = mpf.Context(0)
+    db = mpf.Database(ctx, wl.db.residues, wl.db.offsets, wl.db.lengths)
+    prof = mpf.Profile(ctx, rec)
+    n = db.n_seqs
+    dev = torch.device("cuda", 0)
+    rng = np.random.default_rng(15)
+    idx = sample_index(wl.db, rng, n_random=300, n_edge=20)
+    for gf, of in ((mpf.MSV, oracle.MSV), (mpf.SSV, oracle.SSV)):
+        out = [torch.empty(n, dtype=t, device=dev) for t in (torch.uint8, torch.uint8, torch.float32)]
+        plan = mpf.Plan(ctx, gf, [prof], db, *out)
+        plan.launch()
+        ctx.sync()
+        plan.close()
+        got = [t.cpu().numpy() for t in out]
+        want = oracle.scan(of, rec, wl.db.residues, wl.db.offsets, wl.db.lengths, index=idx, nthreads=16)
+        j = idx.astype(np.int64)
+        assert np.array_equal(got[0][j], want[0]) and np.array_equal(got[1][j], want[1])
+        assert np.array_equal(got[2][j].view(np.uint32), want[2].view(np.uint32))
+    prof.close()
+    db.close()
+    ctx.close()
