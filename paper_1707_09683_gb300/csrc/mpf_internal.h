@@ -113,10 +113,8 @@ int launch_select(const uint32_t *seq_orig, uint64_t n, int n_q, const uint8_t *
 int launch_pvalues(const float *nat, uint64_t n, float mu, float lambda, float *p, int num_sms,
                    cudaStream_t st);
 
-// P7Viterbi filter (mpf_viterbi.cu).  Tables are int16 in device memory;
-// -32768 is minus infinity.  General layout: node k (0-based) at column k of
-// rows Mpad long.
-constexpr int kVitThreads = 256;
+// P7Viterbi filter (mpf_viterbi.cu).  Tables are int16 in device memory,
+// striped (node l*Q + j in slot j*32 + l); -32768 is minus infinity.
 constexpr int kVitFastMaxThreads = 512;
 constexpr int kVitRows = 32;         // msc rows: residue codes 0..31
 constexpr int kVitTrans = 8;         // BM, MM, IM, DM, MI, II, MD, DD
@@ -150,16 +148,18 @@ struct VitParams {
   const VitQuery *queries;
   uint32_t *counters;         // one per query, zero before the launch
 };
-// fast: every transition and special score <= 0; tables in the striped
-// layout (msc [32][Q][32] int16, trans [Q][32] x 8 int16 with Q = Mpad / 32).
-// n_codes: distinct residue codes in the database (sizes the L1 share).
-// Returns 0, 1 on a CUDA error, 2 if the rows do not fit in shared memory.
+// fast: every transition and special score <= 0 (else the general kernel);
+// tables in the striped layout (msc [32][Q][32] int16, trans [Q][32] x 8
+// int16 with Q = Mpad / 32).  n_codes: distinct residue codes in the
+// database (sizes the L1 share).  Returns 0, 1 on a CUDA error, 2 if the
+// rows do not fit in shared memory.
 int launch_viterbi(const VitParams &p, bool fast, int n_codes, int max_smem, int num_sms,
                    cudaStream_t st);
-size_t viterbi_smem_bytes(int Mpad);
+// Shared memory of a block of `warps` warps that store the D row.
 size_t viterbi_fast_smem_bytes(int Mpad, int warps);
-// Launch shape of the fast kernel for one model length (equal keys share a launch).
-int viterbi_fast_shape_key(int Mpad, int n_codes, int max_smem);
+// Launch shape of a kernel for one model length (equal keys share a launch),
+// or -1 if no shape fits.
+int viterbi_shape_key(bool fast, int Mpad, int n_codes, int max_smem);
 
 // Kernel instantiation for (lanes, words, mode), or nullptr if not built.
 KernelFn kernel_for(int lanes, int words, int mode);

@@ -23,8 +23,8 @@ struct mpf_vprofile {
   mpf_ctx *ctx = nullptr;
   int M = 0, K = 0, Mpad = 0;
   bool fast = false;            // every transition and special score <= 0
-  int16_t *d_msc = nullptr;     // kVitRows x Mpad (striped when fast)
-  int16_t *d_trans = nullptr;   // kVitTrans x Mpad (striped when fast)
+  int16_t *d_msc = nullptr;     // kVitRows x Mpad, striped
+  int16_t *d_trans = nullptr;   // Mpad x kVitTrans, striped
   int sp[kVitSpecial] = {};
   int base = 0;
   float scale = 1.f;
@@ -34,20 +34,21 @@ namespace {
 
 // Launch the Viterbi kernels over n_q queries: the general kernel for the
 // profiles with a positive move, the fast kernel for the others, one launch
-// per group of queries that share the fast kernel's launch shape (queries of
-// one launch are scored one after the other by every block).  ranks /
+// per group of queries that share a kernel and launch shape (queries of one
+// launch are scored one after the other by every block).  ranks /
 // n_ranks (nullable) are [n_q][n_seqs] and [n_q] device arrays of selected
 // length ranks.
 int viterbi_enqueue(mpf_ctx *ctx, const mpf_vprofile *const *vps, int n_q, const mpf_db *db,
                     int16_t *score, uint8_t *flag, float *nat, const uint32_t *ranks,
                     const uint32_t *n_ranks) {
   const uint64_t n = db->n_seqs;
-  // Order: general queries first (key -1), then fast ones by launch shape and length.
+  // Group by kernel and launch shape (the key), then order by length.
   std::vector<std::tuple<int, int, int>> order;   // (key, Mpad, query)
   std::map<int, int> group_max;                    // key -> longest model of the group
   for (int q = 0; q < n_q; ++q) {
     const mpf_vprofile *v = vps[q];
-    const int key = v->fast ? viterbi_fast_shape_key(v->Mpad, db->n_codes, ctx->max_smem) : -1;
+    const int key = viterbi_shape_key(v->fast, v->Mpad, db->n_codes, ctx->max_smem);
+    if (key < 0) return MPF_EUNSUPPORTED;
     order.emplace_back(key, v->Mpad, q);
     group_max[key] = std::max(group_max[key], v->Mpad);
   }
@@ -138,7 +139,8 @@ int viterbi_enqueue(mpf_ctx *ctx, const mpf_vprofile *const *vps, int n_q, const
     p.max_Mpad = max_Mpad;
     p.queries = reinterpret_cast<const VitQuery *>(dev) + first;
     p.counters = counters + first;
-    const int lr = launch_viterbi(p, key >= 0, db->n_codes, ctx->max_smem, ctx->num_sms, st);
+    const int lr = launch_viterbi(p, vps[std::get<2>(order[(size_t)first])]->fast, db->n_codes, ctx->max_smem,
+                                  ctx->num_sms, st);
     if (lr) rc = lr == 2 ? MPF_EUNSUPPORTED : MPF_ECUDA;
     if (fork && cudaEventRecord(evs[gi], st) != cudaSuccess) rc = MPF_ECUDA;
   }
@@ -175,22 +177,14 @@ int mpf_vit_profile_create(mpf_ctx *ctx, int M, int K, const int16_t *msc, const
   bool fast = true;
   for (size_t i = 0; i < (size_t)kVitTrans * M; ++i) fast = fast && trans[i] <= 0;
   for (int i = 0; i < kVitSpecial; ++i) fast = fast && special[i] <= 0;
-  const size_t need = fast ? viterbi_fast_smem_bytes(Mpad, 1) : viterbi_smem_bytes(Mpad);
-  if (need > (size_t)ctx->max_smem) return MPF_EUNSUPPORTED;
+  if (viterbi_fast_smem_bytes(Mpad, 1) > (size_t)ctx->max_smem) return MPF_EUNSUPPORTED;
   std::vector<int16_t> hm((size_t)kVitRows * Mpad, (int16_t)-32768);
   std::vector<int16_t> ht((size_t)kVitTrans * Mpad, (int16_t)-32768);
-  if (fast) {
-    // Striped: node k = l*Q + j in slot j*32 + l; transitions 8 per slot.
-    for (int k = 0; k < M; ++k) {
-      const size_t slot = (size_t)(k % Q) * 32 + (size_t)(k / Q);
-      for (int x = 0; x < K; ++x) hm[(size_t)x * Mpad + slot] = msc[(size_t)x * M + k];
-      for (int t = 0; t < kVitTrans; ++t) ht[slot * kVitTrans + t] = trans[(size_t)t * M + k];
-    }
-  } else {
-    for (int x = 0; x < K; ++x)
-      memcpy(&hm[(size_t)x * Mpad], msc + (size_t)x * M, sizeof(int16_t) * (size_t)M);
-    for (int t = 0; t < kVitTrans; ++t)
-      memcpy(&ht[(size_t)t * Mpad], trans + (size_t)t * M, sizeof(int16_t) * (size_t)M);
+  // Striped: node k = l*Q + j in slot j*32 + l; transitions 8 per slot.
+  for (int k = 0; k < M; ++k) {
+    const size_t slot = (size_t)(k % Q) * 32 + (size_t)(k / Q);
+    for (int x = 0; x < K; ++x) hm[(size_t)x * Mpad + slot] = msc[(size_t)x * M + k];
+    for (int t = 0; t < kVitTrans; ++t) ht[slot * kVitTrans + t] = trans[(size_t)t * M + k];
   }
   mpf_vprofile *v = new (std::nothrow) mpf_vprofile;
   if (!v) return MPF_ENOMEM;

@@ -1,38 +1,38 @@
 // mpf_viterbi.cu -- the P7Viterbi filter (Eq. 1 of Sec. 2.1) for sm_103a.
 //
-// One warp scores one sequence; all arithmetic is the 16-bit saturating word
-// arithmetic of the Viterbi filter, carried in 32-bit registers.  Two kernels:
-//
-// viterbi_kernel (any profile).  The DP row (M, I, D of every node) lives in
-// the warp's slice of shared memory and is swept in chunks of 32 consecutive
-// nodes, node k handled by lane k mod 32:
-//   * the diagonal terms of Eq. 1 (node k-1 of the previous row) come from the
-//     neighbouring lane by one shuffle, and from the previous chunk's last
-//     lane across a chunk boundary;
-//   * the insert term uses the same node of the previous row (lane-local);
+// One warp scores one sequence against one query, in the 16-bit saturating
+// word arithmetic of the Viterbi filter carried in 32-bit registers.  Lane l
+// owns a contiguous segment of Q = ceil(M/32) nodes (Farrar's striped order:
+// node l*Q + j sits in slot j*32 + l, so every shared access of a warp is one
+// contiguous line).  Per DP row each lane sweeps its segment once:
+//   * the diagonal terms of Eq. 1 (node k-1 of the previous row) come from
+//     the lane's previous node, or for a segment's first node from the last
+//     node of the lane before (one shuffle per row);
+//   * the insert term uses the same node of the previous row;
 //   * the delete chain D[k] = max(M[k-1] + tMD, D[k-1] + tDD) runs along the
-//     row: each node is the map d -> max(A, min(d + B, C)) of its
-//     predecessor, these maps compose, and a 5-step warp scan gives every lane
-//     its node's value from the chunk's carry-in;
-//   * E is a warp max, then the N, C, J, B special states are scalar.
+//     row.  Each lane computes a segment-local chain that assumes minus
+//     infinity enters the segment; each segment is a map d -> max(A,
+//     min(d + B, C)) of the delete score entering it, these maps compose, and
+//     a 5-step warp scan gives the true delete score entering every segment.
+//     The next row completes the previous row's chain on the fly (D' =
+//     max(local D', carried chain)), so no second pass is needed;
+//   * E is a warp maximum, then the N, C, J, B special states are scalar.
 //
-// viterbi_fast_kernel (every transition and special score <= 0, as for any
-// profile of log-probabilities).  Then no sum can pass the upper bound
-// except M[k] itself, whose saturation at 32767 is the overflow, so every
-// sat() reduces to max(., -32768) and a chain of them to one DPX
-// add-then-max per term; and D[k] <= max of the M of earlier nodes, so E is
-// the maximum of M alone.  Lane l owns a contiguous segment of Q = ceil(M/32)
-// nodes (Farrar's striped order: node l*Q + j sits in slot j*32 + l, so
-// every shared access of a warp is one contiguous line):
-//   pass 1  each lane sweeps its segment, computing M and I and a local
-//           delete chain that assumes minus infinity enters the segment;
-//   carry   the delete score entering each segment is an exclusive warp scan
-//           of the segments' maps d -> max(A, d + B) (B = sum of tDD over the
-//           segment, a per-query constant);
-//   pass 2  each lane raises its local delete chain by the entering score
-//           only while that raises anything (the "lazy F" idea of the SIMD
-//           Viterbi of HMMER3): once the carried value falls below the local
-//           chain it can never win again.
+// viterbi_fast_kernel takes profiles whose transition and special scores are
+// all <= 0 (any profile of log-probabilities).  Then no sum can pass the
+// upper bound except M[k] itself, whose saturation at 32767 is the overflow,
+// so every sat() reduces to max(., -32768), a chain of them to one DPX
+// add-then-max per term, the maps lose their cap (C), and D[k] <= max of the
+// M of earlier nodes, so E is the maximum of M alone.
+//
+// viterbi_general_kernel takes any int16 scores: every sum is clamped on
+// both sides, the maps keep their cap, -32768 is a number that positive moves
+// can raise (so the carried chain of the row before the first starts at true
+// minus infinity, not at -32768, and D_1 = -32768 re-enters every row), and
+// E also takes the true delete scores: the local chain's maximum and the
+// carried chain's, whose maximum over a segment is its entry value plus the
+// largest prefix sum of tDD there (once a cap binds the row has overflowed).
+//
 // The transition table is staged once per query into shared memory and read
 // by all warps of a block; match scores are read from global memory in the
 // same striped order.
@@ -50,139 +50,6 @@ namespace mpf {
 namespace {
 
 constexpr uint32_t kAll = 0xffffffffu;
-
-__device__ __forceinline__ int sat16(int v) { return min(32767, max(-32768, v)); }
-
-// Score one sequence (length-rank r) against query Q; the warp's three DP
-// rows are sM, sI, sD (Mpad int16 each).
-__device__ __forceinline__ void viterbi_one(const VitParams &p, const VitQuery &Q, uint32_t r,
-                                            int16_t *sM, int16_t *sI, int16_t *sD, int lane) {
-  const int Mpad = Q.Mpad, M = Q.M;
-  const int nch = Mpad >> 5;
-  const int tNN = Q.sp[0], tNB = Q.sp[1], tEC = Q.sp[2], tCC = Q.sp[3];
-  const int tCT = Q.sp[4], tEJ = Q.sp[5], tJJ = Q.sp[6], tJB = Q.sp[7];
-  if (!MPF_DCHECK(p.status, r < p.n_seqs)) return;
-  const uint32_t w0 = __ldg(p.seq_word + r);
-  const int len = (int)__ldg(p.seq_len + r);
-  const uint32_t orig = __ldg(p.seq_orig + r);
-  if (!MPF_DCHECK(p.status, (uint64_t)w0 + (uint64_t)((len + 3) >> 2) <= p.n_words && orig < p.n_seqs))
-    return;
-
-  for (int k = lane; k < Mpad; k += 32) sM[k] = sI[k] = sD[k] = (int16_t)-32768;
-  __syncwarp();
-  int xN = Q.base, xJ = -32768, xC = -32768;
-  int xB = sat16(xN + tNB);
-  bool ovf = false;
-  uint32_t word = 0;
-  for (int i = 0; i < len; ++i) {
-    if ((i & 3) == 0) word = __ldg(p.residues + w0 + (uint32_t)(i >> 2));
-    int x = (int)((word >> (8 * (i & 3))) & 0xffu);
-    if (!MPF_DCHECK(p.status, x < kVitRows)) x = 0;
-    const int16_t *msc_row = Q.msc + (size_t)x * Mpad;
-    int coM = -32768, coI = -32768, coD = -32768;   // previous row, node before the chunk
-    int cnM = -32768, cnD = -32768;                  // this row, node before the chunk
-    int xE = -32768;
-    for (int c = 0; c < nch; ++c) {
-      const int k = (c << 5) + lane;                 // 0-based node index
-      const int Mo = sM[k], Io = sI[k], Do = sD[k];
-      int pM = __shfl_up_sync(kAll, Mo, 1);
-      int pI = __shfl_up_sync(kAll, Io, 1);
-      int pD = __shfl_up_sync(kAll, Do, 1);
-      if (lane == 0) {
-        pM = coM;
-        pI = coI;
-        pD = coD;
-      }
-      coM = __shfl_sync(kAll, Mo, 31);
-      coI = __shfl_sync(kAll, Io, 31);
-      coD = __shfl_sync(kAll, Do, 31);
-      const int e = __ldg(msc_row + k);
-      const int16_t *t = Q.trans + k;
-      const int tBM = __ldg(t), tMM = __ldg(t + Mpad), tIM = __ldg(t + 2 * Mpad);
-      const int tDM = __ldg(t + 3 * Mpad), tMI = __ldg(t + 4 * Mpad), tII = __ldg(t + 5 * Mpad);
-      const int tMD = __ldg(t + 6 * Mpad), tDD = __ldg(t + 7 * Mpad);
-      const int best = max(max(sat16(pM + tMM), sat16(pI + tIM)), max(sat16(pD + tDM), sat16(xB + tBM)));
-      const int Mn = sat16(best + e);
-      const int In = (k < M - 1) ? max(sat16(Mo + tMI), sat16(Io + tII)) : -32768;
-      // Delete chain along the row: node k maps the delete score of node k-1
-      // to max(A, min(d + B, C)); an inclusive warp scan composes the maps.
-      int pMn = __shfl_up_sync(kAll, Mn, 1);
-      if (lane == 0) pMn = cnM;
-      int A = sat16(pMn + tMD), B = tDD, C = 32767;
-      if (k == 0) {               // node 1 has no delete state
-        A = -32768;
-        B = -(1 << 20);
-      }
-#pragma unroll
-      for (int off = 1; off < 32; off <<= 1) {
-        const int Ap = __shfl_up_sync(kAll, A, off);
-        const int Bp = __shfl_up_sync(kAll, B, off);
-        const int Cp = __shfl_up_sync(kAll, C, off);
-        if (lane >= off) {        // this lane's map after the earlier lanes' maps
-          A = max(A, min(Ap + B, C));
-          C = min(Cp + B, C);
-          B = Bp + B;
-        }
-      }
-      const int Dn = max(A, min(cnD + B, C));
-      cnM = __shfl_sync(kAll, Mn, 31);
-      cnD = __shfl_sync(kAll, Dn, 31);
-      if (k < M) {
-        xE = max(xE, max(Mn, Dn));
-        sM[k] = (int16_t)Mn;
-        sI[k] = (int16_t)In;
-        sD[k] = (int16_t)Dn;
-      }
-    }
-    xE = __reduce_max_sync(kAll, xE);
-    if (xE >= 32767) {
-      ovf = true;
-      break;
-    }
-    xN = sat16(xN + tNN);
-    xC = max(sat16(xC + tCC), sat16(xE + tEC));
-    xJ = max(sat16(xJ + tJJ), sat16(xE + tEJ));
-    xB = max(sat16(xN + tNB), sat16(xJ + tJB));
-  }
-  if (lane == 0) {
-    if (ovf) {
-      Q.score[orig] = 32767;
-      Q.flag[orig] = 1;
-      if (Q.nat) Q.nat[orig] = __int_as_float(0x7f800000);
-    } else {
-      const int sc = sat16(xC + tCT);
-      Q.score[orig] = (int16_t)sc;
-      Q.flag[orig] = 0;
-      if (Q.nat) Q.nat[orig] = __fsub_rn(__fdiv_rn(__int2float_rn(sc - Q.base), Q.scale), 3.0f);
-    }
-  }
-  __syncwarp();
-}
-
-// Persistent kernel: every warp walks the queries in order and, within a
-// query, pulls the next length rank from that query's counter.
-__global__ void __launch_bounds__(kVitThreads) viterbi_kernel(VitParams p) {
-  extern __shared__ __align__(16) int16_t vsm[];
-  const int lane = threadIdx.x & 31;
-  const int warp = threadIdx.x >> 5;
-  int16_t *sM = vsm + (size_t)warp * 3 * p.max_Mpad;
-  int16_t *sI = sM + p.max_Mpad;
-  int16_t *sD = sI + p.max_Mpad;
-  if (!MPF_DCHECK(p.status, (size_t)(blockDim.x >> 5) * 3 * p.max_Mpad * 2 <= dynamic_smem_bytes())) return;
-  for (uint32_t qi = 0; qi < p.n_queries; ++qi) {
-    const VitQuery Q = p.queries[qi];
-    const uint64_t n_sel = Q.ranks ? (uint64_t)*Q.n_ranks : (uint64_t)p.n_seqs;
-    if (!MPF_DCHECK(p.status, Q.Mpad <= p.max_Mpad && n_sel <= p.n_seqs)) continue;
-    for (;;) {
-      uint32_t q = 0;
-      if (lane == 0) q = atomicAdd(p.counters + qi, 1u);
-      q = __shfl_sync(kAll, q, 0);
-      if ((uint64_t)q >= n_sel) break;
-      const uint32_t r = Q.ranks ? __ldg(Q.ranks + q) : q;
-      viterbi_one(p, Q, r, sM, sI, sD, lane);
-    }
-  }
-}
 
 // ------------------------------------------------------------ fast kernel
 
@@ -379,18 +246,192 @@ __global__ void __launch_bounds__(kVitFastMaxThreads, 1) viterbi_fast_kernel(Vit
   }
 }
 
+// ---------------------------------------------------------- general kernel
+
+constexpr int kPos = 32767;
+constexpr int kMinusInf = -(1 << 29);   // true minus infinity in 32-bit registers
+
+// sat(a + b), the 16-bit saturating add of the Viterbi filter.
+__device__ __forceinline__ int satadd(int a, int b) { return max(__viaddmin_s32(a, b, kPos), kNeg); }
+
+// Any int16 scores (see the file comment).  Shared memory as for the plain
+// fast kernel: transitions, then per warp the M, I and segment-local D rows.
+template <int U>
+__global__ void __launch_bounds__(kVitFastMaxThreads, 1) viterbi_general_kernel(VitParams p) {
+  extern __shared__ __align__(16) uint4 fsm[];
+  const int lane = threadIdx.x & 31;
+  const int warp = threadIdx.x >> 5;
+  const int Qmax = p.max_Mpad >> 5;
+  uint4 *tr = fsm;
+  int16_t *sM = reinterpret_cast<int16_t *>(fsm + (size_t)Qmax * 32) + (size_t)warp * Qmax * 32 * 3;
+  int16_t *sI = sM + (size_t)Qmax * 32;
+  int16_t *sD = sI + (size_t)Qmax * 32;
+  if (!MPF_DCHECK(p.status, (size_t)Qmax * 32 * (16 + (blockDim.x >> 5) * 6) <= dynamic_smem_bytes()))
+    return;
+
+  for (uint32_t qi = 0; qi < p.n_queries; ++qi) {
+    const VitQuery Q = p.queries[qi];
+    const int nq = Q.Mpad >> 5;
+    if (!MPF_DCHECK(p.status, Q.Mpad <= p.max_Mpad && (!Q.ranks || *Q.n_ranks <= p.n_seqs))) continue;
+    __syncthreads();   // every warp is done with the previous query's table
+    const uint4 *gtr = reinterpret_cast<const uint4 *>(Q.trans);
+    for (int i = threadIdx.x; i < nq * 32; i += blockDim.x) tr[i] = __ldg(gtr + i);
+    __syncthreads();
+
+    // Per-lane constants: the segment's map of the delete score entering it
+    // is d -> max(A, min(d + Bl, Cl)), built from tDD of the first node (t0)
+    // and the composite (Bsuf, Csuf) of x -> min(x + tDD, 32767) over the
+    // others; maxP is the largest prefix sum of those tDD (0 included).
+    const int nv = min(max(Q.M - lane * nq, 0), nq);
+    int t0 = 0, tMD0 = kNeg, Bsuf = 0, Csuf = 1 << 29, maxP = 0;
+    if (nv > 0) {
+      t0 = hi16(tr[lane].w);
+      tMD0 = lo16(tr[lane].w);
+    }
+    for (int j = 1; j < nv; ++j) {
+      const int t = hi16(tr[j * 32 + lane].w);
+      Bsuf += t;
+      Csuf = min(Csuf + t, kPos);
+      maxP = max(maxP, Bsuf);
+    }
+    // Lane 0's segment starts at node 1, whose delete state is fixed: a
+    // constant map.  Lanes without nodes pass the entering score through.
+    int Bl = lane == 0 ? kMinusInf : t0 + Bsuf;
+    int Cl = nv > 0 ? min(kPos + Bsuf, Csuf) : kPos;
+    if (nv == 0 && lane > 0) Bl = 0;
+    // Composites of the maps over the windows (lane - 2^r, lane] of the
+    // Hillis-Steele scan, or a sentinel below the window.
+    int Wb[5], Wc[5];
+    {
+      int B = Bl, C = Cl;
+#pragma unroll
+      for (int r = 0; r < 5; ++r) {
+        Wb[r] = lane >= (1 << r) ? B : kMinusInf;
+        Wc[r] = C;
+        const int Bp = __shfl_up_sync(kAll, B, 1 << r);
+        const int Cp = __shfl_up_sync(kAll, C, 1 << r);
+        if (lane >= (1 << r)) {   // this lane's window after the earlier one
+          C = min(Cp + B, C);
+          B = Bp + B;
+        }
+      }
+    }
+    const int tNN = Q.sp[0], tNB = Q.sp[1], tEC = Q.sp[2], tCC = Q.sp[3];
+    const int tCT = Q.sp[4], tEJ = Q.sp[5], tJJ = Q.sp[6], tJB = Q.sp[7];
+    const uint64_t n_sel = Q.ranks ? (uint64_t)*Q.n_ranks : (uint64_t)p.n_seqs;
+
+    for (;;) {
+      uint32_t q = 0;
+      if (lane == 0) q = atomicAdd(p.counters + qi, 1u);
+      q = __shfl_sync(kAll, q, 0);
+      if ((uint64_t)q >= n_sel) break;
+      const uint32_t r = Q.ranks ? __ldg(Q.ranks + q) : q;
+      if (!MPF_DCHECK(p.status, r < p.n_seqs)) continue;
+      const uint32_t w0 = __ldg(p.seq_word + r);
+      const int len = (int)__ldg(p.seq_len + r);
+      const uint32_t orig = __ldg(p.seq_orig + r);
+      if (!MPF_DCHECK(p.status, (uint64_t)w0 + (uint64_t)((len + 3) >> 2) <= p.n_words && orig < p.n_seqs))
+        continue;
+
+      for (int j = 0; j < nq; ++j) sM[j * 32 + lane] = sI[j * 32 + lane] = sD[j * 32 + lane] = (int16_t)kNeg;
+      int xN = Q.base, xJ = kNeg, xC = kNeg;
+      int xB = satadd(xN, tNB);
+      // Previous row: M, I and true D of the node before the segment, and the
+      // carried delete chain at the segment's first node (row 0 carries none).
+      int pM0 = kNeg, pI0 = kNeg, pD0 = kNeg, X0 = kMinusInf;
+      bool ovf = false;
+      uint32_t word = 0;
+      for (int i = 0; i < len; ++i) {
+        if ((i & 3) == 0) word = __ldg(p.residues + w0 + (uint32_t)(i >> 2));
+        int x = (int)((word >> (8 * (i & 3))) & 0xffu);
+        if (!MPF_DCHECK(p.status, x < kVitRows)) x = 0;
+        const int16_t *erow = Q.msc + (size_t)x * nq * 32 + lane;
+
+        int dM = pM0, dI = pI0, dD = pD0, X = X0, mprev = kNeg, d = kMinusInf;
+        int mxM = kNeg, mxD = kNeg, Mn = kNeg, In = kNeg;
+#pragma unroll U
+        for (int j = 0; j < nv; ++j) {
+          const int sl = j * 32 + lane;
+          const int Mo = sM[sl], Io = sI[sl], Dl = sD[sl];
+          const uint4 t = tr[sl];
+          const int e = __ldg(erow + j * 32);
+          const int tDD = hi16(t.w);
+          if (j > 0) X = __viaddmin_s32(X, tDD, kPos);   // previous row's carried chain
+          const int Do = max(Dl, X);
+          const int best = max(max(__viaddmin_s32(dM, hi16(t.x), kPos), __viaddmin_s32(dI, lo16(t.y), kPos)),
+                               max(__viaddmin_s32(dD, hi16(t.y), kPos), __viaddmin_s32(xB, lo16(t.x), kPos)));
+          Mn = satadd(max(best, kNeg), e);
+          In = max(max(__viaddmin_s32(Mo, lo16(t.z), kPos), __viaddmin_s32(Io, hi16(t.z), kPos)), kNeg);
+          // Segment-local chain: minus infinity enters the segment's first node.
+          d = j > 0 ? max(satadd(mprev, lo16(t.w)), __viaddmin_s32(d, tDD, kPos)) : kMinusInf;
+          mxM = max(mxM, Mn);
+          mxD = max(mxD, d);
+          sM[sl] = (int16_t)Mn;
+          sI[sl] = (int16_t)In;
+          sD[sl] = (int16_t)(j > 0 ? d : kNeg);
+          dM = Mo;
+          dI = Io;
+          dD = Do;
+          mprev = Mn;
+        }
+
+        // True delete score at the end of every segment (inclusive scan of
+        // the segments' maps), the chain carried into the next row, and E.
+        int Mlp = __shfl_up_sync(kAll, Mn, 1);
+        int Ilp = __shfl_up_sync(kAll, In, 1);
+        if (lane == 0) Mlp = Ilp = kNeg;
+        const int a0 = satadd(Mlp, tMD0);
+        int A = nv > 0 ? max(d, min((lane == 0 ? kNeg : a0) + Bsuf, Csuf)) : kMinusInf;
+#pragma unroll
+        for (int rr = 0; rr < 5; ++rr) {
+          const int Ap = __shfl_up_sync(kAll, A, 1 << rr);
+          A = max(A, min(Ap + Wb[rr], Wc[rr]));
+        }
+        int carry = __shfl_up_sync(kAll, A, 1);
+        if (lane == 0) carry = kNeg;
+        const int newX0 = lane == 0 ? kNeg : max(__viaddmin_s32(carry, t0, kPos), a0);
+        const int xd = nv > 0 ? max(mxD, newX0 + maxP) : kNeg;
+        const int xE = __reduce_max_sync(kAll, max(mxM, min(xd, kPos)));
+        if (xE >= kPos) {
+          ovf = true;
+          break;
+        }
+        pM0 = Mlp;
+        pI0 = Ilp;
+        pD0 = carry;
+        X0 = newX0;
+        xN = satadd(xN, tNN);
+        xC = max(satadd(xC, tCC), satadd(xE, tEC));
+        xJ = max(satadd(xJ, tJJ), satadd(xE, tEJ));
+        xB = max(satadd(xN, tNB), satadd(xJ, tJB));
+      }
+      if (lane == 0) {
+        if (ovf) {
+          Q.score[orig] = 32767;
+          Q.flag[orig] = 1;
+          if (Q.nat) Q.nat[orig] = __int_as_float(0x7f800000);
+        } else {
+          const int sc = satadd(xC, tCT);
+          Q.score[orig] = (int16_t)sc;
+          Q.flag[orig] = 0;
+          if (Q.nat) Q.nat[orig] = __fsub_rn(__fdiv_rn(__int2float_rn(sc - Q.base), Q.scale), 3.0f);
+        }
+      }
+      __syncwarp();
+    }
+  }
+}
+
 }  // namespace
 
 size_t viterbi_fast_smem_bytes(int Mpad, int warps) {
   return (size_t)(Mpad >> 5) * 32 * (16 + 6 * (size_t)warps);
 }
 
-size_t viterbi_smem_bytes(int Mpad) { return (size_t)(kVitThreads / 32) * 3 * (size_t)Mpad * sizeof(int16_t); }
-
 namespace {
 
-// Shared memory of a fast-kernel block: transitions + per warp the DP rows
-// (M, I and D, or M and I with ND).
+// Shared memory of a block: transitions + per warp the DP rows (M, I and D,
+// or M and I with ND; the general kernel always keeps D).
 size_t fast_smem(int Mpad, int warps, bool nd) {
   const size_t q = (size_t)(Mpad >> 5);
   return q * 32 * 16 + (size_t)warps * q * 32 * (nd ? 4 : 6);
@@ -400,13 +441,15 @@ typedef void (*VitKernelFn)(VitParams);
 
 // Variants: the unroll depth of the node loop (8 for segments of 32 nodes or
 // more, which measured 5-10% faster there; 4 below, where the deeper unroll
-// measured slower) and whether the D row is stored.
-VitKernelFn fast_kernel_for(int Q, bool nd) {
+// measured slower) and whether the D row is stored.  The general kernel
+// takes the same unroll rule and always stores D.
+VitKernelFn vit_kernel_for(bool general, int Q, bool nd) {
+  if (general) return Q >= 32 ? viterbi_general_kernel<8> : viterbi_general_kernel<4>;
   if (nd) return viterbi_fast_kernel<8, true>;
   return Q >= 32 ? viterbi_fast_kernel<8, false> : viterbi_fast_kernel<4, false>;
 }
 
-// Launch shape of the fast kernel: variant, warps per block, resident blocks
+// Launch shape of a kernel: variant, warps per block, resident blocks
 // per SM and the shared-memory carveout.  Each warp reads the match-score
 // rows of its residues from global memory, so the L1 left beside shared
 // memory should hold the rows of the codes the database uses (n_codes x Mpad
@@ -416,7 +459,8 @@ VitKernelFn fast_kernel_for(int Q, bool nd) {
 // a third less shared memory per warp; it is taken where the plain kernel
 // keeps five warps or fewer per SM (measured, one query against 10,000
 // sequences: M = 2800 510 against 435 GCUPS, M = 3072 513 against 377; at
-// M = 2000-2405, with 6-11 plain warps, it measured 6-13% slower).
+// M = 2000-2405, with 6-11 plain warps, it measured 6-13% slower).  The
+// general kernel has no such variant.
 struct FastShape {
   bool nd = false;
   int warps = 0, blocks = 1;
@@ -424,22 +468,23 @@ struct FastShape {
   int carve_pct = 100;
 };
 
-FastShape fast_shape(int Mpad, int n_codes, int max_smem_block) {
+FastShape fast_shape(bool general, int Mpad, int n_codes, int max_smem_block) {
   constexpr size_t kKB = 1024, kUnified = 256 * kKB, kCarveMax = 228 * kKB;
   const int Q = Mpad >> 5;
   // Registers per thread of every instantiation, looked up once (thread-safe
   // static initialisation).
-  static const std::array<int, 3> regs_tab = [] {
-    std::array<int, 3> t{};
-    const VitKernelFn fns[3] = {viterbi_fast_kernel<4, false>, viterbi_fast_kernel<8, false>,
-                                viterbi_fast_kernel<8, true>};
-    for (int i = 0; i < 3; ++i) {
+  static const std::array<int, 5> regs_tab = [] {
+    std::array<int, 5> t{};
+    const VitKernelFn fns[5] = {viterbi_fast_kernel<4, false>, viterbi_fast_kernel<8, false>,
+                                viterbi_fast_kernel<8, true>, viterbi_general_kernel<4>,
+                                viterbi_general_kernel<8>};
+    for (int i = 0; i < 5; ++i) {
       cudaFuncAttributes a;
       t[i] = cudaFuncGetAttributes(&a, (const void *)fns[i]) == cudaSuccess ? a.numRegs : 255;
     }
     return t;
   }();
-  const int regs[2] = {regs_tab[Q >= 32 ? 1 : 0], regs_tab[2]};
+  const int regs[2] = {regs_tab[(general ? 3 : 0) + (Q >= 32 ? 1 : 0)], regs_tab[2]};
   const size_t ws = std::min((size_t)std::max(n_codes, 1) * 2 * (size_t)Mpad, 124 * kKB);
   static const int carves_kb[] = {228, 196, 164, 132, 100};   // supported carveouts
   for (int c : carves_kb) {
@@ -448,7 +493,7 @@ FastShape fast_shape(int Mpad, int n_codes, int max_smem_block) {
     FastShape best;
     for (int v = 0; v < 2; ++v) {
       const bool nd = v == 1;
-      if (nd && best.warps * best.blocks > 5) continue;
+      if (nd && (general || best.warps * best.blocks > 5)) continue;
       const int warp_regs = ((regs[v] + 7) / 8) * 8 * 32;
       FastShape cand;
       for (int w = kVitFastMaxThreads / 32; w >= 1; --w) {
@@ -478,30 +523,18 @@ FastShape fast_shape(int Mpad, int n_codes, int max_smem_block) {
 
 }  // namespace
 
-int viterbi_fast_shape_key(int Mpad, int n_codes, int max_smem) {
-  const FastShape s = fast_shape(Mpad, n_codes, max_smem);
-  return (s.nd ? 1000000 : 0) + s.warps * 10000 + s.blocks * 100 + s.carve_pct;
+int viterbi_shape_key(bool fast, int Mpad, int n_codes, int max_smem) {
+  const FastShape s = fast_shape(!fast, Mpad, n_codes, max_smem);
+  if (s.warps == 0) return -1;
+  return (fast ? 0 : 2000000) + (s.nd ? 1000000 : 0) + s.warps * 10000 + s.blocks * 100 + s.carve_pct;
 }
 
 int launch_viterbi(const VitParams &p, bool fast, int n_codes, int max_smem, int num_sms,
                    cudaStream_t st) {
   if (p.n_queries == 0) return 0;
-  if (!fast) {
-    const size_t smem = viterbi_smem_bytes(p.max_Mpad);
-    if (smem > (size_t)max_smem) return 2;
-    if (cudaFuncSetAttribute((const void *)viterbi_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                             (int)smem) != cudaSuccess)
-      return 1;
-    int per_sm = 0;
-    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, (const void *)viterbi_kernel, kVitThreads,
-                                                      smem) != cudaSuccess || per_sm < 1)
-      return 1;
-    viterbi_kernel<<<num_sms * per_sm, kVitThreads, smem, st>>>(p);
-    return cudaGetLastError() == cudaSuccess ? 0 : 1;
-  }
-  const FastShape s = fast_shape(p.max_Mpad, n_codes, max_smem);
+  const FastShape s = fast_shape(!fast, p.max_Mpad, n_codes, max_smem);
   if (s.warps == 0) return 2;
-  const VitKernelFn k = fast_kernel_for(p.max_Mpad >> 5, s.nd);
+  const VitKernelFn k = vit_kernel_for(!fast, p.max_Mpad >> 5, s.nd);
   const void *fn = (const void *)k;
   if (cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)s.smem) != cudaSuccess ||
       cudaFuncSetAttribute(fn, cudaFuncAttributePreferredSharedMemoryCarveout, s.carve_pct) != cudaSuccess)

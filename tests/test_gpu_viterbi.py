@@ -1,11 +1,13 @@
 """P7Viterbi filter (Eq. 1) on the GPU against the oracle, bit-exact.
 
 Scores, overflow flags and nat scores of the CUDA kernel must equal the
-scalar oracle's for every sequence: realistic profiles at model lengths that
-span one to many 32-node chunks with ragged ends, adversarial profiles with
-uniform int16 scores (saturation at both ends, overflow, positive
-transitions), several queries of different lengths in one launch, host and
-device outputs, the hand-worked golden cases, and the MSV -> Viterbi stage.
+scalar oracle's for every sequence: realistic profiles at model lengths from
+one node to the largest, with every kind of ragged end of the 32 lane
+segments; adversarial profiles with uniform int16 scores (saturation at both
+ends, overflow, positive transitions) for both kernels; positive delete
+chains that start from -32768 and reach the begin state's row; several
+queries of different lengths and kernels in one launch; host and device
+outputs; the hand-worked golden cases; and the MSV -> Viterbi stage.
 """
 import json
 import os
@@ -120,13 +122,48 @@ def test_adversarial_nonpositive_moves(ctx, seed):
 @pytest.mark.parametrize("M", [1100, 2100, 2600, 3000])
 def test_long_segment_variants(ctx, M):
     """Model lengths that select the fast kernel's long-segment variants
-    (deeper unrolling; the recomputed D row near M = 2,400-2,900; the
-    register-resident prefix near 3,000): realistic and adversarial (moves
-    <= 0)."""
+    (deeper unrolling from 32 nodes per lane; the recomputed D row where few
+    warps fit): realistic and adversarial (moves <= 0)."""
     rng = np.random.default_rng(400 + M)
     db = synth.random_database(160, 220, rng, alphabet=32)
     _run(ctx, [synth.make_vit_profile(M, rng),
                synth.random_vit_profile(M - 7, 29, rng, lo=-2500, hi=2500, moves_hi=0)], db)
+
+
+def _positive_chain_profile(M, K, rng, kind):
+    """Positive moves that only the general kernel's semantics get right:
+    kind 0, large positive D->D and D->M with a begin state near -32768 (the
+    delete chain climbs from -32768 across lane segments and caps);
+    kind 1, small positive D->D and large positive D->M with nonnegative
+    match scores (the first row reads the initial row's D through D->M)."""
+    v = synth.random_vit_profile(M, K, rng, lo=-3000, hi=3000)
+    if kind == 0:
+        v.trans[7] = rng.integers(1, 3000, M).astype(np.int16)
+        v.trans[3] = rng.integers(0, 3000, M).astype(np.int16)
+    else:
+        v.trans[7] = rng.integers(1, 100, M).astype(np.int16)
+        v.trans[3] = rng.integers(10000, 25000, M).astype(np.int16)
+        v.msc[:] = rng.integers(0, 3000, v.msc.shape).astype(np.int16)
+    v.base = -32000
+    return v
+
+
+@pytest.mark.parametrize("M", [1, 2, 33, 95, 300, 1000, 2405, 3072])
+@pytest.mark.parametrize("kind", [0, 1])
+def test_positive_delete_chains(ctx, M, kind):
+    rng = np.random.default_rng(500 + 7 * M + kind)
+    db = synth.random_database(200 if M > 1000 else 600, 60, rng, alphabet=32, min_len=0)
+    _run(ctx, [_positive_chain_profile(M, int(rng.integers(1, 33)), rng, kind)], db)
+
+
+@pytest.mark.parametrize("M", [700, 1500, 2405, 3072])
+def test_general_kernel_long_models(ctx, M):
+    """The general kernel at segment lengths where it unrolls deeper, with
+    mixed-sign scores of realistic and saturating size."""
+    rng = np.random.default_rng(600 + M)
+    db = synth.random_database(150, 200, rng, alphabet=32)
+    _run(ctx, [synth.random_vit_profile(M, 25, rng, lo=-3000, hi=400),
+               synth.random_vit_profile(M - 5, 32, rng, lo=-32768, hi=32767)], db)
 
 
 def test_multi_query_launch(ctx):
