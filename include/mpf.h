@@ -69,15 +69,15 @@ enum {
 
 enum { MPF_MSV = 0, MPF_SSV = 1 };
 
-/* Largest model length M a byte-filter profile may have (100,000). */
+/* Largest model length M a byte-filter or Viterbi profile may have (100,000). */
 int mpf_max_model_length(void);
 
 /* Largest model length the striped shared-memory scan kernels hold (3,072).
  * Longer byte-filter profiles are scored by the long-model kernel: one warp
  * per sequence, each lane a contiguous segment of nodes, the cost bytes read
  * from device memory (the paper's tables end at M = 2405; models beyond the
- * on-chip table are the large-model case of its Sec. 6).  It is also the
- * largest Viterbi profile. */
+ * on-chip table are the large-model case of its Sec. 6).  Longer Viterbi
+ * profiles keep their DP rows in device memory instead of shared memory. */
 int mpf_max_striped_length(void);
 
 /* Message for a status code (static string, never NULL). */
@@ -270,7 +270,7 @@ typedef struct mpf_vprofile mpf_vprofile;
 
 /*
  * Create a Viterbi profile.  Host inputs, copied.
- *   M: 1 <= M <= mpf_max_striped_length(); K: 1 <= K <= 32 residue codes
+ *   M: 1 <= M <= mpf_max_model_length(); K: 1 <= K <= 32 residue codes
  *   msc: K*M int16, row-major [x][k-1] match scores; codes K..31 score -32768
  *   trans: 8*M int16, rows BM, MM, IM, DM, MI, II, MD, DD, column k-1 holds
  *          the transition into (BM, MM, IM, DM: M_k; MD, DD: D_k) or out of

@@ -116,6 +116,8 @@ int launch_pvalues(const float *nat, uint64_t n, float mu, float lambda, float *
 // P7Viterbi filter (mpf_viterbi.cu).  Tables are int16 in device memory,
 // striped (node l*Q + j in slot j*32 + l); -32768 is minus infinity.
 constexpr int kVitFastMaxThreads = 512;
+// Viterbi launch keys at or above this keep their DP rows in device memory.
+constexpr int kVitDeviceRowsKey = 3000000;
 constexpr int kVitRows = 32;         // msc rows: residue codes 0..31
 constexpr int kVitTrans = 8;         // BM, MM, IM, DM, MI, II, MD, DD
 constexpr int kVitSpecial = 8;       // NN, NB, EC, CC, CT, EJ, JJ, JB
@@ -147,6 +149,8 @@ struct VitParams {
   int max_Mpad;               // largest Mpad of the queries (sets shared memory)
   const VitQuery *queries;
   uint32_t *counters;         // one per query, zero before the launch
+  uint2 *state;               // models past the shared-memory rows: per-warp DP rows, else null
+  uint64_t state_bytes;
 };
 // fast: every transition and special score <= 0 (else the general kernel);
 // tables in the striped layout (msc [32][Q][32] int16, trans [Q][32] x 8
@@ -155,10 +159,16 @@ struct VitParams {
 // rows do not fit in shared memory.
 int launch_viterbi(const VitParams &p, bool fast, int n_codes, int max_smem, int num_sms,
                    cudaStream_t st);
+// With p.state set (models longer than kStripedMaxM), the variants that keep
+// the DP rows in device memory; p.state must hold viterbi_state_bytes().
 // Shared memory of a block of `warps` warps that store the D row.
 size_t viterbi_fast_smem_bytes(int Mpad, int warps);
-// Launch shape of a kernel for one model length (equal keys share a launch),
-// or -1 if no shape fits.
+// Device scratch of a launch over models of up to Mpad nodes that keeps its
+// rows in device memory.
+size_t viterbi_state_bytes(bool fast, int Mpad, int num_sms);
+// Launch shape of a kernel for one model length (equal keys share a launch;
+// keys >= kVitDeviceRowsKey keep the rows in device memory), or -1 if no
+// shape fits.
 int viterbi_shape_key(bool fast, int Mpad, int n_codes, int max_smem);
 
 // Kernel instantiation for (lanes, words, mode), or nullptr if not built.

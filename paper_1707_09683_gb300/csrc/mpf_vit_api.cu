@@ -83,22 +83,36 @@ int viterbi_enqueue(mpf_ctx *ctx, const mpf_vprofile *const *vps, int n_q, const
     d.n_ranks = n_ranks ? n_ranks + q : nullptr;
     qs.push_back(d);
   }
+  // Groups run concurrently on the context's fork streams, so that one
+  // group's tail overlaps the others' work.  Groups of models longer than
+  // the shared-memory rows hold get their own slice of device scratch.
+  std::vector<std::pair<int, int>> groups;
+  std::vector<size_t> state_off, state_len;
   const size_t desc_bytes = sizeof(VitQuery) * (size_t)n_q;
+  size_t total = (desc_bytes + 4 * (size_t)n_q + 255) & ~(size_t)255;
+  for (int first = 0; first < n_q;) {
+    int last = first;
+    int max_Mpad = 32;
+    while (last < n_q && std::get<0>(order[(size_t)last]) == std::get<0>(order[(size_t)first])) {
+      max_Mpad = std::max(max_Mpad, std::get<1>(order[(size_t)last]));
+      ++last;
+    }
+    const mpf_vprofile *v0 = vps[std::get<2>(order[(size_t)first])];
+    const size_t len = std::get<0>(order[(size_t)first]) >= kVitDeviceRowsKey
+                           ? viterbi_state_bytes(v0->fast, max_Mpad, ctx->num_sms)
+                           : 0;
+    groups.emplace_back(first, last);
+    state_off.push_back(total);
+    state_len.push_back(len);
+    total += (len + 255) & ~(size_t)255;
+    first = last;
+  }
   uint8_t *dev = nullptr;
-  MPF_CUDA(cudaMallocAsync((void **)&dev, desc_bytes + 4 * (size_t)n_q, ctx->stream));
+  MPF_CUDA(cudaMallocAsync((void **)&dev, total, ctx->stream));
   cudaError_t e = cudaMemcpyAsync(dev, qs.data(), desc_bytes, cudaMemcpyHostToDevice, ctx->stream);
   uint32_t *counters = reinterpret_cast<uint32_t *>(dev + desc_bytes);
   if (e == cudaSuccess) e = cudaMemsetAsync(counters, 0, 4 * (size_t)n_q, ctx->stream);
   int rc = e == cudaSuccess ? MPF_OK : MPF_ECUDA;
-  // Groups run concurrently on the context's fork streams, so that one
-  // group's tail overlaps the others' work.
-  std::vector<std::pair<int, int>> groups;
-  for (int first = 0; first < n_q;) {
-    int last = first;
-    while (last < n_q && std::get<0>(order[(size_t)last]) == std::get<0>(order[(size_t)first])) ++last;
-    groups.emplace_back(first, last);
-    first = last;
-  }
   const bool fork = groups.size() > 1;
   std::vector<cudaEvent_t> evs;
   if (fork && rc == MPF_OK) {
@@ -139,6 +153,8 @@ int viterbi_enqueue(mpf_ctx *ctx, const mpf_vprofile *const *vps, int n_q, const
     p.max_Mpad = max_Mpad;
     p.queries = reinterpret_cast<const VitQuery *>(dev) + first;
     p.counters = counters + first;
+    p.state = state_len[gi] ? reinterpret_cast<uint2 *>(dev + state_off[gi]) : nullptr;
+    p.state_bytes = state_len[gi];
     const int lr = launch_viterbi(p, vps[std::get<2>(order[(size_t)first])]->fast, db->n_codes, ctx->max_smem,
                                   ctx->num_sms, st);
     if (lr) rc = lr == 2 ? MPF_EUNSUPPORTED : MPF_ECUDA;
@@ -172,12 +188,11 @@ int mpf_vit_profile_create(mpf_ctx *ctx, int M, int K, const int16_t *msc, const
   *out = nullptr;
   if (!ctx || !msc || !trans || !special || M < 1 || K < 1 || K > kVitRows) return MPF_EINVAL;
   if (base < -32768 || base > 32767 || !isfinite(scale) || !(scale > 0.f)) return MPF_EINVAL;
-  if (M > kStripedMaxM) return MPF_EUNSUPPORTED;
+  if (M > kMaxLongM) return MPF_EUNSUPPORTED;
   const int Mpad = (M + 31) & ~31, Q = Mpad / 32;
   bool fast = true;
   for (size_t i = 0; i < (size_t)kVitTrans * M; ++i) fast = fast && trans[i] <= 0;
   for (int i = 0; i < kVitSpecial; ++i) fast = fast && special[i] <= 0;
-  if (viterbi_fast_smem_bytes(Mpad, 1) > (size_t)ctx->max_smem) return MPF_EUNSUPPORTED;
   std::vector<int16_t> hm((size_t)kVitRows * Mpad, (int16_t)-32768);
   std::vector<int16_t> ht((size_t)kVitTrans * Mpad, (int16_t)-32768);
   // Striped: node k = l*Q + j in slot j*32 + l; transitions 8 per slot.

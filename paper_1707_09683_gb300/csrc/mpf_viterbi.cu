@@ -35,7 +35,8 @@
 //
 // The transition table is staged once per query into shared memory and read
 // by all warps of a block; match scores are read from global memory in the
-// same striped order.
+// same striped order.  Models longer than 3,072 nodes take the same kernels
+// with their DP rows in device memory (GM, below).
 #include <cuda_runtime.h>
 #include <math.h>
 #include <stdint.h>
@@ -59,6 +60,50 @@ __device__ __forceinline__ int lo16(uint32_t w) { return (int)(int16_t)(w & 0xff
 __device__ __forceinline__ int hi16(uint32_t w) { return ((int)w) >> 16; }
 // max(a + b, c), one DPX instruction.
 __device__ __forceinline__ int addmax(int a, int b, int c) { return __viaddmax_s32(a, b, c); }
+
+// Where a kernel keeps its tables and DP rows.  Models that fit (GM =
+// false): the query's transitions staged into shared memory, read by every
+// warp of the block, and each warp's M, I, D rows in shared memory.  Longer
+// models (GM = true): transitions read through the L1 from device memory,
+// and each warp's rows in its slice of a device scratch buffer as one 8-byte
+// record per node (M | I, D), at slot j*32 + lane like the shared rows, so a
+// warp's access is 256 contiguous bytes; the rows are read and written at
+// the L2 (ld/st.global.cg), which keeps the L1 for the tables.
+template <bool GM>
+__device__ __forceinline__ void stage_transitions(uint4 *tr, const uint4 *gtr, int nq) {
+  if (GM) return;
+  __syncthreads();   // every warp is done with the previous query's table
+  for (int i = threadIdx.x; i < nq * 32; i += blockDim.x) tr[i] = __ldg(gtr + i);
+  __syncthreads();
+}
+
+template <bool GM>
+struct TransSrc {
+  const uint4 *s, *g;
+  __device__ __forceinline__ uint4 operator[](int i) const { return GM ? __ldg(g + i) : s[i]; }
+};
+
+// This warp's records in the device scratch (GM), or nullptr (also when the
+// scratch is too small: debug builds report it).
+template <bool GM>
+__device__ __forceinline__ uint2 *warp_rows(const VitParams &p, int Qmax, int warp) {
+  if (!GM) return nullptr;
+  const uint64_t w = (uint64_t)blockIdx.x * (blockDim.x >> 5) + (uint64_t)warp;
+  const uint64_t per = (uint64_t)Qmax * 32;
+  if (!MPF_DCHECK(p.status, p.state && (w + 1) * per * sizeof(uint2) <= p.state_bytes)) return nullptr;
+  return p.state + w * per;
+}
+
+__device__ __forceinline__ void load_rows(const uint2 *g, int sl, int &Mo, int &Io, int &Dl) {
+  const uint2 r = __ldcg(g + sl);
+  Mo = (int)(int16_t)(r.x & 0xffffu);
+  Io = ((int)r.x) >> 16;
+  Dl = (int)r.y;
+}
+
+__device__ __forceinline__ void store_rows(uint2 *g, int sl, int Mn, int In, int d) {
+  __stcg(g + sl, make_uint2(__byte_perm((uint32_t)Mn, (uint32_t)In, 0x5410), (uint32_t)d));
+}
 
 // One node of a lane's sweep (fast kernel): the previous row's M, I and
 // segment-local D of this node arrive in Mo, Io, Dl; the node's new M, I and
@@ -107,8 +152,9 @@ struct FastCell {
 // chain from the stored M row (4 bytes of state per node instead of 6, two
 // more DPX operations per node), so more warps fit on long models.  U is the
 // unroll depth of the node loop.
-template <int U, bool ND>
+template <int U, bool ND, bool GM>
 __global__ void __launch_bounds__(kVitFastMaxThreads, 1) viterbi_fast_kernel(VitParams p) {
+  static_assert(!(ND && GM), "the global-row variant stores D");
   extern __shared__ __align__(16) uint4 fsm[];
   const int lane = threadIdx.x & 31;
   const int warp = threadIdx.x >> 5;
@@ -117,40 +163,44 @@ __global__ void __launch_bounds__(kVitFastMaxThreads, 1) viterbi_fast_kernel(Vit
   int16_t *sM = reinterpret_cast<int16_t *>(fsm + (size_t)Qmax * 32) + (size_t)warp * Qmax * 32 * (ND ? 2 : 3);
   int16_t *sI = sM + (size_t)Qmax * 32;
   int16_t *sD = sI + (size_t)Qmax * 32;   // unused with ND
+  uint2 *gst = warp_rows<GM>(p, Qmax, warp);
   // Debug builds: the transitions and the warps' DP rows must fit the block's
-  // shared memory.
-  if (!MPF_DCHECK(p.status, (size_t)Qmax * 32 * (16 + (blockDim.x >> 5) * (ND ? 4 : 6)) <= dynamic_smem_bytes()))
+  // shared memory (or the rows the device scratch).
+  if (!GM && !MPF_DCHECK(p.status, (size_t)Qmax * 32 * (16 + (blockDim.x >> 5) * (ND ? 4 : 6)) <= dynamic_smem_bytes()))
     return;
+  if (GM && !gst) return;
 
   for (uint32_t qi = 0; qi < p.n_queries; ++qi) {
     const VitQuery Q = p.queries[qi];
     const int nq = Q.Mpad >> 5;
     if (!MPF_DCHECK(p.status, Q.Mpad <= p.max_Mpad && (!Q.ranks || *Q.n_ranks <= p.n_seqs))) continue;
-    __syncthreads();   // every warp is done with the previous query's table
     const uint4 *gtr = reinterpret_cast<const uint4 *>(Q.trans);
-    for (int i = threadIdx.x; i < nq * 32; i += blockDim.x) tr[i] = __ldg(gtr + i);
-    __syncthreads();
+    stage_transitions<GM>(tr, gtr, nq);
+    const TransSrc<GM> T{tr, gtr};
 
     // Per-lane constants of the query.
     const int nv = min(max(Q.M - lane * nq, 0), nq);   // real nodes in this lane's segment
     int tMD0 = kNeg, tDD0 = 0, Bl = 0;
     if (nv > 0) {
-      tMD0 = lo16(tr[lane].w);
-      tDD0 = hi16(tr[lane].w);
+      tMD0 = lo16(T[lane].w);
+      tDD0 = hi16(T[lane].w);
     }
-    for (int j = 0; j < nv; ++j) Bl += hi16(tr[j * 32 + lane].w);
+    for (int j = 0; j < nv; ++j) Bl += hi16(T[j * 32 + lane].w);
     const int Bsuf = Bl - tDD0;
-    int P = Bl;   // inclusive prefix over lanes
+    // Inclusive prefix over lanes, modulo 2^32: the whole model's sum of tDD
+    // can pass the int32 range at 100,000 nodes, a window of 16 lanes cannot,
+    // so the differences below are exact.
+    uint32_t P = (uint32_t)Bl;
 #pragma unroll
     for (int off = 1; off < 32; off <<= 1) {
-      const int y = __shfl_up_sync(kAll, P, off);
+      const uint32_t y = __shfl_up_sync(kAll, P, off);
       if (lane >= off) P += y;
     }
     int Wn[5];    // sum of B over lanes (lane - 2^r, lane], or a sentinel
 #pragma unroll
     for (int r = 0; r < 5; ++r) {
-      const int y = __shfl_up_sync(kAll, P, 1 << r);
-      Wn[r] = lane >= (1 << r) ? P - y : -(1 << 29);
+      const uint32_t y = __shfl_up_sync(kAll, P, 1 << r);
+      Wn[r] = lane >= (1 << r) ? (int)(P - y) : -(1 << 29);
     }
     const int tNN = Q.sp[0], tNB = Q.sp[1], tEC = Q.sp[2], tCC = Q.sp[3];
     const int tCT = Q.sp[4], tEJ = Q.sp[5], tJJ = Q.sp[6], tJB = Q.sp[7];
@@ -170,8 +220,12 @@ __global__ void __launch_bounds__(kVitFastMaxThreads, 1) viterbi_fast_kernel(Vit
         continue;
 
       for (int j = 0; j < nq; ++j) {
-        sM[j * 32 + lane] = sI[j * 32 + lane] = (int16_t)kNeg;
-        if (!ND) sD[j * 32 + lane] = (int16_t)kNeg;
+        if (GM) {
+          store_rows(gst, j * 32 + lane, kNeg, kNeg, kNeg);
+        } else {
+          sM[j * 32 + lane] = sI[j * 32 + lane] = (int16_t)kNeg;
+          if (!ND) sD[j * 32 + lane] = (int16_t)kNeg;
+        }
       }
       int xN = Q.base, xJ = kNeg, xC = kNeg;
       int xB = addmax(xN, tNB, kNeg);
@@ -194,14 +248,21 @@ __global__ void __launch_bounds__(kVitFastMaxThreads, 1) viterbi_fast_kernel(Vit
 #pragma unroll U
         for (int j = 0; j < nv; ++j) {
           const int sl = j * 32 + lane;
-          if (ND) {
+          if (GM) {
+            int Mo, Io, Dl;
+            load_rows(gst, sl, Mo, Io, Dl);
+            c.step(T[sl], __ldg(erow + j * 32), Mo, Io, Dl, xB);
+            store_rows(gst, sl, c.Mn, c.In, c.d);
+          } else if (ND) {
             c.step_nd(tr[sl], __ldg(erow + j * 32), sM[sl], sI[sl], xB);
+            sM[sl] = (int16_t)c.Mn;
+            sI[sl] = (int16_t)c.In;
           } else {
             c.step(tr[sl], __ldg(erow + j * 32), sM[sl], sI[sl], sD[sl], xB);
             sD[sl] = (int16_t)c.d;
+            sM[sl] = (int16_t)c.Mn;
+            sI[sl] = (int16_t)c.In;
           }
-          sM[sl] = (int16_t)c.Mn;
-          sI[sl] = (int16_t)c.In;
         }
         const int xE = __reduce_max_sync(kAll, c.mx);
         if (xE >= 32767) {
@@ -256,7 +317,7 @@ __device__ __forceinline__ int satadd(int a, int b) { return max(__viaddmin_s32(
 
 // Any int16 scores (see the file comment).  Shared memory as for the plain
 // fast kernel: transitions, then per warp the M, I and segment-local D rows.
-template <int U>
+template <int U, bool GM>
 __global__ void __launch_bounds__(kVitFastMaxThreads, 1) viterbi_general_kernel(VitParams p) {
   extern __shared__ __align__(16) uint4 fsm[];
   const int lane = threadIdx.x & 31;
@@ -266,17 +327,18 @@ __global__ void __launch_bounds__(kVitFastMaxThreads, 1) viterbi_general_kernel(
   int16_t *sM = reinterpret_cast<int16_t *>(fsm + (size_t)Qmax * 32) + (size_t)warp * Qmax * 32 * 3;
   int16_t *sI = sM + (size_t)Qmax * 32;
   int16_t *sD = sI + (size_t)Qmax * 32;
-  if (!MPF_DCHECK(p.status, (size_t)Qmax * 32 * (16 + (blockDim.x >> 5) * 6) <= dynamic_smem_bytes()))
+  uint2 *gst = warp_rows<GM>(p, Qmax, warp);
+  if (!GM && !MPF_DCHECK(p.status, (size_t)Qmax * 32 * (16 + (blockDim.x >> 5) * 6) <= dynamic_smem_bytes()))
     return;
+  if (GM && !gst) return;
 
   for (uint32_t qi = 0; qi < p.n_queries; ++qi) {
     const VitQuery Q = p.queries[qi];
     const int nq = Q.Mpad >> 5;
     if (!MPF_DCHECK(p.status, Q.Mpad <= p.max_Mpad && (!Q.ranks || *Q.n_ranks <= p.n_seqs))) continue;
-    __syncthreads();   // every warp is done with the previous query's table
     const uint4 *gtr = reinterpret_cast<const uint4 *>(Q.trans);
-    for (int i = threadIdx.x; i < nq * 32; i += blockDim.x) tr[i] = __ldg(gtr + i);
-    __syncthreads();
+    stage_transitions<GM>(tr, gtr, nq);
+    const TransSrc<GM> T{tr, gtr};
 
     // Per-lane constants: the segment's map of the delete score entering it
     // is d -> max(A, min(d + Bl, Cl)), built from tDD of the first node (t0)
@@ -285,11 +347,11 @@ __global__ void __launch_bounds__(kVitFastMaxThreads, 1) viterbi_general_kernel(
     const int nv = min(max(Q.M - lane * nq, 0), nq);
     int t0 = 0, tMD0 = kNeg, Bsuf = 0, Csuf = 1 << 29, maxP = 0;
     if (nv > 0) {
-      t0 = hi16(tr[lane].w);
-      tMD0 = lo16(tr[lane].w);
+      t0 = hi16(T[lane].w);
+      tMD0 = lo16(T[lane].w);
     }
     for (int j = 1; j < nv; ++j) {
-      const int t = hi16(tr[j * 32 + lane].w);
+      const int t = hi16(T[j * 32 + lane].w);
       Bsuf += t;
       Csuf = min(Csuf + t, kPos);
       maxP = max(maxP, Bsuf);
@@ -308,6 +370,7 @@ __global__ void __launch_bounds__(kVitFastMaxThreads, 1) viterbi_general_kernel(
       for (int r = 0; r < 5; ++r) {
         Wb[r] = lane >= (1 << r) ? B : kMinusInf;
         Wc[r] = C;
+        if (r == 4) break;        // the 32-lane composite is never used
         const int Bp = __shfl_up_sync(kAll, B, 1 << r);
         const int Cp = __shfl_up_sync(kAll, C, 1 << r);
         if (lane >= (1 << r)) {   // this lane's window after the earlier one
@@ -333,7 +396,10 @@ __global__ void __launch_bounds__(kVitFastMaxThreads, 1) viterbi_general_kernel(
       if (!MPF_DCHECK(p.status, (uint64_t)w0 + (uint64_t)((len + 3) >> 2) <= p.n_words && orig < p.n_seqs))
         continue;
 
-      for (int j = 0; j < nq; ++j) sM[j * 32 + lane] = sI[j * 32 + lane] = sD[j * 32 + lane] = (int16_t)kNeg;
+      for (int j = 0; j < nq; ++j) {
+        if (GM) store_rows(gst, j * 32 + lane, kNeg, kNeg, kNeg);
+        else sM[j * 32 + lane] = sI[j * 32 + lane] = sD[j * 32 + lane] = (int16_t)kNeg;
+      }
       int xN = Q.base, xJ = kNeg, xC = kNeg;
       int xB = satadd(xN, tNB);
       // Previous row: M, I and true D of the node before the segment, and the
@@ -352,8 +418,15 @@ __global__ void __launch_bounds__(kVitFastMaxThreads, 1) viterbi_general_kernel(
 #pragma unroll U
         for (int j = 0; j < nv; ++j) {
           const int sl = j * 32 + lane;
-          const int Mo = sM[sl], Io = sI[sl], Dl = sD[sl];
-          const uint4 t = tr[sl];
+          int Mo, Io, Dl;
+          if (GM) {
+            load_rows(gst, sl, Mo, Io, Dl);
+          } else {
+            Mo = sM[sl];
+            Io = sI[sl];
+            Dl = sD[sl];
+          }
+          const uint4 t = T[sl];
           const int e = __ldg(erow + j * 32);
           const int tDD = hi16(t.w);
           if (j > 0) X = __viaddmin_s32(X, tDD, kPos);   // previous row's carried chain
@@ -366,9 +439,13 @@ __global__ void __launch_bounds__(kVitFastMaxThreads, 1) viterbi_general_kernel(
           d = j > 0 ? max(satadd(mprev, lo16(t.w)), __viaddmin_s32(d, tDD, kPos)) : kMinusInf;
           mxM = max(mxM, Mn);
           mxD = max(mxD, d);
-          sM[sl] = (int16_t)Mn;
-          sI[sl] = (int16_t)In;
-          sD[sl] = (int16_t)(j > 0 ? d : kNeg);
+          if (GM) {
+            store_rows(gst, sl, Mn, In, j > 0 ? d : kNeg);
+          } else {
+            sM[sl] = (int16_t)Mn;
+            sI[sl] = (int16_t)In;
+            sD[sl] = (int16_t)(j > 0 ? d : kNeg);
+          }
           dM = Mo;
           dI = Io;
           dD = Do;
@@ -444,9 +521,35 @@ typedef void (*VitKernelFn)(VitParams);
 // measured slower) and whether the D row is stored.  The general kernel
 // takes the same unroll rule and always stores D.
 VitKernelFn vit_kernel_for(bool general, int Q, bool nd) {
-  if (general) return Q >= 32 ? viterbi_general_kernel<8> : viterbi_general_kernel<4>;
-  if (nd) return viterbi_fast_kernel<8, true>;
-  return Q >= 32 ? viterbi_fast_kernel<8, false> : viterbi_fast_kernel<4, false>;
+  if (general) return Q >= 32 ? viterbi_general_kernel<8, false> : viterbi_general_kernel<4, false>;
+  if (nd) return viterbi_fast_kernel<8, true, false>;
+  return Q >= 32 ? viterbi_fast_kernel<8, false, false> : viterbi_fast_kernel<4, false, false>;
+}
+
+VitKernelFn gm_kernel_for(bool general) {
+  return general ? viterbi_general_kernel<8, true> : viterbi_fast_kernel<8, false, true>;
+}
+
+// Launch shape of the device-row variants: blocks of kGmWarps warps, as
+// many blocks per SM as registers allow, at most kGmWarpsPerSm warps (each
+// warp's rows are 8 bytes per node, so this bounds the scratch: 16 warps x
+// 152 SMs x 8 B x 100,000 nodes = 1.9 GB at the longest model).  No shared
+// memory, so the carveout leaves the whole L1 to the tables.
+constexpr int kGmWarps = 8, kGmWarpsPerSm = 16;
+
+int gm_blocks_per_sm(bool general) {
+  static const std::array<int, 2> occ = [] {
+    std::array<int, 2> t{};
+    for (int g = 0; g < 2; ++g) {
+      int b = 0;
+      if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&b, (const void *)gm_kernel_for(g == 1), kGmWarps * 32, 0) !=
+          cudaSuccess)
+        b = 0;
+      t[g] = std::min(b, kGmWarpsPerSm / kGmWarps);
+    }
+    return t;
+  }();
+  return occ[general ? 1 : 0];
 }
 
 // Launch shape of a kernel: variant, warps per block, resident blocks
@@ -475,9 +578,9 @@ FastShape fast_shape(bool general, int Mpad, int n_codes, int max_smem_block) {
   // static initialisation).
   static const std::array<int, 5> regs_tab = [] {
     std::array<int, 5> t{};
-    const VitKernelFn fns[5] = {viterbi_fast_kernel<4, false>, viterbi_fast_kernel<8, false>,
-                                viterbi_fast_kernel<8, true>, viterbi_general_kernel<4>,
-                                viterbi_general_kernel<8>};
+    const VitKernelFn fns[5] = {viterbi_fast_kernel<4, false, false>, viterbi_fast_kernel<8, false, false>,
+                                viterbi_fast_kernel<8, true, false>, viterbi_general_kernel<4, false>,
+                                viterbi_general_kernel<8, false>};
     for (int i = 0; i < 5; ++i) {
       cudaFuncAttributes a;
       t[i] = cudaFuncGetAttributes(&a, (const void *)fns[i]) == cudaSuccess ? a.numRegs : 255;
@@ -523,8 +626,25 @@ FastShape fast_shape(bool general, int Mpad, int n_codes, int max_smem_block) {
 
 }  // namespace
 
+size_t viterbi_state_bytes(bool fast, int Mpad, int num_sms) {
+  return (size_t)num_sms * gm_blocks_per_sm(!fast) * kGmWarps * (size_t)Mpad * sizeof(uint2);
+}
+
+// Rows in shared memory pay off while they leave enough warps resident to
+// hide the latency of the match-score loads; with six or fewer per SM the
+// device-memory rows (16 warps per SM, the whole L1 for the tables) were
+// faster (one query against 20,000-40,000 sequences, GCUPS shared / device
+// rows: fast kernel, 6 warps, M = 2350: 488 / 678, 2405: 488 / 612, 2500:
+// 491 / 523; general kernel, 4-6 warps, M = 2405: 417 / 529, 2800: 381 /
+// 530, 3072: 340 / 505; with 7-12 warps the shared rows were within 12% either
+// way, and ahead below M = 2200).
+constexpr int kVitSmemMinWarps = 7;
+
 int viterbi_shape_key(bool fast, int Mpad, int n_codes, int max_smem) {
+  const int gm_key = gm_blocks_per_sm(!fast) > 0 ? kVitDeviceRowsKey + (fast ? 0 : 1000000) : -1;
+  if (Mpad > kStripedMaxM) return gm_key;
   const FastShape s = fast_shape(!fast, Mpad, n_codes, max_smem);
+  if (s.warps * s.blocks < kVitSmemMinWarps && gm_key >= 0) return gm_key;
   if (s.warps == 0) return -1;
   return (fast ? 0 : 2000000) + (s.nd ? 1000000 : 0) + s.warps * 10000 + s.blocks * 100 + s.carve_pct;
 }
@@ -532,6 +652,15 @@ int viterbi_shape_key(bool fast, int Mpad, int n_codes, int max_smem) {
 int launch_viterbi(const VitParams &p, bool fast, int n_codes, int max_smem, int num_sms,
                    cudaStream_t st) {
   if (p.n_queries == 0) return 0;
+  if (p.state) {
+    const int b = gm_blocks_per_sm(!fast);
+    if (b < 1) return 2;
+    if (p.state_bytes < viterbi_state_bytes(fast, p.max_Mpad, num_sms)) return 1;
+    const void *fn = (const void *)gm_kernel_for(!fast);
+    if (cudaFuncSetAttribute(fn, cudaFuncAttributePreferredSharedMemoryCarveout, 0) != cudaSuccess) return 1;
+    gm_kernel_for(!fast)<<<num_sms * b, kGmWarps * 32, 0, st>>>(p);
+    return cudaGetLastError() == cudaSuccess ? 0 : 1;
+  }
   const FastShape s = fast_shape(!fast, p.max_Mpad, n_codes, max_smem);
   if (s.warps == 0) return 2;
   const VitKernelFn k = vit_kernel_for(!fast, p.max_Mpad >> 5, s.nd);

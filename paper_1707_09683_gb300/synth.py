@@ -339,3 +339,21 @@ def random_vit_profile(M: int, K: int, rng: np.random.Generator, lo: int = -3276
     return VitProfile(M=M, K=K, msc=u((K, M)), trans=u((8, M), mh), special=u(8, mh),
                       base=int(rng.integers(-32768, 32768)) if base is None else int(base),
                       scale=float(np.float32(VIT_SCALE)))
+
+
+def positive_chain_vit_profile(M: int, K: int, rng: np.random.Generator, kind: int) -> VitProfile:
+    """Adversarial Viterbi profile with positive delete moves and a begin
+    state near -32768: kind 0, large positive D->D and D->M (the delete chain
+    climbs from -32768 across many nodes and reaches the upper bound);
+    kind 1, small positive D->D, large positive D->M and nonnegative match
+    scores (a row reads the previous row's delete scores through D->M)."""
+    v = random_vit_profile(M, K, rng, lo=-3000, hi=3000)
+    if kind == 0:
+        v.trans[7] = rng.integers(1, 3000, M).astype(np.int16)
+        v.trans[3] = rng.integers(0, 3000, M).astype(np.int16)
+    else:
+        v.trans[7] = rng.integers(1, 100, M).astype(np.int16)
+        v.trans[3] = rng.integers(10000, 25000, M).astype(np.int16)
+        v.msc[:] = rng.integers(0, 3000, v.msc.shape).astype(np.int16)
+    v.base = -32000
+    return v

@@ -130,30 +130,12 @@ def test_long_segment_variants(ctx, M):
                synth.random_vit_profile(M - 7, 29, rng, lo=-2500, hi=2500, moves_hi=0)], db)
 
 
-def _positive_chain_profile(M, K, rng, kind):
-    """Positive moves that only the general kernel's semantics get right:
-    kind 0, large positive D->D and D->M with a begin state near -32768 (the
-    delete chain climbs from -32768 across lane segments and caps);
-    kind 1, small positive D->D and large positive D->M with nonnegative
-    match scores (the first row reads the initial row's D through D->M)."""
-    v = synth.random_vit_profile(M, K, rng, lo=-3000, hi=3000)
-    if kind == 0:
-        v.trans[7] = rng.integers(1, 3000, M).astype(np.int16)
-        v.trans[3] = rng.integers(0, 3000, M).astype(np.int16)
-    else:
-        v.trans[7] = rng.integers(1, 100, M).astype(np.int16)
-        v.trans[3] = rng.integers(10000, 25000, M).astype(np.int16)
-        v.msc[:] = rng.integers(0, 3000, v.msc.shape).astype(np.int16)
-    v.base = -32000
-    return v
-
-
 @pytest.mark.parametrize("M", [1, 2, 33, 95, 300, 1000, 2405, 3072])
 @pytest.mark.parametrize("kind", [0, 1])
 def test_positive_delete_chains(ctx, M, kind):
     rng = np.random.default_rng(500 + 7 * M + kind)
     db = synth.random_database(200 if M > 1000 else 600, 60, rng, alphabet=32, min_len=0)
-    _run(ctx, [_positive_chain_profile(M, int(rng.integers(1, 33)), rng, kind)], db)
+    _run(ctx, [synth.positive_chain_vit_profile(M, int(rng.integers(1, 33)), rng, kind)], db)
 
 
 @pytest.mark.parametrize("M", [700, 1500, 2405, 3072])
@@ -285,7 +267,7 @@ def test_three_stage_pipeline(ctx):
 
 def test_invalid_arguments(ctx):
     rng = np.random.default_rng(14)
-    too_long = synth.make_vit_profile(mpf.max_striped_length() + 1, rng)
+    too_long = synth.make_vit_profile(mpf.max_model_length() + 1, rng)
     with pytest.raises(mpf.MpfError) as e:
         mpf.VitProfile(ctx, too_long)
     assert e.value.status == mpf.MPF_EUNSUPPORTED
