@@ -168,8 +168,9 @@ size_t viterbi_fast_smem_bytes(int Mpad, int warps);
 size_t viterbi_state_bytes(bool fast, int Mpad, int num_sms);
 // Launch shape of a kernel for one model length (equal keys share a launch;
 // keys >= kVitDeviceRowsKey keep the rows in device memory), or -1 if no
-// shape fits.
-int viterbi_shape_key(bool fast, int Mpad, int n_codes, int max_smem);
+// shape fits.  n_seqs: sequences each query of the launch scores, 0 when
+// the host does not know (a rank list counted on the device).
+int viterbi_shape_key(bool fast, int Mpad, int n_codes, int max_smem, int num_sms, uint64_t n_seqs);
 
 // Kernel instantiation for (lanes, words, mode), or nullptr if not built.
 KernelFn kernel_for(int lanes, int words, int mode);

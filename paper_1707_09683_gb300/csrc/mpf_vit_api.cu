@@ -47,7 +47,8 @@ int viterbi_enqueue(mpf_ctx *ctx, const mpf_vprofile *const *vps, int n_q, const
   std::map<int, int> group_max;                    // key -> longest model of the group
   for (int q = 0; q < n_q; ++q) {
     const mpf_vprofile *v = vps[q];
-    const int key = viterbi_shape_key(v->fast, v->Mpad, db->n_codes, ctx->max_smem);
+    const int key = viterbi_shape_key(v->fast, v->Mpad, db->n_codes, ctx->max_smem, ctx->num_sms,
+                                      ranks ? 0 : n);
     if (key < 0) return MPF_EUNSUPPORTED;
     order.emplace_back(key, v->Mpad, q);
     group_max[key] = std::max(group_max[key], v->Mpad);

@@ -633,18 +633,29 @@ size_t viterbi_state_bytes(bool fast, int Mpad, int num_sms) {
 // Rows in shared memory pay off while they leave enough warps resident to
 // hide the latency of the match-score loads; with six or fewer per SM the
 // device-memory rows (16 warps per SM, the whole L1 for the tables) were
-// faster (one query against 20,000-40,000 sequences, GCUPS shared / device
-// rows: fast kernel, 6 warps, M = 2350: 488 / 678, 2405: 488 / 612, 2500:
-// 491 / 523; general kernel, 4-6 warps, M = 2405: 417 / 529, 2800: 381 /
-// 530, 3072: 340 / 505; with 7-12 warps the shared rows were within 12% either
-// way, and ahead below M = 2200).
+// faster when every warp had several sequences to score (one query against
+// 20,000-40,000 sequences, 8-16 per warp; GCUPS shared / device rows: fast
+// kernel, 6 warps, M = 2350: 488 / 678, 2405: 488 / 612, 2500: 491 / 523;
+// general kernel, 4-6 warps, M = 2405: 417 / 529, 2800: 381 / 530, 3072:
+// 340 / 505; with 7-12 warps the shared rows were within 12% either way,
+// and ahead below M = 2200).  With few sequences per warp the launch ends
+// with the longest sequences, which a warp scores more slowly among 16 than
+// among 6 (M = 3500, device rows: 40,000 sequences 665 GCUPS, 16,326 470;
+// the MSV -> Viterbi stage over 2% of 500,000 sequences, M = 48-2405: 486
+// GCUPS with shared rows, 351 with device rows for M = 2405).  So device
+// rows are taken there only with at least 8 sequences per warp.
 constexpr int kVitSmemMinWarps = 7;
+constexpr uint64_t kGmMinSeqsPerWarp = 8;
 
-int viterbi_shape_key(bool fast, int Mpad, int n_codes, int max_smem) {
-  const int gm_key = gm_blocks_per_sm(!fast) > 0 ? kVitDeviceRowsKey + (fast ? 0 : 1000000) : -1;
+int viterbi_shape_key(bool fast, int Mpad, int n_codes, int max_smem, int num_sms, uint64_t n_seqs) {
+  const int gb = gm_blocks_per_sm(!fast);
+  const int gm_key = gb > 0 ? kVitDeviceRowsKey + (fast ? 0 : 1000000) : -1;
   if (Mpad > kStripedMaxM) return gm_key;
   const FastShape s = fast_shape(!fast, Mpad, n_codes, max_smem);
-  if (s.warps * s.blocks < kVitSmemMinWarps && gm_key >= 0) return gm_key;
+  const uint64_t gm_warps = (uint64_t)num_sms * gb * kGmWarps;
+  if (gm_key >= 0 && (s.warps == 0 || (s.warps * s.blocks < kVitSmemMinWarps &&
+                                       n_seqs >= kGmMinSeqsPerWarp * gm_warps)))
+    return gm_key;
   if (s.warps == 0) return -1;
   return (fast ? 0 : 2000000) + (s.nd ? 1000000 : 0) + s.warps * 10000 + s.blocks * 100 + s.carve_pct;
 }

@@ -93,6 +93,17 @@ def test_longest_model(ctx):
     _run(ctx, [synth.make_vit_profile(M, rng), synth.random_vit_profile(M - 31, 20, rng, lo=-3000, hi=500)], db)
 
 
+@pytest.mark.parametrize("M", [2405, 2800])
+def test_device_rows_below_striped_length(ctx, M):
+    """Lengths where shared-memory rows leave six or fewer warps per SM, on a
+    database with enough sequences (8 per resident warp: 19,456 on 152 SMs)
+    that the scan keeps the rows in device memory; a fast and a general
+    profile."""
+    rng = np.random.default_rng(905 + M)
+    db = synth.random_database(21000, 24, rng, alphabet=20, min_len=1)
+    _run(ctx, [synth.make_vit_profile(M, rng), synth.random_vit_profile(M, 20, rng, lo=-2500, hi=300)], db)
+
+
 def test_mixed_groups_in_one_call(ctx):
     """Shared-memory and device-memory groups of both kernels, concurrently
     on the context's fork streams, each device-memory group with its own
