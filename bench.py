@@ -521,6 +521,25 @@ def run_long_model(args, ctx, db, wl, time_steps, clocks, dev):
         log(f"long model M={args.long_m}: {name} {g:.1f} GCUPS ({ms:.1f} ms per launch)")
     prof.close()
     out["roofline_basis"] = "integer-SIMD roofline of the striped kernels (same formula as roofline.peak)"
+    # P7Viterbi on the same model length (DP rows in device memory), one
+    # query against the first sequences of the database.
+    k = min(args.long_vit_seqs, wl.db.n_seqs)
+    vdb = mpf.Database(ctx, wl.db.residues, wl.db.offsets[:k], wl.db.lengths[:k])
+    vp = mpf.VitProfile(ctx, synth.make_vit_profile(args.long_m, np.random.default_rng(901)))
+    vouts = (torch.empty(k, dtype=torch.int16, device=dev), torch.empty(k, dtype=torch.uint8, device=dev),
+             torch.empty(k, dtype=torch.float32, device=dev))
+    run = lambda: mpf.viterbi_scan(ctx, [vp], vdb, *vouts)
+    run()
+    ms = time_steps(run, steps)
+    cells = float(args.long_m) * vdb.n_residues
+    g = cells / (ms * 1e-3) / 1e9
+    peak = nsm * INT_LANES_PER_SM_CLK / VIT_OPS_PER_CELL * sm_mhz * 1e6 / 1e9
+    out["viterbi"] = {"gcups": g, "ms_per_launch": ms, "n_seqs": k, "cells_per_launch": cells,
+                      "roofline_frac": g / peak, "peak": peak,
+                      "kernel": "viterbi_fast_kernel, DP rows in device memory"}
+    log(f"long model M={args.long_m}: viterbi {g:.1f} GCUPS on {k} sequences ({ms:.1f} ms per launch)")
+    vp.close()
+    vdb.close()
     return out
 
 
@@ -624,6 +643,8 @@ def main():
     ap.add_argument("--no-viterbi", dest="viterbi", action="store_false")
     ap.add_argument("--long-m", type=int, default=5000,
                     help="model length of the long-model measurement (0: skip)")
+    ap.add_argument("--long-vit-seqs", type=int, default=40000,
+                    help="sequences of the long-model Viterbi measurement")
     ap.add_argument("--serve-rates", type=float, nargs="+", default=[10, 50, 100, 200, 500])
     ap.add_argument("--serve-requests", type=int, default=24)
     ap.add_argument("--profile-case", action="store_true")

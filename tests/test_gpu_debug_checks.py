@@ -3,8 +3,9 @@
 Every kernel family runs on the debug library over inputs that exercise its
 ragged edges -- striped scans in every lane-group size, rank lists from the
 SSV -> MSV hand-off, long models with 16-bit and byte rows, the Viterbi
-kernels and variants, the MSV -> Viterbi stage -- and no check may fire
-(mpf_sync would raise MPF_EDEVICE); results are compared with the oracle.
+kernels and variants (rows in shared or device memory), the MSV -> Viterbi
+stage -- and no check may fire (mpf_sync would raise MPF_EDEVICE); results
+are compared with the oracle.
 The self-test shows a failed check reaching mpf_sync as MPF_EDEVICE.  The
 debug library runs in a child process so it never mixes with the release
 library the other tests load.
@@ -84,7 +85,7 @@ ssv_out = (mk(torch.uint8), mk(torch.uint8), mk(torch.float32))
 msv_out = (mk(torch.uint8), mk(torch.uint8), mk(torch.float32))
 n_pass = torch.empty(q, dtype=torch.int32, device=dev)
 mpf.pipeline_scan(ctx, profs, db2, -5.0, ssv_out, msv_out, n_pass)
-vrecs = [synth.make_vit_profile(r.M if r.M <= 3072 else 2600, rng) for r in recs]
+vrecs = [synth.make_vit_profile(r.M, rng) for r in recs]   # M = 4000: rows in device memory
 vps = [mpf.VitProfile(ctx, v) for v in vrecs]
 vs, vf, vn = mk(torch.int16), mk(torch.uint8), mk(torch.float32)
 n2 = torch.empty(q, dtype=torch.int32, device=dev)
@@ -101,9 +102,11 @@ for i, r in enumerate(recs):
     assert int(n2.cpu()[i]) == nv
     assert same(vs.cpu().numpy()[sl], want[0]) and same(vn.cpu().numpy()[sl], want[2])
 
-# Viterbi kernels directly: fast (unroll 4 and 8, no D row) and general.
-vrecs = [synth.make_vit_profile(M, rng) for M in (40, 700, 2600)]
+# Viterbi kernels directly: fast (unroll 4 and 8, no D row) and general,
+# with the rows in shared memory and (M > 3072) in device memory.
+vrecs = [synth.make_vit_profile(M, rng) for M in (40, 700, 2600, 3500)]
 vrecs.append(synth.random_vit_profile(150, 20, rng, lo=-500, hi=300))
+vrecs.append(synth.random_vit_profile(3300, 20, rng, lo=-500, hi=300))
 vps = [mpf.VitProfile(ctx, v) for v in vrecs]
 q = len(vps)
 vs, vf, vn = (torch.empty(q * n, dtype=t, device=dev) for t in (torch.int16, torch.uint8, torch.float32))
