@@ -116,8 +116,22 @@ int launch_pvalues(const float *nat, uint64_t n, float mu, float lambda, float *
 // P7Viterbi filter (mpf_viterbi.cu).  Tables are int16 in device memory,
 // striped (node l*Q + j in slot j*32 + l); -32768 is minus infinity.
 constexpr int kVitFastMaxThreads = 512;
-// Viterbi launch keys at or above this keep their DP rows in device memory.
-constexpr int kVitDeviceRowsKey = 3000000;
+// Viterbi launch keys: kind * kVitKeyKind + the launch shape; queries with
+// equal keys share a launch.
+constexpr int kVitKeyKind = 1000000;
+enum VitKind {
+  kVitFastShared = 0,      // fast kernel, DP rows in shared memory
+  kVitFastSharedNoD = 1,   // the same without the stored D row
+  kVitGeneralShared = 2,   // general kernel, rows in shared memory
+  kVitFastDevice = 3,      // fast kernel, rows in device memory
+  kVitGeneralDevice = 4,   // general kernel, rows in device memory
+  kVitFastTeam = 5,        // fast kernel, a team of warps per sequence
+  kVitFastDual = 6,        // both kinds 0/1 and 5, each taking the queries on its side of team_max
+};
+inline int vit_key_kind(int key) { return key / kVitKeyKind; }
+inline bool vit_key_device_rows(int key) {
+  return vit_key_kind(key) == kVitFastDevice || vit_key_kind(key) == kVitGeneralDevice;
+}
 constexpr int kVitRows = 32;         // msc rows: residue codes 0..31
 constexpr int kVitTrans = 8;         // BM, MM, IM, DM, MI, II, MD, DD
 constexpr int kVitSpecial = 8;       // NN, NB, EC, CC, CT, EJ, JJ, JB
@@ -135,6 +149,8 @@ struct VitQuery {
   float *nat;                 // nullable
   const uint32_t *ranks;      // nullable: score only these length ranks (ascending),
   const uint32_t *n_ranks;    //   *n_ranks of them
+  int64_t team_max;           // the team kernel scores the query when it selects at most
+                              //   this many sequences, the one-warp kernels otherwise
 };
 
 struct VitParams {
@@ -152,24 +168,23 @@ struct VitParams {
   uint2 *state;               // models past the shared-memory rows: per-warp DP rows, else null
   uint64_t state_bytes;
 };
-// fast: every transition and special score <= 0 (else the general kernel);
-// tables in the striped layout (msc [32][Q][32] int16, trans [Q][32] x 8
-// int16 with Q = Mpad / 32).  n_codes: distinct residue codes in the
-// database (sizes the L1 share).  Returns 0, 1 on a CUDA error, 2 if the
-// rows do not fit in shared memory.
-int launch_viterbi(const VitParams &p, bool fast, int n_codes, int max_smem, int num_sms,
-                   cudaStream_t st);
-// With p.state set (models longer than kStripedMaxM), the variants that keep
-// the DP rows in device memory; p.state must hold viterbi_state_bytes().
+// key: from viterbi_shape_key for the group's longest model (the kernel
+// and launch shape; kinds with device rows need p.state).  Tables in the
+// striped layout (msc [32][Q][32] int16, trans [Q][32] x 8 int16 with Q =
+// Mpad / 32).  n_codes: distinct residue codes in the database (sizes the
+// L1 share).  Returns 0, 1 on a CUDA error, 2 if the rows do not fit.
+int launch_viterbi(const VitParams &p, int key, int n_codes, int max_smem, int num_sms, cudaStream_t st);
 // Shared memory of a block of `warps` warps that store the D row.
 size_t viterbi_fast_smem_bytes(int Mpad, int warps);
 // Device scratch of a launch over models of up to Mpad nodes that keeps its
 // rows in device memory.
 size_t viterbi_state_bytes(bool fast, int Mpad, int num_sms);
-// Launch shape of a kernel for one model length (equal keys share a launch;
-// keys >= kVitDeviceRowsKey keep the rows in device memory), or -1 if no
-// shape fits.  n_seqs: sequences each query of the launch scores, 0 when
-// the host does not know (a rank list counted on the device).
+// The VitQuery::team_max of a query with this key and length.
+int64_t viterbi_team_max(int key, int Mpad, int n_codes, int max_smem, int num_sms);
+// Launch key (kernel and launch shape) for one model length, or -1 if no
+// shape fits.  fast: every transition and special score <= 0 (else the
+// general kernel).  n_seqs: sequences each query of the launch scores, 0
+// when the host does not know (a rank list counted on the device).
 int viterbi_shape_key(bool fast, int Mpad, int n_codes, int max_smem, int num_sms, uint64_t n_seqs);
 
 // Kernel instantiation for (lanes, words, mode), or nullptr if not built.

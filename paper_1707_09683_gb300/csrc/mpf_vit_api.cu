@@ -82,6 +82,7 @@ int viterbi_enqueue(mpf_ctx *ctx, const mpf_vprofile *const *vps, int n_q, const
     d.nat = nat ? nat + (uint64_t)q * n : nullptr;
     d.ranks = ranks ? ranks + (uint64_t)q * n : nullptr;
     d.n_ranks = n_ranks ? n_ranks + q : nullptr;
+    d.team_max = viterbi_team_max(std::get<0>(o), v->Mpad, db->n_codes, ctx->max_smem, ctx->num_sms);
     qs.push_back(d);
   }
   // Groups run concurrently on the context's fork streams, so that one
@@ -99,7 +100,7 @@ int viterbi_enqueue(mpf_ctx *ctx, const mpf_vprofile *const *vps, int n_q, const
       ++last;
     }
     const mpf_vprofile *v0 = vps[std::get<2>(order[(size_t)first])];
-    const size_t len = std::get<0>(order[(size_t)first]) >= kVitDeviceRowsKey
+    const size_t len = vit_key_device_rows(std::get<0>(order[(size_t)first]))
                            ? viterbi_state_bytes(v0->fast, max_Mpad, ctx->num_sms)
                            : 0;
     groups.emplace_back(first, last);
@@ -156,8 +157,7 @@ int viterbi_enqueue(mpf_ctx *ctx, const mpf_vprofile *const *vps, int n_q, const
     p.counters = counters + first;
     p.state = state_len[gi] ? reinterpret_cast<uint2 *>(dev + state_off[gi]) : nullptr;
     p.state_bytes = state_len[gi];
-    const int lr = launch_viterbi(p, vps[std::get<2>(order[(size_t)first])]->fast, db->n_codes, ctx->max_smem,
-                                  ctx->num_sms, st);
+    const int lr = launch_viterbi(p, key, db->n_codes, ctx->max_smem, ctx->num_sms, st);
     if (lr) rc = lr == 2 ? MPF_EUNSUPPORTED : MPF_ECUDA;
     if (fork && cudaEventRecord(evs[gi], st) != cudaSuccess) rc = MPF_ECUDA;
   }

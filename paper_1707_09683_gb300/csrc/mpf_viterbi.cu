@@ -105,6 +105,14 @@ __device__ __forceinline__ void store_rows(uint2 *g, int sl, int Mn, int In, int
   __stcg(g + sl, make_uint2(__byte_perm((uint32_t)Mn, (uint32_t)In, 0x5410), (uint32_t)d));
 }
 
+// Whether a launch scores query Q: the team kernel takes it when it selects
+// at most Q.team_max sequences (a count the host may not know: rank lists
+// are counted on the device), the one-warp kernels otherwise.
+__device__ __forceinline__ bool takes_query(const VitQuery &Q, uint32_t n_seqs, bool team) {
+  const int64_t n = Q.ranks ? (int64_t)*Q.n_ranks : (int64_t)n_seqs;
+  return team ? n <= Q.team_max : n > Q.team_max;
+}
+
 // One node of a lane's sweep (fast kernel): the previous row's M, I and
 // segment-local D of this node arrive in Mo, Io, Dl; the node's new M, I and
 // local D leave in Mn, In, d.  dM, dI, dD hold the previous row's values of
@@ -174,6 +182,7 @@ __global__ void __launch_bounds__(kVitFastMaxThreads, 1) viterbi_fast_kernel(Vit
     const VitQuery Q = p.queries[qi];
     const int nq = Q.Mpad >> 5;
     if (!MPF_DCHECK(p.status, Q.Mpad <= p.max_Mpad && (!Q.ranks || *Q.n_ranks <= p.n_seqs))) continue;
+    if (!takes_query(Q, p.n_seqs, false)) continue;
     const uint4 *gtr = reinterpret_cast<const uint4 *>(Q.trans);
     stage_transitions<GM>(tr, gtr, nq);
     const TransSrc<GM> T{tr, gtr};
@@ -336,6 +345,7 @@ __global__ void __launch_bounds__(kVitFastMaxThreads, 1) viterbi_general_kernel(
     const VitQuery Q = p.queries[qi];
     const int nq = Q.Mpad >> 5;
     if (!MPF_DCHECK(p.status, Q.Mpad <= p.max_Mpad && (!Q.ranks || *Q.n_ranks <= p.n_seqs))) continue;
+    if (!takes_query(Q, p.n_seqs, false)) continue;
     const uint4 *gtr = reinterpret_cast<const uint4 *>(Q.trans);
     stage_transitions<GM>(tr, gtr, nq);
     const TransSrc<GM> T{tr, gtr};
@@ -499,6 +509,220 @@ __global__ void __launch_bounds__(kVitFastMaxThreads, 1) viterbi_general_kernel(
   }
 }
 
+// ------------------------------------------------------------ team kernel
+//
+// One team of kTeamW warps scores one sequence (fast-kernel scores).  Lane
+// l's segment of Q nodes is cut into kTeamW sub-segments of ceil(Q/kTeamW)
+// nodes, sub-segment w swept by warp w of the team, so a row takes about
+// Q/kTeamW node steps instead of Q.  In node order the sub-segments form
+// one chain, lane-major: (0,0) .. (0,W-1), (1,0) ...  After its sweep each
+// warp publishes, per lane, the M and I of its sub-segment's last node, its
+// local delete-chain end and its row maximum; one named barrier per row
+// makes them visible to the team (two buffers, by row parity).  Every warp
+// then composes, per lane, the maps d -> max(A, d + B) of the lane's
+// sub-segments in order, runs the warp scan over lanes as the one-warp
+// kernel does, and applies the first w maps of its lane to the delete score
+// entering the lane: the true delete score entering its own sub-segment.
+// All warps of a team keep identical special states and leave a sequence
+// together.  For launches with few sequences per warp, whose time is set by
+// the longest sequences' rows.
+
+constexpr int kTeamW = 4;
+
+struct TeamExchange {
+  int Mlast[kTeamW][32];
+  int Ilast[kTeamW][32];
+  int dlast[kTeamW][32];
+  int xe[kTeamW];
+};
+
+__host__ __device__ constexpr size_t team_bytes(int Qmax) {
+  return (((size_t)Qmax * 32 * 6 + 2 * sizeof(TeamExchange) + 16) + 15) & ~(size_t)15;
+}
+
+__device__ __forceinline__ void team_barrier(int id) {
+  asm volatile("bar.sync %0, %1;" ::"r"(id), "r"(kTeamW * 32) : "memory");
+}
+
+template <int U>
+__global__ void __launch_bounds__(kVitFastMaxThreads, 1) viterbi_team_kernel(VitParams p) {
+  extern __shared__ __align__(16) uint4 fsm[];
+  const int lane = threadIdx.x & 31;
+  const int warp = threadIdx.x >> 5;
+  const int team = warp / kTeamW, w = warp % kTeamW;
+  const int Qmax = p.max_Mpad >> 5;
+  uint4 *tr = fsm;
+  uint8_t *tb = reinterpret_cast<uint8_t *>(fsm + (size_t)Qmax * 32) + (size_t)team * team_bytes(Qmax);
+  int16_t *sM = reinterpret_cast<int16_t *>(tb);
+  int16_t *sI = sM + (size_t)Qmax * 32;
+  int16_t *sD = sI + (size_t)Qmax * 32;
+  TeamExchange *ex = reinterpret_cast<TeamExchange *>(tb + (size_t)Qmax * 32 * 6);
+  volatile uint32_t *bcast = reinterpret_cast<volatile uint32_t *>(ex + 2);
+  const int bar = 1 + team;   // named barrier of this team (0 is __syncthreads)
+  // Debug builds: whole teams, at most 15 per block, and their rows and
+  // exchange buffers within the block's shared memory.
+  if (!MPF_DCHECK(p.status, (blockDim.x & (kTeamW * 32 - 1)) == 0 && (blockDim.x >> 5) / kTeamW <= 15 &&
+                                (size_t)Qmax * 32 * 16 + ((blockDim.x >> 5) / kTeamW) * team_bytes(Qmax) <=
+                                    dynamic_smem_bytes()))
+    return;
+
+  for (uint32_t qi = 0; qi < p.n_queries; ++qi) {
+    const VitQuery Q = p.queries[qi];
+    const int nq = Q.Mpad >> 5;
+    if (!MPF_DCHECK(p.status, Q.Mpad <= p.max_Mpad && (!Q.ranks || *Q.n_ranks <= p.n_seqs))) continue;
+    if (!takes_query(Q, p.n_seqs, true)) continue;
+    const uint4 *gtr = reinterpret_cast<const uint4 *>(Q.trans);
+    stage_transitions<false>(tr, gtr, nq);
+
+    // Per-lane constants.  Whole segment: nv nodes, Bl = sum of tDD, the
+    // window sums Wn of the lane scan (as in the one-warp kernel).  Per
+    // sub-segment v of this lane: Bw[v] = sum of its tDD, and cMB[v] = tMD +
+    // (Bw - tDD) of its first node, so that its map's A is max(M of the node
+    // before + cMB, local chain end); an empty sub-segment is the identity.
+    const int nv = min(max(Q.M - lane * nq, 0), nq);
+    const int qw = (nq + kTeamW - 1) / kTeamW;
+    int Bw[kTeamW], cMB[kTeamW];
+    int Bl = 0, tDDf = 0, tMDf = kNeg;
+#pragma unroll
+    for (int v = 0; v < kTeamW; ++v) {
+      const int jb = v * qw, je = min(nv, jb + qw);
+      int B = 0;
+      for (int j = jb; j < je; ++j) B += hi16(tr[j * 32 + lane].w);
+      Bw[v] = B;
+      Bl += B;
+      cMB[v] = -(1 << 29);
+      if (je > jb) {
+        const uint32_t t = tr[jb * 32 + lane].w;
+        cMB[v] = lo16(t) + (B - hi16(t));
+        if (v == w) {
+          tMDf = lo16(t);
+          tDDf = hi16(t);
+        }
+      }
+    }
+    const int jb = w * qw, je = min(nv, jb + qw);   // this warp's nodes of the lane
+    const int vlast = (nq - 1) / qw;                  // last non-empty sub-segment of a full lane
+    uint32_t P = (uint32_t)Bl;   // prefix over lanes modulo 2^32 (see the one-warp kernel)
+#pragma unroll
+    for (int off = 1; off < 32; off <<= 1) {
+      const uint32_t y = __shfl_up_sync(kAll, P, off);
+      if (lane >= off) P += y;
+    }
+    int Wn[5];
+#pragma unroll
+    for (int r = 0; r < 5; ++r) {
+      const uint32_t y = __shfl_up_sync(kAll, P, 1 << r);
+      Wn[r] = lane >= (1 << r) ? (int)(P - y) : -(1 << 29);
+    }
+    const int tNN = Q.sp[0], tNB = Q.sp[1], tEC = Q.sp[2], tCC = Q.sp[3];
+    const int tCT = Q.sp[4], tEJ = Q.sp[5], tJJ = Q.sp[6], tJB = Q.sp[7];
+    const uint64_t n_sel = Q.ranks ? (uint64_t)*Q.n_ranks : (uint64_t)p.n_seqs;
+
+    for (;;) {
+      if (w == 0 && lane == 0) bcast[0] = atomicAdd(p.counters + qi, 1u);
+      team_barrier(bar);
+      const uint32_t q = bcast[0];
+      team_barrier(bar);   // read by all before the next sequence's write
+      if ((uint64_t)q >= n_sel) break;
+      const uint32_t r = Q.ranks ? __ldg(Q.ranks + q) : q;
+      if (!MPF_DCHECK(p.status, r < p.n_seqs)) continue;
+      const uint32_t w0 = __ldg(p.seq_word + r);
+      const int len = (int)__ldg(p.seq_len + r);
+      const uint32_t orig = __ldg(p.seq_orig + r);
+      if (!MPF_DCHECK(p.status, (uint64_t)w0 + (uint64_t)((len + 3) >> 2) <= p.n_words && orig < p.n_seqs))
+        continue;
+
+      for (int j = jb; j < min(nq, jb + qw); ++j)
+        sM[j * 32 + lane] = sI[j * 32 + lane] = sD[j * 32 + lane] = (int16_t)kNeg;
+      int xN = Q.base, xJ = kNeg, xC = kNeg;
+      int xB = addmax(xN, tNB, kNeg);
+      // Previous row: M, I and true D of the node before this sub-segment,
+      // and the carried delete chain (X0m + tDD of the first node is its
+      // value there).
+      int pM0 = kNeg, pI0 = kNeg, pD0 = kNeg, X0m = kNeg - tDDf;
+      bool ovf = false;
+      int par = 0;
+      uint32_t word = 0;
+      for (int i = 0; i < len; ++i) {
+        if ((i & 3) == 0) word = __ldg(p.residues + w0 + (uint32_t)(i >> 2));
+        int x = (int)((word >> (8 * (i & 3))) & 0xffu);
+        if (!MPF_DCHECK(p.status, x < kVitRows)) x = 0;
+        const int16_t *erow = Q.msc + (size_t)x * nq * 32 + lane;
+
+        FastCell c{pM0, pI0, pD0, X0m, kNeg, kNeg, kNeg, kNeg, kNeg, kNeg, kNeg};
+#pragma unroll U
+        for (int j = jb; j < je; ++j) {
+          const int sl = j * 32 + lane;
+          c.step(tr[sl], __ldg(erow + j * 32), sM[sl], sI[sl], sD[sl], xB);
+          sD[sl] = (int16_t)c.d;
+          sM[sl] = (int16_t)c.Mn;
+          sI[sl] = (int16_t)c.In;
+        }
+        TeamExchange &E = ex[par];
+        E.Mlast[w][lane] = c.Mn;
+        E.Ilast[w][lane] = c.In;
+        E.dlast[w][lane] = c.d;
+        const int mx = __reduce_max_sync(kAll, c.mx);
+        if (lane == 0) E.xe[w] = mx;
+        team_barrier(bar);
+        int xE = E.xe[0];
+#pragma unroll
+        for (int v = 1; v < kTeamW; ++v) xE = max(xE, E.xe[v]);
+        if (xE >= 32767) {
+          ovf = true;
+          break;
+        }
+
+        // The lane's map, composed over its sub-segments in node order; the
+        // node before sub-segment 0 is the last node of the lane before (a
+        // full lane: its last non-empty sub-segment is vlast).
+        const int Mbefore = lane > 0 ? E.Mlast[vlast][lane - 1] : kNeg;
+        const int Ibefore = lane > 0 ? E.Ilast[vlast][lane - 1] : kNeg;
+        int Av[kTeamW];
+        int AF = -(1 << 29);
+#pragma unroll
+        for (int v = 0; v < kTeamW; ++v) {
+          const int Mp = v == 0 ? Mbefore : E.Mlast[v - 1][lane];
+          Av[v] = addmax(Mp, cMB[v], E.dlast[v][lane]);
+          AF = addmax(AF, Bw[v], Av[v]);
+        }
+        int A = AF;
+#pragma unroll
+        for (int rr = 0; rr < 5; ++rr) A = addmax(__shfl_up_sync(kAll, A, 1 << rr), Wn[rr], A);
+        int din = __shfl_up_sync(kAll, A, 1);
+        if (lane == 0) din = kNeg;
+#pragma unroll
+        for (int v = 0; v < kTeamW; ++v)
+          if (v < w) din = addmax(din, Bw[v], Av[v]);
+        const int Mp = w == 0 ? Mbefore : E.Mlast[w - 1][lane];
+        const int Ip = w == 0 ? Ibefore : E.Ilast[w - 1][lane];
+        pM0 = Mp;
+        pI0 = Ip;
+        pD0 = din;
+        X0m = max(din + tDDf, Mp + tMDf) - tDDf;
+        par ^= 1;
+
+        xN = addmax(xN, tNN, kNeg);
+        xC = addmax(xC, tCC, addmax(xE, tEC, kNeg));
+        xJ = addmax(xJ, tJJ, addmax(xE, tEJ, kNeg));
+        xB = addmax(xN, tNB, addmax(xJ, tJB, kNeg));
+      }
+      if (w == 0 && lane == 0) {
+        if (ovf) {
+          Q.score[orig] = 32767;
+          Q.flag[orig] = 1;
+          if (Q.nat) Q.nat[orig] = __int_as_float(0x7f800000);
+        } else {
+          const int sc = addmax(xC, tCT, kNeg);
+          Q.score[orig] = (int16_t)sc;
+          Q.flag[orig] = 0;
+          if (Q.nat) Q.nat[orig] = __fsub_rn(__fdiv_rn(__int2float_rn(sc - Q.base), Q.scale), 3.0f);
+        }
+      }
+    }
+  }
+}
+
 }  // namespace
 
 size_t viterbi_fast_smem_bytes(int Mpad, int warps) {
@@ -624,6 +848,44 @@ FastShape fast_shape(bool general, int Mpad, int n_codes, int max_smem_block) {
   return FastShape();
 }
 
+// Launch shape of the team kernel: teams of kTeamW warps per block (at most
+// 512 threads), each team with its own DP rows and exchange buffers, the
+// same L1-aware carveout choice as fast_shape.
+FastShape team_shape(int Mpad, int n_codes, int max_smem_block) {
+  constexpr size_t kKB = 1024, kUnified = 256 * kKB, kCarveMax = 228 * kKB;
+  const int Q = Mpad >> 5;
+  static const int regs = [] {
+    cudaFuncAttributes a;
+    return cudaFuncGetAttributes(&a, (const void *)viterbi_team_kernel<4>) == cudaSuccess ? a.numRegs : 255;
+  }();
+  const int warp_regs = ((regs + 7) / 8) * 8 * 32;
+  const size_t ws = std::min((size_t)std::max(n_codes, 1) * 2 * (size_t)Mpad, 124 * kKB);
+  static const int carves_kb[] = {228, 196, 164, 132, 100};
+  for (int c : carves_kb) {
+    const size_t C = (size_t)c * kKB;
+    if (kUnified - C < ws && c != 100) continue;
+    FastShape best;
+    for (int t = kVitFastMaxThreads / (32 * kTeamW); t >= 1; --t) {
+      const int w = t * kTeamW;
+      const size_t sm = (size_t)Q * 32 * 16 + (size_t)t * team_bytes(Q);
+      if (sm > (size_t)max_smem_block || sm + kKB > C) continue;
+      int b = (int)(C / (sm + kKB));
+      b = std::min(b, 65536 / (warp_regs * w));
+      b = std::min(b, 64 / w);
+      if (b < 1) continue;
+      if (w * b > best.warps * best.blocks) {
+        best.warps = w;
+        best.blocks = b;
+        best.smem = sm;
+      }
+    }
+    if (best.warps == 0) continue;
+    best.carve_pct = (int)std::min<size_t>(100, ((C - kKB) * 100) / kCarveMax);
+    return best;
+  }
+  return FastShape();
+}
+
 }  // namespace
 
 size_t viterbi_state_bytes(bool fast, int Mpad, int num_sms) {
@@ -646,41 +908,96 @@ size_t viterbi_state_bytes(bool fast, int Mpad, int num_sms) {
 // rows are taken there only with at least 8 sequences per warp.
 constexpr int kVitSmemMinWarps = 7;
 constexpr uint64_t kGmMinSeqsPerWarp = 8;
+// Teams where the host cannot count the sequences (rank lists of the MSV ->
+// Viterbi stage, whose survivors are few per warp), for segments of at
+// least 8 nodes per lane (M > 224): with fewer, the per-row exchange costs
+// more than the shorter sweep saves.
+constexpr int kTeamMinQ = 8;
+
+int shape_bits(const FastShape &s) { return s.warps * 10000 + s.blocks * 100 + s.carve_pct; }
+
+// Sequences up to which the team kernel is ahead of the one-warp kernel of
+// shape s.  Measured (one query, the first N sequences of the sweep
+// database, GCUPS one-warp / team): N = 1,000 and 3,000, M = 256-2405: the
+// team ahead everywhere (1.3-2.2x); N = 15,000: M = 400 397 / 245, 800 514 /
+// 444, 1600 539 / 562, 2405 (six one-warp warps per SM) 486 / 614.  So the
+// team takes every count where the one-warp shape keeps six or fewer warps
+// per SM, and otherwise up to about Q/8 sequences per resident one-warp
+// worker (the break-even grows with the segment length Q).
+int64_t team_max_for(const FastShape &s, int Mpad, int num_sms) {
+  if (s.warps * s.blocks < kVitSmemMinWarps) return INT64_MAX;
+  return (int64_t)(Mpad >> 5) * num_sms * s.warps * s.blocks / 8;
+}
 
 int viterbi_shape_key(bool fast, int Mpad, int n_codes, int max_smem, int num_sms, uint64_t n_seqs) {
   const int gb = gm_blocks_per_sm(!fast);
-  const int gm_key = gb > 0 ? kVitDeviceRowsKey + (fast ? 0 : 1000000) : -1;
+  const int gm_key = gb > 0 ? (fast ? kVitFastDevice : kVitGeneralDevice) * kVitKeyKind : -1;
   if (Mpad > kStripedMaxM) return gm_key;
   const FastShape s = fast_shape(!fast, Mpad, n_codes, max_smem);
   const uint64_t gm_warps = (uint64_t)num_sms * gb * kGmWarps;
-  if (gm_key >= 0 && (s.warps == 0 || (s.warps * s.blocks < kVitSmemMinWarps &&
-                                       n_seqs >= kGmMinSeqsPerWarp * gm_warps)))
-    return gm_key;
+  const bool few_warps = s.warps * s.blocks < kVitSmemMinWarps;
+  if (gm_key >= 0 && (s.warps == 0 || (few_warps && n_seqs >= kGmMinSeqsPerWarp * gm_warps))) return gm_key;
   if (s.warps == 0) return -1;
-  return (fast ? 0 : 2000000) + (s.nd ? 1000000 : 0) + s.warps * 10000 + s.blocks * 100 + s.carve_pct;
+  const int one_kind = !fast ? kVitGeneralShared : s.nd ? kVitFastSharedNoD : kVitFastShared;
+  const int one_key = one_kind * kVitKeyKind + shape_bits(s);
+  if (!fast || (Mpad >> 5) < kTeamMinQ) return one_key;
+  const FastShape t = team_shape(Mpad, n_codes, max_smem);
+  if (t.warps == 0) return one_key;
+  const int team_key = kVitFastTeam * kVitKeyKind + shape_bits(t);
+  if (n_seqs > 0) return (int64_t)n_seqs <= team_max_for(s, Mpad, num_sms) ? team_key : one_key;
+  return few_warps ? team_key : kVitFastDual * kVitKeyKind + shape_bits(s);
 }
 
-int launch_viterbi(const VitParams &p, bool fast, int n_codes, int max_smem, int num_sms,
-                   cudaStream_t st) {
+int64_t viterbi_team_max(int key, int Mpad, int n_codes, int max_smem, int num_sms) {
+  switch (vit_key_kind(key)) {
+    case kVitFastTeam:
+      return INT64_MAX;
+    case kVitFastDual:
+      return team_max_for(fast_shape(false, Mpad, n_codes, max_smem), Mpad, num_sms);
+    default:
+      return -1;
+  }
+}
+
+int launch_viterbi(const VitParams &p, int key, int n_codes, int max_smem, int num_sms, cudaStream_t st) {
   if (p.n_queries == 0) return 0;
-  if (p.state) {
-    const int b = gm_blocks_per_sm(!fast);
+  const int kind = vit_key_kind(key);
+  if (kind == kVitFastDevice || kind == kVitGeneralDevice) {
+    const bool general = kind == kVitGeneralDevice;
+    const int b = gm_blocks_per_sm(general);
     if (b < 1) return 2;
-    if (p.state_bytes < viterbi_state_bytes(fast, p.max_Mpad, num_sms)) return 1;
-    const void *fn = (const void *)gm_kernel_for(!fast);
+    if (!p.state || p.state_bytes < viterbi_state_bytes(!general, p.max_Mpad, num_sms)) return 1;
+    const void *fn = (const void *)gm_kernel_for(general);
     if (cudaFuncSetAttribute(fn, cudaFuncAttributePreferredSharedMemoryCarveout, 0) != cudaSuccess) return 1;
-    gm_kernel_for(!fast)<<<num_sms * b, kGmWarps * 32, 0, st>>>(p);
+    gm_kernel_for(general)<<<num_sms * b, kGmWarps * 32, 0, st>>>(p);
     return cudaGetLastError() == cudaSuccess ? 0 : 1;
   }
-  const FastShape s = fast_shape(!fast, p.max_Mpad, n_codes, max_smem);
-  if (s.warps == 0) return 2;
-  const VitKernelFn k = vit_kernel_for(!fast, p.max_Mpad >> 5, s.nd);
-  const void *fn = (const void *)k;
-  if (cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)s.smem) != cudaSuccess ||
-      cudaFuncSetAttribute(fn, cudaFuncAttributePreferredSharedMemoryCarveout, s.carve_pct) != cudaSuccess)
-    return 1;
-  k<<<num_sms * s.blocks, s.warps * 32, s.smem, st>>>(p);
-  return cudaGetLastError() == cudaSuccess ? 0 : 1;
+  // Shared-memory kernels; a dual launch runs the one-warp kernel, then the
+  // team kernel, each scoring the queries on its side of team_max (the
+  // other exits at once).
+  int rc = 0;
+  for (int pass = 0; pass < 2 && rc == 0; ++pass) {
+    const bool team = kind == kVitFastTeam || (kind == kVitFastDual && pass == 1);
+    if (pass == 1 && !team) break;
+    FastShape s;
+    VitKernelFn k;
+    if (team) {
+      s = team_shape(p.max_Mpad, n_codes, max_smem);
+      k = viterbi_team_kernel<4>;
+    } else {
+      const bool general = kind == kVitGeneralShared;
+      s = fast_shape(general, p.max_Mpad, n_codes, max_smem);
+      k = vit_kernel_for(general, p.max_Mpad >> 5, s.nd);
+    }
+    if (s.warps == 0) return 2;
+    const void *fn = (const void *)k;
+    if (cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)s.smem) != cudaSuccess ||
+        cudaFuncSetAttribute(fn, cudaFuncAttributePreferredSharedMemoryCarveout, s.carve_pct) != cudaSuccess)
+      return 1;
+    k<<<num_sms * s.blocks, s.warps * 32, s.smem, st>>>(p);
+    rc = cudaGetLastError() == cudaSuccess ? 0 : 1;
+  }
+  return rc;
 }
 
 }  // namespace mpf
