@@ -976,9 +976,9 @@ int launch_viterbi(const VitParams &p, int key, int n_codes, int max_smem, int n
   // team kernel, each scoring the queries on its side of team_max (the
   // other exits at once).
   int rc = 0;
-  for (int pass = 0; pass < 2 && rc == 0; ++pass) {
+  const int passes = kind == kVitFastDual ? 2 : 1;
+  for (int pass = 0; pass < passes && rc == 0; ++pass) {
     const bool team = kind == kVitFastTeam || (kind == kVitFastDual && pass == 1);
-    if (pass == 1 && !team) break;
     FastShape s;
     VitKernelFn k;
     if (team) {
