@@ -148,3 +148,15 @@ def test_msv_to_viterbi_stage_long_model(ctx):
     vp.close()
     prof.close()
     db.close()
+
+
+def test_more_groups_than_fork_streams(ctx):
+    """Twelve launch groups in one call (distinct lengths and kernels: one
+    warp per sequence, team, general, rows in device memory), more than the
+    context's eight fork streams, each device-row group with its own slice
+    of scratch."""
+    rng = np.random.default_rng(906)
+    wl = synth.make_workload(0, n_seqs=400)
+    vprofs = [synth.make_vit_profile(m, rng) for m in (40, 90, 150, 230, 500, 1000, 2405, 3500, 6000)]
+    vprofs += [synth.random_vit_profile(m, 20, rng, lo=-3000, hi=300) for m in (120, 1500, 4100)]
+    _run(ctx, vprofs, wl.db)
