@@ -201,6 +201,50 @@ int get_long_table(const mpf_profile *p, const uint8_t **out) {
   return MPF_OK;
 }
 
+// Device copy of a long profile's scores for the tiled SSV kernel: per tile
+// of kTileNodes nodes, [code][chunk][lane] x 8 int16 with lane l holding
+// nodes (l * kTileC .. + kTileC - 1) of the tile, s = bias - cost (codes >= K
+// cost 255), -32768 past M.
+int get_tile_table(const mpf_profile *p, const uint4 **out) {
+  std::lock_guard<std::mutex> lk(p->mu);
+  auto key = std::make_tuple(32, 0, 3);
+  auto it = p->tables.find(key);
+  if (it != p->tables.end()) {
+    *out = it->second.ptr;
+    return MPF_OK;
+  }
+  const int M = p->M, nt = (M + kTileNodes - 1) / kTileNodes;
+  constexpr int kChunks = kTileC / 8;
+  std::vector<int16_t> img((size_t)nt * kTileTableBytes / 2);
+  for (int t = 0; t < nt; ++t)
+    for (int x = 0; x < 32; ++x)
+      for (int l = 0; l < 32; ++l)
+        for (int c = 0; c < kTileC; ++c) {
+          const int k = t * kTileNodes + l * kTileC + c;
+          int16_t s = -32768;
+          if (k < M) s = (int16_t)(p->bias - (x < p->K ? (int)p->cost[(size_t)x * M + k] : 255));
+          const size_t chunk = (((size_t)t * 32 + x) * kChunks + c / 8) * 32 + l;
+          img[chunk * 8 + c % 8] = s;
+        }
+  mpf_ctx *ctx = p->ctx;
+  DeviceGuard dg(ctx->device);
+  uint4 *d = nullptr;
+  const size_t bytes = img.size() * sizeof(int16_t);
+  MPF_CUDA(cudaMallocAsync((void **)&d, bytes, ctx->util));
+  cudaError_t e = cudaMemcpyAsync(d, img.data(), bytes, cudaMemcpyHostToDevice, ctx->util);
+  if (e == cudaSuccess) e = cudaStreamSynchronize(ctx->util);
+  if (e != cudaSuccess) {
+    (void)cudaGetLastError();
+    cudaFreeAsync(d, ctx->util);
+    return MPF_ECUDA;
+  }
+  DevTable t;
+  t.ptr = d;
+  p->tables[key] = t;
+  *out = d;
+  return MPF_OK;
+}
+
 int ensure_out_scratch(mpf_ctx *ctx, size_t bytes) {
   if (ctx->d_out_bytes >= bytes) return MPF_OK;
   if (ctx->d_out) {
@@ -217,7 +261,7 @@ int ensure_out_scratch(mpf_ctx *ctx, size_t bytes) {
 // Kernel mode of a profile for a filter.  Automatic arithmetic: fp16 cells
 // (FMA pipe) for both filters.
 int kernel_mode(const mpf_profile *p, int filter) {
-  if (p->seg_words) return filter == MPF_MSV ? MODE_LONG_MSV : MODE_LONG_SSV;
+  if (p->seg_words) return filter == MPF_MSV ? MODE_LONG_MSV : MODE_TILE_SSV;
   const bool f16 = p->arith[filter] != MPF_ARITH_I16;
   if (filter == MPF_SSV) return f16 ? MODE_SSV_F16 : MODE_SSV;
   if (!msv_fast_ok(p)) return MODE_MSV_DIRECT;
@@ -241,6 +285,9 @@ struct LaunchGroup {
   QueryDesc *d_queries = nullptr;
   uint32_t n_queries = 0;
   uint32_t *d_counter = nullptr;
+  uint8_t *d_col = nullptr;      // tiled SSV kernel: one column of col_stride bytes per resident warp
+  uint32_t col_stride = 0;
+  uint64_t col_bytes = 0;
 };
 
 struct mpf_plan {
@@ -261,6 +308,7 @@ void plan_free(mpf_plan *pl) {
   for (auto &g : pl->groups) {
     if (g.d_queries) cudaFreeAsync(g.d_queries, pl->ctx->stream);
     if (g.d_counter) cudaFreeAsync(g.d_counter, pl->ctx->stream);
+    if (g.d_col) cudaFreeAsync(g.d_col, pl->ctx->stream);
   }
   for (auto e : pl->events) cudaEventDestroy(e);
   (void)cudaGetLastError();
@@ -276,6 +324,22 @@ int free_pending(mpf_ctx *ctx) {
 }
 
 int configure_kernel(mpf_ctx *ctx, LaunchGroup *g) {
+  if (g->mode == MODE_TILE_SSV) {
+    // Blocks of kTileWarps warps with one tile's scores in shared memory.
+    g->fn = tile_ssv_kernel_fn();
+    g->threads = kTileWarps * 32;
+    g->smem = (uint32_t)kTileTableBytes;
+    MPF_CUDA(cudaFuncSetAttribute((const void *)g->fn, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                  (int)g->smem));
+    MPF_CUDA(cudaFuncSetAttribute((const void *)g->fn, cudaFuncAttributePreferredSharedMemoryCarveout, 100));
+    int per_sm = 0;
+    MPF_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, (const void *)g->fn, g->threads,
+                                                           g->smem));
+    if (per_sm < 1) return MPF_EUNSUPPORTED;
+    g->grid = ctx->num_sms * per_sm;
+    g->n_shards = (uint32_t)g->grid;
+    return MPF_OK;
+  }
   if (g->mode == MODE_LONG_MSV || g->mode == MODE_LONG_SSV) {
     // Each warp reads the cost rows of its residues from device memory, so
     // when the rows of the codes the database uses (n_codes x 128 x
@@ -366,7 +430,16 @@ int plan_create(mpf_ctx *ctx, int filter, const mpf_profile *const *profs, int n
     QueryDesc q;
     memset(&q, 0, sizeof(q));
     int lanes = 32, words = 0;
-    if (p->seg_words) {
+    if (mode == MODE_TILE_SSV) {
+      const uint4 *tt = nullptr;
+      int rc = get_tile_table(p, &tt);
+      if (rc) {
+        plan_free(pl);
+        return rc;
+      }
+      q.table = tt;
+      q.M = (uint32_t)p->M;
+    } else if (p->seg_words) {
       const uint8_t *lt = nullptr;
       int rc = get_long_table(p, &lt);
       if (rc) {
@@ -431,12 +504,18 @@ int plan_create(mpf_ctx *ctx, int filter, const mpf_profile *const *profs, int n
     g.n_queries = (uint32_t)kv.second.size();
     cudaError_t e = cudaMallocAsync((void **)&g.d_queries, sizeof(QueryDesc) * kv.second.size(), ctx->stream);
     if (e == cudaSuccess) e = cudaMallocAsync((void **)&g.d_counter, sizeof(uint32_t), ctx->stream);
+    if (e == cudaSuccess && g.mode == MODE_TILE_SSV) {
+      g.col_stride = (std::max<uint32_t>(db->max_len, 1) + 15u) & ~15u;
+      g.col_bytes = (uint64_t)g.grid * kTileWarps * g.col_stride;
+      e = cudaMallocAsync((void **)&g.d_col, g.col_bytes, ctx->stream);
+    }
     if (e == cudaSuccess)
       e = cudaMemcpyAsync(g.d_queries, kv.second.data(), sizeof(QueryDesc) * kv.second.size(),
                           cudaMemcpyHostToDevice, ctx->stream);
     if (e != cudaSuccess) {
       if (g.d_queries) cudaFreeAsync(g.d_queries, ctx->stream);
       if (g.d_counter) cudaFreeAsync(g.d_counter, ctx->stream);
+      if (g.d_col) cudaFreeAsync(g.d_col, ctx->stream);
       (void)cudaGetLastError();
       plan_free(pl);
       return e == cudaErrorMemoryAllocation ? MPF_ENOMEM : MPF_ECUDA;
@@ -468,7 +547,7 @@ int plan_create(mpf_ctx *ctx, int filter, const mpf_profile *const *profs, int n
 
 int enqueue_group(const mpf_db *db, mpf_ctx *ctx, LaunchGroup &g, cudaStream_t st) {
   MPF_CUDA(cudaMemsetAsync(g.d_counter, 0, sizeof(uint32_t), st));
-  ScanParams sp;
+  ScanParams sp{};
   sp.residues = db->d_words;
   sp.n_words = db->n_words;
   sp.seq_word = db->d_seq_word;
@@ -482,6 +561,9 @@ int enqueue_group(const mpf_db *db, mpf_ctx *ctx, LaunchGroup &g, cudaStream_t s
   sp.item_counter = g.d_counter;
   sp.status = ctx->d_status;
   sp.long_words = g.long_words;
+  sp.tile_col = g.d_col;
+  sp.tile_col_stride = g.col_stride;
+  sp.tile_col_bytes = g.col_bytes;
   const int grid = (int)std::min<uint64_t>((uint64_t)g.grid, (uint64_t)g.n_queries * g.n_shards);
   g.fn<<<grid, g.threads, g.smem, st>>>(sp);
   MPF_CUDA(cudaGetLastError());
@@ -817,6 +899,7 @@ int mpf_db_upload(mpf_ctx *ctx, const uint8_t *residues, uint64_t n_residues,
   for (uint64_t s = 0; s < n_seqs; ++s) db->n_residues += lengths[s];
   db->pad_word = 0;
   db->n_codes = __builtin_popcount(seen);
+  db->max_len = n_seqs ? seq_len[0] : 0;
   const size_t ns = std::max<uint64_t>(n_seqs, 1);
   db->n_words = (uint32_t)(chunks * 4);
   cudaError_t e = cudaMalloc(&db->d_words, chunks * 16);

@@ -69,6 +69,7 @@ struct mpf_db {
   uint32_t *d_seq_orig = nullptr;
   uint32_t pad_word = 0;
   int n_codes = 0;                  // distinct residue codes present
+  uint32_t max_len = 0;             // longest sequence
 };
 
 // ---------------------------------------------------------------- helpers --

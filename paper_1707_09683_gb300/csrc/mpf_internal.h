@@ -47,6 +47,7 @@ enum Mode : int {
   MODE_MSV_FAST_F16 = 4,  // MODE_MSV_FAST with cells as fp16 integers
   MODE_LONG_MSV = 5,      // models beyond kStripedMaxM: long_kernel<MSV>
   MODE_LONG_SSV = 6,      // long_kernel<SSV>
+  MODE_TILE_SSV = 7,      // models beyond kStripedMaxM, SSV: tile_ssv_kernel
 };
 constexpr int kNumModes = 5;   // modes of the striped scan kernel
 
@@ -94,6 +95,9 @@ struct ScanParams {
   uint32_t *item_counter;     // zero before the launch
   int *status;                // nonzero: error reported by a kernel
   uint32_t long_words;        // long-model kernel: largest seg_words of its queries
+  uint8_t *tile_col;          // tiled SSV kernel: per resident warp a column of
+  uint32_t tile_col_stride;   //   tile_col_stride bytes (one per row)
+  uint64_t tile_col_bytes;
 };
 
 typedef void (*KernelFn)(ScanParams);
@@ -102,6 +106,16 @@ typedef void (*KernelFn)(ScanParams);
 // DP row as 16-bit pairs or (bytes) as bytes.
 KernelFn long_kernel_for(int mode, bool bytes, int seg_words);
 size_t long_smem_per_warp(int seg_words, bool bytes);
+
+// Tiled SSV kernel for long models (mpf_tile_kernel.cu, MODE_TILE_SSV):
+// tiles of kTileNodes nodes, kTileC per lane, blocks of kTileWarps warps.
+// Table: per tile [code 0..31][chunk 0..kTileC/8-1][lane] x 8 int16 scores
+// s = bias - cost (codes >= K: bias - 255; nodes past M: -32768).
+constexpr int kTileC = 32;
+constexpr int kTileNodes = 32 * kTileC;
+constexpr int kTileWarps = 8;
+constexpr size_t kTileTableBytes = (size_t)32 * kTileNodes * 2;   // per tile
+KernelFn tile_ssv_kernel_fn();
 
 // Stage-to-stage hand-off (mpf_pipeline.cu): SSV -> MSV (raw_bytes 1) and
 // MSV -> Viterbi (raw_bytes 2).

@@ -115,7 +115,7 @@ extern "C" int mpf_scan_noalloc(mpf_ctx *ctx, int filter, const mpf_profile *pro
   MPF_CUDA(cudaMemcpyAsync(scratch, &q, sizeof(q), cudaMemcpyHostToDevice, ctx->stream));
   MPF_CUDA(cudaMemsetAsync(scratch + 256, 0, 8, ctx->stream));
 
-  ScanParams sp;
+  ScanParams sp{};
   sp.residues = db->d_words;
   sp.n_words = db->n_words;
   sp.seq_word = db->d_seq_word;
