@@ -202,9 +202,9 @@ int get_long_table(const mpf_profile *p, const uint8_t **out) {
 }
 
 // Device copy of a long profile's scores for the tiled SSV kernel: per tile
-// of kTileNodes nodes, [code][chunk][lane] x 8 int16 with lane l holding
-// nodes (l * kTileC .. + kTileC - 1) of the tile, s = bias - cost (codes >= K
-// cost 255), -32768 past M.
+// of kTileNodes nodes, [code][chunk][lane] x 4 pairs of int16, lane l's pair
+// p = (node l * kTileC + p, the same + kTileC / 2) of the tile, chunk p / 4;
+// s = bias - cost (codes >= K cost 255), -32768 past M.
 int get_tile_table(const mpf_profile *p, const uint4 **out) {
   std::lock_guard<std::mutex> lk(p->mu);
   auto key = std::make_tuple(32, 0, 3);
@@ -223,8 +223,9 @@ int get_tile_table(const mpf_profile *p, const uint4 **out) {
           const int k = t * kTileNodes + l * kTileC + c;
           int16_t s = -32768;
           if (k < M) s = (int16_t)(p->bias - (x < p->K ? (int)p->cost[(size_t)x * M + k] : 255));
-          const size_t chunk = (((size_t)t * 32 + x) * kChunks + c / 8) * 32 + l;
-          img[chunk * 8 + c % 8] = s;
+          const int pr = c % (kTileC / 2), half = c / (kTileC / 2);
+          const size_t chunk = (((size_t)t * 32 + x) * kChunks + pr / 4) * 32 + l;
+          img[chunk * 8 + (pr % 4) * 2 + half] = s;
         }
   mpf_ctx *ctx = p->ctx;
   DeviceGuard dg(ctx->device);
@@ -285,7 +286,7 @@ struct LaunchGroup {
   QueryDesc *d_queries = nullptr;
   uint32_t n_queries = 0;
   uint32_t *d_counter = nullptr;
-  uint8_t *d_col = nullptr;      // tiled SSV kernel: one column of col_stride bytes per resident warp
+  uint8_t *d_col = nullptr;      // tiled SSV kernel: two columns of col_stride bytes per resident warp
   uint32_t col_stride = 0;
   uint64_t col_bytes = 0;
 };
@@ -505,8 +506,10 @@ int plan_create(mpf_ctx *ctx, int filter, const mpf_profile *const *profs, int n
     cudaError_t e = cudaMallocAsync((void **)&g.d_queries, sizeof(QueryDesc) * kv.second.size(), ctx->stream);
     if (e == cudaSuccess) e = cudaMallocAsync((void **)&g.d_counter, sizeof(uint32_t), ctx->stream);
     if (e == cudaSuccess && g.mode == MODE_TILE_SSV) {
-      g.col_stride = (std::max<uint32_t>(db->max_len, 1) + 15u) & ~15u;
-      g.col_bytes = (uint64_t)g.grid * kTileWarps * g.col_stride;
+      // Per resident warp two columns of int16 (positions 0..max_len and
+      // the prefetch's overrun), col_stride bytes each.
+      g.col_stride = (uint32_t)((((uint64_t)db->max_len + 12) * 2 + 15) & ~(uint64_t)15);
+      g.col_bytes = (uint64_t)g.grid * kTileWarps * 2 * g.col_stride;
       e = cudaMallocAsync((void **)&g.d_col, g.col_bytes, ctx->stream);
     }
     if (e == cudaSuccess)

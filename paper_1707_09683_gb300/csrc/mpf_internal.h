@@ -95,8 +95,8 @@ struct ScanParams {
   uint32_t *item_counter;     // zero before the launch
   int *status;                // nonzero: error reported by a kernel
   uint32_t long_words;        // long-model kernel: largest seg_words of its queries
-  uint8_t *tile_col;          // tiled SSV kernel: per resident warp a column of
-  uint32_t tile_col_stride;   //   tile_col_stride bytes (one per row)
+  uint8_t *tile_col;          // tiled SSV kernel: per resident warp two columns of
+  uint32_t tile_col_stride;   //   tile_col_stride bytes (an int16 per row)
   uint64_t tile_col_bytes;
 };
 
@@ -109,7 +109,8 @@ size_t long_smem_per_warp(int seg_words, bool bytes);
 
 // Tiled SSV kernel for long models (mpf_tile_kernel.cu, MODE_TILE_SSV):
 // tiles of kTileNodes nodes, kTileC per lane, blocks of kTileWarps warps.
-// Table: per tile [code 0..31][chunk 0..kTileC/8-1][lane] x 8 int16 scores
+// Table: per tile [code 0..31][chunk 0..kTileC/8-1][lane] x 4 int16 pairs,
+// pair p of lane l = nodes (l*kTileC + p, l*kTileC + p + kTileC/2), scores
 // s = bias - cost (codes >= K: bias - 255; nodes past M: -32768).
 constexpr int kTileC = 32;
 constexpr int kTileNodes = 32 * kTileC;

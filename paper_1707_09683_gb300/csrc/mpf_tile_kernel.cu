@@ -9,18 +9,21 @@
 // consecutive length ranks (one sequence per warp, similar lengths) through
 // all tiles of its query together: per tile the block stages the tile's
 // scores into shared memory, and each warp sweeps its sequence with the
-// tile's DP row in registers -- lane l holds kTileC consecutive nodes as
-// 16-bit pairs -- reading the previous tile's boundary value for each row
-// from, and writing its own to, the warp's column in device memory (one
-// byte per row).
+// tile's DP row in registers.  Lane l holds the kTileC consecutive nodes
+// l*kTileC + c as kTileC/2 16-bit pairs, pair p = (node p, node p + kTileC/2)
+// of the lane, so the diagonal of pair p is the previous row's pair p - 1 as
+// it stands and only pair 0 is assembled (from the lane before's last node
+// and this lane's node kTileC/2 - 1).  The previous tile's last node reaches
+// lane 0 through the warp's boundary column in device memory: one int16 per
+// row, written by lane 31 one row later than read (position i + 1 holds row
+// i), two buffers by tile parity.
 //
 // Cells are the unsaturated form r = max(0, r'[k-1] + s) with s = bias -
 // cost, one DPX add-then-max per pair of cells; R >= 255 is the overflow
-// (Sec. 2.1 reading of Alg. 7, as in the other kernels).  A boundary value is
-// stored as min(r, 255): a value of 255 there means R >= 255 already, so
-// the result no longer depends on what follows.  Values above 32767 wrap to
-// negative and restart at 0, which likewise only happens after R >= 255.
-// Nodes past M score -32768, which keeps them at 0.
+// (the Sec. 2.1 reading of Alg. 7 the other kernels use).  Values above
+// 32767 wrap to negative and restart at 0, which only happens after some
+// cell has passed 255, so after R >= 255.  Nodes past M score -32768, which
+// keeps them at 0.
 #include <cuda_runtime.h>
 #include <math.h>
 #include <stdint.h>
@@ -32,14 +35,32 @@ namespace mpf {
 namespace {
 
 constexpr uint32_t kAll = 0xffffffffu;
-constexpr int kChunks = kTileC / 8;   // 16-byte chunks (8 cells) per lane and residue row
+constexpr int kChunks = kTileC / 8;   // 16-byte chunks (4 pairs) per lane and residue row
+constexpr int kPairs = kTileC / 2;
 
-// (r[k-1], r[k]) for the pair (k, k+1): high half of the previous pair, low
-// half of this one.
-__device__ __forceinline__ uint32_t diag(uint32_t prev, uint32_t cur) { return __byte_perm(prev, cur, 0x5432); }
+// One row of the lane's tile segment: v holds the previous row and receives
+// this row; `in` is the previous row's score of the node before the lane's
+// segment.  rmax collects the row's cells.
+__device__ __forceinline__ void tile_row(uint32_t (&v)[kPairs], uint32_t in, const uint4 *srow,
+                                         uint32_t &rmax) {
+  // Pair 0's diagonal: (node before the segment, node kPairs - 1), previous row.
+  const uint32_t d0 = __byte_perm(in, v[kPairs - 1], 0x5410);
+#pragma unroll
+  for (int q = kChunks - 1; q >= 0; --q) {
+    const uint4 s = srow[q * 32];
+    const uint32_t sq[4] = {s.x, s.y, s.z, s.w};
+#pragma unroll
+    for (int e = 3; e >= 0; --e) {
+      const int p = q * 4 + e;
+      v[p] = __viaddmax_s16x2(p > 0 ? v[p - 1] : d0, sq[e], 0u);
+    }
+    rmax = __vimax3_s16x2(rmax, v[q * 4], v[q * 4 + 1]);
+    rmax = __vimax3_s16x2(rmax, v[q * 4 + 2], v[q * 4 + 3]);
+  }
+}
 
 __global__ void __launch_bounds__(kTileWarps * 32) tile_ssv_kernel(ScanParams sp) {
-  // Shared memory: the tile's scores, [code][chunk][lane] x 8 int16.
+  // Shared memory: the tile's scores, [code][chunk][lane] x 4 pairs.
   extern __shared__ __align__(16) uint4 tsm[];
   __shared__ uint32_t s_item;
   const int lane = threadIdx.x & 31;
@@ -47,10 +68,13 @@ __global__ void __launch_bounds__(kTileWarps * 32) tile_ssv_kernel(ScanParams sp
   const int W = blockDim.x >> 5;
   constexpr int kTileWords = 32 * kChunks * 32;   // uint4 per tile
   const uint64_t cw = (uint64_t)blockIdx.x * W + warp;
-  uint8_t *col = sp.tile_col + cw * sp.tile_col_stride;
-  // Debug builds: the table and this warp's column within their buffers.
+  // This warp's two columns (int16 per row, position i + 1 = row i).
+  int16_t *colbuf = reinterpret_cast<int16_t *>(sp.tile_col + cw * 2 * (uint64_t)sp.tile_col_stride);
+  const uint32_t col_elems = sp.tile_col_stride / 2;
+  // Debug builds: the table and this warp's columns within their buffers.
   if (!MPF_DCHECK(sp.status, (size_t)kTileWords * 16 <= dynamic_smem_bytes() &&
-                                 (cw + 1) * sp.tile_col_stride <= sp.tile_col_bytes))
+                                 (cw + 1) * 2 * sp.tile_col_stride <= sp.tile_col_bytes &&
+                                 (sp.tile_col_stride & 15) == 0))
     return;
 
   for (;;) {
@@ -81,8 +105,10 @@ __global__ void __launch_bounds__(kTileWarps * 32) tile_ssv_kernel(ScanParams sp
       w0 = __ldg(sp.seq_word + r);
       len = __ldg(sp.seq_len + r);
       orig = __ldg(sp.seq_orig + r);
+      // The columns hold positions 0..len, and the prefetch reads up to
+      // position len + 10.
       active = MPF_DCHECK(sp.status, (uint64_t)w0 + ((len + 3u) >> 2) <= sp.n_words && orig < sp.n_seqs &&
-                                         len <= sp.tile_col_stride);
+                                         (uint64_t)len + 11 <= col_elems);
     }
     const int nt = (int)((qd.M + kTileNodes - 1) / kTileNodes);
     uint32_t rmax = 0;   // running maximum, two 16-bit halves
@@ -92,54 +118,48 @@ __global__ void __launch_bounds__(kTileWarps * 32) tile_ssv_kernel(ScanParams sp
       for (int i = threadIdx.x; i < kTileWords; i += blockDim.x) tsm[i] = __ldg(g + i);
       __syncthreads();
       if (!active) continue;
-      const bool first = t == 0, last_tile = t == nt - 1;
-      uint32_t v[kTileC / 2];
+      const int16_t *cin = colbuf + (size_t)((t + 1) & 1) * col_elems;   // previous tile's column
+      int16_t *cout = colbuf + (size_t)(t & 1) * col_elems;              // this tile's column
+      const bool first = t == 0, write = t + 1 < nt;
+      if (write && lane == 31) cout[0] = 0;   // row -1
+      uint32_t v[kPairs];
 #pragma unroll
-      for (int p = 0; p < kTileC / 2; ++p) v[p] = 0u;
-      uint32_t word = 0, cin = 0, cout = 0, cprev = 0;
-      for (uint32_t i = 0; i < len; ++i) {
-        if ((i & 3) == 0) {
-          word = __ldg(sp.residues + w0 + (i >> 2));
-          if (lane == 0 && !first) cin = __ldcg(reinterpret_cast<const uint32_t *>(col) + (i >> 2));
+      for (int p = 0; p < kPairs; ++p) v[p] = 0u;
+      const uint4 *sbase = tsm + lane;
+      // Rolling prefetch of the boundary column, four rows per 64-bit word.
+      uint2 cur = make_uint2(0, 0), nxt = make_uint2(0, 0);
+      if (lane == 0 && !first) {
+        cur = __ldcg(reinterpret_cast<const uint2 *>(cin));
+        nxt = __ldcg(reinterpret_cast<const uint2 *>(cin) + 1);
+      }
+      for (uint32_t i0 = 0; i0 < len; i0 += 4) {
+        const uint32_t word = __ldg(sp.residues + w0 + (i0 >> 2));
+        uint2 c = cur;
+        if (lane == 0 && !first) {
+          cur = nxt;
+          nxt = __ldcg(reinterpret_cast<const uint2 *>(cin) + (i0 >> 2) + 2);
         }
-        uint32_t x = (word >> (8 * (i & 3))) & 0xffu;
-        if (!MPF_DCHECK(sp.status, x < 32u)) x = 0;
-        // Diagonal into the lane's first node: the lane before's last node
-        // of the previous row; for lane 0 the previous tile's boundary
-        // value of the previous row (0 before the first tile and row).
-        uint32_t in = __shfl_up_sync(kAll, v[kTileC / 2 - 1] >> 16, 1);
-        if (lane == 0) in = cprev;
-        const uint4 *srow = tsm + (size_t)x * kChunks * 32 + lane;
+        const uint32_t xs[4] = {__byte_perm(word, 0u, 0x4440), __byte_perm(word, 0u, 0x4441),
+                                __byte_perm(word, 0u, 0x4442), __byte_perm(word, 0u, 0x4443)};
+        const uint32_t cs[4] = {c.x & 0xffffu, c.x >> 16, c.y & 0xffffu, c.y >> 16};
 #pragma unroll
-        for (int q = kChunks - 1; q >= 0; --q) {
-          const uint4 s = srow[q * 32];
-          const uint32_t sq[4] = {s.x, s.y, s.z, s.w};
-#pragma unroll
-          for (int e = 3; e >= 0; --e) {
-            const int p = q * 4 + e;
-            const uint32_t prev = p > 0 ? v[p - 1] : (in << 16);
-            v[p] = __viaddmax_s16x2(diag(prev, v[p]), sq[e], 0u);
+        for (int u = 0; u < 4; ++u) {
+          if (i0 + u < len) {
+            uint32_t x = xs[u];
+            if (!MPF_DCHECK(sp.status, x < 32u)) x = 0;
+            // The node before the lane's segment, previous row: the lane
+            // before's last node; for lane 0 the previous tile's last node.
+            uint32_t in = __shfl_up_sync(kAll, v[kPairs - 1] >> 16, 1);
+            if (lane == 0) in = cs[u];
+            tile_row(v, in, sbase + x * (kChunks * 32), rmax);
+            if (write && lane == 31) cout[i0 + u + 1] = (int16_t)(v[kPairs - 1] >> 16);
           }
-          rmax = __vimax3_s16x2(rmax, v[q * 4], v[q * 4 + 1]);
-          rmax = __vimax3_s16x2(rmax, v[q * 4 + 2], v[q * 4 + 3]);
-        }
-        if (lane == 0 && !first) cprev = (cin >> (8 * (i & 3))) & 0xffu;
-        if (!last_tile) {
-          const uint32_t b = min(v[kTileC / 2 - 1] >> 16, 255u);   // this row's last node (>= 0 here)
-          cout |= b << (8 * (i & 3));
-          if (lane == 31 && ((i & 3) == 3 || i + 1 == len)) {
-            __stcg(reinterpret_cast<uint32_t *>(col) + (i >> 2), cout);
-          }
-          if ((i & 3) == 3) cout = 0;
         }
       }
     }
     // R over the sequence: the largest half of any lane.
     int R = 0;
-    if (active) {
-      const int m = max((int)(int16_t)(rmax & 0xffffu), (int)(int16_t)(rmax >> 16));
-      R = m;
-    }
+    if (active) R = max((int)(int16_t)(rmax & 0xffffu), (int)(int16_t)(rmax >> 16));
     R = __reduce_max_sync(kAll, R);
     if (active && lane == 0) {
       const int t = qd.tjb ? (int)__ldg(qd.tjb + min(len, qd.n_tjb - 1u)) : qd.tjb_fixed;
