@@ -508,7 +508,8 @@ def run_long_model(args, ctx, db, wl, time_steps, clocks, dev):
     nsm = torch.cuda.get_device_properties(dev).multi_processor_count
     sm_mhz = clocks.get("sm_mhz") or 2070.0
     out = {"M": args.long_m, "config": list(prof.get_config(mpf.MSV)), "n_seqs": n,
-           "cells_per_launch": args.long_m * res, "kernel": "long_kernel (lane segments, costs from HBM/L2)"}
+           "cells_per_launch": args.long_m * res, "kernel": "MSV: long_kernel (lane segments, DP row in shared memory, costs through L1); "
+                     "SSV: tile_ssv_kernel (1,024-node tiles, DP row in registers)"}
     steps = max(1, min(args.steps, 3))
     for name, code in (("msv", mpf.MSV), ("ssv", mpf.SSV)):
         pl = mpf.Plan(ctx, code, [prof], db, *outs)
@@ -517,7 +518,8 @@ def run_long_model(args, ctx, db, wl, time_steps, clocks, dev):
         pl.close()
         g = args.long_m * res / (ms * 1e-3) / 1e9
         peak = nsm * INT_LANES_PER_SM_CLK * CELLS_PER_LANE_OP / OPS_PER_CELL[name] * sm_mhz * 1e6 / 1e9
-        out[name] = {"gcups": g, "ms_per_launch": ms, "roofline_frac": g / peak, "peak": peak}
+        out[name] = {"gcups": g, "ms_per_launch": ms, "roofline_frac": g / peak, "peak": peak,
+                     "kernel": "long_kernel" if name == "msv" else "tile_ssv_kernel"}
         log(f"long model M={args.long_m}: {name} {g:.1f} GCUPS ({ms:.1f} ms per launch)")
     prof.close()
     out["roofline_basis"] = "integer-SIMD roofline of the striped kernels (same formula as roofline.peak)"

@@ -341,7 +341,7 @@ int configure_kernel(mpf_ctx *ctx, LaunchGroup *g) {
     g->n_shards = (uint32_t)g->grid;
     return MPF_OK;
   }
-  if (g->mode == MODE_LONG_MSV || g->mode == MODE_LONG_SSV) {
+  if (g->mode == MODE_LONG_MSV) {
     // Each warp reads the cost rows of its residues from device memory, so
     // when the rows of the codes the database uses (n_codes x 128 x
     // seg_words bytes) fit in the L1 of the smallest carveout (156 KB, with

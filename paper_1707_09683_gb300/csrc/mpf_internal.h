@@ -45,8 +45,7 @@ enum Mode : int {
   MODE_MSV_DIRECT = 2,    // Alg. 2, J/B update after every row
   MODE_SSV_F16 = 3,       // MODE_SSV with cells as fp16 integers (FMA pipe)
   MODE_MSV_FAST_F16 = 4,  // MODE_MSV_FAST with cells as fp16 integers
-  MODE_LONG_MSV = 5,      // models beyond kStripedMaxM: long_kernel<MSV>
-  MODE_LONG_SSV = 6,      // long_kernel<SSV>
+  MODE_LONG_MSV = 5,      // models beyond kStripedMaxM, MSV: long_kernel
   MODE_TILE_SSV = 7,      // models beyond kStripedMaxM, SSV: tile_ssv_kernel
 };
 constexpr int kNumModes = 5;   // modes of the striped scan kernel
@@ -102,8 +101,8 @@ struct ScanParams {
 
 typedef void (*KernelFn)(ScanParams);
 
-// Long-model kernel (mpf_long_kernel.cu): MODE_LONG_MSV or MODE_LONG_SSV,
-// DP row as 16-bit pairs or (bytes) as bytes.
+// Long-model MSV kernel (mpf_long_kernel.cu, MODE_LONG_MSV), DP row as
+// 16-bit pairs or (bytes) as bytes.
 KernelFn long_kernel_for(int mode, bool bytes, int seg_words);
 size_t long_smem_per_warp(int seg_words, bool bytes);
 

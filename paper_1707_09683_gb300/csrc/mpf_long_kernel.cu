@@ -1,5 +1,7 @@
-// mpf_long_kernel.cu -- MSV and SSV scans of models longer than the striped
-// shared-memory table holds (Sec. 2.1 recurrences, Alg. 2 and Alg. 7).
+// mpf_long_kernel.cu -- MSV scans (Alg. 2) of models longer than the striped
+// shared-memory table holds.  (SSV of such models runs tiled, with the DP row
+// in registers: mpf_tile_kernel.cu.  MSV couples every row through xE, so it
+// keeps the whole row, here in shared memory.)
 //
 // One warp scores one sequence.  Lane l owns the contiguous node segment
 // [l*Q, l*Q + Q) (Q = 4 * seg_words); the byte costs are read from global
@@ -11,12 +13,10 @@
 // packing permute per four cells).
 //
 // Cells are held as u = 255 - v (v the byte score) in 16-bit halves, so that
-// every byte saturation of the recurrences becomes one DPX add-then-min/max
+// every byte saturation of the recurrence becomes one DPX add-then-min/max
 // on a pair of cells with no wrap-around (all values stay in [0, 510]):
-//   MSV  v = sat(sat(max(v'[k-1], xB) + bias) - c)
-//        u = min(min(max(u'[k-1] - bias, 0), max(uB - bias, 0)) + c, 255)
-//   SSV  v = min(255, max(0, v'[k-1] + bias - c))
-//        u = min(max(u'[k-1] + c, bias) - bias, 255)
+//   v = sat(sat(max(v'[k-1], xB) + bias) - c)
+//   u = min(min(max(u'[k-1] - bias, 0), max(uB - bias, 0)) + c, 255)
 // and the row maximum of v is 255 minus the row minimum of u.  Node k-1 of
 // the previous row is the previous half of the same lane, or for a
 // segment's first node the last node of the lane before (one shuffle per
@@ -39,15 +39,9 @@ __device__ __forceinline__ uint32_t hi_cost_pair(uint32_t w) { return __byte_per
 // (u[k-1], u[k]) for the pair (k, k+1): high half of the previous pair, low half of this one.
 __device__ __forceinline__ uint32_t diag_pair(uint32_t prev, uint32_t cur) { return __byte_perm(prev, cur, 0x5432); }
 
-template <bool MSV>
-__device__ __forceinline__ uint32_t cell_pair(uint32_t d, uint32_t c, uint32_t negbias2, uint32_t bias2,
-                                              uint32_t uBb2) {
-  if (MSV) {
-    const uint32_t t = __vimin_s16x2_relu(__viaddmax_s16x2(d, negbias2, 0u), uBb2);
-    return __viaddmin_s16x2(t, c, kU255);
-  } else {
-    return __viaddmin_s16x2(__viaddmax_s16x2(d, c, bias2), negbias2, kU255);
-  }
+__device__ __forceinline__ uint32_t cell_pair(uint32_t d, uint32_t c, uint32_t negbias2, uint32_t uBb2) {
+  const uint32_t t = __vimin_s16x2_relu(__viaddmax_s16x2(d, negbias2, 0u), uBb2);
+  return __viaddmin_s16x2(t, c, kU255);
 }
 
 // Force the halves of pair `p` (nodes 2p, 2p+1 of the lane's last word) that
@@ -85,7 +79,7 @@ struct RowSlot<true> {
   static __device__ __forceinline__ T join(uint32_t u0, uint32_t u1) { return __byte_perm(u0, u1, 0x6420); }
 };
 
-template <bool MSV, bool B8, int U, bool PF>
+template <bool B8, int U, bool PF>
 __global__ void __launch_bounds__(kLongThreads) long_kernel(ScanParams sp) {
   typedef RowSlot<B8> Slot;
   extern __shared__ __align__(16) uint32_t lsm[];
@@ -126,7 +120,6 @@ __global__ void __launch_bounds__(kLongThreads) long_kernel(ScanParams sp) {
     const int nfull = nv >> 2, part = nv & 3;
     const int nw = nfull + (part ? 1 : 0);
     const uint32_t *tab = reinterpret_cast<const uint32_t *>(qd.table) + lane;
-    const uint32_t bias2 = (uint32_t)bias * 0x00010001u;
     const uint32_t negbias2 = ((uint32_t)(-bias) & 0xffffu) * 0x00010001u;
     const uint32_t pm0 = part ? pad_mask(0, part) : 0u, pm1 = part ? pad_mask(1, part) : 0u;
 
@@ -135,7 +128,6 @@ __global__ void __launch_bounds__(kLongThreads) long_kernel(ScanParams sp) {
     int xB = min(255, max(0, qd.base - (t + qd.tbm)));
     uint32_t uBb2 = (uint32_t)max(255 - xB - bias, 0) * 0x00010001u;
     uint32_t carry = 255;                 // u of the node before the segment, previous row
-    uint32_t umin2 = kU255;               // SSV: running minimum over the sequence
     bool ovf = false;
     uint32_t word = 0;
     for (uint32_t i = 0; i < len; ++i) {
@@ -143,7 +135,7 @@ __global__ void __launch_bounds__(kLongThreads) long_kernel(ScanParams sp) {
       uint32_t x = (word >> (8 * (i & 3))) & 0xffu;
       if (!MPF_DCHECK(sp.status, x < 32u)) x = 0;
       const uint32_t *row = tab + (size_t)x * sw * 32;
-      if (MSV) umin2 = kU255;
+      uint32_t umin2 = kU255;             // row minimum
       uint32_t prev = carry << 16, last = kU255;
       // PF: a rolling window of the next four cost words, so four loads per
       // lane stay in flight whatever the unroll depth (the cost rows come
@@ -169,8 +161,8 @@ __global__ void __launch_bounds__(kLongThreads) long_kernel(ScanParams sp) {
         }
         uint32_t sx, sy;
         Slot::split(st[(size_t)w * 32], sx, sy);
-        const uint32_t u0 = cell_pair<MSV>(diag_pair(prev, sx), lo_cost_pair(cw), negbias2, bias2, uBb2);
-        const uint32_t u1 = cell_pair<MSV>(diag_pair(sx, sy), hi_cost_pair(cw), negbias2, bias2, uBb2);
+        const uint32_t u0 = cell_pair(diag_pair(prev, sx), lo_cost_pair(cw), negbias2, uBb2);
+        const uint32_t u1 = cell_pair(diag_pair(sx, sy), hi_cost_pair(cw), negbias2, uBb2);
         umin2 = __vimin3_u16x2(umin2, u0, u1);
         st[(size_t)w * 32] = Slot::join(u0, u1);
         prev = sy;
@@ -180,8 +172,8 @@ __global__ void __launch_bounds__(kLongThreads) long_kernel(ScanParams sp) {
         const uint32_t cw = __ldg(row + (size_t)nfull * 32);
         uint32_t sx, sy;
         Slot::split(st[(size_t)nfull * 32], sx, sy);
-        uint32_t u0 = cell_pair<MSV>(diag_pair(prev, sx), lo_cost_pair(cw), negbias2, bias2, uBb2);
-        uint32_t u1 = cell_pair<MSV>(diag_pair(sx, sy), hi_cost_pair(cw), negbias2, bias2, uBb2);
+        uint32_t u0 = cell_pair(diag_pair(prev, sx), lo_cost_pair(cw), negbias2, uBb2);
+        uint32_t u1 = cell_pair(diag_pair(sx, sy), hi_cost_pair(cw), negbias2, uBb2);
         u0 = __vimax_s16x2_relu(u0, pm0);
         u1 = __vimax_s16x2_relu(u1, pm1);
         umin2 = __vimin3_u16x2(umin2, u0, u1);
@@ -190,29 +182,19 @@ __global__ void __launch_bounds__(kLongThreads) long_kernel(ScanParams sp) {
       }
       carry = __shfl_up_sync(kAll, last >> 16, 1);
       if (lane == 0) carry = 255;
-      if (MSV) {
-        const int umin = (int)__reduce_min_sync(kAll, min(umin2 & 0xffffu, umin2 >> 16));
-        const int xE = 255 - umin;
-        if (xE >= 255 - bias) {
-          ovf = true;
-          break;
-        }
-        xJ = max(xJ, max(0, xE - qd.tec));
-        xB = min(255, max(0, max(qd.base, xJ) - (t + qd.tbm)));
-        uBb2 = (uint32_t)max(255 - xB - bias, 0) * 0x00010001u;
-      }
-    }
-    int raw, flag, num;
-    if (MSV) {
-      raw = ovf ? 255 : xJ;
-      flag = ovf ? 1 : 0;
-      num = xJ - t - qd.base;
-    } else {
       const int umin = (int)__reduce_min_sync(kAll, min(umin2 & 0xffffu, umin2 >> 16));
-      raw = 255 - umin;
-      flag = raw == 255 ? 1 : 0;
-      num = raw - qd.tbm - qd.tec - 2 * t;
+      const int xE = 255 - umin;
+      if (xE >= 255 - bias) {
+        ovf = true;
+        break;
+      }
+      xJ = max(xJ, max(0, xE - qd.tec));
+      xB = min(255, max(0, max(qd.base, xJ) - (t + qd.tbm)));
+      uBb2 = (uint32_t)max(255 - xB - bias, 0) * 0x00010001u;
     }
+    const int raw = ovf ? 255 : xJ;
+    const int flag = ovf ? 1 : 0;
+    const int num = xJ - t - qd.base;
     if (lane == 0) {
       qd.raw[orig] = (uint8_t)raw;
       qd.flag[orig] = (uint8_t)flag;
@@ -229,15 +211,14 @@ __global__ void __launch_bounds__(kLongThreads) long_kernel(ScanParams sp) {
 // Unroll depth of the word loop and the rolling cost prefetch (measured on
 // one query against 3,000-40,000 sequences): unroll 8 for segments of at most
 // 48 words (M <= 6,144; 9-16% faster than 4), 16 with byte rows (M = 40,000:
-// 35% faster), 4 in between; the prefetch for MSV in those two bands
-// (M = 12,345: 1,597 against 1,138 GCUPS; M = 40,000: 934 against 877), not
-// for MSV at unroll 8 (mixed) nor for SSV (slower).
+// 35% faster), 4 in between; the prefetch in those two bands (M = 12,345:
+// 1,597 against 1,138 GCUPS; M = 40,000: 934 against 877), not at unroll 8
+// (mixed).
 KernelFn long_kernel_for(int mode, bool bytes, int seg_words) {
-  const bool msv = mode == MODE_LONG_MSV;
-  if (mode != MODE_LONG_MSV && mode != MODE_LONG_SSV) return nullptr;
-  if (bytes) return msv ? long_kernel<true, true, 16, true> : long_kernel<false, true, 16, false>;
-  if (seg_words <= 48) return msv ? long_kernel<true, false, 8, false> : long_kernel<false, false, 8, false>;
-  return msv ? long_kernel<true, false, 4, true> : long_kernel<false, false, 4, false>;
+  if (mode != MODE_LONG_MSV) return nullptr;
+  if (bytes) return long_kernel<true, 16, true>;
+  if (seg_words <= 48) return long_kernel<false, 8, false>;
+  return long_kernel<false, 4, true>;
 }
 
 size_t long_smem_per_warp(int seg_words, bool bytes) {
