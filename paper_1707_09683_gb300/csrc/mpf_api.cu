@@ -13,6 +13,7 @@
 
 #include <algorithm>
 #include <map>
+#include <memory>
 #include <mutex>
 #include <new>
 #include <numeric>
@@ -201,10 +202,11 @@ int get_long_table(const mpf_profile *p, const uint8_t **out) {
   return MPF_OK;
 }
 
-// Device copy of a long profile's scores for the tiled SSV kernel: per tile
-// of kTileNodes nodes, [code][chunk][lane] x 4 pairs of int16, lane l's pair
+// Device copy of a long profile's scores for the tiled kernel: per tile of
+// kTileNodes nodes, [code][chunk][lane] x 4 pairs of int16, lane l's pair
 // p = (node l * kTileC + p, the same + kTileC / 2) of the tile, chunk p / 4;
-// s = bias - cost (codes >= K cost 255), -32768 past M.
+// s = bias - cost (codes >= K cost 255), -32768 past M; then the 32 per-code
+// maxima of s over the model.
 int get_tile_table(const mpf_profile *p, const uint4 **out) {
   std::lock_guard<std::mutex> lk(p->mu);
   auto key = std::make_tuple(32, 0, 3);
@@ -215,7 +217,13 @@ int get_tile_table(const mpf_profile *p, const uint4 **out) {
   }
   const int M = p->M, nt = (M + kTileNodes - 1) / kTileNodes;
   constexpr int kChunks = kTileC / 8;
-  std::vector<int16_t> img((size_t)nt * kTileTableBytes / 2);
+  std::vector<int16_t> img((size_t)nt * kTileTableBytes / 2 + 32);
+  for (int x = 0; x < 32; ++x) {
+    int m = p->bias - 255;
+    if (x < p->K)
+      for (int k = 0; k < M; ++k) m = std::max(m, p->bias - (int)p->cost[(size_t)x * M + k]);
+    img[(size_t)nt * kTileTableBytes / 2 + x] = (int16_t)m;
+  }
   for (int t = 0; t < nt; ++t)
     for (int x = 0; x < 32; ++x)
       for (int l = 0; l < 32; ++l)
@@ -262,7 +270,7 @@ int ensure_out_scratch(mpf_ctx *ctx, size_t bytes) {
 // Kernel mode of a profile for a filter.  Automatic arithmetic: fp16 cells
 // (FMA pipe) for both filters.
 int kernel_mode(const mpf_profile *p, int filter) {
-  if (p->seg_words) return filter == MPF_MSV ? MODE_LONG_MSV : MODE_TILE_SSV;
+  if (p->seg_words) return filter == MPF_SSV ? MODE_TILE_SSV : msv_fast_ok(p) ? MODE_TILE_MSV : MODE_LONG_MSV;
   const bool f16 = p->arith[filter] != MPF_ARITH_I16;
   if (filter == MPF_SSV) return f16 ? MODE_SSV_F16 : MODE_SSV;
   if (!msv_fast_ok(p)) return MODE_MSV_DIRECT;
@@ -286,9 +294,11 @@ struct LaunchGroup {
   QueryDesc *d_queries = nullptr;
   uint32_t n_queries = 0;
   uint32_t *d_counter = nullptr;
-  uint8_t *d_col = nullptr;      // tiled SSV kernel: two columns of col_stride bytes per resident warp
+  uint8_t *d_col = nullptr;      // tiled kernel: two or three columns of col_stride bytes per resident warp
   uint32_t col_stride = 0;
   uint64_t col_bytes = 0;
+  uint32_t *d_fallback = nullptr;   // tiled MSV: per query a count, then n_seqs ranks per query
+  std::shared_ptr<LaunchGroup> next;   // launched after this group on the same stream
 };
 
 struct mpf_plan {
@@ -306,11 +316,13 @@ void plan_free(mpf_plan *pl) {
   DeviceGuard dg(pl->ctx->device);
   if (pl->graph) cudaGraphExecDestroy(pl->graph);
   // Ordered after the plan's last launch, which joins back into this stream.
-  for (auto &g : pl->groups) {
-    if (g.d_queries) cudaFreeAsync(g.d_queries, pl->ctx->stream);
-    if (g.d_counter) cudaFreeAsync(g.d_counter, pl->ctx->stream);
-    if (g.d_col) cudaFreeAsync(g.d_col, pl->ctx->stream);
-  }
+  for (auto &g0 : pl->groups)
+    for (LaunchGroup *g = &g0; g; g = g->next.get()) {
+      if (g->d_queries) cudaFreeAsync(g->d_queries, pl->ctx->stream);
+      if (g->d_counter) cudaFreeAsync(g->d_counter, pl->ctx->stream);
+      if (g->d_col) cudaFreeAsync(g->d_col, pl->ctx->stream);
+      if (g->d_fallback) cudaFreeAsync(g->d_fallback, pl->ctx->stream);
+    }
   for (auto e : pl->events) cudaEventDestroy(e);
   (void)cudaGetLastError();
   delete pl;
@@ -325,9 +337,9 @@ int free_pending(mpf_ctx *ctx) {
 }
 
 int configure_kernel(mpf_ctx *ctx, LaunchGroup *g) {
-  if (g->mode == MODE_TILE_SSV) {
+  if (g->mode == MODE_TILE_SSV || g->mode == MODE_TILE_MSV) {
     // Blocks of kTileWarps warps with one tile's scores in shared memory.
-    g->fn = tile_ssv_kernel_fn();
+    g->fn = tile_kernel_fn(g->mode == MODE_TILE_MSV);
     g->threads = kTileWarps * 32;
     g->smem = (uint32_t)kTileTableBytes;
     MPF_CUDA(cudaFuncSetAttribute((const void *)g->fn, cudaFuncAttributeMaxDynamicSharedMemorySize,
@@ -421,6 +433,8 @@ int plan_create(mpf_ctx *ctx, int filter, const mpf_profile *const *profs, int n
   pl->ctx = ctx;
   pl->db = db;
   std::map<std::tuple<int, int, int>, std::vector<QueryDesc>> byconf;
+  std::map<std::tuple<int, int, int>, std::vector<const uint8_t *>> fb_table;   // tiled MSV: long tables
+  std::map<std::tuple<int, int, int>, std::vector<uint32_t>> fb_seg_words;
   for (int i = 0; i < n_q; ++i) {
     const mpf_profile *p = profs[i];
     if (!p || p->ctx->device != ctx->device) {
@@ -431,7 +445,7 @@ int plan_create(mpf_ctx *ctx, int filter, const mpf_profile *const *profs, int n
     QueryDesc q;
     memset(&q, 0, sizeof(q));
     int lanes = 32, words = 0;
-    if (mode == MODE_TILE_SSV) {
+    if (mode == MODE_TILE_SSV || mode == MODE_TILE_MSV) {
       const uint4 *tt = nullptr;
       int rc = get_tile_table(p, &tt);
       if (rc) {
@@ -440,6 +454,17 @@ int plan_create(mpf_ctx *ctx, int filter, const mpf_profile *const *profs, int n
       }
       q.table = tt;
       q.M = (uint32_t)p->M;
+      q.smax_off = (uint32_t)(((size_t)(p->M + kTileNodes - 1) / kTileNodes) * kTileTableBytes);
+      if (mode == MODE_TILE_MSV) {   // the lane-segment kernel's table, for the fallback
+        const uint8_t *lt = nullptr;
+        rc = get_long_table(p, &lt);
+        if (rc) {
+          plan_free(pl);
+          return rc;
+        }
+        fb_table[std::make_tuple(lanes, words, mode)].push_back(lt);
+        fb_seg_words[std::make_tuple(lanes, words, mode)].push_back((uint32_t)p->seg_words);
+      }
     } else if (p->seg_words) {
       const uint8_t *lt = nullptr;
       int rc = get_long_table(p, &lt);
@@ -505,21 +530,52 @@ int plan_create(mpf_ctx *ctx, int filter, const mpf_profile *const *profs, int n
     g.n_queries = (uint32_t)kv.second.size();
     cudaError_t e = cudaMallocAsync((void **)&g.d_queries, sizeof(QueryDesc) * kv.second.size(), ctx->stream);
     if (e == cudaSuccess) e = cudaMallocAsync((void **)&g.d_counter, sizeof(uint32_t), ctx->stream);
-    if (e == cudaSuccess && g.mode == MODE_TILE_SSV) {
-      // Per resident warp two columns of int16 (positions 0..max_len and
-      // the prefetch's overrun), col_stride bytes each.
+    if (e == cudaSuccess && (g.mode == MODE_TILE_SSV || g.mode == MODE_TILE_MSV)) {
+      // Per resident warp two (SSV) or three (MSV) columns of int16
+      // (positions 0..max_len and the prefetch's overrun), col_stride bytes each.
       g.col_stride = (uint32_t)((((uint64_t)db->max_len + 12) * 2 + 15) & ~(uint64_t)15);
-      g.col_bytes = (uint64_t)g.grid * kTileWarps * 2 * g.col_stride;
+      g.col_bytes = (uint64_t)g.grid * kTileWarps * (g.mode == MODE_TILE_MSV ? 3 : 2) * g.col_stride;
       e = cudaMallocAsync((void **)&g.d_col, g.col_bytes, ctx->stream);
+    }
+    if (e == cudaSuccess && g.mode == MODE_TILE_MSV) {
+      // Fallback lists, and the lane-segment launch that scores them.
+      const size_t nq = kv.second.size(), ns = std::max<uint64_t>(db->n_seqs, 1);
+      e = cudaMallocAsync((void **)&g.d_fallback, (nq + nq * ns) * 4, ctx->stream);
+      if (e == cudaSuccess) {
+        auto nx = std::make_shared<LaunchGroup>();
+        nx->mode = MODE_LONG_MSV;
+        nx->n_codes = db->n_codes;
+        std::vector<QueryDesc> fq = kv.second;
+        for (size_t i = 0; i < nq; ++i) {
+          kv.second[i].fallback_count = g.d_fallback + i;
+          kv.second[i].fallback_ranks = g.d_fallback + nq + i * ns;
+          fq[i].table = reinterpret_cast<const uint4 *>(fb_table[kv.first][i]);
+          fq[i].seg_words = fb_seg_words[kv.first][i];
+          fq[i].ranks = kv.second[i].fallback_ranks;
+          fq[i].n_ranks = kv.second[i].fallback_count;
+          nx->long_words = std::max(nx->long_words, fq[i].seg_words);
+        }
+        g.next = nx;
+        int rc2 = configure_kernel(ctx, nx.get());
+        if (rc2) {
+          pl->groups.push_back(g);
+          plan_free(pl);
+          return rc2;
+        }
+        nx->n_queries = (uint32_t)nq;
+        e = cudaMallocAsync((void **)&nx->d_queries, sizeof(QueryDesc) * nq, ctx->stream);
+        if (e == cudaSuccess) e = cudaMallocAsync((void **)&nx->d_counter, sizeof(uint32_t), ctx->stream);
+        if (e == cudaSuccess)
+          e = cudaMemcpyAsync(nx->d_queries, fq.data(), sizeof(QueryDesc) * nq, cudaMemcpyHostToDevice,
+                              ctx->stream);
+      }
     }
     if (e == cudaSuccess)
       e = cudaMemcpyAsync(g.d_queries, kv.second.data(), sizeof(QueryDesc) * kv.second.size(),
                           cudaMemcpyHostToDevice, ctx->stream);
     if (e != cudaSuccess) {
-      if (g.d_queries) cudaFreeAsync(g.d_queries, ctx->stream);
-      if (g.d_counter) cudaFreeAsync(g.d_counter, ctx->stream);
-      if (g.d_col) cudaFreeAsync(g.d_col, ctx->stream);
       (void)cudaGetLastError();
+      pl->groups.push_back(g);   // plan_free releases what the group holds
       plan_free(pl);
       return e == cudaErrorMemoryAllocation ? MPF_ENOMEM : MPF_ECUDA;
     }
@@ -550,6 +606,7 @@ int plan_create(mpf_ctx *ctx, int filter, const mpf_profile *const *profs, int n
 
 int enqueue_group(const mpf_db *db, mpf_ctx *ctx, LaunchGroup &g, cudaStream_t st) {
   MPF_CUDA(cudaMemsetAsync(g.d_counter, 0, sizeof(uint32_t), st));
+  if (g.d_fallback) MPF_CUDA(cudaMemsetAsync(g.d_fallback, 0, sizeof(uint32_t) * g.n_queries, st));
   ScanParams sp{};
   sp.residues = db->d_words;
   sp.n_words = db->n_words;
@@ -570,6 +627,7 @@ int enqueue_group(const mpf_db *db, mpf_ctx *ctx, LaunchGroup &g, cudaStream_t s
   const int grid = (int)std::min<uint64_t>((uint64_t)g.grid, (uint64_t)g.n_queries * g.n_shards);
   g.fn<<<grid, g.threads, g.smem, st>>>(sp);
   MPF_CUDA(cudaGetLastError());
+  if (g.next) return enqueue_group(db, ctx, *g.next, st);
   return MPF_OK;
 }
 

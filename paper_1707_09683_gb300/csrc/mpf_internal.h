@@ -46,7 +46,9 @@ enum Mode : int {
   MODE_SSV_F16 = 3,       // MODE_SSV with cells as fp16 integers (FMA pipe)
   MODE_MSV_FAST_F16 = 4,  // MODE_MSV_FAST with cells as fp16 integers
   MODE_LONG_MSV = 5,      // models beyond kStripedMaxM, MSV: long_kernel
-  MODE_TILE_SSV = 7,      // models beyond kStripedMaxM, SSV: tile_ssv_kernel
+  MODE_TILE_SSV = 7,      // models beyond kStripedMaxM, SSV: tile_kernel<SSV>
+  MODE_TILE_MSV = 8,      // models beyond kStripedMaxM, MSV when b may be held: tile_kernel<MSV>
+                          //   (with MODE_LONG_MSV over the sequences it leaves)
 };
 constexpr int kNumModes = 5;   // modes of the striped scan kernel
 
@@ -78,6 +80,10 @@ struct QueryDesc {
   // (a device count written by an earlier kernel on the same stream).
   const uint32_t *ranks;
   const uint32_t *n_ranks;
+  // Tiled MSV kernel: sequences it leaves to the exact lane-segment kernel
+  // (their ranks, and the count, zero before the launch).
+  uint32_t *fallback_ranks;
+  uint32_t *fallback_count;
 };
 
 struct ScanParams {
@@ -94,8 +100,8 @@ struct ScanParams {
   uint32_t *item_counter;     // zero before the launch
   int *status;                // nonzero: error reported by a kernel
   uint32_t long_words;        // long-model kernel: largest seg_words of its queries
-  uint8_t *tile_col;          // tiled SSV kernel: per resident warp two columns of
-  uint32_t tile_col_stride;   //   tile_col_stride bytes (an int16 per row)
+  uint8_t *tile_col;          // tiled kernel: per resident warp two or three columns
+  uint32_t tile_col_stride;   //   of tile_col_stride bytes (an int16 per row)
   uint64_t tile_col_bytes;
 };
 
@@ -106,16 +112,19 @@ typedef void (*KernelFn)(ScanParams);
 KernelFn long_kernel_for(int mode, bool bytes, int seg_words);
 size_t long_smem_per_warp(int seg_words, bool bytes);
 
-// Tiled SSV kernel for long models (mpf_tile_kernel.cu, MODE_TILE_SSV):
-// tiles of kTileNodes nodes, kTileC per lane, blocks of kTileWarps warps.
+// Tiled kernel for long models (mpf_tile_kernel.cu, MODE_TILE_SSV and
+// MODE_TILE_MSV): tiles of kTileNodes nodes, kTileC per lane, blocks of
+// kTileWarps warps; per resident warp 2 (SSV) or 3 (MSV) columns of
+// tile_col_stride bytes.
 // Table: per tile [code 0..31][chunk 0..kTileC/8-1][lane] x 4 int16 pairs,
 // pair p of lane l = nodes (l*kTileC + p, l*kTileC + p + kTileC/2), scores
-// s = bias - cost (codes >= K: bias - 255; nodes past M: -32768).
+// s = bias - cost (codes >= K: bias - 255; nodes past M: -32768); after the
+// tiles (QueryDesc::smax_off) 32 int16 per-code maxima of s over the model.
 constexpr int kTileC = 32;
 constexpr int kTileNodes = 32 * kTileC;
 constexpr int kTileWarps = 8;
 constexpr size_t kTileTableBytes = (size_t)32 * kTileNodes * 2;   // per tile
-KernelFn tile_ssv_kernel_fn();
+KernelFn tile_kernel_fn(bool msv);
 
 // Stage-to-stage hand-off (mpf_pipeline.cu): SSV -> MSV (raw_bytes 1) and
 // MSV -> Viterbi (raw_bytes 2).

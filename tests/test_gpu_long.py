@@ -2,10 +2,12 @@
 the GPU against the oracle, bit-exact on raw, flag and nat.
 
 Realistic and adversarial profiles at lengths that leave every possible
-ragged end (M mod 128 and the partial last word of a lane), the largest
-supported model, single scans, batches and plans that mix long and striped
-profiles, rank lists from the SSV -> MSV hand-off, and the configuration
-and allocation-free calls that long profiles do not take.
+ragged end (M mod 128, the partial last word of a lane, the last tile of
+the tiled kernels), planted hits that send some sequences from the tiled
+MSV pass to the exact kernel, the largest supported model, single scans,
+batches and plans that mix long and striped profiles, rank lists from the
+SSV -> MSV hand-off, and the configuration and allocation-free calls that
+long profiles do not take.
 """
 import numpy as np
 import pytest
@@ -90,6 +92,20 @@ def test_strong_long_profile_overflows_and_chains(ctx):
     rec = synth.random_profile(4100, 20, rng, cost_hi=40, bias=30, tbm=5, tec=2)
     db = synth.random_database(200, 400, rng, alphabet=20, min_len=1)
     assert _both(ctx, [rec], db) > 0
+
+
+@pytest.mark.parametrize("M", [3500, 5000])
+def test_planted_hits_mix_tiled_and_exact_msv(ctx, M):
+    """Realistic long profile, 30% of the sequences carrying a segment drawn
+    from its own emissions: for about a third of them xJ passes base in
+    mid-sequence, so the tiled MSV pass leaves them to the exact
+    lane-segment kernel, and the others it scores itself; both filters,
+    bit-exact."""
+    rng = np.random.default_rng(10 + M)
+    rec = synth.make_profile(M, rng)
+    db = synth.make_database(400, 355, 10, 2000, rng)
+    synth.plant_segments(db, [rec], 0.3, rng)
+    _both(ctx, [rec], db)
 
 
 def test_largest_model(ctx):
