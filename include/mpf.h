@@ -73,11 +73,14 @@ enum { MPF_MSV = 0, MPF_SSV = 1 };
 int mpf_max_model_length(void);
 
 /* Largest model length the striped shared-memory scan kernels hold (3,072).
- * Longer byte-filter profiles are scored by the long-model kernel: one warp
- * per sequence, each lane a contiguous segment of nodes, the cost bytes read
- * from device memory (the paper's tables end at M = 2405; models beyond the
- * on-chip table are the large-model case of its Sec. 6).  Longer Viterbi
- * profiles keep their DP rows in device memory instead of shared memory. */
+ * Longer byte-filter profiles are scored by the long-model kernels, one
+ * warp per sequence: the model swept in tiles of 1,024 nodes with the DP
+ * row in registers (SSV; MSV with the begin score held, rescoring exactly
+ * the sequences where it would move), or each lane a contiguous segment of
+ * nodes with the row in shared memory (MSV otherwise).  The paper's tables
+ * end at M = 2405; models beyond the on-chip table are the large-model case
+ * of its Sec. 6.  Longer Viterbi profiles keep their DP rows in device
+ * memory instead of shared memory. */
 int mpf_max_striped_length(void);
 
 /* Message for a status code (static string, never NULL). */
