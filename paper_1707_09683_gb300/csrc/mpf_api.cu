@@ -294,7 +294,7 @@ struct LaunchGroup {
   QueryDesc *d_queries = nullptr;
   uint32_t n_queries = 0;
   uint32_t *d_counter = nullptr;
-  uint8_t *d_col = nullptr;      // tiled kernel: two or three columns of col_stride bytes per resident warp
+  uint8_t *d_col = nullptr;      // tiled kernel: two columns of col_stride bytes per resident warp
   uint32_t col_stride = 0;
   uint64_t col_bytes = 0;
   uint32_t *d_fallback = nullptr;   // tiled MSV: per query a count, then n_seqs ranks per query
@@ -531,10 +531,10 @@ int plan_create(mpf_ctx *ctx, int filter, const mpf_profile *const *profs, int n
     cudaError_t e = cudaMallocAsync((void **)&g.d_queries, sizeof(QueryDesc) * kv.second.size(), ctx->stream);
     if (e == cudaSuccess) e = cudaMallocAsync((void **)&g.d_counter, sizeof(uint32_t), ctx->stream);
     if (e == cudaSuccess && (g.mode == MODE_TILE_SSV || g.mode == MODE_TILE_MSV)) {
-      // Per resident warp two (SSV) or three (MSV) columns of int16
-      // (positions 0..max_len and the prefetch's overrun), col_stride bytes each.
+      // Per resident warp two columns of int16 (positions 0..max_len and
+      // the prefetch's overrun), col_stride bytes each.
       g.col_stride = (uint32_t)((((uint64_t)db->max_len + 12) * 2 + 15) & ~(uint64_t)15);
-      g.col_bytes = (uint64_t)g.grid * kTileWarps * (g.mode == MODE_TILE_MSV ? 3 : 2) * g.col_stride;
+      g.col_bytes = (uint64_t)g.grid * kTileWarps * 2 * g.col_stride;
       e = cudaMallocAsync((void **)&g.d_col, g.col_bytes, ctx->stream);
     }
     if (e == cudaSuccess && g.mode == MODE_TILE_MSV) {

@@ -100,8 +100,8 @@ struct ScanParams {
   uint32_t *item_counter;     // zero before the launch
   int *status;                // nonzero: error reported by a kernel
   uint32_t long_words;        // long-model kernel: largest seg_words of its queries
-  uint8_t *tile_col;          // tiled kernel: per resident warp two or three columns
-  uint32_t tile_col_stride;   //   of tile_col_stride bytes (an int16 per row)
+  uint8_t *tile_col;          // tiled kernel: per resident warp two columns of
+  uint32_t tile_col_stride;   //   tile_col_stride bytes (an int16 per row)
   uint64_t tile_col_bytes;
 };
 
@@ -114,8 +114,7 @@ size_t long_smem_per_warp(int seg_words, bool bytes);
 
 // Tiled kernel for long models (mpf_tile_kernel.cu, MODE_TILE_SSV and
 // MODE_TILE_MSV): tiles of kTileNodes nodes, kTileC per lane, blocks of
-// kTileWarps warps; per resident warp 2 (SSV) or 3 (MSV) columns of
-// tile_col_stride bytes.
+// kTileWarps warps; per resident warp two columns of tile_col_stride bytes.
 // Table: per tile [code 0..31][chunk 0..kTileC/8-1][lane] x 4 int16 pairs,
 // pair p of lane l = nodes (l*kTileC + p, l*kTileC + p + kTileC/2), scores
 // s = bias - cost (codes >= K: bias - 255; nodes past M: -32768); after the

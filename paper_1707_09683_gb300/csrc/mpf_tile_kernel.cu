@@ -29,13 +29,16 @@
 // in the striped kernels' lazy form, v = max(0, dp - b) follows the same
 // recurrence as SSV while the begin score b stays constant, and b moves
 // only once xJ passes base.  So the tiles are swept with b held at its
-// initial value, each row's maximum over all tiles is kept in a second
-// column, and a final pass over that column finds the first row whose
-// maximum passes the threshold T = min(base + tec - b, 255 - bias - b - 1):
-// none (raw from the largest row maximum, or, if no cell rose above b, from
-// the best single-cell score of the residues), an overflow (raw 255, flag),
-// the last row (raw as if none), or a row after which xB would move -- then
-// the sequence's rank goes to the query's fallback list, which the exact
+// initial value.  What decides the sequence is the first row whose maximum
+// over the whole model passes T = min(base + tec - b, 255 - bias - b - 1),
+// and that maximum: a row's maximum passes T exactly when some lane of some
+// tile has a cell above T in it, so each lane keeps the first such row of
+// its own cells (over the tiles) and its largest cell there, and one warp
+// reduction per sequence gives the row and the row maximum.  Then: no such
+// row (raw from the largest cell, or, if no cell rose above b, from the
+// best single-cell score of the residues); an overflow there (raw 255,
+// flag); the last row (raw as if none); or a row after which xB would move
+// -- the sequence's rank goes to the query's fallback list, which the exact
 // lane-segment kernel scores next (Alg. 2 row by row).
 #include <cuda_runtime.h>
 #include <math.h>
@@ -48,8 +51,12 @@ namespace mpf {
 namespace {
 
 constexpr uint32_t kAll = 0xffffffffu;
+constexpr uint32_t kNone = 0xffffffffu;
 constexpr int kChunks = kTileC / 8;   // 16-byte chunks (4 pairs) per lane and residue row
 constexpr int kPairs = kTileC / 2;
+
+// The larger of the two 16-bit halves.
+__device__ __forceinline__ int half_max(uint32_t w) { return max((int)(int16_t)(w & 0xffffu), (int)(int16_t)(w >> 16)); }
 
 // One row of the lane's tile segment: v holds the previous row and receives
 // this row; `in` is the previous row's score of the node before the lane's
@@ -72,45 +79,37 @@ __device__ __forceinline__ void tile_row(uint32_t (&v)[kPairs], uint32_t in, con
   }
 }
 
-// MSV result of one sequence from its row maxima (colmax[0..len), v-space),
-// by the whole warp; see the file comment.
-__device__ __noinline__ void msv_finish(const ScanParams &sp, const QueryDesc &qd, const int16_t *colmax,
-                                        uint32_t r, uint32_t len, uint32_t orig, int lane) {
-  __syncwarp();   // lane 0's row maxima are visible to the warp
-  const int t = qd.tjb ? (int)__ldg(qd.tjb + min(len, qd.n_tjb - 1u)) : qd.tjb_fixed;
+// MSV result of one sequence, by the whole warp: frow / fval, this lane's
+// first row with a cell above T and its largest cell there (kNone: none),
+// V this lane's largest cell.
+__device__ __noinline__ void msv_finish(const ScanParams &sp, const QueryDesc &qd, uint32_t r, uint32_t len,
+                                        uint32_t orig, int lane, int b, int t, uint32_t frow, int fval, int V) {
   const int cap = 255 - qd.bias;
-  const int b = min(min(255, max(0, qd.base - (t + qd.tbm))), cap);
-  const int T = min(qd.base + qd.tec - b, cap - b - 1);
-  int V = 0;
-  uint32_t first = 0xffffffffu;
-  for (uint32_t j = lane; j < len; j += 32) {
-    const int m = colmax[j];
-    V = max(V, m);
-    if (m > T && first == 0xffffffffu) first = j;
-  }
-  V = (int)__reduce_max_sync(kAll, (uint32_t)V);
-  first = __reduce_min_sync(kAll, first);
+  const uint32_t first = __reduce_min_sync(kAll, frow);
+  const int m = __reduce_max_sync(kAll, frow == first ? fval : -1);
+  V = __reduce_max_sync(kAll, V);
   // No cell rose above b: the best row maximum is the best single-cell
-  // score of the residues (per-code maxima after the tiles).
+  // score of the residues (per-code maxima stored after the tiles).
   int g = -(1 << 20);
-  if (V == 0 && len > 0 && first == 0xffffffffu) {
-    const int16_t *smax = reinterpret_cast<const int16_t *>(reinterpret_cast<const uint8_t *>(qd.table) + qd.smax_off);
+  if (V == 0 && len > 0 && first == kNone) {
+    const int16_t *smax =
+        reinterpret_cast<const int16_t *>(reinterpret_cast<const uint8_t *>(qd.table) + qd.smax_off);
     const int mine = (int)__ldg(smax + lane);
+    const uint32_t w0 = __ldg(sp.seq_word + r);
     for (uint32_t j0 = 0; j0 < len; j0 += 32) {
       const uint32_t j = j0 + lane;
       uint32_t x = 0;
-      if (j < len) x = (__ldg(sp.residues + (__ldg(sp.seq_word + r) + (j >> 2))) >> (8 * (j & 3))) & 0xffu;
+      if (j < len) x = (__ldg(sp.residues + w0 + (j >> 2)) >> (8 * (j & 3))) & 0xffu;
       if (!MPF_DCHECK(sp.status, x < 32u)) x = 0;
       const int sx = __shfl_sync(kAll, mine, (int)x);
       if (j < len) g = max(g, sx);
     }
-    g = __reduce_max_sync(kAll, g + (1 << 20)) - (1 << 20);
+    g = __reduce_max_sync(kAll, g);
   }
   if (lane != 0) return;
   int raw = 0, flag = 0;
   if (len > 0) {
-    if (first != 0xffffffffu) {
-      const int m = colmax[first];
+    if (first != kNone) {
       if (b + m >= cap) {
         raw = 255;
         flag = 1;
@@ -143,15 +142,12 @@ __global__ void __launch_bounds__(kTileWarps * 32) tile_kernel(ScanParams sp) {
   const int W = blockDim.x >> 5;
   constexpr int kTileWords = 32 * kChunks * 32;   // uint4 per tile
   const uint64_t cw = (uint64_t)blockIdx.x * W + warp;
-  // This warp's columns: two boundary columns (int16 per row, position
-  // i + 1 = row i) and, for MSV, the row maxima (position i = row i).
-  constexpr int kCols = MSV ? 3 : 2;
-  int16_t *colbuf = reinterpret_cast<int16_t *>(sp.tile_col + cw * kCols * (uint64_t)sp.tile_col_stride);
+  // This warp's two boundary columns (int16 per row, position i + 1 = row i).
+  int16_t *colbuf = reinterpret_cast<int16_t *>(sp.tile_col + cw * 2 * (uint64_t)sp.tile_col_stride);
   const uint32_t col_elems = sp.tile_col_stride / 2;
-  int16_t *colmax = colbuf + 2 * (size_t)col_elems;   // MSV only
   // Debug builds: the table and this warp's columns within their buffers.
   if (!MPF_DCHECK(sp.status, (size_t)kTileWords * 16 <= dynamic_smem_bytes() &&
-                                 (cw + 1) * kCols * sp.tile_col_stride <= sp.tile_col_bytes &&
+                                 (cw + 1) * 2 * sp.tile_col_stride <= sp.tile_col_bytes &&
                                  (sp.tile_col_stride & 15) == 0))
     return;
 
@@ -188,6 +184,12 @@ __global__ void __launch_bounds__(kTileWarps * 32) tile_kernel(ScanParams sp) {
       active = MPF_DCHECK(sp.status, (uint64_t)w0 + ((len + 3u) >> 2) <= sp.n_words && orig < sp.n_seqs &&
                                          (uint64_t)len + 11 <= col_elems);
     }
+    const int tj = qd.tjb ? (int)__ldg(qd.tjb + min(len, qd.n_tjb - 1u)) : qd.tjb_fixed;
+    // MSV: the begin score held over the tiles, and the threshold T.
+    const int b = min(min(255, max(0, qd.base - (tj + qd.tbm))), 255 - qd.bias);
+    const int T = min(qd.base + qd.tec - b, 255 - qd.bias - b - 1);
+    uint32_t frow = kNone;   // MSV: this lane's first row with a cell above T
+    int fval = -1;
     const int nt = (int)((qd.M + kTileNodes - 1) / kTileNodes);
     uint32_t rmax = 0;   // running maximum, two 16-bit halves
     for (int t = 0; t < nt; ++t) {
@@ -204,34 +206,23 @@ __global__ void __launch_bounds__(kTileWarps * 32) tile_kernel(ScanParams sp) {
 #pragma unroll
       for (int p = 0; p < kPairs; ++p) v[p] = 0u;
       const uint4 *sbase = tsm + lane;
-      // Rolling prefetch of the boundary column (and for MSV of the row
-      // maxima so far), four rows per 64-bit word.
-      uint2 cur = make_uint2(0, 0), nxt = make_uint2(0, 0), mcur = make_uint2(0, 0), mnxt = make_uint2(0, 0);
+      // Rolling prefetch of the boundary column, four rows per 64-bit word.
+      uint2 cur = make_uint2(0, 0), nxt = make_uint2(0, 0);
       if (lane == 0 && !first) {
         cur = __ldcg(reinterpret_cast<const uint2 *>(cin));
         nxt = __ldcg(reinterpret_cast<const uint2 *>(cin) + 1);
-        if (MSV) {
-          mcur = __ldcg(reinterpret_cast<const uint2 *>(colmax));
-          mnxt = __ldcg(reinterpret_cast<const uint2 *>(colmax) + 1);
-        }
       }
       for (uint32_t i0 = 0; i0 < len; i0 += 4) {
         const uint32_t word = __ldg(sp.residues + w0 + (i0 >> 2));
-        uint2 c = cur, mc = mcur;
+        uint2 c = cur;
         if (lane == 0 && !first) {
           cur = nxt;
           nxt = __ldcg(reinterpret_cast<const uint2 *>(cin) + (i0 >> 2) + 2);
-          if (MSV) {
-            // Rows i0 + 8 .. i0 + 11 are not written by this tile yet: these
-            // are the earlier tiles' maxima.
-            mcur = mnxt;
-            mnxt = __ldcg(reinterpret_cast<const uint2 *>(colmax) + (i0 >> 2) + 2);
-          }
         }
         const uint32_t xs[4] = {__byte_perm(word, 0u, 0x4440), __byte_perm(word, 0u, 0x4441),
                                 __byte_perm(word, 0u, 0x4442), __byte_perm(word, 0u, 0x4443)};
         const uint32_t cs[4] = {c.x & 0xffffu, c.x >> 16, c.y & 0xffffu, c.y >> 16};
-        const uint32_t ms[4] = {mc.x & 0xffffu, mc.x >> 16, mc.y & 0xffffu, mc.y >> 16};
+        uint32_t rq[4] = {0u, 0u, 0u, 0u};   // MSV: this lane's maxima of the four rows
 #pragma unroll
         for (int u = 0; u < 4; ++u) {
           if (i0 + u < len) {
@@ -241,39 +232,52 @@ __global__ void __launch_bounds__(kTileWarps * 32) tile_kernel(ScanParams sp) {
             // before's last node; for lane 0 the previous tile's last node.
             uint32_t in = __shfl_up_sync(kAll, v[kPairs - 1] >> 16, 1);
             if (lane == 0) in = cs[u];
-            if (MSV) {
-              uint32_t racc = 0;
-              tile_row(v, in, sbase + x * (kChunks * 32), racc);
-              // This row's maximum over the tile, merged with the earlier
-              // tiles' (all cells are >= 0 before any overflow).
-              const int m = __reduce_max_sync(
-                  kAll, max((int)(int16_t)(racc & 0xffffu), (int)(int16_t)(racc >> 16)));
-              if (lane == 0) colmax[i0 + u] = (int16_t)(first ? m : max(m, (int)(int16_t)ms[u]));
-            } else {
-              tile_row(v, in, sbase + x * (kChunks * 32), rmax);
-            }
+            tile_row(v, in, sbase + x * (kChunks * 32), MSV ? rq[u] : rmax);
             if (write && lane == 31) cout[i0 + u + 1] = (int16_t)(v[kPairs - 1] >> 16);
+          }
+        }
+        if (MSV) {
+          // (Cells are >= 0 until an overflow, so the relu forms are exact.)
+          const uint32_t r4 = __vimax3_s16x2(rq[0], rq[1], __vimax_s16x2_relu(rq[2], rq[3]));
+          rmax = __vimax_s16x2_relu(rmax, r4);
+          // The first of these rows with a cell above T, if not later than
+          // this lane's first so far (rows after it cannot matter; the same
+          // row in another tile keeps the larger cell).  Rows past the end
+          // hold 0, which T = -1 would count: they are left out.
+          if (i0 <= frow && half_max(r4) > T) {
+#pragma unroll
+            for (int u = 3; u >= 0; --u) {
+              const int mu = half_max(rq[u]);
+              const uint32_t row = i0 + u;
+              if (mu > T && row < len) {
+                if (row < frow) {
+                  frow = row;
+                  fval = mu;
+                } else if (row == frow) {
+                  fval = max(fval, mu);
+                }
+              }
+            }
           }
         }
       }
     }
     if (MSV) {
-      if (active) msv_finish(sp, qd, colmax, r, len, orig, lane);
+      if (active) msv_finish(sp, qd, r, len, orig, lane, b, tj, frow, fval, half_max(rmax));
       continue;
     }
     // R over the sequence: the largest half of any lane.
     int R = 0;
-    if (active) R = max((int)(int16_t)(rmax & 0xffffu), (int)(int16_t)(rmax >> 16));
+    if (active) R = half_max(rmax);
     R = __reduce_max_sync(kAll, R);
     if (active && lane == 0) {
-      const int t = qd.tjb ? (int)__ldg(qd.tjb + min(len, qd.n_tjb - 1u)) : qd.tjb_fixed;
       const int raw = min(R, 255);
       const int flag = R >= 255 ? 1 : 0;
       qd.raw[orig] = (uint8_t)raw;
       qd.flag[orig] = (uint8_t)flag;
       if (qd.nat)
         qd.nat[orig] = flag ? __int_as_float(0x7f800000)
-                            : __fsub_rn(__fdiv_rn(__int2float_rn(raw - qd.tbm - qd.tec - 2 * t), qd.scale), 3.0f);
+                            : __fsub_rn(__fdiv_rn(__int2float_rn(raw - qd.tbm - qd.tec - 2 * tj), qd.scale), 3.0f);
     }
   }
 }
