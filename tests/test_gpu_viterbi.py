@@ -121,9 +121,10 @@ def test_adversarial_nonpositive_moves(ctx, seed):
 
 @pytest.mark.parametrize("M", [1100, 2100, 2600, 3000])
 def test_long_segment_variants(ctx, M):
-    """Model lengths that select the fast kernel's long-segment variants
-    (deeper unrolling from 32 nodes per lane; the recomputed D row where few
-    warps fit): realistic and adversarial (moves <= 0)."""
+    """Long segments (35-94 nodes per lane), realistic and adversarial (moves
+    <= 0).  With 160 sequences these scans go to the team kernel; the
+    one-warp kernel's long-segment variants (deeper unrolling, no stored D
+    row) are checked on 20,000 sequences in test_gpu_viterbi_team."""
     rng = np.random.default_rng(400 + M)
     db = synth.random_database(160, 220, rng, alphabet=32)
     _run(ctx, [synth.make_vit_profile(M, rng),
