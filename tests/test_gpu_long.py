@@ -108,6 +108,30 @@ def test_planted_hits_mix_tiled_and_exact_msv(ctx, M):
     _both(ctx, [rec], db)
 
 
+def test_long_profiles_on_empty_and_zero_length_databases(ctx):
+    """No sequences, and only sequences of length 0 or 1: the tiled kernels'
+    columns and the MSV fallback list at their smallest."""
+    rng = np.random.default_rng(11)
+    recs = [synth.make_profile(4000, rng), synth.random_profile(3300, 20, rng, cost_hi=40, bias=30, tbm=5, tec=2)]
+    lengths = np.array([0, 1, 0, 1, 1, 0], np.uint32)
+    offsets = np.zeros(lengths.size, np.uint64)
+    np.cumsum(lengths[:-1], dtype=np.uint64, out=offsets[1:])
+    tiny = synth.Database(residues=rng.integers(0, 20, int(lengths.sum())).astype(np.uint8),
+                          offsets=offsets, lengths=lengths)
+    _both(ctx, recs, tiny)
+    empty = synth.Database(residues=np.zeros(0, np.uint8), offsets=np.zeros(0, np.uint64),
+                           lengths=np.zeros(0, np.uint32))
+    db = mpf.Database(ctx, empty.residues, empty.offsets, empty.lengths)
+    profs = [mpf.Profile(ctx, r) for r in recs]
+    out = (_dev(0, torch.uint8), _dev(0, torch.uint8), _dev(0, torch.float32))
+    for f in (mpf.MSV, mpf.SSV):
+        mpf.scan_batch(ctx, f, profs, db, *out)
+    ctx.sync()
+    for p in profs:
+        p.close()
+    db.close()
+
+
 def test_largest_model(ctx):
     rng = np.random.default_rng(6)
     M = mpf.max_model_length()
