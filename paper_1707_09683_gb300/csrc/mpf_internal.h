@@ -145,7 +145,7 @@ enum VitKind {
   kVitFastShared = 0,      // fast kernel, DP rows in shared memory
   kVitFastSharedNoD = 1,   // the same without the stored D row
   kVitGeneralShared = 2,   // general kernel, rows in shared memory
-  kVitFastDevice = 3,      // fast kernel, rows in device memory
+  kVitFastDevice = 3,      // fast kernel, rows in device memory (key + 1: without the stored D row)
   kVitGeneralDevice = 4,   // general kernel, rows in device memory
   kVitFastTeam = 5,        // fast kernel, a team of warps per sequence
   kVitFastDual = 6,        // both kinds 0/1 and 5, each taking the queries on its side of team_max

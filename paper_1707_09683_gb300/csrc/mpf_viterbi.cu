@@ -67,8 +67,9 @@ __device__ __forceinline__ int addmax(int a, int b, int c) { return __viaddmax_s
 // models (GM = true): transitions read through the L1 from device memory,
 // and each warp's rows in its slice of a device scratch buffer as one 8-byte
 // record per node (M | I, D), at slot j*32 + lane like the shared rows, so a
-// warp's access is 256 contiguous bytes; the rows are read and written at
-// the L2 (ld/st.global.cg), which keeps the L1 for the tables.
+// warp's access is 256 contiguous bytes (4-byte records M | I in the fast
+// kernel's variant without the stored D row); the rows are read and written
+// at the L2 (ld/st.global.cg), which keeps the L1 for the tables.
 template <bool GM>
 __device__ __forceinline__ void stage_transitions(uint4 *tr, const uint4 *gtr, int nq) {
   if (GM) return;
@@ -162,7 +163,6 @@ struct FastCell {
 // unroll depth of the node loop.
 template <int U, bool ND, bool GM>
 __global__ void __launch_bounds__(kVitFastMaxThreads, 1) viterbi_fast_kernel(VitParams p) {
-  static_assert(!(ND && GM), "the global-row variant stores D");
   extern __shared__ __align__(16) uint4 fsm[];
   const int lane = threadIdx.x & 31;
   const int warp = threadIdx.x >> 5;
@@ -172,6 +172,7 @@ __global__ void __launch_bounds__(kVitFastMaxThreads, 1) viterbi_fast_kernel(Vit
   int16_t *sI = sM + (size_t)Qmax * 32;
   int16_t *sD = sI + (size_t)Qmax * 32;   // unused with ND
   uint2 *gst = warp_rows<GM>(p, Qmax, warp);
+  uint32_t *gst32 = reinterpret_cast<uint32_t *>(gst);   // GM with ND: 4-byte records (M | I)
   // Debug builds: the transitions and the warps' DP rows must fit the block's
   // shared memory (or the rows the device scratch).
   if (!GM && !MPF_DCHECK(p.status, (size_t)Qmax * 32 * (16 + (blockDim.x >> 5) * (ND ? 4 : 6)) <= dynamic_smem_bytes()))
@@ -229,7 +230,9 @@ __global__ void __launch_bounds__(kVitFastMaxThreads, 1) viterbi_fast_kernel(Vit
         continue;
 
       for (int j = 0; j < nq; ++j) {
-        if (GM) {
+        if (GM && ND) {
+          __stcg(gst32 + j * 32 + lane, __byte_perm((uint32_t)kNeg, (uint32_t)kNeg, 0x5410));
+        } else if (GM) {
           store_rows(gst, j * 32 + lane, kNeg, kNeg, kNeg);
         } else {
           sM[j * 32 + lane] = sI[j * 32 + lane] = (int16_t)kNeg;
@@ -257,7 +260,11 @@ __global__ void __launch_bounds__(kVitFastMaxThreads, 1) viterbi_fast_kernel(Vit
 #pragma unroll U
         for (int j = 0; j < nv; ++j) {
           const int sl = j * 32 + lane;
-          if (GM) {
+          if (GM && ND) {
+            const uint32_t rr = __ldcg(gst32 + sl);
+            c.step_nd(T[sl], __ldg(erow + j * 32), lo16(rr), hi16(rr), xB);
+            __stcg(gst32 + sl, __byte_perm((uint32_t)c.Mn, (uint32_t)c.In, 0x5410));
+          } else if (GM) {
             int Mo, Io, Dl;
             load_rows(gst, sl, Mo, Io, Dl);
             c.step(T[sl], __ldg(erow + j * 32), Mo, Io, Dl, xB);
@@ -750,8 +757,21 @@ VitKernelFn vit_kernel_for(bool general, int Q, bool nd) {
   return Q >= 32 ? viterbi_fast_kernel<8, false, false> : viterbi_fast_kernel<4, false, false>;
 }
 
-VitKernelFn gm_kernel_for(bool general) {
-  return general ? viterbi_general_kernel<8, true> : viterbi_fast_kernel<8, false, true>;
+// Device rows of the fast kernel without the stored D row (4-byte records
+// M | I; the next row recomputes the local delete chain, two more DPX
+// operations per cell) where the tables overflow the L1: then every cell
+// also fetches its transitions and match score from L2, and halving the
+// row traffic pays (one query, 14,000-40,000 sequences, GCUPS with / without
+// D: M = 5,000 604 / 644, 7,000 354 / 606, 10,000 298 / 454; at M = 2,405
+// and 3,500, tables in L1, 655 / 626 and 663 / 645).
+VitKernelFn gm_kernel_for(bool general, bool nd = false) {
+  if (general) return viterbi_general_kernel<8, true>;
+  return nd ? viterbi_fast_kernel<8, true, true> : viterbi_fast_kernel<8, false, true>;
+}
+
+constexpr size_t kGmL1TableBytes = 224 * 1024;
+bool gm_no_d(int Mpad, int n_codes) {
+  return (16 + 2 * (size_t)std::max(n_codes, 1)) * (size_t)Mpad > kGmL1TableBytes;
 }
 
 // Launch shape of the device-row variants: blocks of kGmWarps warps, as
@@ -762,14 +782,19 @@ VitKernelFn gm_kernel_for(bool general) {
 constexpr int kGmWarps = 8, kGmWarpsPerSm = 16;
 
 int gm_blocks_per_sm(bool general) {
+  // The smallest occupancy of the kernel's variants (the scratch is sized for it).
   static const std::array<int, 2> occ = [] {
     std::array<int, 2> t{};
     for (int g = 0; g < 2; ++g) {
-      int b = 0;
-      if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&b, (const void *)gm_kernel_for(g == 1), kGmWarps * 32, 0) !=
-          cudaSuccess)
-        b = 0;
-      t[g] = std::min(b, kGmWarpsPerSm / kGmWarps);
+      int best = kGmWarpsPerSm / kGmWarps;
+      for (int nd = 0; nd < 2; ++nd) {
+        int b = 0;
+        if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&b, (const void *)gm_kernel_for(g == 1, nd == 1),
+                                                          kGmWarps * 32, 0) != cudaSuccess)
+          b = 0;
+        best = std::min(best, b);
+      }
+      t[g] = best;
     }
     return t;
   }();
@@ -931,7 +956,9 @@ int64_t team_max_for(const FastShape &s, int Mpad, int num_sms) {
 
 int viterbi_shape_key(bool fast, int Mpad, int n_codes, int max_smem, int num_sms, uint64_t n_seqs) {
   const int gb = gm_blocks_per_sm(!fast);
-  const int gm_key = gb > 0 ? (fast ? kVitFastDevice : kVitGeneralDevice) * kVitKeyKind : -1;
+  const int gm_key =
+      gb > 0 ? (fast ? kVitFastDevice : kVitGeneralDevice) * kVitKeyKind + (fast && gm_no_d(Mpad, n_codes) ? 1 : 0)
+             : -1;
   if (Mpad > kStripedMaxM) return gm_key;
   const FastShape s = fast_shape(!fast, Mpad, n_codes, max_smem);
   const uint64_t gm_warps = (uint64_t)num_sms * gb * kGmWarps;
@@ -967,9 +994,11 @@ int launch_viterbi(const VitParams &p, int key, int n_codes, int max_smem, int n
     const int b = gm_blocks_per_sm(general);
     if (b < 1) return 2;
     if (!p.state || p.state_bytes < viterbi_state_bytes(!general, p.max_Mpad, num_sms)) return 1;
-    const void *fn = (const void *)gm_kernel_for(general);
-    if (cudaFuncSetAttribute(fn, cudaFuncAttributePreferredSharedMemoryCarveout, 0) != cudaSuccess) return 1;
-    gm_kernel_for(general)<<<num_sms * b, kGmWarps * 32, 0, st>>>(p);
+    const bool nd = key % kVitKeyKind == 1;   // fast kernel without the stored D row
+    const VitKernelFn k = gm_kernel_for(general, nd);
+    if (cudaFuncSetAttribute((const void *)k, cudaFuncAttributePreferredSharedMemoryCarveout, 0) != cudaSuccess)
+      return 1;
+    k<<<num_sms * b, kGmWarps * 32, 0, st>>>(p);
     return cudaGetLastError() == cudaSuccess ? 0 : 1;
   }
   // Shared-memory kernels; a dual launch runs the one-warp kernel, then the
