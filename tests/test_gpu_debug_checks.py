@@ -2,10 +2,11 @@
 
 Every kernel family runs on the debug library over inputs that exercise its
 ragged edges -- striped scans in every lane-group size, rank lists from the
-SSV -> MSV hand-off, long models with 16-bit and byte rows, the Viterbi
-kernels and variants (rows in shared or device memory), the MSV -> Viterbi
-stage -- and no check may fire (mpf_sync would raise MPF_EDEVICE); results
-are compared with the oracle.
+SSV -> MSV hand-off, long models through the tiled kernels (with the MSV
+fallback list) and the lane-segment kernel with 16-bit and byte rows, the
+Viterbi kernels and variants (rows in shared or device memory), the MSV ->
+Viterbi stage -- and no check may fire (mpf_sync would raise MPF_EDEVICE);
+results are compared with the oracle.
 The self-test shows a failed check reaching mpf_sync as MPF_EDEVICE.  The
 debug library runs in a child process so it never mixes with the release
 library the other tests load.
@@ -72,6 +73,29 @@ for M, lanes, words in ((48, 1, 24), (100, 2, 26), (100, 4, 14), (300, 8, 20), (
         for g, w in zip(out, want):
             assert same(g.cpu().numpy()[idx.astype(np.int64)], w), (M, gf)
     p.close()
+
+# The exact lane-segment MSV kernel with 16-bit and byte rows (profiles
+# whose begin score cannot be held), and the tiled MSV pass handing planted
+# hits to it through the fallback list.
+pl_db = synth.make_database(300, 355, 10, 2000, rng)
+pl_rec = synth.make_profile(3500, rng)
+synth.plant_segments(pl_db, [pl_rec], 0.3, rng)
+cases = [(synth.random_profile(3500, 20, rng, bias=250), dbh),
+         (synth.random_profile(31000, 20, rng, bias=250), dbh),
+         (pl_rec, pl_db)]
+for rec, d in cases:
+    dd = mpf.Database(ctx, d.residues, d.offsets, d.lengths)
+    p = mpf.Profile(ctx, rec)
+    m = dd.n_seqs
+    out = [torch.empty(m, dtype=t, device=dev) for t in (torch.uint8, torch.uint8, torch.float32)]
+    mpf.scan_batch(ctx, mpf.MSV, [p], dd, *out)
+    ctx.sync()
+    idx = np.arange(0, m, 7, dtype=np.uint64)
+    want = oracle.scan(oracle.MSV, rec, d.residues, d.offsets, d.lengths, index=idx, nthreads=8)
+    for g, w in zip(out, want):
+        assert same(g.cpu().numpy()[idx.astype(np.int64)], w), rec.M
+    p.close()
+    dd.close()
 
 # The SSV -> MSV hand-off (rank lists) with a striped and a long profile,
 # then the MSV -> Viterbi stage.
