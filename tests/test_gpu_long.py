@@ -80,11 +80,14 @@ def test_adversarial_long_profiles(ctx, seed):
 
 @pytest.mark.parametrize("M", [29000, 31000])
 def test_byte_row_storage_lengths(ctx, M):
-    """Around the length where the DP row switches from 16-bit pairs to
-    bytes (fewer than four warps per SM with pairs)."""
+    """Around the length where the exact MSV kernel's DP row switches from
+    16-bit pairs to bytes (fewer than four warps per SM with pairs): a
+    profile whose begin score cannot be held (bias 250) takes that kernel;
+    the others the tiled kernels."""
     rng = np.random.default_rng(M)
     wl = synth.make_workload(0, n_seqs=120)
-    _both(ctx, [synth.make_profile(M, rng), synth.random_profile(M + 77, 24, rng, bias=90)], wl.db)
+    _both(ctx, [synth.make_profile(M, rng), synth.random_profile(M + 77, 24, rng, bias=90),
+                synth.random_profile(M + 5, 20, rng, bias=250)], wl.db)
 
 
 def test_strong_long_profile_overflows_and_chains(ctx):
