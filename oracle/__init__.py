@@ -151,13 +151,24 @@ def gumbel_pvalue(x, mu: float, lam: float):
     return p
 
 
+def ssv_passes(flag, nat, ssv_min_nat: float):
+    """The SSV -> MSV hand-off rule of Sec. 2.1, as a boolean mask: a
+    sequence goes on to MSV when its SSV score overflowed (flag != 0; it
+    certainly scores high) or its SSV nat score is at least ssv_min_nat
+    (inclusive), compared in float32."""
+    flag = np.asarray(flag)
+    nat = np.asarray(nat, dtype=np.float32)
+    with np.errstate(invalid="ignore"):
+        return (flag != 0) | (nat >= np.float32(ssv_min_nat))
+
+
 def pipeline(prof, residues, offsets, lengths, ssv_min_nat: float, nthreads: int = 1):
     """SSV over every sequence, MSV over those whose SSV nat score is
     >= ssv_min_nat or whose SSV score overflowed (Sec. 2.1).  Returns
-    (ssv (raw, flag, nat), msv (raw, flag, nat) with flag 2 / NaN for
+    (ssv (raw, flag, nat), msv (raw, flag, nat) with raw 0 / flag 2 / NaN for
     filtered sequences, number passing)."""
     sr, sf, sn = ssv(prof, residues, offsets, lengths, nthreads=nthreads)
-    keep = (sf != 0) | (sn >= np.float32(ssv_min_nat))
+    keep = ssv_passes(sf, sn, ssv_min_nat)
     idx = np.flatnonzero(keep).astype(np.uint64)
     n = sr.size
     mr = np.zeros(n, np.uint8)
