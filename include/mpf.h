@@ -232,7 +232,10 @@ void mpf_plan_destroy(mpf_plan *plan);
  *   Asynchronous on the context stream (one SSV and one MSV launch per kernel
  *   configuration, three selection kernels between them); temporary device
  *   memory is taken from and returned to the stream-ordered pool.
- * Errors: MPF_EINVAL (null or host buffer, NaN threshold), MPF_ENOMEM, MPF_ECUDA.
+ * The seven buffers must not overlap one another: the hand-off reads the SSV
+ * outputs while it writes the MSV ones.
+ * Errors: MPF_EINVAL (null or host buffer, NaN threshold, overlapping
+ * buffers), MPF_ENOMEM, MPF_ECUDA.
  */
 int mpf_pipeline_scan(mpf_ctx *ctx, const mpf_profile *const *profs, int n_q, const mpf_db *db,
                       float ssv_min_nat, uint8_t *ssv_raw, uint8_t *ssv_flag, float *ssv_nat,
@@ -306,9 +309,11 @@ int mpf_viterbi_scan(mpf_ctx *ctx, const mpf_vprofile *const *vprofs, int n_q, c
  * receive their Viterbi score, flag and nat; the others score -32768, flag 2,
  * nat NaN.  n_pass[n_q] receives the number of passing sequences per query.
  * All buffers are device pointers (nat nullable); asynchronous on the context
- * stream; temporary device memory comes from the stream-ordered pool.
- * Errors: MPF_EINVAL (null or host buffer, NaN threshold), MPF_EUNSUPPORTED,
- * MPF_ENOMEM, MPF_ECUDA.
+ * stream; temporary device memory comes from the stream-ordered pool.  The
+ * buffers must not overlap one another (the MSV inputs are read while the
+ * Viterbi outputs are written).
+ * Errors: MPF_EINVAL (null or host buffer, NaN threshold, overlapping
+ * buffers), MPF_EUNSUPPORTED, MPF_ENOMEM, MPF_ECUDA.
  */
 int mpf_viterbi_rescore(mpf_ctx *ctx, const mpf_vprofile *const *vprofs, int n_q, const mpf_db *db,
                         const uint8_t *msv_flag, const float *msv_nat, float msv_min_nat,
@@ -331,14 +336,15 @@ int mpf_debug_check_selftest(mpf_ctx *ctx);
 /*
  * Allocation-free scan.  The paper has no counterpart: this entry point exists
  * for callers that cannot allocate device memory when they score, such as
- * code recording a CUDA graph under a capture mode that forbids allocation,
- * services that run under a fixed device-memory budget, or hosts whose device
- * allocator is owned by another framework.  It scores like mpf_msv_scan /
- * mpf_ssv_scan (filter = MPF_MSV or MPF_SSV) but calls no cudaMalloc, cudaFree
- * or other allocating routine: its query descriptor, work counter, status word
- * and striped cost table live in one file-scope device array of
- * 512 + 224 KiB = 229,888 bytes that every GPU loading the library holds until
- * the process exits.
+ * services that account for all device memory up front and run under a fixed
+ * budget, or plug-ins whose host application owns the device allocator (its
+ * pool holds the memory, and a cudaMalloc beside it can fail or stall the
+ * device).  It scores like mpf_msv_scan / mpf_ssv_scan (filter = MPF_MSV or
+ * MPF_SSV) but calls no cudaMalloc, cudaFree or other allocating routine: its
+ * query descriptor, work counter and striped cost table live in one
+ * file-scope device array of 512 + 224 KiB = 229,888 bytes that every GPU
+ * loading the library holds until the process exits.  The kernel reports
+ * through the context's status word, as the regular scans do.
  *   raw, overflow: device pointers, n_seqs bytes each; nat: device pointer of
  *     n_seqs floats or NULL.  Host pointers are rejected (MPF_EINVAL).
  *   Asynchronous on the context stream, like a scan into device outputs.
@@ -350,7 +356,7 @@ int mpf_debug_check_selftest(mpf_ctx *ctx);
  *     device, with that device current); make that first call before any
  *     stream capture.
  *   All calls share the one array and each call overwrites it (the counter
- *     and status word are cleared on the stream): calls ordered on one stream
+ *     is cleared on the stream): calls ordered on one stream
  *     are safe, calls whose kernels overlap on the GPU (other streams or
  *     contexts on the same device) race and give wrong results.
  * Errors: MPF_EINVAL, MPF_EUNSUPPORTED, MPF_ECUDA.

@@ -1076,6 +1076,12 @@ int mpf_pipeline_scan(mpf_ctx *ctx, const mpf_profile *const *profs, int n_q, co
     if (!is_device_ptr(ptr)) return MPF_EINVAL;
   if (msv_nat && !is_device_ptr(msv_nat)) return MPF_EINVAL;
   const uint64_t n = db->n_seqs;
+  {  // The hand-off reads the SSV outputs while it writes the MSV ones: no two may share memory.
+    const uint64_t nq = (uint64_t)n_q * n;
+    const void *ptr[7] = {ssv_raw, ssv_flag, ssv_nat, msv_raw, msv_flag, msv_nat, n_pass};
+    const uint64_t bytes[7] = {nq, nq, 4 * nq, nq, nq, msv_nat ? 4 * nq : 0, 4 * (uint64_t)n_q};
+    if (ranges_overlap(ptr, bytes, 7)) return MPF_EINVAL;
+  }
   const uint64_t n_chunks = (n + kSelectChunk - 1) / kSelectChunk;
   uint32_t *ranks = nullptr, *n_ranks = nullptr, *chunk = nullptr;
   cudaError_t e = cudaMallocAsync((void **)&ranks, std::max<uint64_t>(1, (uint64_t)n_q * n) * 4, ctx->stream);

@@ -109,6 +109,18 @@ inline bool is_device_ptr(const void *p) {
   return a.type == cudaMemoryTypeDevice || a.type == cudaMemoryTypeManaged;
 }
 
+// True when any two of the n byte ranges [ptr, ptr + bytes) overlap (empty
+// ranges overlap nothing).
+inline bool ranges_overlap(const void *const *ptr, const uint64_t *bytes, int n) {
+  for (int i = 0; i < n; ++i)
+    for (int j = i + 1; j < n; ++j) {
+      if (!ptr[i] || !ptr[j] || !bytes[i] || !bytes[j]) continue;
+      const uintptr_t a = (uintptr_t)ptr[i], b = (uintptr_t)ptr[j];
+      if (a < b + bytes[j] && b < a + bytes[i]) return true;
+    }
+  return false;
+}
+
 // C status code of a nonzero device status word.
 inline int status_code(int st) {
   if (st == 0) return MPF_OK;

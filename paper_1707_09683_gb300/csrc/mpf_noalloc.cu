@@ -13,15 +13,17 @@ using namespace mpf::host;
 
 //
 // mpf_scan_noalloc serves callers that must not allocate device memory at
-// call time: code running inside a CUDA stream capture that forbids
-// allocation, processes under a fixed memory budget, or hosts whose
-// allocator belongs to someone else.  Everything the scan kernel needs
-// beyond its inputs and outputs -- the query descriptor, the work-item
-// counter, the status word and the striped cost table -- lives in the
-// file-scope device array below instead of memory from cudaMalloc.
+// call time: services that account for every byte of device memory up front
+// and run under a fixed budget, and plug-ins whose host application owns the
+// device allocator (its pool holds the memory, and a cudaMalloc beside it can
+// fail or stall the device).  Everything the scan kernel needs beyond its
+// inputs and outputs -- the query descriptor, the work-item counter and the
+// striped cost table -- lives in the file-scope device array below instead
+// of memory from cudaMalloc; the kernel reports through the context's status
+// word, like the regular scan.
 namespace {
 
-constexpr size_t kNoAllocHeader = 512;                 // descriptor, counter, status
+constexpr size_t kNoAllocHeader = 512;                 // descriptor, counter
 constexpr size_t kNoAllocTableMax = 224u * 1024u;      // largest staged table image
 constexpr size_t kNoAllocBytes = kNoAllocHeader + kNoAllocTableMax;
 
@@ -99,7 +101,6 @@ extern "C" int mpf_scan_noalloc(mpf_ctx *ctx, int filter, const mpf_profile *pro
   q.nat = nat;
   static_assert(sizeof(QueryDesc) + 16 <= 256, "descriptor fits the scratch header");
   uint32_t *counter = reinterpret_cast<uint32_t *>(scratch + 256);
-  int *status = reinterpret_cast<int *>(scratch + 260);
 
   const int smem = (int)g.table_bytes;
   MPF_CUDA(cudaFuncSetAttribute((const void *)fn, cudaFuncAttributeMaxDynamicSharedMemorySize, smem));
@@ -108,12 +109,12 @@ extern "C" int mpf_scan_noalloc(mpf_ctx *ctx, int filter, const mpf_profile *pro
   if (per_sm < 1) return MPF_EUNSUPPORTED;
   const uint32_t n_shards = (uint32_t)(ctx->num_sms * per_sm);
 
-  // Every call reuses the same scratch: the table, descriptor, counter and
-  // status are rewritten (the counter and status cleared) on the stream.
+  // Every call reuses the same scratch: the table and descriptor are
+  // rewritten and the counter cleared on the stream.
   MPF_CUDA(cudaMemcpyAsync(scratch + kNoAllocHeader, g_noalloc_image, g.table_bytes,
                            cudaMemcpyHostToDevice, ctx->stream));
   MPF_CUDA(cudaMemcpyAsync(scratch, &q, sizeof(q), cudaMemcpyHostToDevice, ctx->stream));
-  MPF_CUDA(cudaMemsetAsync(scratch + 256, 0, 8, ctx->stream));
+  MPF_CUDA(cudaMemsetAsync(scratch + 256, 0, 4, ctx->stream));
 
   ScanParams sp{};
   sp.residues = db->d_words;
@@ -127,7 +128,7 @@ extern "C" int mpf_scan_noalloc(mpf_ctx *ctx, int filter, const mpf_profile *pro
   sp.n_queries = 1;
   sp.n_shards = n_shards;
   sp.item_counter = counter;
-  sp.status = status;
+  sp.status = ctx->d_status;   // debug builds: failed index checks reach mpf_sync
   fn<<<(int)n_shards, kBlockThreads, smem, ctx->stream>>>(sp);
   MPF_CUDA(cudaGetLastError());
   return MPF_OK;

@@ -274,6 +274,12 @@ int mpf_viterbi_rescore(mpf_ctx *ctx, const mpf_vprofile *const *vps, int n_q, c
     if (!is_device_ptr(ptr)) return MPF_EINVAL;
   if (nat && !is_device_ptr(nat)) return MPF_EINVAL;
   const uint64_t n = db->n_seqs;
+  {  // The hand-off reads the MSV outputs while it writes the Viterbi ones: no two may share memory.
+    const uint64_t nq = (uint64_t)n_q * n;
+    const void *ptr[6] = {msv_flag, msv_nat, score, overflow, nat, n_pass};
+    const uint64_t bytes[6] = {nq, 4 * nq, 2 * nq, nq, nat ? 4 * nq : 0, 4 * (uint64_t)n_q};
+    if (ranges_overlap(ptr, bytes, 6)) return MPF_EINVAL;
+  }
   const uint64_t n_chunks = (n + kSelectChunk - 1) / kSelectChunk;
   uint32_t *ranks = nullptr, *n_ranks = nullptr, *chunk = nullptr;
   cudaError_t e = cudaMallocAsync((void **)&ranks, std::max<uint64_t>(1, (uint64_t)n_q * n) * 4, ctx->stream);

@@ -1,7 +1,8 @@
 """The debug build's kernel index checks (libmpf_debug.so).
 
 Every kernel family runs on the debug library over inputs that exercise its
-ragged edges -- striped scans in every lane-group size, rank lists from the
+ragged edges -- striped scans in every lane-group size (and through the
+allocation-free entry point), rank lists from the
 SSV -> MSV hand-off, long models through the tiled kernels (with the MSV
 fallback list) and the lane-segment kernel with 16-bit and byte rows, the
 Viterbi kernels and variants (rows in shared or device memory), the MSV ->
@@ -73,6 +74,21 @@ for M, lanes, words in ((48, 1, 24), (100, 2, 26), (100, 4, 14), (300, 8, 20), (
         for g, w in zip(out, want):
             assert same(g.cpu().numpy()[idx.astype(np.int64)], w), (M, gf)
     p.close()
+
+# The allocation-free entry point (its kernel reports through the context's
+# status word too).
+rec = synth.make_profile(300, rng)
+p = mpf.Profile(ctx, rec)
+lib = mpf.load()
+for gf, of in ((mpf.MSV, oracle.MSV), (mpf.SSV, oracle.SSV)):
+    out = [torch.empty(n, dtype=t, device=dev) for t in (torch.uint8, torch.uint8, torch.float32)]
+    st = lib.mpf_scan_noalloc(ctx.handle, gf, p.handle, db.handle, *[t.data_ptr() for t in out])
+    assert st == mpf.MPF_OK, st
+    ctx.sync()
+    want = oracle.scan(of, rec, dbh.residues, dbh.offsets, dbh.lengths, nthreads=8)
+    for g, w in zip(out, want):
+        assert same(g.cpu().numpy(), w), ("noalloc", gf)
+p.close()
 
 # The exact lane-segment MSV kernel with 16-bit and byte rows (profiles
 # whose begin score cannot be held), and the tiled MSV pass handing planted

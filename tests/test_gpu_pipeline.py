@@ -72,3 +72,48 @@ def test_pvalues_within_float32_error(ctx):
     ok = np.isfinite(want)
     assert np.all(np.abs(got[ok] - want[ok]) <= tol[ok])
     assert got[-5] == 0.0 and np.isnan(got[-4])
+
+
+def test_hand_off_rejects_overlapping_buffers(ctx):
+    """The hand-offs read one stage's outputs while they write the next
+    stage's: buffers that share memory are refused (MPF_EINVAL) before any
+    work is queued, and a correct call on the same context still succeeds."""
+    wl = synth.make_workload(0, n_seqs=500, n_queries=1)
+    db = mpf.Database(ctx, wl.db.residues, wl.db.offsets, wl.db.lengths)
+    prof = mpf.Profile(ctx, wl.profiles[0])
+    n = db.n_seqs
+    lib = mpf.load()
+    arr = mpf._handles([prof])
+    ssv = (_dev(n, torch.uint8), _dev(n, torch.uint8), _dev(n, torch.float32))
+    msv = (_dev(n, torch.uint8), _dev(n, torch.uint8), _dev(n, torch.float32))
+    n_pass = _dev(1, torch.int32)
+    big = _dev(8 * n, torch.float32)
+    p = lambda t: t.data_ptr()
+    aliased = [
+        (p(ssv[0]), p(ssv[1]), p(ssv[2]), p(msv[0]), p(ssv[1]), p(msv[2])),   # msv_flag = ssv_flag
+        (p(ssv[0]), p(ssv[1]), p(ssv[2]), p(msv[0]), p(msv[1]), p(ssv[2])),   # msv_nat = ssv_nat
+        (p(ssv[0]), p(ssv[1]), p(big), p(msv[0]), p(msv[1]), p(big) + 4 * n - 4),   # one float shared
+    ]
+    for a in aliased:
+        st = lib.mpf_pipeline_scan(ctx.handle, arr, 1, db.handle, 0.0, *a, p(n_pass))
+        assert st == mpf.MPF_EINVAL, mpf.strerror(st)
+    # MSV -> Viterbi: the Viterbi outputs may not overlap the MSV inputs.
+    vp = mpf.VitProfile(ctx, synth.make_vit_profile(wl.profiles[0].M, np.random.default_rng(2)))
+    varr = mpf._handles([vp])
+    score = _dev(n, torch.int16)
+    st = lib.mpf_viterbi_rescore(ctx.handle, varr, 1, db.handle, p(msv[1]), p(msv[2]), 0.0,
+                                 p(score), p(msv[1]), p(big), p(n_pass))
+    assert st == mpf.MPF_EINVAL, mpf.strerror(st)
+    st = lib.mpf_viterbi_rescore(ctx.handle, varr, 1, db.handle, p(msv[1]), p(msv[2]), 0.0,
+                                 p(score), p(ssv[1]), p(msv[2]), p(n_pass))
+    assert st == mpf.MPF_EINVAL, mpf.strerror(st)
+    ctx.sync()
+    mpf.pipeline_scan(ctx, [prof], db, 0.0, ssv, msv, n_pass)
+    ctx.sync()
+    (sr, sf, sn), (mr, mf, mn), npass = oracle.pipeline(wl.profiles[0], wl.db.residues, wl.db.offsets,
+                                                        wl.db.lengths, 0.0, nthreads=4)
+    assert int(n_pass.item()) == npass
+    assert np.array_equal(msv[1].cpu().numpy(), mf) and np.array_equal(msv[0].cpu().numpy(), mr)
+    vp.close()
+    prof.close()
+    db.close()

@@ -1,10 +1,11 @@
 """The allocation-free scan entry point against the regular one.
 
 mpf_scan_noalloc is for callers that cannot allocate device memory when they
-score (graph capture that forbids allocation, fixed memory budgets, a host
-framework that owns the allocator).  Its scratch lives in a fixed device
-array inside the library, so two calls in a row must each reproduce the
-regular scan exactly: the second call must not see state left by the first.
+score: services that budget all device memory up front, and plug-ins whose
+host application owns the device allocator.  Its scratch lives in a fixed
+device array inside the library, so two calls in a row must each reproduce
+the regular scan exactly: the second call must not see state left by the
+first.
 This file is collected last so that a run stopping at its first failure has
 already run every other test.
 """
