@@ -408,7 +408,12 @@ def run_mpf(args):
     # in the serving workload) against the resident database, per offered load.
     serving = None
     if world == 1 and not args.no_serve:
-        serving = run_serving(wl.db, args.serve_rates, args.serve_requests, local)
+        t_s = time.time()
+        wl_serv = synth.make_workload(args.serve_workload, n_seqs=args.serve_seqs)
+        log(f"serving workload {wl_serv.name}: {wl_serv.db.n_seqs} seqs ({time.time() - t_s:.1f} s)")
+        serving = run_serving(wl_serv, args.serve_rates, args.serve_requests, local,
+                              work_budget_queries=args.serve_work_budget)
+        del wl_serv
 
     cpu = None
     if rank == 0 and world == 1 and not args.no_cpu:
@@ -545,32 +550,46 @@ def run_long_model(args, ctx, db, wl, time_steps, clocks, dev):
     return out
 
 
-def run_serving(db_record, rates, n_requests, device, seed=3):
+def run_serving(wl_serv, rates, n_requests, device, seed=3, work_budget_queries=None):
     """p50/p99 latency and GCUPS of the continuous-batching server per offered
-    load (Poisson arrivals); queries drawn like the serving workload (M
-    log-uniform in [50, 2000])."""
+    load (Poisson arrivals) on the serving workload's database: each query's
+    M is log-uniform in [50, 2000] (the workload's own query draws, reused
+    across rates), both filters over every sequence.  Profiles are made
+    resident before the first rate (the server's profile cache)."""
     from paper_1707_09683_gb300 import synth
     from paper_1707_09683_gb300.serve import Request, ScanServer
     import math
-    rng = np.random.default_rng(seed)
-    Ms = [int(round(math.exp(v))) for v in rng.uniform(math.log(50), math.log(2000), n_requests)]
-    profiles = [synth.make_profile(m, rng) for m in Ms]
-    server = ScanServer(db_record, device=device, n_streams=4, max_batch=8, max_queue=4 * n_requests)
-    warm = [Request(-1 - i, profiles[i], arrival=0.0) for i in range(min(4, n_requests))]
-    server.run(warm)
+    recs = [wl_serv.profiles[i % len(wl_serv.profiles)] for i in range(n_requests)]
+    res = int(wl_serv.db.lengths.sum(dtype=np.uint64))
+    mean_m = sum(p.M for p in recs) / len(recs)
+    budget = None
+    if work_budget_queries:
+        budget = int(work_budget_queries * 2 * res * mean_m)
+    server = ScanServer(wl_serv.db, device=device, n_streams=4, max_batch=8,
+                        max_queue=max(256, 2 * n_requests), work_budget=budget)
+    t0 = time.time()
+    server.prepare(list({id(p): p for p in recs}.values()))
+    log(f"serving: {len(set(map(id, recs)))} profiles resident in {time.time() - t0:.1f} s")
+    server.run([Request(-1 - i, recs[i], arrival=0.0) for i in range(min(8, n_requests))])
     out = []
     for rate in rates:
         arr = synth.poisson_arrivals(rate, n_requests, seed)
-        reqs = [Request(i, profiles[i], arrival=float(arr[i] - arr[0])) for i in range(n_requests)]
-        st = server.run(reqs, offered_rate=rate)
+        reqs = [Request(i, recs[i], arrival=float(arr[i] - arr[0])) for i in range(n_requests)]
+        st = server.run(reqs, offered_rate=rate, timeout_s=900.0)
         out.append(st.as_dict())
         log(f"serving {rate:6.1f} q/s: p50 {st.p50_ms:8.1f} ms p99 {st.p99_ms:8.1f} ms "
-            f"{st.gcups:9.1f} GCUPS batch {st.mean_batch:.1f}")
+            f"{st.gcups:9.1f} GCUPS batch {st.mean_batch:.1f} wait {st.mean_wait_ms:.1f} ms")
     fp = server.footprint_bytes
     server.close()
-    return {"unit": "ms / GCUPS", "requests_per_rate": n_requests, "filters": ["ssv", "msv"],
-            "query_M": "log-uniform [50, 2000]", "streams": 4, "max_batch": 8,
-            "output_arena_bytes": fp, "by_rate": out}
+    # Capacity: the served rate at the highest offered load (queries per second).
+    top = out[-1]
+    capacity = top["served"] / top["wall_s"] if top["wall_s"] > 0 else None
+    return {"unit": "ms / GCUPS", "workload": wl_serv.name, "n_seqs": int(wl_serv.db.n_seqs),
+            "residues": res, "requests_per_rate": n_requests, "filters": ["ssv", "msv"],
+            "query_M": "log-uniform [50, 2000] (mean %.0f)" % mean_m, "streams": 4, "max_batch": 8,
+            "admission": "by footprint: output slot + score tables (HBM), shared memory per block, "
+                         "work budget %s" % ("none" if budget is None else f"{budget:.3e} cells"),
+            "output_arena_bytes": fp, "capacity_qps": capacity, "by_rate": out}
 
 
 def run_profile_case(args):
@@ -626,6 +645,46 @@ def run_profile_viterbi(args):
                       "residues": db.n_residues}))
 
 
+UBENCH_OPS = [  # (code, name, unit) of the microbenchmarks in ubench/mpf_ubench.cu
+    (0, "iadd (add.u32)", "lane-ops/clk/SM"), (1, "lop3", "lane-ops/clk/SM"),
+    (2, "prmt", "lane-ops/clk/SM"), (3, "imad (mad.lo.u32)", "lane-ops/clk/SM"),
+    (4, "dpx viaddmax.s16x2", "lane-ops/clk/SM"), (5, "dpx vimax3.s16x2", "lane-ops/clk/SM"),
+    (6, "hfma2.relu", "lane-ops/clk/SM"), (7, "vaddus4 (4x8-bit SIMD)", "lane-ops/clk/SM"),
+    (8, "vsubus4 (4x8-bit SIMD)", "lane-ops/clk/SM"), (9, "vmaxu4 (4x8-bit SIMD)", "lane-ops/clk/SM"),
+    (10, "viaddmax.s16x2 + hfma2.relu pairs", "lane-ops/clk/SM"),
+    (11, "viaddmax.s16x2 + prmt pairs", "lane-ops/clk/SM"),
+    (20, "lds.128 conflict-free", "B/clk/SM"), (21, "tcgen05.ld 32x32b.x16 (TMEM)", "B/clk/SM"),
+    (22, "lds.128 + tcgen05.ld together", "B/clk/SM"), (23, "shfl.bfly", "lane-ops/clk/SM"),
+]
+
+
+def run_ubench(args):
+    """Issue rates and on-chip bandwidths per SM and SM clock cycle (clock64
+    between block barriers, so independent of the clock frequency): the
+    denominators of the integer-SIMD roofline and of the shared-memory /
+    tensor-memory table ceilings."""
+    import ctypes
+    from paper_1707_09683_gb300 import build
+    lib = ctypes.CDLL(build.build_ubench())
+    lib.mpf_ubench_run.argtypes = [ctypes.c_int, ctypes.c_int, ctypes.c_int,
+                                   ctypes.POINTER(ctypes.c_double), ctypes.POINTER(ctypes.c_double)]
+    lib.mpf_ubench_run.restype = ctypes.c_int
+    out = []
+    for code, name, unit in UBENCH_OPS:
+        iters = 1500 if code < 20 else 3000
+        best, cyc = 0.0, 0.0
+        for _ in range(3):
+            r, c = ctypes.c_double(), ctypes.c_double()
+            rc = lib.mpf_ubench_run(0, code, iters, ctypes.byref(r), ctypes.byref(c))
+            if rc != 0:
+                raise RuntimeError(f"ubench {name}: status {rc}")
+            if r.value > best:
+                best, cyc = r.value, c.value
+        out.append({"op": name, "rate": best, "unit": unit, "cycles": cyc})
+        log(f"ubench {name:38s} {best:8.2f} {unit}")
+    print(json.dumps({"ubench": out}), flush=True)
+
+
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
@@ -647,16 +706,25 @@ def main():
                     help="model length of the long-model measurement (0: skip)")
     ap.add_argument("--long-vit-seqs", type=int, default=40000,
                     help="sequences of the long-model Viterbi measurement")
-    ap.add_argument("--serve-rates", type=float, nargs="+", default=[10, 50, 100, 200, 500])
-    ap.add_argument("--serve-requests", type=int, default=24)
+    ap.add_argument("--serve-rates", type=float, nargs="+", default=[5, 8, 10, 12, 15, 25, 100, 500])
+    ap.add_argument("--serve-requests", type=int, default=200)
+    ap.add_argument("--serve-workload", type=int, default=3,
+                    help="workload whose database the serving measurement uses (3: 5 M sequences)")
+    ap.add_argument("--serve-seqs", type=int, default=None, help="serving: first N sequences only")
+    ap.add_argument("--serve-work-budget", type=float, default=None,
+                    help="serving: work budget in mean-query units (default: none)")
     ap.add_argument("--profile-case", action="store_true")
     ap.add_argument("--profile-m", type=int, default=2405)
     ap.add_argument("--profile-seqs", type=int, default=0,
                     help="profile case: first N sequences of the database (0: all)")
     ap.add_argument("--profile-viterbi", action="store_true")
     ap.add_argument("--profile-vit-seqs", type=int, default=20000)
+    ap.add_argument("--ubench", action="store_true",
+                    help="run the issue-rate / on-chip bandwidth microbenchmarks and exit")
     args = ap.parse_args()
-    if args.profile_viterbi:
+    if args.ubench:
+        run_ubench(args)
+    elif args.profile_viterbi:
         run_profile_viterbi(args)
     elif args.profile_case:
         run_profile_case(args)
