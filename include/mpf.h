@@ -133,7 +133,7 @@ void mpf_profile_destroy(mpf_profile *prof);
 /*
  * Kernel configuration of a profile for one filter: `lanes` threads of a warp
  * share one sequence (1, 2, 4, 8, 16 or 32) and each holds `words` 32-bit
- * words of two 16-bit cells (4 <= words <= 48, multiple of 4), so the striped
+ * words of two 16-bit cells (4 <= words <= 48, even), so the striped
  * model holds 2 * lanes * words >= M cells (Sec. 3.1: S = 32 / lanes
  * sequences per warp, W = 2 * lanes cells per row step, H = words).
  * set: MPF_EINVAL if the pair is not built or does not cover M, or if the
@@ -143,6 +143,20 @@ void mpf_profile_destroy(mpf_profile *prof);
  */
 int mpf_profile_set_config(mpf_profile *prof, int filter, int lanes, int words);
 int mpf_profile_get_config(const mpf_profile *prof, int filter, int *lanes, int *words);
+
+/*
+ * On-chip and device-memory footprint of a profile's scans with one filter
+ * (for admission control by a server; not in the paper).  smem_bytes: the
+ * shared memory one thread block of its kernel takes (the staged score table
+ * or tile; for the lane-segment long-model kernel, one warp's DP row), with
+ * the configuration the next scan will use.  table_bytes: the device memory
+ * the profile's score tables for that kernel hold once built.  A scan also
+ * writes 6 bytes per database sequence (raw, flag, nat) into the caller's
+ * buffers.
+ * Errors: MPF_EINVAL (null pointer or bad filter).
+ */
+int mpf_profile_footprint(const mpf_profile *prof, int filter, uint32_t *smem_bytes,
+                          uint64_t *table_bytes);
 
 /*
  * Cell arithmetic of a profile's scans for one filter.  Both give identical

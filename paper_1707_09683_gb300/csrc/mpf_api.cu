@@ -903,6 +903,30 @@ int mpf_profile_get_config(const mpf_profile *p, int filter, int *lanes, int *wo
   return MPF_OK;
 }
 
+int mpf_profile_footprint(const mpf_profile *p, int filter, uint32_t *smem_bytes, uint64_t *table_bytes) {
+  if (!p || !smem_bytes || !table_bytes || (filter != MPF_MSV && filter != MPF_SSV)) return MPF_EINVAL;
+  const int mode = kernel_mode(p, filter);
+  if (mode == MODE_TILE_SSV || mode == MODE_TILE_MSV || mode == MODE_LONG_MSV) {
+    const uint64_t tiles = (uint64_t)(p->M + kTileNodes - 1) / kTileNodes;
+    const uint64_t long_table = (uint64_t)32 * p->seg_words * 32 * 4;   // cost bytes, lane-segment order
+    if (mode == MODE_LONG_MSV) {
+      *smem_bytes = (uint32_t)long_smem_per_warp(p->seg_words, 4 * long_smem_per_warp(p->seg_words, false) > 228 * 1024);
+      *table_bytes = long_table;
+    } else {
+      *smem_bytes = (uint32_t)kTileTableBytes;
+      *table_bytes = tiles * kTileTableBytes + 64 + (mode == MODE_TILE_MSV ? long_table : 0);
+    }
+    return MPF_OK;
+  }
+  int lanes = p->cfg_lanes[filter], words = p->cfg_words[filter];
+  if (!lanes) default_config(p->ctx, p->M, mode, &lanes, &words);
+  if (!lanes) return MPF_EUNSUPPORTED;
+  const TableGeom g = table_geom(lanes, words);
+  *smem_bytes = g.table_bytes;
+  *table_bytes = g.table_bytes;
+  return MPF_OK;
+}
+
 int mpf_db_upload(mpf_ctx *ctx, const uint8_t *residues, uint64_t n_residues,
                   const uint64_t *offsets, const uint32_t *lengths, uint64_t n_seqs,
                   mpf_db **out) {

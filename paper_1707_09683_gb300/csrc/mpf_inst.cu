@@ -1,0 +1,55 @@
+// mpf_inst.cu -- scan-kernel instantiations for one lane-group size.
+//
+// Compiled once per size (-DMPF_LG=1, 2, 4, 8, 16, 32; see build.py) into
+// kernel_lg<MPF_LG>(): every mode of the striped scan kernel for each built
+// word count -- multiples of four, and the counts with a two-word tail.
+#include "mpf_scan_kernel.cuh"
+
+#ifndef MPF_LG
+#error "compile with -DMPF_LG=<lanes per sequence>"
+#endif
+#define MPF_CAT2(a, b) a##b
+#define MPF_CAT(a, b) MPF_CAT2(a, b)
+
+namespace mpf {
+
+#define MPF_WORDS_CASE(W)                                                            \
+  case W:                                                                            \
+    if (mode == MODE_SSV) return scan_kernel<MPF_LG, W, MODE_SSV>;                   \
+    if (mode == MODE_MSV_FAST) return scan_kernel<MPF_LG, W, MODE_MSV_FAST>;         \
+    if (mode == MODE_MSV_DIRECT) return scan_kernel<MPF_LG, W, MODE_MSV_DIRECT>;     \
+    if (mode == MODE_SSV_F16) return scan_kernel<MPF_LG, W, MODE_SSV_F16>;           \
+    if (mode == MODE_MSV_FAST_F16) return scan_kernel<MPF_LG, W, MODE_MSV_FAST_F16>; \
+    return nullptr;
+
+KernelFn MPF_CAT(kernel_lg, MPF_LG)(int words, int mode) {
+  switch (words) {
+    MPF_WORDS_CASE(4)
+    MPF_WORDS_CASE(6)
+    MPF_WORDS_CASE(8)
+    MPF_WORDS_CASE(10)
+    MPF_WORDS_CASE(12)
+    MPF_WORDS_CASE(14)
+    MPF_WORDS_CASE(16)
+    MPF_WORDS_CASE(18)
+    MPF_WORDS_CASE(20)
+    MPF_WORDS_CASE(22)
+    MPF_WORDS_CASE(24)
+    MPF_WORDS_CASE(26)
+    MPF_WORDS_CASE(28)
+    MPF_WORDS_CASE(30)
+    MPF_WORDS_CASE(32)
+    MPF_WORDS_CASE(34)
+    MPF_WORDS_CASE(36)
+    MPF_WORDS_CASE(38)
+    MPF_WORDS_CASE(40)
+    MPF_WORDS_CASE(42)
+    MPF_WORDS_CASE(44)
+    MPF_WORDS_CASE(46)
+    MPF_WORDS_CASE(48)
+    default:
+      return nullptr;
+  }
+}
+
+}  // namespace mpf

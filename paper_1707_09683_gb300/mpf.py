@@ -77,6 +77,7 @@ def load(path: str = LIB_PATH):
         "mpf_plan_kernel_launches": (i32, [vp]),
         "mpf_plan_destroy": (None, [vp]),
         "mpf_scan_noalloc": (i32, [vp, i32, vp, vp, vp, vp, vp]),
+        "mpf_profile_footprint": (i32, [vp, i32, vp, vp]),
         "mpf_pipeline_scan": (i32, [vp, vp, i32, vp, ctypes.c_float, vp, vp, vp, vp, vp, vp, vp]),
         "mpf_pvalues": (i32, [vp, vp, u64, ctypes.c_float, ctypes.c_float, vp]),
         "mpf_debug_check_selftest": (i32, [vp]),
@@ -238,6 +239,14 @@ class Profile:
         _check(load().mpf_profile_get_config(self.handle, int(filter), ctypes.byref(a),
                                              ctypes.byref(b)), "mpf_profile_get_config")
         return a.value, b.value
+
+    def footprint(self, filter: int):
+        """(shared memory per block, device bytes of the score tables) of
+        this profile's scans with one filter (``mpf_profile_footprint``)."""
+        sm, tb = ctypes.c_uint32(), ctypes.c_uint64()
+        _check(load().mpf_profile_footprint(self.handle, int(filter), ctypes.byref(sm), ctypes.byref(tb)),
+               "mpf_profile_footprint")
+        return sm.value, tb.value
 
     def close(self):
         if getattr(self, "handle", None):
