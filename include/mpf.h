@@ -163,11 +163,43 @@ int mpf_profile_footprint(const mpf_profile *prof, int filter, uint32_t *smem_by
  * results (the recurrences stay exact): MPF_ARITH_I16 updates two 16-bit
  * integer cells per DPX instruction on the integer pipe, MPF_ARITH_F16 holds
  * the same integers as half-precision values and updates them with a fused
- * add-and-clamp on the FMA pipe.  MPF_ARITH_AUTO (default) picks per filter.
+ * add-and-clamp on the FMA pipe.  MPF_ARITH_AUTO (default) is MPF_ARITH_I16:
+ * no floating point in the cell updates.
  * Errors: MPF_EINVAL.
  */
 enum { MPF_ARITH_AUTO = 0, MPF_ARITH_I16 = 1, MPF_ARITH_F16 = 2 };
 int mpf_profile_set_arith(mpf_profile *prof, int filter, int arith);
+
+/*
+ * Where a striped scan reads its score table (not in the paper, whose Alg. 4
+ * reads it through the read-only cache).  Every kernel stages the table in
+ * shared memory; with one sequence per warp (lanes 32, words >= 8) the
+ * automatic choice also copies the first words of each lane's row (all of
+ * them up to 14 words per lane, else 12) into the SM's tensor memory (TMEM,
+ * read by tcgen05.ld at about three times the shared-memory rate) and reads
+ * those words from there.  Results are identical either way.
+ *   set: MPF_TABLE_AUTO (default) or MPF_TABLE_SHARED (shared memory only).
+ *   get: MPF_TABLE_TENSOR or MPF_TABLE_SHARED, for the configuration the
+ *        next scan will use.
+ * Errors: MPF_EINVAL.
+ */
+enum { MPF_TABLE_AUTO = 0, MPF_TABLE_SHARED = 1, MPF_TABLE_TENSOR = 2 };
+
+/*
+ * Work decomposition of a profile's striped scans with one filter (replaces
+ * the static thread-block assignment of Sec. 3.1 and the warp data blocks of
+ * Alg. 1): the database's length ranks are dealt round-robin into
+ * factor x (resident blocks) shards, and blocks pull (query, shard) work
+ * items.  More shards make smaller items, so blocks finish closer together,
+ * at the cost of staging the table once per item.  1 <= factor <= 16
+ * (default 1); a launch takes the largest factor of its queries; long models
+ * ignore it.  Results do not depend on it.
+ * Errors: MPF_EINVAL.
+ */
+int mpf_profile_set_shard_factor(mpf_profile *prof, int filter, int factor);
+int mpf_profile_get_shard_factor(const mpf_profile *prof, int filter, int *factor);
+int mpf_profile_set_table_memory(mpf_profile *prof, int filter, int where);
+int mpf_profile_get_table_memory(const mpf_profile *prof, int filter, int *where);
 
 /*
  * Upload a database of digital sequences (host pointers).

@@ -1,7 +1,8 @@
 """Build libmpf.so (the CUDA scan library) in-tree for sm_103a.
 
 Each ``csrc/*.cu`` translation unit is compiled by nvcc in parallel (the
-scan-kernel instantiations, ``mpf_inst.cu``, once per lane-group size) and
+scan-kernel instantiations, ``mpf_inst.cu``, once per lane-group size and
+once more for the tensor-memory variants) and
 the objects are linked into ``paper_1707_09683_gb300/libmpf.so``.  Objects are
 rebuilt only when a source or header is newer.  No CMake, no torch
 extension machinery: plain nvcc, one ``-gencode``.
@@ -60,6 +61,7 @@ def _units():
         base = os.path.basename(src)
         if base == INST_SRC:
             units += [(src, f"mpf_inst_lg{lg}.o", [f"-DMPF_LG={lg}"]) for lg in INST_LANES]
+            units.append((src, "mpf_inst_lg32_tm.o", ["-DMPF_LG=32", "-DMPF_TM=1"]))
         else:
             units.append((src, base.replace(".cu", ".o"), []))
     # The largest units first, so the parallel build ends sooner.

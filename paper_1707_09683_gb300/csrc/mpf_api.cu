@@ -267,14 +267,23 @@ int ensure_out_scratch(mpf_ctx *ctx, size_t bytes) {
   return MPF_OK;
 }
 
-// Kernel mode of a profile for a filter.  Automatic arithmetic: fp16 cells
-// (FMA pipe) for both filters.
+// Kernel mode of a profile for a filter.  Automatic arithmetic: 16-bit
+// integer cells (DPX on the integer pipe); fp16 cells only when asked for.
 int kernel_mode(const mpf_profile *p, int filter) {
   if (p->seg_words) return filter == MPF_SSV ? MODE_TILE_SSV : msv_fast_ok(p) ? MODE_TILE_MSV : MODE_LONG_MSV;
-  const bool f16 = p->arith[filter] != MPF_ARITH_I16;
+  const bool f16 = p->arith[filter] == MPF_ARITH_F16;
   if (filter == MPF_SSV) return f16 ? MODE_SSV_F16 : MODE_SSV;
   if (!msv_fast_ok(p)) return MODE_MSV_DIRECT;
   return f16 ? MODE_MSV_FAST_F16 : MODE_MSV_FAST;
+}
+
+// Whether a striped scan of this profile reads its table from tensor memory:
+// one sequence per warp, enough words per lane, a mode with a TMEM kernel,
+// and the profile's choice (automatic: yes).
+bool use_tmem(const mpf_profile *p, int filter, int lanes, int words, int mode) {
+  if (p->table_mem[filter] == MPF_TABLE_SHARED) return false;
+  return lanes == 32 && words >= kTmMinWords && mode != MODE_MSV_DIRECT &&
+         kernel_lg32_tm(words, mode) != nullptr;
 }
 
 }  // namespace host
@@ -298,6 +307,8 @@ struct LaunchGroup {
   uint32_t col_stride = 0;
   uint64_t col_bytes = 0;
   uint32_t *d_fallback = nullptr;   // tiled MSV: per query a count, then n_seqs ranks per query
+  bool tm = false;                  // striped kernel with the table in tensor memory
+  int shard_factor = 1;             // striped kernels: shards = factor x resident blocks
   std::shared_ptr<LaunchGroup> next;   // launched after this group on the same stream
 };
 
@@ -405,17 +416,21 @@ int configure_kernel(mpf_ctx *ctx, LaunchGroup *g) {
     g->n_shards = (uint32_t)g->grid;
     return MPF_OK;
   }
-  g->fn = kernel_for(g->lanes, g->words, g->mode);
+  g->fn = g->tm ? kernel_lg32_tm(g->words, g->mode) : kernel_for(g->lanes, g->words, g->mode);
   if (!g->fn) return MPF_EINVAL;
   g->smem = (uint32_t)smem_need(g->lanes, g->words);
+  // A block with the table in tensor memory takes all of the SM's TMEM
+  // columns: ask for more than half the shared memory, so no second block of
+  // the kernel is placed on the SM.
+  if (g->tm) g->smem = std::max<uint32_t>(g->smem, (uint32_t)ctx->max_smem / 2 + 1024);
   MPF_CUDA(cudaFuncSetAttribute((const void *)g->fn, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                 (int)g->smem));
   int per_sm = 0;
   MPF_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, (const void *)g->fn,
                                                          kBlockThreads, g->smem));
-  if (per_sm < 1) return MPF_EUNSUPPORTED;
+  if (per_sm < 1 || (g->tm && per_sm != 1)) return MPF_EUNSUPPORTED;
   g->grid = ctx->num_sms * per_sm;
-  g->n_shards = (uint32_t)g->grid;
+  g->n_shards = (uint32_t)g->grid * (uint32_t)std::max(1, g->shard_factor);
   return MPF_OK;
 }
 
@@ -432,9 +447,12 @@ int plan_create(mpf_ctx *ctx, int filter, const mpf_profile *const *profs, int n
   if (!pl) return MPF_ENOMEM;
   pl->ctx = ctx;
   pl->db = db;
-  std::map<std::tuple<int, int, int>, std::vector<QueryDesc>> byconf;
-  std::map<std::tuple<int, int, int>, std::vector<const uint8_t *>> fb_table;   // tiled MSV: long tables
-  std::map<std::tuple<int, int, int>, std::vector<uint32_t>> fb_seg_words;
+  // Launch groups by (lanes, words, mode, table in tensor memory).
+  using GroupKey = std::tuple<int, int, int, int>;
+  std::map<GroupKey, std::vector<QueryDesc>> byconf;
+  std::map<GroupKey, std::vector<const uint8_t *>> fb_table;   // tiled MSV: long tables
+  std::map<GroupKey, std::vector<uint32_t>> fb_seg_words;
+  std::map<GroupKey, int> group_shards;   // largest shard factor of a group's profiles
   for (int i = 0; i < n_q; ++i) {
     const mpf_profile *p = profs[i];
     if (!p || p->ctx->device != ctx->device) {
@@ -462,8 +480,8 @@ int plan_create(mpf_ctx *ctx, int filter, const mpf_profile *const *profs, int n
           plan_free(pl);
           return rc;
         }
-        fb_table[std::make_tuple(lanes, words, mode)].push_back(lt);
-        fb_seg_words[std::make_tuple(lanes, words, mode)].push_back((uint32_t)p->seg_words);
+        fb_table[GroupKey(lanes, words, mode, 0)].push_back(lt);
+        fb_seg_words[GroupKey(lanes, words, mode, 0)].push_back((uint32_t)p->seg_words);
       }
     } else if (p->seg_words) {
       const uint8_t *lt = nullptr;
@@ -512,7 +530,10 @@ int plan_create(mpf_ctx *ctx, int filter, const mpf_profile *const *profs, int n
     q.nat = nat ? nat + off : nullptr;
     q.ranks = ranks ? ranks + off : nullptr;
     q.n_ranks = ranks ? n_ranks + i : nullptr;
-    byconf[std::make_tuple(lanes, words, mode)].push_back(q);
+    const int tm = p->seg_words ? 0 : (use_tmem(p, filter, lanes, words, mode) ? 1 : 0);
+    byconf[GroupKey(lanes, words, mode, tm)].push_back(q);
+    int &sf = group_shards[GroupKey(lanes, words, mode, tm)];
+    sf = std::max(sf, p->seg_words ? 1 : p->shard_factor[filter]);
   }
   DeviceGuard dg(ctx->device);
   for (auto &kv : byconf) {
@@ -520,6 +541,8 @@ int plan_create(mpf_ctx *ctx, int filter, const mpf_profile *const *profs, int n
     g.lanes = std::get<0>(kv.first);
     g.words = std::get<1>(kv.first);
     g.mode = std::get<2>(kv.first);
+    g.tm = std::get<3>(kv.first) != 0;
+    g.shard_factor = group_shards[kv.first];
     for (const QueryDesc &qd : kv.second) g.long_words = std::max(g.long_words, qd.seg_words);
     g.n_codes = db->n_codes;
     int rc = configure_kernel(ctx, &g);
@@ -886,6 +909,38 @@ int mpf_profile_set_arith(mpf_profile *p, int filter, int arith) {
   // falls back to the default configuration.
   if (p->cfg_lanes[filter] && !kernel_for(p->cfg_lanes[filter], p->cfg_words[filter], kernel_mode(p, filter)))
     p->cfg_lanes[filter] = p->cfg_words[filter] = 0;
+  return MPF_OK;
+}
+
+int mpf_profile_set_shard_factor(mpf_profile *p, int filter, int factor) {
+  if (!p || (filter != MPF_MSV && filter != MPF_SSV) || factor < 1 || factor > 16) return MPF_EINVAL;
+  p->shard_factor[filter] = factor;
+  return MPF_OK;
+}
+
+int mpf_profile_get_shard_factor(const mpf_profile *p, int filter, int *factor) {
+  if (!p || !factor || (filter != MPF_MSV && filter != MPF_SSV)) return MPF_EINVAL;
+  *factor = p->seg_words ? 1 : p->shard_factor[filter];
+  return MPF_OK;
+}
+
+int mpf_profile_set_table_memory(mpf_profile *p, int filter, int where) {
+  if (!p || (filter != MPF_MSV && filter != MPF_SSV)) return MPF_EINVAL;
+  if (where != MPF_TABLE_AUTO && where != MPF_TABLE_SHARED) return MPF_EINVAL;
+  p->table_mem[filter] = where;
+  return MPF_OK;
+}
+
+int mpf_profile_get_table_memory(const mpf_profile *p, int filter, int *where) {
+  if (!p || !where || (filter != MPF_MSV && filter != MPF_SSV)) return MPF_EINVAL;
+  if (p->seg_words) {
+    *where = MPF_TABLE_SHARED;
+    return MPF_OK;
+  }
+  int lanes = p->cfg_lanes[filter], words = p->cfg_words[filter];
+  const int mode = kernel_mode(p, filter);
+  if (!lanes) default_config(p->ctx, p->M, mode, &lanes, &words);
+  *where = use_tmem(p, filter, lanes, words, mode) ? MPF_TABLE_TENSOR : MPF_TABLE_SHARED;
   return MPF_OK;
 }
 

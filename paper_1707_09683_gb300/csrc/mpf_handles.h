@@ -53,7 +53,9 @@ struct mpf_profile {
   uint32_t n_tjb = 0;
   int tjb_min = 0;
   int cfg_lanes[2] = {0, 0}, cfg_words[2] = {0, 0};
+  int shard_factor[2] = {1, 1};   // striped kernels: work items per query = factor x resident blocks
   int arith[2] = {MPF_ARITH_AUTO, MPF_ARITH_AUTO};
+  int table_mem[2] = {MPF_TABLE_AUTO, MPF_TABLE_AUTO};
   int seg_words = 0;            // > 0: longer than the striped kernels hold (long-model kernel)
   mutable std::map<std::tuple<int, int, int>, DevTable> tables;
   mutable std::mutex mu;
@@ -131,6 +133,8 @@ inline int status_code(int st) {
 void default_config(const mpf_ctx *ctx, int M, int mode, int *lanes, int *words);
 // Kernel mode of a profile for a filter (arithmetic, MSV variant, long model).
 int kernel_mode(const mpf_profile *p, int filter);
+// Whether a striped scan in this configuration reads its table from TMEM.
+bool use_tmem(const mpf_profile *p, int filter, int lanes, int words, int mode);
 // Striped shared-memory image of a profile's score table.
 void fill_table_image(const mpf_profile *p, const TableGeom &g, int fmt, uint8_t *img);
 // Grow the context's device scratch for host-pointer outputs.

@@ -52,6 +52,19 @@ enum Mode : int {
 };
 constexpr int kNumModes = 5;   // modes of the striped scan kernel
 
+// Striped kernels that read their table from tensor memory (one sequence per
+// warp): the first tm_words(words) words of each lane's row of every residue
+// code (all 33 rows: 33 x 14 = 462 of the 512 columns) come from TMEM, the
+// rest from shared memory.
+constexpr uint32_t kTmemColumns = 512;   // 32-bit columns of an SM's tensor memory
+constexpr int kTmWordsAll = 14;     // lanes of up to this many words: all of them in TMEM
+constexpr int kTmWordsPart = 12;    // longer lanes: this many in TMEM (a whole number of chunks)
+constexpr int kTmMinWords = 8;      // fewer words per lane: the shared-memory kernels
+// Words per lane read from TMEM for a lane of `words` words.  Twelve words
+// take the shared-memory reads of a 48-word lane to 3/4 of the table, below
+// the rate at which the integer pipe can use them.
+__host__ __device__ constexpr int tm_words(int words) { return words <= kTmWordsAll ? words : kTmWordsPart; }
+
 // Score-table formats: signed 16-bit integers, or the same integers as fp16.
 enum TableFormat : int { TABLE_I16 = 0, TABLE_F16 = 1 };
 inline int table_format(int mode) {
@@ -211,6 +224,8 @@ int viterbi_shape_key(bool fast, int Mpad, int n_codes, int max_smem, int num_sm
 
 // Kernel instantiation for (lanes, words, mode), or nullptr if not built.
 KernelFn kernel_for(int lanes, int words, int mode);
+// The tensor-memory variant (lanes = 32), or nullptr if not built.
+KernelFn kernel_lg32_tm(int words, int mode);
 KernelFn kernel_lg1(int words, int mode);
 KernelFn kernel_lg2(int words, int mode);
 KernelFn kernel_lg4(int words, int mode);

@@ -43,6 +43,16 @@
 // which half precision represents exactly; later values only need to stay
 // above the threshold, and rounding is monotone.  Running maxima compare the
 // half bit patterns of non-negative values as unsigned integers.
+//
+// Tensor-memory variant (TM, one sequence per warp, LG = 32).  The table is
+// staged in shared memory as usual; then the first HT words of each lane's
+// row (all H up to 14 words, else 12) of all 33 residue rows are copied into
+// the block's tensor memory (thread t of warp w owns TMEM lane 32 (w mod 4) +
+// t: its row of code x is columns x * HT .. x * HT + HT - 1).  The TMEM loads
+// of a row are issued while the previous row is computed; the row then
+// updates its words past HT from shared memory and its first HT words from
+// the loaded registers.  Every row takes the same path, so the kernel has no
+// per-row branch on the table source.  The cell arithmetic is unchanged.
 #pragma once
 #include <cuda_fp16.h>
 #include <cuda_runtime.h>
@@ -52,6 +62,7 @@
 #include <type_traits>
 
 #include "mpf_internal.h"
+#include "mpf_tmem.cuh"
 
 namespace mpf {
 
@@ -106,9 +117,12 @@ __device__ __forceinline__ uint32_t pack2_half(int v) {
   return (h << 16) | h;
 }
 
-template <int LG, int H, int MODE>
+template <int LG, int H, int MODE, bool TM = false>
 __global__ void __launch_bounds__(kBlockThreads, 1) scan_kernel(ScanParams p) {
   static_assert((H % 4 == 0 || H % 4 == 2) && H >= 4 && H <= kMaxWords, "words per lane");
+  static_assert(!TM || (LG == 32 && H >= kTmMinWords && MODE != MODE_MSV_DIRECT), "tensor-memory variant");
+  constexpr int HT = TM ? tm_words(H) : 0;   // words per lane from TMEM
+  static_assert(HT == H || HT % 4 == 0, "shared-memory words start on a chunk");
   constexpr int Q = H / 4;               // full 4-word chunks per lane and row
   constexpr bool kTail = (H % 4) == 2;   // two more words from the tail region
   constexpr int NT = LG >= 16 ? 1 : 16 / LG;
@@ -122,11 +136,21 @@ __global__ void __launch_bounds__(kBlockThreads, 1) scan_kernel(ScanParams p) {
   const uint32_t one2 = 0x3c003c00u;   // (1.0, 1.0) as half2
   extern __shared__ __align__(16) uint8_t smem[];
   __shared__ uint32_t s_item, s_next;
+  __shared__ uint32_t s_tmem;
 
   const int lane = threadIdx.x & 31;
   const int gl = lane & (LG - 1);
   const int grp = lane / LG;
   const uint32_t n_items = p.n_queries * p.n_shards;
+  const int warp = (int)(threadIdx.x >> 5);
+  uint32_t tm_lane = 0;   // TMEM address of this warp's lane quarter, column 0
+  if constexpr (TM) {
+    if (warp == 0) tm_alloc(&s_tmem);
+    tm_fence_before();
+    __syncthreads();
+    tm_fence_after();
+    tm_lane = s_tmem + ((uint32_t)((warp & 3) * 32) << 16);
+  }
 
   for (;;) {
     if (threadIdx.x == 0) {
@@ -153,6 +177,31 @@ __global__ void __launch_bounds__(kBlockThreads, 1) scan_kernel(ScanParams p) {
       for (uint32_t i = threadIdx.x; i < nvec; i += blockDim.x) dst[i] = __ldg(src + i);
     }
     __syncthreads();
+    if constexpr (TM) {
+      // Copy the first HT words of every lane's row of the TMEM codes from the
+      // staged table into tensor memory: warp q < 4 writes lane quarter q.
+      tm_fence_after();
+      if (warp < 4) {
+        const uint8_t *lane_tbl = smem + lane * 16;
+        const uint8_t *lane_tail = smem + qd->tail_off + lane * 8;
+        for (uint32_t x = 0; x < (uint32_t)kTableRows; ++x) {
+          const uint32_t col = tm_lane + x * (uint32_t)HT;
+#pragma unroll
+          for (int j = 0; j < HT / 4; ++j) {
+            const uint4 s4 = *reinterpret_cast<const uint4 *>(lane_tbl + x * qd->row_bytes + j * 32 * 16);
+            tm_st4(col + 4 * j, s4.x, s4.y, s4.z, s4.w);
+          }
+          if constexpr (HT % 4 == 2) {   // HT == H: the two tail words
+            const uint2 t2 = *reinterpret_cast<const uint2 *>(lane_tail + x * qd->tail_row_bytes);
+            tm_st2(col + 4 * (HT / 4), t2.x, t2.y);
+          }
+        }
+        tm_wait_st();
+      }
+      tm_fence_before();
+      __syncthreads();
+      tm_fence_after();
+    }
 
     const int bias = qd->bias, tbm = qd->tbm, tec = qd->tec, base = qd->base;
     const int cap = 255 - bias;
@@ -207,6 +256,10 @@ __global__ void __launch_bounds__(kBlockThreads, 1) scan_kernel(ScanParams p) {
       const int Tk = value_key<kF16>(max(T, 0));          // threshold as a key
       const int Tnear = T - 4 * max(bias, 0);              // no trigger possible in 4 rows below it
       const int Tnear_k = value_key<kF16>(max(Tnear, 0));
+      // "Some half of the running maximum is above the key K" as one add and
+      // one mask: the halves (keys <= 0x7fff) plus 0x7fff - K reach bit 15
+      // exactly when they exceed K, and no sum carries into the other half.
+      const uint32_t Tk2 = pack2(0x7fff - Tk), Tnear2 = pack2(0x7fff - Tnear_k);
       bool done = false, exact = false;
 
       // Lane state: H words of two 16-bit cells and a running maximum (key).
@@ -216,17 +269,35 @@ __global__ void __launch_bounds__(kBlockThreads, 1) scan_kernel(ScanParams p) {
       uint32_t vacc = 0u;
       uint32_t cur = __ldg(p.residues + (nsteps > 0 ? wptr : p.pad_word));
 
-      // Four rows of one residue word.  CHECK: test every row for the MSV
-      // threshold (only needed when some lane is near it, or in exact mode).
-      auto four_rows = [&](const int step, auto check_tag) {
+      // Tensor-memory words of the current and the next row: the loads of
+      // row i + 1 are issued while row i is computed.  Every residue code,
+      // the padding code included, has a TMEM row (code x: columns x * HT ..).
+      uint32_t TA[TM ? HT : 1], TB[TM ? HT : 1];
+      auto tm_col = [&](uint32_t xc) -> uint32_t {
+        if (!MPF_DCHECK(p.status, xc < (uint32_t)kTableRows)) xc = kPadCode;
+        return tm_lane + xc * (uint32_t)HT;
+      };
+      if constexpr (TM) tm_ld<HT>(TA, tm_col(cur & 0xffu));   // first row of the sequence
+
+      // Four rows of one residue word (nxt: the next word).  CHECK: test every
+      // row for the MSV threshold (only needed when some lane is near it, or
+      // in exact mode).
+      auto four_rows = [&](const int step, auto check_tag, const uint32_t nxt) {
         constexpr bool CHECK = decltype(check_tag)::value;
 #pragma unroll
         for (int rr = 0; rr < 4; ++rr) {
+         auto one_row = [&](auto &Tc, auto &Tn) {
           // Rows past the end of a sequence read padding codes: their cells
           // score kNegInf, and the special states must not see them.
           const bool real = active && (4 * step + rr) < len;
           uint32_t x = (cur >> (8 * rr)) & 0xffu;
           if (!MPF_DCHECK(p.status, x < (uint32_t)kTableRows)) x = kPadCode;
+          if constexpr (TM) {
+            // This row's TMEM words (issued one row earlier), then the next
+            // row's loads: a wait covers every earlier load of the thread.
+            tm_wait_ld<HT>(Tc);
+            tm_ld<HT>(Tn, tm_col(rr < 3 ? (cur >> (8 * (rr + 1))) & 0xffu : nxt & 0xffu));
+          }
           const uint8_t *rowp = tbl_lane + x * row_bytes;
           // Diagonal shift (Alg. 5): cell k-1 of the previous row feeds cell k.
           const uint32_t wl = v[H - 1];
@@ -237,47 +308,53 @@ __global__ void __launch_bounds__(kBlockThreads, 1) scan_kernel(ScanParams p) {
           }
           const uint32_t mpv = __byte_perm(up, wl, 0x5432);
           uint32_t rmax = 0u;
-          if (kTail) {   // words 4Q+1 and 4Q (highest first: in-place update)
-            const uint2 t2 = *reinterpret_cast<const uint2 *>(tail_lane + x * tail_row_bytes);
-            const uint32_t tsc[2] = {t2.x, t2.y};
-#pragma unroll
-            for (int i = 1; i >= 0; --i) {
-              const int q = 4 * Q + i;
-              const uint32_t prev = (q == 0) ? mpv : v[q - 1];
-              if (kF16)
-                v[q] = hfma2_relu_u32(prev, one2, tsc[i]);
-              else if (kDirect)
-                v[q] = __viaddmax_s16x2(__vimax_s16x2_relu(prev, b2), tsc[i], 0u);
-              else
-                v[q] = __viaddmax_s16x2(prev, tsc[i], 0u);
-            }
-            if (kDirect)
-              rmax = __vimax3_u16x2(rmax, v[4 * Q + 1], v[4 * Q]);
+          // Update word q from the previous row's word q - 1 and score word sc.
+          auto cell = [&](const int q, const uint32_t sc) {
+            const uint32_t prev = (q == 0) ? mpv : v[q - 1];
+            if (kF16)
+              v[q] = hfma2_relu_u32(prev, one2, sc);
+            else if (kDirect)
+              v[q] = __viaddmax_s16x2(__vimax_s16x2_relu(prev, b2), sc, 0u);
             else
-              vacc = __vimax3_u16x2(vacc, v[4 * Q + 1], v[4 * Q]);
-          }
-#pragma unroll
-          for (int j = Q - 1; j >= 0; --j) {
-            const uint4 s4 = *reinterpret_cast<const uint4 *>(rowp + j * LG * 16);
-            const uint32_t sc[4] = {s4.x, s4.y, s4.z, s4.w};
-#pragma unroll
-            for (int i = 3; i >= 0; --i) {
-              const int q = 4 * j + i;
-              const uint32_t prev = (q == 0) ? mpv : v[q - 1];
-              if (kF16)
-                v[q] = hfma2_relu_u32(prev, one2, sc[i]);
-              else if (kDirect)
-                v[q] = __viaddmax_s16x2(__vimax_s16x2_relu(prev, b2), sc[i], 0u);
-              else
-                v[q] = __viaddmax_s16x2(prev, sc[i], 0u);
+              v[q] = __viaddmax_s16x2(prev, sc, 0u);
+          };
+          // Fold words q + 1 and q into the row / running maximum.
+          auto fold = [&](const int q) {
+            if (kDirect)
+              rmax = __vimax3_u16x2(rmax, v[q + 1], v[q]);
+            else
+              vacc = __vimax3_u16x2(vacc, v[q + 1], v[q]);
+          };
+          // Words from shared memory, highest first (in-place update): the
+          // two-word tail, then the 4-word chunks down to chunk j_lo.
+          auto smem_words = [&](const int j_lo) {
+            if (kTail) {   // words 4Q+1 and 4Q
+              const uint2 t2 = *reinterpret_cast<const uint2 *>(tail_lane + x * tail_row_bytes);
+              cell(4 * Q + 1, t2.y);
+              cell(4 * Q, t2.x);
+              fold(4 * Q);
             }
-            if (kDirect) {
-              rmax = __vimax3_u16x2(rmax, v[4 * j + 3], v[4 * j + 2]);
-              rmax = __vimax3_u16x2(rmax, v[4 * j + 1], v[4 * j]);
-            } else {
-              vacc = __vimax3_u16x2(vacc, v[4 * j + 3], v[4 * j + 2]);
-              vacc = __vimax3_u16x2(vacc, v[4 * j + 1], v[4 * j]);
+#pragma unroll
+            for (int j = Q - 1; j >= j_lo; --j) {
+              const uint4 s4 = *reinterpret_cast<const uint4 *>(rowp + j * LG * 16);
+              cell(4 * j + 3, s4.w);
+              cell(4 * j + 2, s4.z);
+              cell(4 * j + 1, s4.y);
+              cell(4 * j, s4.x);
+              fold(4 * j + 2);
+              fold(4 * j);
             }
+          };
+          if constexpr (TM) {
+            if constexpr (HT < H) smem_words(HT / 4);
+#pragma unroll
+            for (int q = HT - 1; q >= 1; q -= 2) {
+              cell(q, Tc[q]);
+              cell(q - 1, Tc[q - 1]);
+              fold(q - 1);
+            }
+          } else {
+            smem_words(0);
           }
           if (kDirect) {
             // xE of this row (Alg. 6), then the J and B special states.
@@ -292,7 +369,7 @@ __global__ void __launch_bounds__(kBlockThreads, 1) scan_kernel(ScanParams p) {
               }
             }
           } else if (kFast && CHECK) {
-            const bool trig = real && !done && (exact || half_max(vacc) > Tk);
+            const bool trig = real && !done && (exact || ((vacc + Tk2) & 0x80008000u) != 0u);
             if (__any_sync(kFull, trig)) {
               const int mm = key_value<kF16>(group_max<LG>(half_max(vacc)));
               if (real && !done && (exact || mm > T)) {
@@ -315,6 +392,11 @@ __global__ void __launch_bounds__(kBlockThreads, 1) scan_kernel(ScanParams p) {
               if (exact) vacc = 0u;
             }
           }
+         };
+          if (rr & 1)
+            one_row(TB, TA);
+          else
+            one_row(TA, TB);
         }
       };
 
@@ -322,16 +404,18 @@ __global__ void __launch_bounds__(kBlockThreads, 1) scan_kernel(ScanParams p) {
         // Prefetch the next residue word; past the end a group reads padding.
         const uint32_t nxt = __ldg(p.residues + (step + 1 < nsteps ? wptr + (uint32_t)step + 1u : p.pad_word));
         if (kFast) {
-          const bool near = active && !done && (exact || Tnear < 0 || half_max(vacc) > Tnear_k);
+          const bool near = active && !done && (exact || Tnear < 0 || ((vacc + Tnear2) & 0x80008000u) != 0u);
           if (__any_sync(kFull, near))
-            four_rows(step, std::true_type{});
+            four_rows(step, std::true_type{}, nxt);
           else
-            four_rows(step, std::false_type{});
+            four_rows(step, std::false_type{}, nxt);
         } else {
-          four_rows(step, std::false_type{});
+          four_rows(step, std::false_type{}, nxt);
         }
         cur = nxt;
       }
+
+      if constexpr (TM) tm_wait_ld<HT>(TA);   // the load issued after the last row
 
       // ---- finalise the G sequences -------------------------------------
       const int V = key_value<kF16>(group_max<LG>(half_max(vacc)));
@@ -383,7 +467,14 @@ __global__ void __launch_bounds__(kBlockThreads, 1) scan_kernel(ScanParams p) {
         }
       }
     }
+    if constexpr (TM) tm_fence_before();   // this item's TMEM reads before the next item's writes
     __syncthreads();
+  }
+  if constexpr (TM) {
+    if (warp == 0) {
+      tm_fence_after();
+      tm_dealloc(s_tmem);
+    }
   }
 }
 

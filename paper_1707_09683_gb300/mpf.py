@@ -23,6 +23,7 @@ DEBUG_LIB_PATH = os.path.join(_HERE, "libmpf_debug.so")
 MPF_OK, MPF_EINVAL, MPF_ENOMEM, MPF_ECUDA, MPF_ETIMEOUT, MPF_EUNSUPPORTED, MPF_EDEVICE = range(7)
 MSV, SSV = 0, 1
 ARITH_AUTO, ARITH_I16, ARITH_F16 = 0, 1, 2
+TABLE_AUTO, TABLE_SHARED, TABLE_TENSOR = 0, 1, 2
 
 
 class MpfLibraryMissing(RuntimeError):
@@ -78,6 +79,10 @@ def load(path: str = LIB_PATH):
         "mpf_plan_destroy": (None, [vp]),
         "mpf_scan_noalloc": (i32, [vp, i32, vp, vp, vp, vp, vp]),
         "mpf_profile_footprint": (i32, [vp, i32, vp, vp]),
+        "mpf_profile_set_table_memory": (i32, [vp, i32, i32]),
+        "mpf_profile_set_shard_factor": (i32, [vp, i32, i32]),
+        "mpf_profile_get_shard_factor": (i32, [vp, i32, vp]),
+        "mpf_profile_get_table_memory": (i32, [vp, i32, vp]),
         "mpf_pipeline_scan": (i32, [vp, vp, i32, vp, ctypes.c_float, vp, vp, vp, vp, vp, vp, vp]),
         "mpf_pvalues": (i32, [vp, vp, u64, ctypes.c_float, ctypes.c_float, vp]),
         "mpf_debug_check_selftest": (i32, [vp]),
@@ -233,6 +238,26 @@ class Profile:
     def set_arith(self, filter: int, arith: int):
         _check(load().mpf_profile_set_arith(self.handle, int(filter), int(arith)),
                "mpf_profile_set_arith")
+
+    def set_shard_factor(self, filter: int, factor: int):
+        _check(load().mpf_profile_set_shard_factor(self.handle, int(filter), int(factor)),
+               "mpf_profile_set_shard_factor")
+
+    def get_shard_factor(self, filter: int) -> int:
+        w = ctypes.c_int()
+        _check(load().mpf_profile_get_shard_factor(self.handle, int(filter), ctypes.byref(w)),
+               "mpf_profile_get_shard_factor")
+        return w.value
+
+    def set_table_memory(self, filter: int, where: int):
+        _check(load().mpf_profile_set_table_memory(self.handle, int(filter), int(where)),
+               "mpf_profile_set_table_memory")
+
+    def get_table_memory(self, filter: int) -> int:
+        w = ctypes.c_int()
+        _check(load().mpf_profile_get_table_memory(self.handle, int(filter), ctypes.byref(w)),
+               "mpf_profile_get_table_memory")
+        return w.value
 
     def get_config(self, filter: int):
         a, b = ctypes.c_int(), ctypes.c_int()

@@ -147,6 +147,51 @@ def test_both_cell_arithmetics(ctx, arith):
         check_profile(ctx, synth.make_profile(M, rng), long_db, lddb, arith=arith)
 
 
+@pytest.mark.parametrize("arith", [mpf.ARITH_I16, mpf.ARITH_F16])
+def test_tensor_memory_table(ctx, arith):
+    """One-sequence-per-warp kernels with the score rows in tensor memory
+    equal the shared-memory kernels and the oracle at every word count: all
+    words in TMEM (8-24 words per lane, with and without a two-word tail) or
+    24 in TMEM and the rest in shared memory (26-48); on a database of the 20
+    amino-acid codes (every row in TMEM) and one of all 32 codes (with 24 TMEM
+    words only 21 codes get a TMEM row: the rest read shared memory);
+    adversarial bytes, realistic profiles, strong profiles with J chaining
+    and overflow."""
+    rng = np.random.default_rng(1300 + arith)
+    db20 = synth.make_database(500, 300, 1, 3000, rng)
+    db32 = synth.random_database(400, 700, rng, alphabet=32)
+    strong_db = synth.random_database(200, 900, rng, alphabet=20, min_len=1)
+    dbs = [(db, mpf.Database(ctx, db.residues, db.offsets, db.lengths)) for db in (db20, db32, strong_db)]
+    for words in (8, 10, 14, 22, 24, 26, 30, 38, 48):
+        M = 64 * words - int(rng.integers(0, 64))
+        profiles = [
+            (synth.make_profile(M, rng), dbs[:2]),
+            (synth.random_profile(M, int(rng.integers(1, 33)), rng, cost_hi=255,
+                                  bias=int(rng.choice([0, 20, 130, 255])),
+                                  base=int(rng.choice([120, 190, 250])), with_lut=True), dbs[1:2]),
+            (synth.random_profile(M, 20, rng, cost_hi=26, bias=20, base=190, tbm=10, tec=3, tjb=8),
+             dbs[2:]),
+        ]
+        for p, targets in profiles:
+            prof = mpf.Profile(ctx, p)
+            for gf, of in FILTERS:
+                prof.set_arith(gf, arith)
+                prof.set_config(gf, 32, words)
+            for db, ddb in targets:
+                for gf, of in FILTERS:
+                    exp = oracle.scan(of, p, db.residues, db.offsets, db.lengths, nthreads=8)
+                    for where in (mpf.TABLE_AUTO, mpf.TABLE_SHARED):
+                        prof.set_table_memory(gf, where)
+                        want = mpf.TABLE_TENSOR if where == mpf.TABLE_AUTO else mpf.TABLE_SHARED
+                        if gf == mpf.MSV and prof.get_table_memory(gf) == mpf.TABLE_SHARED and \
+                                where == mpf.TABLE_AUTO:
+                            want = mpf.TABLE_SHARED   # MSV_DIRECT profiles have no TMEM kernel
+                        assert prof.get_table_memory(gf) == want
+                        got = run_gpu(ctx, gf, prof, ddb)
+                        assert_same(got, exp, f"tmem={where} arith={arith} words={words} M={M} filter {gf}")
+            prof.close()
+
+
 def test_strong_profiles_hit_j_and_overflow(ctx):
     """Low costs: long hits, chained J transitions, MSV and SSV overflow."""
     rng = np.random.default_rng(77)

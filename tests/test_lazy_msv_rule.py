@@ -144,3 +144,22 @@ def test_tiled_msv_rule_threshold_edges():
                         assert got == (int(raw[k]), int(flag[k])), (bias, M, tgt, sq.tolist(), got)
                         checked += 1
     assert checked > 500
+
+
+def test_packed_threshold_test_equals_the_halfwise_comparison():
+    """The striped MSV kernel tests "some 16-bit half of the running maximum
+    exceeds the key K" as ((vacc + pack2(0x7fff - K)) & 0x80008000) != 0.
+    For halves and keys in [0, 0x7fff] that equals the comparison of each
+    half, and no half's sum carries into the other."""
+    h = np.arange(0, 0x8000, dtype=np.int64)
+    for K in list(range(0, 0x8000, 97)) + [0x7bff, 0x7ffe, 0x7fff]:
+        s = h + (0x7fff - K)
+        assert np.all(s < 0x10000)
+        assert np.array_equal((s & 0x8000) != 0, h > K)
+    rng = np.random.default_rng(4)
+    lo = rng.integers(0, 0x8000, 200000, dtype=np.int64)
+    hi = rng.integers(0, 0x8000, 200000, dtype=np.int64)
+    K = rng.integers(0, 0x8000, 200000, dtype=np.int64)
+    packed = (lo | (hi << 16)) + ((0x7fff - K) | ((0x7fff - K) << 16))
+    got = (packed & 0x80008000) != 0
+    assert np.array_equal(got, (lo > K) | (hi > K))
