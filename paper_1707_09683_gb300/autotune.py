@@ -13,7 +13,12 @@ Two selectors:
   32-sequence kernel and models above m_max (2450 MSV, 1000 SSV) to S = 1.
 * ``Autotuner`` times every built (lanes, words) configuration that covers a
   model on the caller's database and keeps the fastest; the paper's point,
-  mapped onto this library's kernels, is one of the candidates.
+  mapped onto this library's kernels, is one of the candidates.  It then
+  times the shard factor of the winner (work items per query = factor x
+  resident blocks: the granularity of the dynamic load balance that replaces
+  the paper's static block assignment and Alg. 1) and keeps the best.  For
+  whole-warp configurations it also times the table in shared memory only
+  against the table in tensor memory.
 
 In this library a lane group of ``lanes`` threads holds one sequence (the
 paper's L, so S = 32 / lanes) and each thread holds ``words`` registers of
@@ -35,6 +40,7 @@ M_MIN = 20
 M_MAX = {"msv": 2450, "ssv": 1000}
 
 LANES = (1, 2, 4, 8, 16, 32)
+SHARD_FACTORS = (1, 2, 4)
 WORDS = tuple(sorted(set(range(4, 49, 4)) | set(range(6, 48, 4))))   # %4 == 2: two-word tail
 
 
@@ -109,8 +115,10 @@ class Autotuner:
     """Times candidate configurations on a database and remembers the best
     per (filter, model length).  Results can be saved to / loaded from JSON."""
 
-    def __init__(self, ctx, db, cache_path: Optional[str] = None, reps: int = 3):
+    def __init__(self, ctx, db, cache_path: Optional[str] = None, reps: int = 3,
+                 tensor_memory: bool = True):
         self.ctx = ctx
+        self.tensor_memory = tensor_memory   # False: every candidate keeps its table in shared memory
         self.db = db
         self.reps = reps
         self.cache_path = cache_path
@@ -124,11 +132,12 @@ class Autotuner:
     def key(filt: int, m: int) -> str:
         return f"{'msv' if filt == 0 else 'ssv'}:{m}"
 
-    def _time(self, prof, filt, lanes, words, outs) -> float:
+    def _time(self, prof, filt, lanes, words, outs, factor: int = 1) -> float:
         import torch
         from . import mpf
         try:
             prof.set_config(filt, lanes, words)
+            prof.set_shard_factor(filt, factor)
         except mpf.MpfError:      # no kernel built for this pair in this arithmetic
             return float("inf")
         plan = mpf.Plan(self.ctx, filt, [prof], self.db, *outs)
@@ -147,26 +156,46 @@ class Autotuner:
         plan.close()
         return best
 
-    def tune(self, prof, filt: int, force: bool = False) -> Tuple[int, int]:
-        """Pick and set the fastest configuration for this profile."""
+    def tune(self, prof, filt: int, force: bool = False, shards: bool = True) -> Tuple[int, int]:
+        """Pick and set the fastest configuration (lanes, words) for this
+        profile, then its shard factor; returns (lanes, words)."""
         import torch
         k = self.key(filt, prof.M)
+        from . import mpf
         if not force and k in self.table:
-            prof.set_config(filt, *self.table[k])
-            return self.table[k]
+            cfg = self.table[k]
+            prof.set_config(filt, cfg[0], cfg[1])
+            prof.set_shard_factor(filt, cfg[2] if len(cfg) > 2 else 1)
+            prof.set_table_memory(filt, cfg[3] if len(cfg) > 3 else mpf.TABLE_AUTO)
+            return cfg[0], cfg[1]
         n = self.db.n_seqs
         dev = torch.device("cuda", self.ctx.device)
         outs = (torch.empty(n, dtype=torch.uint8, device=dev),
                 torch.empty(n, dtype=torch.uint8, device=dev), None)
         times = {}
         for lanes, words in candidates(prof.M):
+            prof.set_table_memory(filt, mpf.TABLE_AUTO if self.tensor_memory else mpf.TABLE_SHARED)
             times[f"{lanes}x{words}"] = self._time(prof, filt, lanes, words, outs)
+            if lanes == 32 and prof.get_table_memory(filt) == mpf.TABLE_TENSOR:
+                # the same configuration with the table in shared memory only
+                prof.set_table_memory(filt, mpf.TABLE_SHARED)
+                times[f"{lanes}x{words}s"] = self._time(prof, filt, lanes, words, outs)
         best = min(times, key=times.get)
-        cfg = tuple(int(x) for x in best.split("x"))
-        prof.set_config(filt, *cfg)
-        self.table[k] = cfg
+        table = mpf.TABLE_SHARED if best.endswith("s") or not self.tensor_memory else mpf.TABLE_AUTO
+        lanes, words = (int(x) for x in best.rstrip("s").split("x"))
+        prof.set_table_memory(filt, table)
+        factor = 1
+        if shards:
+            ft = {1: times[best]}
+            for f in SHARD_FACTORS[1:]:
+                ft[f] = self._time(prof, filt, lanes, words, outs, f)
+                times[f"{best}/{f}"] = ft[f]
+            factor = min(ft, key=ft.get)
+        prof.set_config(filt, lanes, words)
+        prof.set_shard_factor(filt, factor)
+        self.table[k] = (lanes, words, factor, table)
         self.timings[k] = times
-        return cfg
+        return lanes, words
 
     def save(self, path: Optional[str] = None):
         path = path or self.cache_path

@@ -27,7 +27,16 @@ def test_autotune_picks_a_candidate_and_keeps_parity(tmp_path):
             assert cfg in autotune.candidates(rec.M)
             assert prof.get_config(filt) == cfg
             times = tuner.timings[tuner.key(filt, rec.M)]
-            assert min(times.values()) == times[f"{cfg[0]}x{cfg[1]}"]
+            configs = {k: v for k, v in times.items() if "/" not in k}
+            shared = prof.get_table_memory(filt) == mpf.TABLE_SHARED and cfg[0] == 32 and \
+                f"{cfg[0]}x{cfg[1]}s" in configs
+            best = f"{cfg[0]}x{cfg[1]}" + ("s" if shared else "")
+            assert min(configs.values()) == times[best]
+            factor = prof.get_shard_factor(filt)
+            shard_t = {1: times[best]}
+            shard_t.update({int(k.split("/")[1]): v for k, v in times.items() if k.startswith(best + "/")})
+            assert set(shard_t) == set(autotune.SHARD_FACTORS)
+            assert shard_t[factor] == min(shard_t.values())
             n = db.n_seqs
             raw, flag = np.empty(n, np.uint8), np.empty(n, np.uint8)
             (mpf.ssv_scan if filt == mpf.SSV else mpf.msv_scan)(ctx, prof, db, raw, flag)
