@@ -174,3 +174,32 @@ def test_long_model_full_database():
     prof.close()
     db.close()
     ctx.close()
+
+
+def test_serving_workload_full_database_through_the_server():
+    """The serving workload at its stated size: 5,000,000 sequences (1.78 G
+    residues) resident on the device, ten queries of log-uniform M served
+    through the continuous-batching server with overlapping batches; a sample
+    of every query's SSV and MSV outputs (the longest and shortest sequences
+    and random ones) equals the oracle one sequence at a time."""
+    from paper_1707_09683_gb300.serve import Request, ScanServer
+    wl = synth.make_workload(3, n_queries=10)
+    assert wl.db.n_seqs == 5_000_000
+    rng = np.random.default_rng(13)
+    idx = sample_index(wl.db, rng, n_random=500, n_edge=40)
+    server = ScanServer(wl.db, n_streams=3, max_batch=2, max_queue=32, keep_results=True)
+    reqs = [Request(i, p, arrival=0.002 * i) for i, p in enumerate(wl.profiles)]
+    stats = server.run(reqs, offered_rate=500.0)
+    assert stats.served == len(reqs) and stats.rejected == 0
+    assert stats.max_inflight_batches >= 2
+    sel = idx.astype(np.int64)
+    for r in reqs:
+        for gf, of in ((mpf.SSV, oracle.SSV), (mpf.MSV, oracle.MSV)):
+            exp = oracle.scan(of, r.profile, wl.db.residues, wl.db.offsets, wl.db.lengths,
+                              index=idx, nthreads=16)
+            got = r.result[gf]
+            assert np.array_equal(got[0][sel], exp[0]), (r.rid, gf)
+            assert np.array_equal(got[1][sel], exp[1]), (r.rid, gf)
+            assert np.array_equal(got[2][sel].view(np.uint32), exp[2].view(np.uint32)), (r.rid, gf)
+        r.result = None
+    server.close()

@@ -70,3 +70,59 @@ def test_bounded_queue_rejects_overload(setup):
     assert stats.rejected > 0 and stats.served + stats.rejected == 10
     assert all(r.completed >= r.arrival for r in reqs if not r.rejected)
     server.close()
+
+
+def test_long_model_waits_while_short_ones_are_admitted_past_it(setup):
+    """Admission by footprint: with a work budget that holds one long model
+    and a few short ones, a second long model that arrives while the first
+    is on the GPU waits, the short models queued behind it are admitted past
+    it, and it runs once the first has retired.  Every result still equals
+    the standalone scan."""
+    wl = setup
+    rng = np.random.default_rng(21)
+    long1, long2 = synth.make_profile(2000, rng), synth.make_profile(1800, rng)
+    shorts = [synth.make_profile(m, rng) for m in (50, 64, 72, 80)]
+    res = int(wl.db.lengths.sum())
+    budget = 2 * res * (long1.M + 4 * 80)
+    server = ScanServer(wl.db, n_streams=4, max_batch=1, max_queue=16, keep_results=True,
+                        work_budget=budget)
+    recs = [long1, long2] + shorts
+    reqs = [Request(i, p, arrival=0.0) for i, p in enumerate(recs)]
+    fp = [server.footprint(r) for r in reqs]
+    assert fp[0].smem_bytes > fp[2].smem_bytes and fp[0].cells > fp[2].cells
+    assert all(f.hbm_bytes >= server.slot_bytes for f in fp)
+    stats = server.run(reqs, offered_rate=0.0)
+    assert stats.served == len(reqs) and stats.rejected == 0
+    order = server.admit_order
+    assert order[0] == 0, order
+    assert order.index(1) > order.index(2), order          # a short model passed the long one
+    assert reqs[1].bypassed >= 1 and stats.waited_for_budget >= 1
+    assert reqs[1].admitted >= reqs[0].completed - 1e-6   # it ran after the first long model
+    ctx = server.ctxs[1]
+    for r in reqs:
+        alone = standalone(ctx, server.db, r.profile)
+        for filt in (mpf.SSV, mpf.MSV):
+            got, exp = r.result[filt], alone[filt]
+            assert np.array_equal(got[0], exp[0]) and np.array_equal(got[1], exp[1]), (r.rid, filt)
+            assert np.array_equal(got[2].view(np.uint32), exp[2].view(np.uint32)), (r.rid, filt)
+    server.close()
+
+
+def test_starving_request_blocks_further_bypass(setup):
+    """After a waiting request has been passed over max_bypass times, no later
+    request is admitted before it."""
+    wl = setup
+    rng = np.random.default_rng(22)
+    long1, long2 = synth.make_profile(2000, rng), synth.make_profile(1900, rng)
+    shorts = [synth.make_profile(60, rng) for _ in range(6)]
+    res = int(wl.db.lengths.sum())
+    server = ScanServer(wl.db, n_streams=2, max_batch=1, max_queue=16,
+                        work_budget=2 * res * (long1.M + 60), max_bypass=1)
+    reqs = [Request(i, p, arrival=0.0) for i, p in enumerate([long1, long2] + shorts)]
+    stats = server.run(reqs)
+    assert stats.served == len(reqs)
+    order = server.admit_order
+    # long2 is passed at most once; every short model after the first waits for it.
+    assert reqs[1].bypassed <= 1
+    assert all(order.index(1) < order.index(i) for i in range(3, len(reqs))), order
+    server.close()
