@@ -71,6 +71,58 @@ def test_sharded_scan_gathers_to_the_single_process_result():
     assert spans[0][0] == 0 and spans[-1][1] == 900 and spans[0][1] == spans[1][0]
 
 
+def _sharded_worker(rank, world, port, result_q):
+    """The bench's N > 1 path (shard.ShardedScan) with the oracle as the
+    scorer: several queries, outputs [query][sequence] gathered in database
+    order."""
+    os.environ["MASTER_ADDR"] = "127.0.0.1"
+    os.environ["MASTER_PORT"] = str(port)
+    dist.init_process_group("gloo", rank=rank, world_size=world)
+    try:
+        import oracle
+        wl = synth.make_workload(1, n_seqs=700, n_queries=3)
+        job = shard.ShardedScan(wl.db, rank, world, len(wl.profiles))
+
+        def scorer(res, off, ln):
+            outs = []
+            for f in (oracle.MSV, oracle.SSV):
+                per = [oracle.scan(f, p, res, off, ln) for p in wl.profiles]
+                for k in range(3):
+                    outs.append(torch.from_numpy(np.concatenate([o[k] for o in per])))
+            return outs
+
+        full = job.gather(job.run(scorer))
+        result_q.put((rank, [t.numpy() for t in full], job.n_local))
+    finally:
+        dist.destroy_process_group()
+
+
+@pytest.mark.parametrize("world", [2, 3])
+def test_sharded_scan_class_gathers_query_major_outputs(world):
+    import oracle
+    oracle.build()
+    ctx = mp.get_context("spawn")
+    q = ctx.Queue()
+    port = _free_port()
+    procs = [ctx.Process(target=_sharded_worker, args=(r, world, port, q)) for r in range(world)]
+    for pr in procs:
+        pr.start()
+    got = [q.get(timeout=180) for _ in range(world)]
+    for pr in procs:
+        pr.join(timeout=60)
+        assert pr.exitcode == 0
+    wl = synth.make_workload(1, n_seqs=700, n_queries=3)
+    ref = []
+    for f in (oracle.MSV, oracle.SSV):
+        per = [oracle.scan(f, p, wl.db.residues, wl.db.offsets, wl.db.lengths) for p in wl.profiles]
+        for k in range(3):
+            ref.append(np.concatenate([o[k] for o in per]))
+    assert sum(n for _, _, n in got) == 700
+    for rank, full, _ in got:
+        for a, b in zip(full, ref):
+            assert np.array_equal(a.view(np.uint8), b.view(np.uint8)), rank
+
+
 def test_shard_bounds_balance_and_cover():
     rng = np.random.default_rng(2)
     lengths = rng.integers(0, 5000, size=10_001).astype(np.uint32)
