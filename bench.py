@@ -143,6 +143,46 @@ def max_over_ranks(x: float, world: int) -> float:
     return float(t.item())
 
 
+def r_int(filt: str, nsm: int, sm_mhz: float) -> float:
+    """Integer-SIMD roofline of a filter in GCUPS."""
+    return nsm * INT_LANES_PER_SM_CLK * CELLS_PER_LANE_OP / OPS_PER_CELL[filt] * sm_mhz * 1e6 / 1e9
+
+
+# Per-SM-clock rates from profiles/ubench_issue_rates_gb300.md.
+SMEM_B_PER_CLK = 128.0
+TMEM_B_PER_CLK = 385.7
+ALU_LANES_PER_CLK = 64.0
+FMA_LANES_PER_CLK = 64.0
+TM_WORDS_ALL, TM_WORDS_PART = 14, 12   # words per lane from TMEM (all up to 14, else 12)
+
+
+def design_ceiling(filt, lanes, words, tm, f16, m, nsm, sm_mhz):
+    """Ceiling of a striped kernel configuration in GCUPS (model cells): the
+    lowest of its table-read and cell-update limits per SM clock, times the
+    model's share of the padded cells.  Per 32-bit word (two cells) and DP
+    row: 4 B of table (from TMEM for the first 12 or 14 words of a lane
+    with tm, else from shared memory), one cell update (DPX on the ALU pipe, or
+    HFMA2 on the FMA pipe) and half a 3-input max (ALU)."""
+    ht = (words if words <= TM_WORDS_ALL else TM_WORDS_PART) if tm else 0
+    lim = {}
+    smem_b = 4.0 * (words - ht) / words
+    if smem_b > 0:
+        lim["shared-memory table reads"] = SMEM_B_PER_CLK / smem_b * 2
+    if ht:
+        lim["TMEM table reads"] = TMEM_B_PER_CLK / (4.0 * ht / words) * 2
+    alu_ops = 0.5 + (0.0 if f16 else 1.0)
+    lim["ALU pipe (cell update + running max)" if not f16 else "ALU pipe (running max)"] = \
+        ALU_LANES_PER_CLK / alu_ops * 2
+    if f16:
+        lim["FMA pipe (cell update)"] = FMA_LANES_PER_CLK / 1.0 * 2
+    name = min(lim, key=lim.get)
+    cells_clk = lim[name]
+    g = nsm * cells_clk * sm_mhz * 1e6 / 1e9 * m / (2 * lanes * words)
+    basis = ("per SM clock: " + ", ".join(f"{k} {v:.1f}" for k, v in lim.items()) +
+             f" cells; x {nsm} SMs x {sm_mhz:.0f} MHz x M / padded cells ({m}/{2 * lanes * words})")
+    return g, name, basis
+
+
 def cpu_baseline(wl, n_sample: int, seed: int = 7):
     """The oracle as it stands, on a bounded sample of the workload."""
     import oracle
@@ -199,30 +239,43 @@ def run_mpf(args):
     dev = torch.device("cuda", local)
 
     t0 = time.time()
-    wl = synth.make_workload(args.workload, n_seqs=args.n_seqs, n_queries=args.n_queries)
-    if world > 1:   # weak scaling: every rank scores its own database of the same shape
-        wl.db = synth.make_database(wl.db.n_seqs, wl.meta["mean"], *wl.meta["clip"],
-                                    np.random.default_rng(1000 + rank))
-    log(f"[rank {rank}] workload {wl.name}: {wl.db.n_seqs} seqs, {wl.db.n_residues} residues, "
+    # N > 1: one database of N times the workload's sequences (the same seeded
+    # draws on every rank), sharded by residues; rank r scores shard r and
+    # the outputs are gathered (weak scaling: a rank's share stays the size of
+    # the one-GPU workload).
+    base_n = args.n_seqs or synth.WORKLOADS[args.workload]["n_seqs"]
+    wl = synth.make_workload(args.workload, n_seqs=base_n * world, n_queries=args.n_queries)
+    job = None
+    if world > 1:
+        from paper_1707_09683_gb300 import shard
+        job = shard.ShardedScan(wl.db, rank, world, len(wl.profiles))
+        db_arrays = (job.residues, job.offsets, job.lengths)
+    else:
+        db_arrays = (wl.db.residues, wl.db.offsets, wl.db.lengths)
+    total_res = int(wl.db.lengths.sum(dtype=np.uint64))
+    log(f"[rank {rank}] workload {wl.name}: {wl.db.n_seqs} seqs, {total_res} residues, "
         f"{len(wl.profiles)} queries ({time.time() - t0:.1f} s)")
     ctx = mpf.Context(local)
     stream = ctx.torch_stream()
-    db = mpf.Database(ctx, wl.db.residues, wl.db.offsets, wl.db.lengths)
+    db = mpf.Database(ctx, *db_arrays)
     profs = [mpf.Profile(ctx, p) for p in wl.profiles]
     arith = {"auto": mpf.ARITH_AUTO, "i16": mpf.ARITH_I16, "f16": mpf.ARITH_F16}[args.arith]
+    table = {"auto": mpf.TABLE_AUTO, "shared": mpf.TABLE_SHARED}[args.table]
     for pr in profs:
         for code in (mpf.MSV, mpf.SSV):
             pr.set_arith(code, arith)
+            pr.set_table_memory(code, table)
     # Kernel configurations (lanes per sequence, words per lane) from the
     # autotuner, each candidate timed on the whole database.
     tuned = {}
     if args.tune and len({p.M for p in wl.profiles}) <= 16:
         from paper_1707_09683_gb300 import autotune
         t_tune = time.time()
-        tuner = autotune.Autotuner(ctx, db, reps=1)
+        tuner = autotune.Autotuner(ctx, db, reps=1, tensor_memory=args.table == "auto")
         for pr in profs:
             for name, code in (("msv", mpf.MSV), ("ssv", mpf.SSV)):
-                tuned.setdefault(name, {})[pr.M] = list(tuner.tune(pr, code))
+                tuner.tune(pr, code)
+                tuned.setdefault(name, {})[pr.M] = list(tuner.table[tuner.key(code, pr.M)])
         log(f"[rank {rank}] autotuned {len(profs)} queries in {time.time() - t_tune:.1f} s: {tuned}")
     n, q = db.n_seqs, len(profs)
     res = db.n_residues
@@ -309,35 +362,77 @@ def run_mpf(args):
     avg_ms = sum(durs) / len(durs)
     dom_m = wl.profiles[dom_i].M
     achieved = dom_m * res / (avg_ms * 1e-3) / 1e9      # GCUPS of one launch
-    lanes, words = profs[dom_i].get_config(mpf.MSV if dom_f == "msv" else mpf.SSV)
+    dom_code = mpf.MSV if dom_f == "msv" else mpf.SSV
+    lanes, words = profs[dom_i].get_config(dom_code)
+    dom_tm = profs[dom_i].get_table_memory(dom_code) == mpf.TABLE_TENSOR
     sm_mhz = clocks.get("sm_mhz") or 2070.0
     nsm = torch.cuda.get_device_properties(dev).multi_processor_count
-    peak = nsm * INT_LANES_PER_SM_CLK * CELLS_PER_LANE_OP / OPS_PER_CELL[dom_f] * sm_mhz * 1e6 / 1e9
-    mode_name = ("MSV_FAST" if dom_f == "msv" else "SSV") + ("_F16" if args.arith != "i16" else "")
+    peak = r_int(dom_f, nsm, sm_mhz)
+    f16 = args.arith == "f16"
+    mode_name = ("MSV_FAST" if dom_f == "msv" else "SSV") + ("_F16" if f16 else "") + (",TMEM" if dom_tm else "")
     import hashlib
     src_ok = hashlib.sha256(open(KERNEL_SOURCE, "rb").read()).hexdigest() == KERNEL_SOURCE_SHA256
-    traffic = NCU_TRAFFIC.get((f"scan_kernel<{lanes},{words},{mode_name}>", wl.name, dom_m)) if src_ok else None
+    kname = f"scan_kernel<{lanes},{words},{mode_name}>"
+    traffic = NCU_TRAFFIC.get((kname, wl.name, dom_m)) if src_ok else None
+    ceiling = design_ceiling(dom_f, lanes, words, dom_tm, f16, dom_m, nsm, sm_mhz)
     roofline = {"bound": "alu", "achieved": achieved, "peak": peak, "unit": "GCUPS",
                 "frac": achieved / peak, "traffic": traffic,
                 "traffic_note": "ncu dram__bytes_read.sum + dram__bytes_write.sum of this kernel on this "
-                                "workload (profiles/scan_kernel_m2405_msweep500k.md); algorithmic bytes "
-                                "per launch: %.0f" % (res + 6 * n),
-                "kernel": f"scan_kernel<{lanes},{words},{'MSV' if dom_f == 'msv' else 'SSV'}> M={dom_m}",
+                                "workload (profiles/); null when the kernel source changed since the "
+                                "capture; algorithmic bytes per launch: %.0f" % (res + 6 * n),
+                "kernel": f"{kname} M={dom_m}",
                 "launches_averaged": len(durs), "avg_launch_ms": avg_ms,
-                "smem_ceiling": {
-                    "peak": nsm * 128 / 2 * sm_mhz * 1e6 * dom_m / (2 * lanes * words) / 1e9,
-                    "frac": achieved / (nsm * 128 / 2 * sm_mhz * 1e6 * dom_m / (2 * lanes * words) / 1e9),
-                    "basis": "128 B/clk/SM of shared memory / 2 B of score table per padded cell "
-                             "x model cells / padded cells (the ceiling of the 16-bit table)"},
+                "design_ceiling": {"peak": ceiling[0], "frac": achieved / ceiling[0], "limiter": ceiling[1],
+                                   "basis": ceiling[2]},
                 "algorithmic_cells_per_launch": dom_m * res,
-                "peak_basis": f"{nsm} SMs x {INT_LANES_PER_SM_CLK} int lanes/clk x "
-                              f"{CELLS_PER_LANE_OP} cells/op / {OPS_PER_CELL[dom_f]} ops/cell x "
-                              f"{sm_mhz:.0f} MHz (median SM clock in the timed region)"}
+                "peak_basis": f"{nsm} SMs x {INT_LANES_PER_SM_CLK} packed-integer lane-ops/clk/SM "
+                              f"(DPX/PRMT/LOP3, profiles/ubench_issue_rates_gb300.md) x "
+                              f"{CELLS_PER_LANE_OP} byte cells/op / {OPS_PER_CELL[dom_f]} ops/cell "
+                              f"(Alg. {'2' if dom_f == 'msv' else '7'}) x {sm_mhz:.0f} MHz "
+                              f"(median SM clock in the timed region)"}
 
-    gcups_batched = 2 * cells_per_filter * world / (ms_batched * 1e-3) / 1e9
-    gcups_plain = 2 * cells_per_filter * world / (ms_plain * 1e-3) / 1e9
+    # Whole-job throughput: every rank's cells (the full database when sharded).
+    job_cells_per_filter = sum(p.M for p in wl.profiles) * total_res
+    gcups_batched = 2 * job_cells_per_filter / (ms_batched * 1e-3) / 1e9
+    gcups_plain = 2 * job_cells_per_filter / (ms_plain * 1e-3) / 1e9
     per_filter_plain = {f: sum(wl.profiles[i].M * res for i, _ in per_kernel[f]) /
                         (tot[f] * 1e-3) / 1e9 for f, _ in filters}
+    # The same over the queries with M >= 400, against R_int of the filter.
+    ge400 = {}
+    for f, _ in filters:
+        sel = [(i, ms) for i, ms in per_kernel[f] if wl.profiles[i].M >= 400]
+        if sel:
+            g = sum(wl.profiles[i].M * res for i, _ in sel) / (sum(ms for _, ms in sel) * 1e-3) / 1e9
+            ge400[f] = {"gcups": g, "r_int": r_int(f, nsm, sm_mhz), "frac": g / r_int(f, nsm, sm_mhz)}
+
+    # Extra line, not the headline: the same batched step with the cells held
+    # as fp16 integers (cell update on the FMA pipe).
+    f16_line = None
+    if args.f16_line and args.arith != "f16":
+        for pr in profs:
+            for _, code in filters:
+                pr.set_arith(code, mpf.ARITH_F16)
+        plans16 = {f: mpf.Plan(ctx, code, profs, db, *outs[f]) for f, code in filters}
+        for pl in plans16.values():
+            pl.capture_graph()
+
+        def step16():
+            for f, _ in filters:
+                plans16[f].launch()
+
+        for _ in range(args.warmup):
+            step16()
+        ms16 = max_over_ranks(time_steps(step16, args.steps), world)
+        for pl in plans16.values():
+            pl.close()
+        for pr in profs:
+            for _, code in filters:
+                pr.set_arith(code, arith)
+        f16_line = {"value": 2 * job_cells_per_filter / (ms16 * 1e-3) / 1e9, "unit": "GCUPS",
+                    "ms_per_step": ms16, "dtype": "f16",
+                    "note": "extra line, not the headline: the batched step with fp16 cells "
+                            "(HFMA2.RELU on the FMA pipe, exact integers below 2048)"}
+        log(f"fp16-cell line: {f16_line['value']:.0f} GCUPS ({ms16:.1f} ms per step)")
 
     # End to end through the public API with host buffers: profiles built from
     # host bytes, both filters batched into host outputs, profiles released.
@@ -353,8 +448,12 @@ def run_mpf(args):
         for pr in ps:
             for name, code in filters:
                 pr.set_arith(code, arith)
+                pr.set_table_memory(code, table)
                 if tuned:
-                    pr.set_config(code, *tuned[name][pr.M])
+                    lanes_w = tuned[name][pr.M]   # lanes, words, shard factor, table memory
+                    pr.set_config(code, lanes_w[0], lanes_w[1])
+                    pr.set_shard_factor(code, lanes_w[2])
+                    pr.set_table_memory(code, lanes_w[3])
         for _, code in filters:
             mpf.scan_batch(ctx, code, ps, db, raw_h, flag_h, nat_h)
         for p in ps:
@@ -368,7 +467,25 @@ def run_mpf(args):
         step_e2e()
     e2e_s = (time.perf_counter() - t1) / e2e_steps
     e2e_s = max_over_ranks(e2e_s, world)
-    e2e_gcups = 2 * cells_per_filter * world / e2e_s / 1e9
+    e2e_gcups = 2 * job_cells_per_filter / e2e_s / 1e9
+
+    # N > 1: the exchange -- every rank's outputs gathered into database
+    # order on every rank (NCCL all-gather of device tensors), after one step.
+    sharding = None
+    if job is not None:
+        step_batched()
+        ctx.sync()
+        barrier(world)
+        t_g = time.perf_counter()
+        full = job.gather([t for f, _ in filters for t in outs[f]])
+        torch.cuda.synchronize()
+        gather_s = max_over_ranks(time.perf_counter() - t_g, world)
+        sharding = {"world": world, "shard": [job.lo, job.hi], "bounds": job.bounds,
+                    "local_residues": job.n_residues_local, "gather_s": gather_s,
+                    "gathered_bytes_per_rank": int(sum(t.numel() * t.element_size() for t in full)),
+                    "path": "shard.ShardedScan: residue-balanced shards of one database, "
+                            "shard.gather_query_outputs (NCCL all_gather) after the scans"}
+        del full
 
     # Two-stage filter (SSV over everything, MSV over the sequences whose SSV
     # score passes): threshold at the 98th percentile of this step's SSV nat
@@ -404,6 +521,14 @@ def run_mpf(args):
     if args.long_m and world == 1:
         long_model = run_long_model(args, ctx, db, wl, time_steps, clocks, dev)
 
+    # Many-query workloads: the 64-query overflow batch (2 M sequences) and
+    # the first queries of the 1,000-query throughput workload (10 M
+    # sequences), batched against plain.
+    batch_workloads = None
+    if world == 1 and args.batch_workloads:
+        batch_workloads = [run_batch_workload(args, ctx, 2, None, time_steps, dev),
+                           run_batch_workload(args, ctx, 4, args.w4_queries, time_steps, dev)]
+
     # Serving: continuous batching of arriving queries (model lengths drawn as
     # in the serving workload) against the resident database, per offered load.
     serving = None
@@ -423,18 +548,26 @@ def run_mpf(args):
         line = {
             "metric": METRIC, "value": gcups_batched, "unit": "GCUPS", "n_gpus": world,
             "steps": args.steps, "warmup": args.warmup, "ms_per_step": ms_batched,
-            "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "u8",
+            "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
+            "dtype": "f16" if args.arith == "f16" else "i16",
+            "sharding": sharding,
             "data": "synthetic",
             "config": {"workload": wl.name, "queries": [p.M for p in wl.profiles],
-                       "n_seqs": n, "residues": res, "filters": ["msv", "ssv"],
+                       "n_seqs": int(wl.db.n_seqs), "residues": total_res, "filters": ["msv", "ssv"],
+                       "per_rank": {"n_seqs": n, "residues": res},
                        "form": "batched persistent plan per filter, CUDA-graph replay",
-                       "cell_arith": args.arith,
+                       "cell_arith": ("fp16 cells holding exact integers, HFMA2.RELU on the FMA pipe"
+                                      if args.arith == "f16" else
+                                      "16-bit integer cells, two per register, DPX on the integer pipe; "
+                                      "exact byte semantics of Alg. 2 / Alg. 7; no floating point"),
+                       "table_memory": args.table,
                        "kernel_configs": tuned or "default",
                        "l2": "database (%.0f MB) larger than L2; no flush" % (res / 1e6),
-                       "cells_per_step": 2 * cells_per_filter},
+                       "cells_per_step": 2 * job_cells_per_filter},
             "plain": {"value": gcups_plain, "unit": "GCUPS", "ms_per_step": ms_plain,
-                      "per_filter_gcups": per_filter_plain},
+                      "per_filter_gcups": per_filter_plain, "m_ge_400": ge400},
             "batched_over_plain": gcups_batched / gcups_plain,
+            "f16_cells_extra_line": f16_line,
             "roofline": roofline,
             "cpu_baseline": cpu,
             "e2e": {"value": e2e_gcups, "unit": "GCUPS", "h2d_bytes_per_step": int(h2d),
@@ -445,6 +578,7 @@ def run_mpf(args):
             "viterbi": vit,
             "long_model": long_model,
             "serving": serving,
+            "batch_workloads": batch_workloads,
             "gpu_launches": launches_per_step * args.steps,
             "clocks": clocks,
         }
@@ -581,15 +715,93 @@ def run_serving(wl_serv, rates, n_requests, device, seed=3, work_budget_queries=
             f"{st.gcups:9.1f} GCUPS batch {st.mean_batch:.1f} wait {st.mean_wait_ms:.1f} ms")
     fp = server.footprint_bytes
     server.close()
-    # Capacity: the served rate at the highest offered load (queries per second).
+    # Capacity: the served rate at the highest offered load (queries per
+    # second); the knee: the first offered load whose p99 latency is more than
+    # three times that of the lightest load.
     top = out[-1]
     capacity = top["served"] / top["wall_s"] if top["wall_s"] > 0 else None
+    knee = next((r["offered_qps"] for r in out if r["p99_ms"] > 3 * out[0]["p99_ms"]), None)
     return {"unit": "ms / GCUPS", "workload": wl_serv.name, "n_seqs": int(wl_serv.db.n_seqs),
             "residues": res, "requests_per_rate": n_requests, "filters": ["ssv", "msv"],
             "query_M": "log-uniform [50, 2000] (mean %.0f)" % mean_m, "streams": 4, "max_batch": 8,
             "admission": "by footprint: output slot + score tables (HBM), shared memory per block, "
                          "work budget %s" % ("none" if budget is None else f"{budget:.3e} cells"),
-            "output_arena_bytes": fp, "capacity_qps": capacity, "by_rate": out}
+            "output_arena_bytes": fp, "capacity_qps": capacity, "knee_offered_qps": knee,
+            "by_rate": out}
+
+
+def run_batch_workload(args, ctx, idx, n_queries, time_steps, dev, steps=3):
+    """Batched vs plain on a many-query workload: every query against the
+    whole database with both filters, default kernel configurations.
+    Batched: one graph-captured plan per filter; plain: one launch per query
+    and filter.  Padding: the padded cells the kernels compute (model padded
+    to whole lane stripes) per model cell."""
+    import torch
+    from paper_1707_09683_gb300 import mpf, synth
+    t0 = time.time()
+    wl = synth.make_workload(idx, n_queries=n_queries)
+    gen_s = time.time() - t0
+    db = mpf.Database(ctx, wl.db.residues, wl.db.offsets, wl.db.lengths)
+    n, res, q = db.n_seqs, db.n_residues, len(wl.profiles)
+    profs = [mpf.Profile(ctx, p) for p in wl.profiles]
+    filters = (("msv", mpf.MSV), ("ssv", mpf.SSV))
+    outs = {f: tuple(torch.empty(q * n, dtype=dt, device=dev)
+                     for dt in (torch.uint8, torch.uint8, torch.float32)) for f, _ in filters}
+    plans = {f: mpf.Plan(ctx, code, profs, db, *outs[f]) for f, code in filters}
+    for pl in plans.values():
+        pl.capture_graph()
+    plain = {f: [mpf.Plan(ctx, code, [pr], db, *(t[i * n:(i + 1) * n] for t in outs[f]))
+                 for i, pr in enumerate(profs)] for f, code in filters}
+
+    def step_b():
+        for f, _ in filters:
+            plans[f].launch()
+
+    def step_p():
+        for f, _ in filters:
+            for pl in plain[f]:
+                pl.launch()
+
+    for _ in range(2):
+        step_b()
+        step_p()
+    ms_b, ms_p = [], []
+    for _ in range(steps):            # interleaved, so drift hits both forms alike
+        ms_b.append(time_steps(step_b, 1))
+        ms_p.append(time_steps(step_p, 1))
+    cells = 2 * sum(p.M for p in wl.profiles) * res
+    padded = 0
+    groups = {}
+    for pr, rec in zip(profs, wl.profiles):
+        for f, code in filters:
+            lanes, words = pr.get_config(code)
+            padded += (2 * lanes * words if words else rec.M) * res
+            key = (lanes, words, pr.get_table_memory(code))
+            groups[key] = groups.get(key, 0) + 1
+    launches = sum(pl.kernel_launches for pl in plans.values())
+    for pl in list(plans.values()) + [p for f in plain for p in plain[f]]:
+        pl.close()
+    for pr in profs:
+        pr.close()
+    db.close()
+    gb = cells / (statistics.median(ms_b) * 1e-3) / 1e9
+    gp = cells / (statistics.median(ms_p) * 1e-3) / 1e9
+    out = {"workload": wl.name, "queries": q, "n_seqs": n, "residues": res,
+           "query_M": [p.M for p in wl.profiles] if q <= 16 else f"{min(p.M for p in wl.profiles)}-"
+                                                                  f"{max(p.M for p in wl.profiles)}",
+           "batched": {"gcups": gb, "ms_per_step": ms_b, "kernel_launches_per_step": launches,
+                       "form": "one graph-captured plan per filter"},
+           "plain": {"gcups": gp, "ms_per_step": ms_p, "kernel_launches_per_step": 2 * q},
+           "batched_over_plain": gb / gp,
+           "spread": {"batched": (max(ms_b) - min(ms_b)) / statistics.median(ms_b),
+                      "plain": (max(ms_p) - min(ms_p)) / statistics.median(ms_p)},
+           "padding_ratio": padded / cells, "cells_per_step": cells,
+           "configs": {f"{k[0]}x{k[1]}{'+tmem' if k[2] == mpf.TABLE_TENSOR else ''}": v
+                       for k, v in sorted(groups.items())},
+           "generate_s": gen_s}
+    log(f"{wl.name}: batched {gb:.0f} GCUPS, plain {gp:.0f}, ratio {gb / gp:.4f}, "
+        f"{launches} launches per batched step, padding {padded / cells:.3f}")
+    return out
 
 
 def run_profile_case(args):
@@ -653,6 +865,7 @@ UBENCH_OPS = [  # (code, name, unit) of the microbenchmarks in ubench/mpf_ubench
     (8, "vsubus4 (4x8-bit SIMD)", "lane-ops/clk/SM"), (9, "vmaxu4 (4x8-bit SIMD)", "lane-ops/clk/SM"),
     (10, "viaddmax.s16x2 + hfma2.relu pairs", "lane-ops/clk/SM"),
     (11, "viaddmax.s16x2 + prmt pairs", "lane-ops/clk/SM"),
+    (12, "dpx viaddmax.s32", "lane-ops/clk/SM"), (13, "dpx vimax3.s32", "lane-ops/clk/SM"),
     (20, "lds.128 conflict-free", "B/clk/SM"), (21, "tcgen05.ld 32x32b.x16 (TMEM)", "B/clk/SM"),
     (22, "lds.128 + tcgen05.ld together", "B/clk/SM"), (23, "shfl.bfly", "lane-ops/clk/SM"),
 ]
@@ -699,14 +912,22 @@ def main():
     ap.add_argument("--ref-sample", type=int, default=12000)
     ap.add_argument("--no-cpu", action="store_true")
     ap.add_argument("--arith", default="auto", choices=["auto", "i16", "f16"])
+    ap.add_argument("--table", default="auto", choices=["auto", "shared"],
+                    help="score-table memory of the striped kernels (auto: TMEM where it applies)")
     ap.add_argument("--no-serve", action="store_true")
+    ap.add_argument("--no-batch-workloads", dest="batch_workloads", action="store_false",
+                    help="skip the 64-query and 10 M-sequence batched-vs-plain measurements")
+    ap.add_argument("--w4-queries", type=int, default=16,
+                    help="queries of the 10 M-sequence workload in its batched-vs-plain measurement")
+    ap.add_argument("--no-f16-line", dest="f16_line", action="store_false",
+                    help="skip the extra fp16-cell measurement")
     ap.add_argument("--no-pipeline", dest="pipeline", action="store_false")
     ap.add_argument("--no-viterbi", dest="viterbi", action="store_false")
     ap.add_argument("--long-m", type=int, default=5000,
                     help="model length of the long-model measurement (0: skip)")
     ap.add_argument("--long-vit-seqs", type=int, default=40000,
                     help="sequences of the long-model Viterbi measurement")
-    ap.add_argument("--serve-rates", type=float, nargs="+", default=[5, 8, 10, 12, 15, 25, 100, 500])
+    ap.add_argument("--serve-rates", type=float, nargs="+", default=[5, 8, 10, 12, 20, 100, 500])
     ap.add_argument("--serve-requests", type=int, default=200)
     ap.add_argument("--serve-workload", type=int, default=3,
                     help="workload whose database the serving measurement uses (3: 5 M sequences)")

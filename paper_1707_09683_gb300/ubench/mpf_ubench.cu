@@ -15,7 +15,8 @@
 // The operations are the candidates for one packed cell update of the MSV /
 // SSV recurrences (Alg. 2, Alg. 7): 32-bit integer add, three-input logic
 // (LOP3), byte permute (PRMT), integer multiply-add (IMAD), the 16x2 DPX
-// forms (add-then-max, three-input max), fp16x2 fused multiply-add with
+// forms (add-then-max, three-input max; and the 32-bit forms of the Viterbi
+// filter), fp16x2 fused multiply-add with
 // ReLU, and the 4x8-bit SIMD intrinsics of the paper's Kepler kernels
 // (__vaddus4, __vsubus4, __vmaxu4).  The memory tests read 128-bit words
 // from shared memory, and 32-bit columns from tensor memory (TMEM, tcgen05.ld
@@ -48,6 +49,8 @@ enum Op : int {
   OP_VMAXU4 = 9,
   OP_DPX_ADDMAX_HFMA2 = 10,   // one DPX and one HFMA2 per step: do the pipes co-issue?
   OP_DPX_ADDMAX_PRMT = 11,    // one DPX and one PRMT per step
+  OP_DPX_ADDMAX_S32 = 12,     // 32-bit DPX forms (the Viterbi filter's cells)
+  OP_DPX_MAX3_S32 = 13,
   OP_LDS128 = 20,
   OP_TMEM_LD = 21,
   OP_LDS128_TMEM_LD = 22,
@@ -69,6 +72,10 @@ __device__ __forceinline__ uint32_t alu_step(uint32_t a, uint32_t b, uint32_t c)
     r = __viaddmax_s16x2(a, b, c);
   } else if constexpr (OP == OP_DPX_MAX3) {
     r = __vimax3_s16x2(a, b, c);
+  } else if constexpr (OP == OP_DPX_ADDMAX_S32) {
+    r = (uint32_t)__viaddmax_s32((int)a, (int)b, (int)c);
+  } else if constexpr (OP == OP_DPX_MAX3_S32) {
+    r = (uint32_t)__vimax3_s32((int)a, (int)b, (int)c);
   } else if constexpr (OP == OP_HFMA2_RELU) {
     const __half2 x = __hfma2_relu(*reinterpret_cast<const __half2 *>(&a),
                                    *reinterpret_cast<const __half2 *>(&b),
@@ -256,6 +263,8 @@ UbenchFn ubench_fn(int op) {
     case OP_VMAXU4: return ubench_alu<OP_VMAXU4>;
     case OP_DPX_ADDMAX_HFMA2: return ubench_alu<OP_DPX_ADDMAX_HFMA2>;
     case OP_DPX_ADDMAX_PRMT: return ubench_alu<OP_DPX_ADDMAX_PRMT>;
+    case OP_DPX_ADDMAX_S32: return ubench_alu<OP_DPX_ADDMAX_S32>;
+    case OP_DPX_MAX3_S32: return ubench_alu<OP_DPX_MAX3_S32>;
     case OP_LDS128: return ubench_mem<OP_LDS128>;
     case OP_TMEM_LD: return ubench_mem<OP_TMEM_LD>;
     case OP_LDS128_TMEM_LD: return ubench_mem<OP_LDS128_TMEM_LD>;
