@@ -369,7 +369,7 @@ def run_mpf(args):
     nsm = torch.cuda.get_device_properties(dev).multi_processor_count
     peak = r_int(dom_f, nsm, sm_mhz)
     f16 = args.arith == "f16"
-    mode_name = ("MSV_FAST" if dom_f == "msv" else "SSV") + ("_F16" if f16 else "") + (",TMEM" if dom_tm else "")
+    mode_name = ("MSV_HELD" if dom_f == "msv" else "SSV") + ("_F16" if f16 else "") + (",TMEM" if dom_tm else "")
     import hashlib
     src_ok = hashlib.sha256(open(KERNEL_SOURCE, "rb").read()).hexdigest() == KERNEL_SOURCE_SHA256
     kname = f"scan_kernel<{lanes},{words},{mode_name}>"

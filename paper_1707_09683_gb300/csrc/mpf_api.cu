@@ -274,7 +274,7 @@ int kernel_mode(const mpf_profile *p, int filter) {
   const bool f16 = p->arith[filter] == MPF_ARITH_F16;
   if (filter == MPF_SSV) return f16 ? MODE_SSV_F16 : MODE_SSV;
   if (!msv_fast_ok(p)) return MODE_MSV_DIRECT;
-  return f16 ? MODE_MSV_FAST_F16 : MODE_MSV_FAST;
+  return f16 ? MODE_MSV_HELD_F16 : MODE_MSV_HELD;
 }
 
 // Whether a striped scan of this profile reads its table from tensor memory:
@@ -515,6 +515,18 @@ int plan_create(mpf_ctx *ctx, int filter, const mpf_profile *const *profs, int n
       q.tail_off = t.geom.tail_off;
       q.tail_row_bytes = t.geom.tail_row_bytes;
       q.M = (uint32_t)p->M;
+      if (mode == MODE_MSV_HELD || mode == MODE_MSV_HELD_F16) {
+        // The integer table of the same layout, for the exact kernel that
+        // rescores the sequences the held pass lists.
+        DevTable ti = t;
+        if (mode == MODE_MSV_HELD_F16) rc = get_table(p, lanes, words, TABLE_I16, &ti);
+        if (rc) {
+          plan_free(pl);
+          return rc;
+        }
+        const int tm_h = use_tmem(p, filter, lanes, words, mode) ? 1 : 0;
+        fb_table[GroupKey(lanes, words, mode, tm_h)].push_back(reinterpret_cast<const uint8_t *>(ti.ptr));
+      }
     }
     q.bias = p->bias;
     q.tbm = p->tbm;
@@ -560,20 +572,25 @@ int plan_create(mpf_ctx *ctx, int filter, const mpf_profile *const *profs, int n
       g.col_bytes = (uint64_t)g.grid * kTileWarps * 2 * g.col_stride;
       e = cudaMallocAsync((void **)&g.d_col, g.col_bytes, ctx->stream);
     }
-    if (e == cudaSuccess && g.mode == MODE_TILE_MSV) {
-      // Fallback lists, and the lane-segment launch that scores them.
+    const bool held = g.mode == MODE_MSV_HELD || g.mode == MODE_MSV_HELD_F16;
+    if (e == cudaSuccess && (g.mode == MODE_TILE_MSV || held)) {
+      // Fallback lists, and the launch that scores them exactly: the
+      // lane-segment kernel after the tiled MSV pass, the striped kernel
+      // with the J/B update every row after the held pass.
       const size_t nq = kv.second.size(), ns = std::max<uint64_t>(db->n_seqs, 1);
       e = cudaMallocAsync((void **)&g.d_fallback, (nq + nq * ns) * 4, ctx->stream);
       if (e == cudaSuccess) {
         auto nx = std::make_shared<LaunchGroup>();
-        nx->mode = MODE_LONG_MSV;
+        nx->mode = held ? MODE_MSV_DIRECT : MODE_LONG_MSV;
+        nx->lanes = g.lanes;
+        nx->words = g.words;
         nx->n_codes = db->n_codes;
         std::vector<QueryDesc> fq = kv.second;
         for (size_t i = 0; i < nq; ++i) {
           kv.second[i].fallback_count = g.d_fallback + i;
           kv.second[i].fallback_ranks = g.d_fallback + nq + i * ns;
           fq[i].table = reinterpret_cast<const uint4 *>(fb_table[kv.first][i]);
-          fq[i].seg_words = fb_seg_words[kv.first][i];
+          if (!held) fq[i].seg_words = fb_seg_words[kv.first][i];
           fq[i].ranks = kv.second[i].fallback_ranks;
           fq[i].n_ranks = kv.second[i].fallback_count;
           nx->long_words = std::max(nx->long_words, fq[i].seg_words);

@@ -1,8 +1,8 @@
 // mpf_inst.cu -- scan-kernel instantiations for one lane-group size.
 //
 // Compiled once per size (-DMPF_LG=1, 2, 4, 8, 16, 32; see build.py) into
-// kernel_lg<MPF_LG>(): every mode of the striped scan kernel for each built
-// word count -- multiples of four, and the counts with a two-word tail.
+// kernel_lg<MPF_LG>(): every mode of the striped scan kernel (seven) for each
+// built word count -- multiples of four, and the counts with a two-word tail.
 // With -DMPF_LG=32 -DMPF_TM=1 it builds kernel_lg32_tm() instead: the
 // tensor-memory variants (every mode but MSV_DIRECT, at least kTmMinWords
 // words).
@@ -24,6 +24,8 @@ namespace mpf {
     if (mode == MODE_MSV_FAST) return scan_kernel<32, W, MODE_MSV_FAST, true>;             \
     if (mode == MODE_SSV_F16) return scan_kernel<32, W, MODE_SSV_F16, true>;               \
     if (mode == MODE_MSV_FAST_F16) return scan_kernel<32, W, MODE_MSV_FAST_F16, true>;     \
+    if (mode == MODE_MSV_HELD) return scan_kernel<32, W, MODE_MSV_HELD, true>;             \
+    if (mode == MODE_MSV_HELD_F16) return scan_kernel<32, W, MODE_MSV_HELD_F16, true>;     \
     return nullptr;
 
 KernelFn kernel_lg32_tm(int words, int mode) {
@@ -63,6 +65,8 @@ KernelFn kernel_lg32_tm(int words, int mode) {
     if (mode == MODE_MSV_DIRECT) return scan_kernel<MPF_LG, W, MODE_MSV_DIRECT>;     \
     if (mode == MODE_SSV_F16) return scan_kernel<MPF_LG, W, MODE_SSV_F16>;           \
     if (mode == MODE_MSV_FAST_F16) return scan_kernel<MPF_LG, W, MODE_MSV_FAST_F16>; \
+    if (mode == MODE_MSV_HELD) return scan_kernel<MPF_LG, W, MODE_MSV_HELD>;         \
+    if (mode == MODE_MSV_HELD_F16) return scan_kernel<MPF_LG, W, MODE_MSV_HELD_F16>; \
     return nullptr;
 
 KernelFn MPF_CAT(kernel_lg, MPF_LG)(int words, int mode) {

@@ -49,8 +49,12 @@ enum Mode : int {
   MODE_TILE_SSV = 7,      // models beyond kStripedMaxM, SSV: tile_kernel<SSV>
   MODE_TILE_MSV = 8,      // models beyond kStripedMaxM, MSV when b may be held: tile_kernel<MSV>
                           //   (with MODE_LONG_MSV over the sequences it leaves)
+  MODE_MSV_HELD = 9,      // Alg. 2 with the begin score held for the whole sequence: no per-row
+                          //   tests; sequences whose running maximum passes T are listed and
+                          //   rescored by MODE_MSV_DIRECT
+  MODE_MSV_HELD_F16 = 10, // MODE_MSV_HELD with cells as fp16 integers
 };
-constexpr int kNumModes = 5;   // modes of the striped scan kernel
+constexpr int kNumModes = 7;   // modes of the striped scan kernel
 
 // Striped kernels that read their table from tensor memory (one sequence per
 // warp): the first tm_words(words) words of each lane's row of every residue
@@ -68,7 +72,8 @@ __host__ __device__ constexpr int tm_words(int words) { return words <= kTmWords
 // Score-table formats: signed 16-bit integers, or the same integers as fp16.
 enum TableFormat : int { TABLE_I16 = 0, TABLE_F16 = 1 };
 inline int table_format(int mode) {
-  return (mode == MODE_SSV_F16 || mode == MODE_MSV_FAST_F16) ? TABLE_F16 : TABLE_I16;
+  return (mode == MODE_SSV_F16 || mode == MODE_MSV_FAST_F16 || mode == MODE_MSV_HELD_F16) ? TABLE_F16
+                                                                                           : TABLE_I16;
 }
 
 // One profile in one kernel layout (lives in device memory).
@@ -93,8 +98,8 @@ struct QueryDesc {
   // (a device count written by an earlier kernel on the same stream).
   const uint32_t *ranks;
   const uint32_t *n_ranks;
-  // Tiled MSV kernel: sequences it leaves to the exact lane-segment kernel
-  // (their ranks, and the count, zero before the launch).
+  // Tiled MSV kernel and MSV_HELD: sequences left to an exact kernel (their
+  // length ranks, and the count, zero before the launch).
   uint32_t *fallback_ranks;
   uint32_t *fallback_count;
 };

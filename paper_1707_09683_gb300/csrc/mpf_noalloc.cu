@@ -53,7 +53,11 @@ extern "C" int mpf_scan_noalloc(mpf_ctx *ctx, int filter, const mpf_profile *pro
   if (db->n_seqs == 0) return MPF_OK;
 
   if (prof->seg_words) return MPF_EUNSUPPORTED;   // long models need the table in device memory
-  const int mode = kernel_mode(prof, filter);
+  // The held-begin-score MSV lists sequences for a second kernel in device
+  // memory; here the MSV kernel that tests the threshold row by row runs.
+  int mode = kernel_mode(prof, filter);
+  if (mode == MODE_MSV_HELD) mode = MODE_MSV_FAST;
+  if (mode == MODE_MSV_HELD_F16) mode = MODE_MSV_FAST_F16;
   int lanes = prof->cfg_lanes[filter], words = prof->cfg_words[filter];
   if (!lanes) default_config(ctx, prof->M, mode, &lanes, &words);
   if (!lanes) return MPF_EUNSUPPORTED;

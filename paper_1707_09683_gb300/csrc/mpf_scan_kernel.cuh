@@ -129,9 +129,10 @@ __global__ void __launch_bounds__(kBlockThreads, 1) scan_kernel(ScanParams p) {
   static_assert(LG == 1 || LG == 2 || LG == 4 || LG == 8 || LG == 16 || LG == 32, "lanes");
   constexpr int NC = LG >= 8 ? 1 : 8 / LG;
   constexpr int G = 32 / LG;
-  constexpr bool kF16 = (MODE == MODE_SSV_F16 || MODE == MODE_MSV_FAST_F16);
+  constexpr bool kF16 = (MODE == MODE_SSV_F16 || MODE == MODE_MSV_FAST_F16 || MODE == MODE_MSV_HELD_F16);
   constexpr bool kSSV = (MODE == MODE_SSV || MODE == MODE_SSV_F16);
   constexpr bool kFast = (MODE == MODE_MSV_FAST || MODE == MODE_MSV_FAST_F16);
+  constexpr bool kHeld = (MODE == MODE_MSV_HELD || MODE == MODE_MSV_HELD_F16);
   constexpr bool kDirect = (MODE == MODE_MSV_DIRECT);
   const uint32_t one2 = 0x3c003c00u;   // (1.0, 1.0) as half2
   extern __shared__ __align__(16) uint8_t smem[];
@@ -419,7 +420,7 @@ __global__ void __launch_bounds__(kBlockThreads, 1) scan_kernel(ScanParams p) {
 
       // ---- finalise the G sequences -------------------------------------
       const int V = key_value<kF16>(group_max<LG>(half_max(vacc)));
-      if (kFast) {
+      if (kFast || kHeld) {
         // A sequence whose cells never rose above the begin score: its best
         // row maximum is the best single-cell score of its residues.
         const bool rescue = active && !done && !exact && V == 0 && len > 0;
@@ -434,7 +435,29 @@ __global__ void __launch_bounds__(kBlockThreads, 1) scan_kernel(ScanParams p) {
           }
         }
         g = group_max<LG>(g);
-        if (active && gl == 0) {
+        if (kHeld && active && gl == 0) {
+          // The begin score b was held for every row.  V, the largest cell
+          // of any row, decides: at or above 255 - bias - b some row
+          // overflowed (with b held or after it rose, cells only grow);
+          // at most T no row could move xJ past base, so the held rows are
+          // exact; in between xB would have moved: an exact kernel rescores
+          // the sequence.
+          if (V >= cap - b) {
+            out_raw[orig] = 255;
+            out_flag[orig] = 1;
+            if (out_nat) out_nat[orig] = __int_as_float(0x7f800000);
+          } else if (V > T) {
+            const uint32_t slot = atomicAdd(qd->fallback_count, 1u);
+            if (MPF_DCHECK(p.status, slot < p.n_seqs)) qd->fallback_ranks[slot] = (uint32_t)r;
+          } else {
+            const int G2 = V > 0 ? V : g;
+            const int raw = len > 0 ? max(0, b + G2 - tec) : 0;
+            out_raw[orig] = (uint8_t)raw;
+            out_flag[orig] = 0;
+            if (out_nat) out_nat[orig] = nat_score(raw - t - base, scale);
+          }
+        }
+        if (kFast && active && gl == 0) {
           int raw;
           uint8_t flag = 0;
           if (done) {

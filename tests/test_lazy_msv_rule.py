@@ -1,5 +1,6 @@
-"""The decision rule of the tiled MSV pass, restated in numpy, against the
-oracle (CPU).
+"""The decision rules of the MSV passes that hold the begin score (the tiled
+pass of long models and the striped kernels' held pass), restated in numpy,
+against the oracle (CPU).
 
 For models longer than the striped table the MSV kernel sweeps the model
 in tiles with the begin score b held at its initial value, where v =
@@ -12,7 +13,10 @@ which xB would move (the sequence is rescored exactly).  This test checks
 that every outcome but the last equals Alg. 2 as the oracle computes it,
 on random profiles that satisfy the rule's precondition (the begin path
 cannot saturate: sat(base - tjb - tbm) < 255 - bias), with enough strong
-profiles and planted hits that every outcome occurs.
+profiles and planted hits that every outcome occurs.  The striped held pass
+decides from the largest cell of the whole sequence instead of the first row
+above T: overflow at or above 255 - bias - b, exact at or below T, rescored
+in between.
 """
 import numpy as np
 import pytest
@@ -67,6 +71,34 @@ def lazy_msv(rec, seq):
     return max(0, b + g - rec.tec), 0
 
 
+def held_msv(rec, seq):
+    """(raw, flag) by the striped kernels' held pass (MSV_HELD), or None for
+    a sequence it lists for exact rescoring: b held for every row, V the
+    largest cell of any row; V >= 255 - bias - b is an overflow, V <= T
+    leaves the held rows exact, anything between is rescored."""
+    M, L = rec.M, len(seq)
+    s = rec.bias - np.vstack([rec.cost.astype(np.int64), np.full((32 - rec.K, M), 255, np.int64)])
+    t = _tjb(rec, L)
+    cap = 255 - rec.bias
+    b = min(_sat8(rec.base - (t + rec.tbm)), cap)
+    T = min(rec.base + rec.tec - b, cap - b - 1)
+    v = np.zeros(M, np.int64)
+    V = 0
+    for x in seq:
+        v = np.maximum(0, np.concatenate(([0], v[:-1])) + s[x])
+        V = max(V, int(v.max()))
+    if L == 0:
+        return 0, 0
+    if V >= cap - b:
+        return 255, 1
+    if V > T:
+        return None
+    if V > 0:
+        return max(0, b + V - rec.tec), 0
+    g = max(int(s[x].max()) for x in seq)
+    return max(0, b + g - rec.tec), 0
+
+
 def _cases(rng):
     """Realistic profiles with planted hits, and uniform profiles of several
     strengths, keeping those that hold b."""
@@ -85,8 +117,9 @@ def _cases(rng):
     return [(r, d) for r, d in out if _holds_b(r)]
 
 
+@pytest.mark.parametrize("rule", [lazy_msv, held_msv], ids=["tiled", "held"])
 @pytest.mark.parametrize("seed", range(3))
-def test_tiled_msv_rule_matches_alg2(seed):
+def test_tiled_msv_rule_matches_alg2(seed, rule):
     oracle.build()
     rng = np.random.default_rng(2024 + seed)
     outcomes = {"none": 0, "overflow": 0, "rescored": 0}
@@ -94,7 +127,7 @@ def test_tiled_msv_rule_matches_alg2(seed):
         raw, flag, _ = oracle.msv(rec, db.residues, db.offsets, db.lengths)
         for k in range(db.n_seqs):
             o, L = int(db.offsets[k]), int(db.lengths[k])
-            got = lazy_msv(rec, db.residues[o:o + L])
+            got = rule(rec, db.residues[o:o + L])
             if got is None:
                 outcomes["rescored"] += 1
                 continue
@@ -103,7 +136,8 @@ def test_tiled_msv_rule_matches_alg2(seed):
     assert all(n > 0 for n in outcomes.values()), outcomes
 
 
-def test_tiled_msv_rule_threshold_edges():
+@pytest.mark.parametrize("rule", [lazy_msv, held_msv], ids=["tiled", "held"])
+def test_tiled_msv_rule_threshold_edges(rule):
     """Scores placed on T, T + 1 and the overflow boundary 255 - bias - b
     (and one either side), on one- to three-node models, over every
     sequence of length 1 to 3: the threshold and the overflow test of the
@@ -139,7 +173,7 @@ def test_tiled_msv_rule_threshold_edges():
                 residues = np.concatenate(seqs)
                 raw, flag, _ = oracle.msv(rec, residues, offsets, lengths)
                 for k, sq in enumerate(seqs):
-                    got = lazy_msv(rec, sq)
+                    got = rule(rec, sq)
                     if got is not None:
                         assert got == (int(raw[k]), int(flag[k])), (bias, M, tgt, sq.tolist(), got)
                         checked += 1
