@@ -43,11 +43,12 @@ OPS_PER_CELL = {"msv": 4, "ssv": 2}
 # ncu captures summarised in profiles/, keyed by kernel, workload and model
 # length; only used while the kernel is the one that was captured.
 NCU_TRAFFIC = {
-    ("scan_kernel<32,38,MSV_FAST_F16>", "msweep_500k", 2405): 189.777664e6 + 3.572992e6,
-    ("scan_kernel<32,38,SSV_F16>", "msweep_500k", 2405): 188.351488e6 + 3.670272e6,
+    # held MSV pass + its exact rescoring launch (profiles/scan_kernel_tmem_m2405_msweep500k.md)
+    ("scan_kernel<32,38,MSV_HELD,TMEM>", "msweep_500k", 2405): 187.923200e6 + 3.751424e6 + 0.258816e6,
+    ("scan_kernel<32,38,SSV,TMEM>", "msweep_500k", 2405): 188.751872e6 + 3.784704e6,
 }
 KERNEL_SOURCE = os.path.join(ROOT, "paper_1707_09683_gb300", "csrc", "mpf_scan_kernel.cuh")
-KERNEL_SOURCE_SHA256 = "2108e2d70071f04ceb30dde837e24a4134888d53fbc1cfcc5811cb162b7a05d4"
+KERNEL_SOURCE_SHA256 = "f3e1653edc51ca18874d7d5ed0f1e363fa0a7ef91f0ecb29134c687bf56925f9"
 
 
 def log(*a):
@@ -298,16 +299,20 @@ def run_mpf(args):
         for f, _ in filters:
             plans[f].launch()
 
-    def time_steps(fn, k):
+    def time_steps(fn, k, name="timed"):
+        # NVTX range around the timed launches: a profiler can keep to them
+        # (ncu --nvtx --nvtx-include "timed_batched/").
         ev0 = torch.cuda.Event(enable_timing=True)
         ev1 = torch.cuda.Event(enable_timing=True)
         ctx.sync()
         barrier(world)
+        torch.cuda.nvtx.range_push(name)
         with torch.cuda.stream(stream):
             ev0.record(stream)
             for _ in range(k):
                 fn()
             ev1.record(stream)
+        torch.cuda.nvtx.range_pop()
         ev1.synchronize()
         ctx.sync()
         barrier(world)
@@ -317,7 +322,7 @@ def run_mpf(args):
         step_batched()
     ctx.sync()
     with ClockSampler(local) as clk:
-        ms_batched = time_steps(step_batched, args.steps)
+        ms_batched = time_steps(step_batched, args.steps, "timed_batched")
     clocks = clk.summary()
     ms_batched = max_over_ranks(ms_batched, world)
 
@@ -343,7 +348,7 @@ def run_mpf(args):
     for _ in range(args.warmup):
         step_plain()
     ctx.sync()
-    ms_plain = time_steps(step_plain, args.steps)
+    ms_plain = time_steps(step_plain, args.steps, "timed_plain")
     ms_plain = max_over_ranks(ms_plain, world)
     for _ in range(max(1, args.steps // 2)):
         for f, i, a, b in step_plain(record=True):
@@ -526,7 +531,8 @@ def run_mpf(args):
     # sequences), batched against plain.
     batch_workloads = None
     if world == 1 and args.batch_workloads:
-        batch_workloads = [run_batch_workload(args, ctx, 2, None, time_steps, dev),
+        batch_workloads = [run_small_workload(args, ctx, dev),
+                           run_batch_workload(args, ctx, 2, None, time_steps, dev),
                            run_batch_workload(args, ctx, 4, args.w4_queries, time_steps, dev)]
 
     # Serving: continuous batching of arriving queries (model lengths drawn as
@@ -786,6 +792,24 @@ def run_batch_workload(args, ctx, idx, n_queries, time_steps, dev, steps=3):
     db.close()
     gb = cells / (statistics.median(ms_b) * 1e-3) / 1e9
     gp = cells / (statistics.median(ms_p) * 1e-3) / 1e9
+    # The oracle on a bounded sample of the same workload (two queries).
+    cpu = None
+    if not args.no_cpu:
+        import oracle
+        rng = np.random.default_rng(31)
+        idx = np.sort(rng.choice(wl.db.n_seqs, size=min(3000, wl.db.n_seqs), replace=False)).astype(np.uint64)
+        sres = int(wl.db.lengths[idx.astype(np.int64)].sum())
+        picks = [wl.profiles[0], wl.profiles[len(wl.profiles) // 2]]
+        t_c = time.perf_counter()
+        for p in picks:
+            for f in (oracle.MSV, oracle.SSV):
+                oracle.scan(f, p, wl.db.residues, wl.db.offsets, wl.db.lengths, index=idx,
+                            nthreads=os.cpu_count() or 1)
+        dt = time.perf_counter() - t_c
+        ccells = 2 * sum(p.M for p in picks) * sres
+        cpu = {"value": ccells / dt / 1e9, "unit": "GCUPS", "cores": os.cpu_count() or 1, "kind": "oracle",
+               "sample": f"{idx.size} random sequences ({sres} residues) x queries M = "
+                         f"{[p.M for p in picks]} x MSV+SSV in {dt:.1f} s"}
     out = {"workload": wl.name, "queries": q, "n_seqs": n, "residues": res,
            "query_M": [p.M for p in wl.profiles] if q <= 16 else f"{min(p.M for p in wl.profiles)}-"
                                                                   f"{max(p.M for p in wl.profiles)}",
@@ -798,9 +822,59 @@ def run_batch_workload(args, ctx, idx, n_queries, time_steps, dev, steps=3):
            "padding_ratio": padded / cells, "cells_per_step": cells,
            "configs": {f"{k[0]}x{k[1]}{'+tmem' if k[2] == mpf.TABLE_TENSOR else ''}": v
                        for k, v in sorted(groups.items())},
-           "generate_s": gen_s}
+           "generate_s": gen_s, "cpu_baseline": cpu}
     log(f"{wl.name}: batched {gb:.0f} GCUPS, plain {gp:.0f}, ratio {gb / gp:.4f}, "
         f"{launches} launches per batched step, padding {padded / cells:.3f}")
+    return out
+
+
+def run_small_workload(args, ctx, dev, reps=5):
+    """The one-query workload (M = 100, 10,000 sequences, 3.5 M residues):
+    both filters, plain scans, each timed after writing a 512 MB buffer (the
+    database fits in L2, so the cache is flushed before every launch); the
+    oracle scores the whole database."""
+    import torch
+    import oracle
+    from paper_1707_09683_gb300 import mpf, synth
+    wl = synth.make_workload(0)
+    db = mpf.Database(ctx, wl.db.residues, wl.db.offsets, wl.db.lengths)
+    n, res = db.n_seqs, db.n_residues
+    prof = mpf.Profile(ctx, wl.profiles[0])
+    outs = [torch.empty(n, dtype=dt, device=dev) for dt in (torch.uint8, torch.uint8, torch.float32)]
+    flush = torch.empty(512 << 20, dtype=torch.uint8, device=dev)
+    stream = ctx.torch_stream()
+    out = {"workload": wl.name, "M": wl.profiles[0].M, "n_seqs": n, "residues": res,
+           "l2": "512 MB written before every timed launch"}
+    for name, code in (("msv", mpf.MSV), ("ssv", mpf.SSV)):
+        pl = mpf.Plan(ctx, code, [prof], db, *outs)
+        pl.launch()
+        ctx.sync()
+        ms = []
+        for _ in range(reps):
+            with torch.cuda.stream(stream):
+                flush.fill_(1)
+                a = torch.cuda.Event(enable_timing=True)
+                b = torch.cuda.Event(enable_timing=True)
+                a.record(stream)
+                pl.launch()
+                b.record(stream)
+            b.synchronize()
+            ms.append(a.elapsed_time(b))
+        pl.close()
+        out[name] = {"gcups": wl.profiles[0].M * res / (statistics.median(ms) * 1e-3) / 1e9,
+                     "ms": statistics.median(ms), "config": list(prof.get_config(code))}
+    if not args.no_cpu:
+        t_c = time.perf_counter()
+        for f in (oracle.MSV, oracle.SSV):
+            oracle.scan(f, wl.profiles[0], wl.db.residues, wl.db.offsets, wl.db.lengths,
+                        nthreads=os.cpu_count() or 1)
+        dt = time.perf_counter() - t_c
+        out["cpu_baseline"] = {"value": 2 * wl.profiles[0].M * res / dt / 1e9, "unit": "GCUPS",
+                               "cores": os.cpu_count() or 1, "kind": "oracle",
+                               "sample": f"the whole database, both filters, in {dt:.2f} s"}
+    prof.close()
+    db.close()
+    log(f"{wl.name}: MSV {out['msv']['gcups']:.0f} SSV {out['ssv']['gcups']:.0f} GCUPS")
     return out
 
 
@@ -927,7 +1001,7 @@ def main():
                     help="model length of the long-model measurement (0: skip)")
     ap.add_argument("--long-vit-seqs", type=int, default=40000,
                     help="sequences of the long-model Viterbi measurement")
-    ap.add_argument("--serve-rates", type=float, nargs="+", default=[5, 8, 10, 12, 20, 100, 500])
+    ap.add_argument("--serve-rates", type=float, nargs="+", default=[5, 8, 12, 20, 500])
     ap.add_argument("--serve-requests", type=int, default=200)
     ap.add_argument("--serve-workload", type=int, default=3,
                     help="workload whose database the serving measurement uses (3: 5 M sequences)")

@@ -47,3 +47,41 @@ def test_autotune_picks_a_candidate_and_keeps_parity(tmp_path):
     tuner.save()
     again = autotune.Autotuner(ctx, db, cache_path=cache)
     assert again.table == tuner.table
+
+
+def test_tuned_configurations_mixed_in_one_batch_match_the_oracle():
+    """Queries shaped like the 64-query workload (M uniform in [50, 2500],
+    planted segments), each tuned on the database -- lanes and words, shared
+    or tensor-memory table, shard factor -- then scored together by one
+    graph-captured batched plan per filter: every output equals the oracle."""
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    build.build()
+    oracle.build()
+    wl = synth.make_workload(2, n_seqs=12000, n_queries=6)
+    ctx = mpf.Context(0)
+    db = mpf.Database(ctx, wl.db.residues, wl.db.offsets, wl.db.lengths)
+    tuner = autotune.Autotuner(ctx, db, reps=1)
+    profs = [mpf.Profile(ctx, p) for p in wl.profiles]
+    for pr in profs:
+        for filt in (mpf.MSV, mpf.SSV):
+            tuner.tune(pr, filt)
+    n, q = db.n_seqs, len(profs)
+    dev = torch.device("cuda", 0)
+    for filt, of in ((mpf.MSV, oracle.MSV), (mpf.SSV, oracle.SSV)):
+        outs = [torch.empty(q * n, dtype=t, device=dev) for t in (torch.uint8, torch.uint8, torch.float32)]
+        plan = mpf.Plan(ctx, filt, profs, db, *outs)
+        plan.capture_graph()
+        plan.launch()
+        ctx.sync()
+        got = [t.cpu().numpy() for t in outs]
+        plan.close()
+        for i, rec in enumerate(wl.profiles):
+            exp = oracle.scan(of, rec, wl.db.residues, wl.db.offsets, wl.db.lengths, nthreads=8)
+            sl = slice(i * n, (i + 1) * n)
+            assert np.array_equal(got[0][sl], exp[0]) and np.array_equal(got[1][sl], exp[1]), (rec.M, filt)
+            assert np.array_equal(got[2][sl].view(np.uint32), exp[2].view(np.uint32)), (rec.M, filt)
+    for pr in profs:
+        pr.close()
+    db.close()
+    ctx.close()
