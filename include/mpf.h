@@ -254,7 +254,9 @@ int mpf_scan_batch(mpf_ctx *ctx, int filter, const mpf_profile *const *profs, in
  *   mpf_plan_launch:  enqueue one run (asynchronous).
  *   mpf_plan_capture_graph: record the run as a CUDA graph; later launches
  *                     replay the graph.  Call it outside any stream capture.
- *   mpf_plan_kernel_launches: kernels one run launches (>= 1).
+ *   mpf_plan_kernel_launches: scan kernels one run launches (>= 1), the
+ *                     exact-rescoring launches after held or tiled MSV passes
+ *                     included.
  *   mpf_plan_destroy: waits for the context stream, then frees the plan.
  */
 typedef struct mpf_plan mpf_plan;

@@ -1158,7 +1158,13 @@ int mpf_plan_capture_graph(mpf_plan *plan) {
   return MPF_OK;
 }
 
-int mpf_plan_kernel_launches(const mpf_plan *plan) { return plan ? (int)plan->groups.size() : 0; }
+int mpf_plan_kernel_launches(const mpf_plan *plan) {
+  if (!plan) return 0;
+  int n = 0;
+  for (const LaunchGroup &g0 : plan->groups)
+    for (const LaunchGroup *g = &g0; g; g = g->next.get()) ++n;   // with the rescoring launches
+  return n;
+}
 
 int mpf_pipeline_scan(mpf_ctx *ctx, const mpf_profile *const *profs, int n_q, const mpf_db *db,
                       float ssv_min_nat, uint8_t *ssv_raw, uint8_t *ssv_flag, float *ssv_nat,
