@@ -79,6 +79,16 @@ __device__ __forceinline__ uint32_t pack2(int v) {
 
 __device__ __forceinline__ int sat8(int v) { return min(255, max(0, v)); }
 
+// PTX prmt in its default mode: each selector nibble picks one of the eight
+// bytes of (a, b) with its low three bits, and with its high bit set copies
+// that byte's sign bit into all eight bits (the CUDA __byte_perm intrinsic
+// uses only the low three bits).
+__device__ __forceinline__ uint32_t prmt(uint32_t a, uint32_t b, uint32_t sel) {
+  uint32_t r;
+  asm("prmt.b32 %0, %1, %2, %3;" : "=r"(r) : "r"(a), "r"(b), "r"(sel));
+  return r;
+}
+
 template <int LG>
 __device__ __forceinline__ int group_max(int v) {
 #pragma unroll
@@ -142,6 +152,11 @@ __global__ void __launch_bounds__(kBlockThreads, 1) scan_kernel(ScanParams p) {
   const int lane = threadIdx.x & 31;
   const int gl = lane & (LG - 1);
   const int grp = lane / LG;
+  // Byte selector of the diagonal shift: bytes 2, 3 of the lane before's last
+  // word, then bytes 0, 1 of this lane's.  With integer cells (0 .. 32767)
+  // the group's first lane takes the sign copies of its own byte 1, which
+  // are zero; fp16 cells zero it with a select instead.
+  const uint32_t shift_sel = (LG > 1 && gl != 0) ? 0x5432u : 0x54ddu;
   const uint32_t n_items = p.n_queries * p.n_shards;
   const int warp = (int)(threadIdx.x >> 5);
   uint32_t tm_lane = 0;   // TMEM address of this warp's lane quarter, column 0
@@ -167,6 +182,12 @@ __global__ void __launch_bounds__(kBlockThreads, 1) scan_kernel(ScanParams p) {
     // selected ranks the database (the item is skipped otherwise).
     if (!MPF_DCHECK(p.status, qd->table_bytes <= dynamic_smem_bytes() && p.pad_word < p.n_words &&
                                   (!qd->ranks || *qd->n_ranks <= p.n_seqs))) {
+      __syncthreads();
+      continue;
+    }
+    // A shard without sequences (a short rank list, such as the few
+    // sequences a held MSV pass leaves for rescoring) stages nothing.
+    if ((uint64_t)shard >= (qd->ranks ? (uint64_t)*qd->n_ranks : (uint64_t)p.n_seqs)) {
       __syncthreads();
       continue;
     }
@@ -291,13 +312,13 @@ __global__ void __launch_bounds__(kBlockThreads, 1) scan_kernel(ScanParams p) {
           // Rows past the end of a sequence read padding codes: their cells
           // score kNegInf, and the special states must not see them.
           const bool real = active && (4 * step + rr) < len;
-          uint32_t x = (cur >> (8 * rr)) & 0xffu;
+          uint32_t x = __byte_perm(cur, 0u, 0x4440u + rr);   // residue code of row rr
           if (!MPF_DCHECK(p.status, x < (uint32_t)kTableRows)) x = kPadCode;
           if constexpr (TM) {
             // This row's TMEM words (issued one row earlier), then the next
             // row's loads: a wait covers every earlier load of the thread.
             tm_wait_ld<HT>(Tc);
-            tm_ld<HT>(Tn, tm_col(rr < 3 ? (cur >> (8 * (rr + 1))) & 0xffu : nxt & 0xffu));
+            tm_ld<HT>(Tn, tm_col(rr < 3 ? __byte_perm(cur, 0u, 0x4440u + rr + 1) : nxt & 0xffu));
           }
           const uint8_t *rowp = tbl_lane + x * row_bytes;
           // Diagonal shift (Alg. 5): cell k-1 of the previous row feeds cell k.
@@ -305,9 +326,12 @@ __global__ void __launch_bounds__(kBlockThreads, 1) scan_kernel(ScanParams p) {
           uint32_t up = 0u;
           if (LG > 1) {
             up = __shfl_up_sync(kFull, wl, 1, LG);
-            if (gl == 0) up = 0u;
+            if (kF16 && gl == 0) up = 0u;
           }
-          const uint32_t mpv = __byte_perm(up, wl, 0x5432);
+          // Cell k - 1 of the previous row: the lane before's last cell and
+          // this lane's high-half cell of the last word.  The group's first
+          // lane takes zero instead, as sign copies of a non-negative cell.
+          const uint32_t mpv = prmt(up, wl, kF16 ? 0x5432u : shift_sel);
           uint32_t rmax = 0u;
           // Update word q from the previous row's word q - 1 and score word sc.
           auto cell = [&](const int q, const uint32_t sc) {

@@ -235,6 +235,28 @@ def test_edge_databases(ctx):
         check_profile(ctx, p, db)
 
 
+def test_tensor_memory_table_edge_databases(ctx):
+    """The TMEM kernels (whole-warp configurations, both filters, the held MSV
+    pass with its rescoring launch) on the edge databases: all sequences
+    empty, a single residue, one 20,000-residue sequence, many 1-8 residue
+    ones, and a mix of empty and long sequences; profiles with all words in
+    TMEM (8 and 14 words) and with part in shared memory (38 words)."""
+    rng = np.random.default_rng(55)
+    cases = [
+        synth.Database(np.zeros(0, np.uint8), np.zeros(3, np.uint64), np.zeros(3, np.uint32)),
+        synth.Database(np.array([4], np.uint8), np.zeros(1, np.uint64), np.ones(1, np.uint32)),
+        synth.make_database(1, 20000, 20000, 20000, rng),
+        synth.make_database(3000, 3, 1, 8, rng),
+    ]
+    mix = synth.make_database(400, 300, 0, 4000, rng)
+    mix.lengths[::3] = 0
+    cases.append(synth.Database(mix.residues, mix.offsets, mix.lengths))
+    for words in (8, 14, 38):
+        p = synth.make_profile(64 * words - 9, rng)
+        for db in cases:
+            check_profile(ctx, p, db, configs=[(32, words)])
+
+
 def test_saturated_bias_and_empty_sequences(ctx):
     """bias = 255 puts the MSV overflow threshold at 0: every non-empty
     sequence overflows at its first row, an empty one never does; padding
