@@ -739,9 +739,13 @@ def run_serving(wl_serv, rates, n_requests, device, seed=3, work_budget_queries=
 def run_batch_workload(args, ctx, idx, n_queries, time_steps, dev, steps=3):
     """Batched vs plain on a many-query workload: every query against the
     whole database with both filters, default kernel configurations.
-    Batched: one graph-captured plan per filter; plain: one launch per query
-    and filter.  Padding: the padded cells the kernels compute (model padded
-    to whole lane stripes) per model cell."""
+    Batched: one graph-captured plan per filter, queries of fewer than 32
+    lanes packed 32 / lanes to a warp where that pays; plain: one launch per
+    query and filter; batched_unpacked: the same plans with packing turned
+    off (the tables of the queries of fewer than 32 lanes set to shared
+    memory, which their plain scans use anyway).  Padding: the padded cells the kernels compute (model padded
+    to whole lane stripes, packed queries to their set's words, empty slots
+    of a set counted) per model cell."""
     import torch
     from paper_1707_09683_gb300 import mpf, synth
     t0 = time.time()
@@ -756,12 +760,24 @@ def run_batch_workload(args, ctx, idx, n_queries, time_steps, dev, steps=3):
     plans = {f: mpf.Plan(ctx, code, profs, db, *outs[f]) for f, code in filters}
     for pl in plans.values():
         pl.capture_graph()
+    narrow = [(pr, code) for pr in profs for _, code in filters if pr.get_config(code)[0] < 32]
+    for pr, code in narrow:
+        pr.set_table_memory(code, mpf.TABLE_SHARED)
+    unpacked = {f: mpf.Plan(ctx, code, profs, db, *outs[f]) for f, code in filters}
+    for pr, code in narrow:
+        pr.set_table_memory(code, mpf.TABLE_AUTO)
+    for pl in unpacked.values():
+        pl.capture_graph()
     plain = {f: [mpf.Plan(ctx, code, [pr], db, *(t[i * n:(i + 1) * n] for t in outs[f]))
                  for i, pr in enumerate(profs)] for f, code in filters}
 
     def step_b():
         for f, _ in filters:
             plans[f].launch()
+
+    def step_u():
+        for f, _ in filters:
+            unpacked[f].launch()
 
     def step_p():
         for f, _ in filters:
@@ -770,27 +786,39 @@ def run_batch_workload(args, ctx, idx, n_queries, time_steps, dev, steps=3):
 
     for _ in range(2):
         step_b()
+        step_u()
         step_p()
-    ms_b, ms_p = [], []
-    for _ in range(steps):            # interleaved, so drift hits both forms alike
+    ms_b, ms_u, ms_p = [], [], []
+    for _ in range(steps):            # interleaved, so drift hits every form alike
         ms_b.append(time_steps(step_b, 1))
+        ms_u.append(time_steps(step_u, 1))
         ms_p.append(time_steps(step_p, 1))
     cells = 2 * sum(p.M for p in wl.profiles) * res
-    padded = 0
-    groups = {}
+    padded = 0                        # plain scans: each query in its own layout
     for pr, rec in zip(profs, wl.profiles):
         for f, code in filters:
             lanes, words = pr.get_config(code)
             padded += (2 * lanes * words if words else rec.M) * res
-            key = (lanes, words, pr.get_table_memory(code))
-            groups[key] = groups.get(key, 0) + 1
+    padded_b = 0                      # batched plans: as their launch groups run
+    groups = {}
+    for (f, code), pl in zip(filters, plans.values()):
+        m_other = sum(rec.M for pr, rec in zip(profs, wl.profiles) if not pr.get_config(code)[1])
+        for g in pl.groups():
+            if g["words"]:
+                slots = -(-g["n_queries"] // g["queries_per_warp"]) * g["queries_per_warp"]
+                padded_b += slots * 2 * g["lanes"] * g["words"] * res
+            key = (g["lanes"], g["words"], g["table"], g["queries_per_warp"])
+            groups[key] = groups.get(key, 0) + g["n_queries"]
+        padded_b += m_other * res
+    packed = sum(v for k, v in groups.items() if k[3] > 1)
     launches = sum(pl.kernel_launches for pl in plans.values())
-    for pl in list(plans.values()) + [p for f in plain for p in plain[f]]:
+    for pl in list(plans.values()) + list(unpacked.values()) + [p for f in plain for p in plain[f]]:
         pl.close()
     for pr in profs:
         pr.close()
     db.close()
     gb = cells / (statistics.median(ms_b) * 1e-3) / 1e9
+    gu = cells / (statistics.median(ms_u) * 1e-3) / 1e9
     gp = cells / (statistics.median(ms_p) * 1e-3) / 1e9
     # The oracle on a bounded sample of the same workload (two queries).
     cpu = None
@@ -814,17 +842,24 @@ def run_batch_workload(args, ctx, idx, n_queries, time_steps, dev, steps=3):
            "query_M": [p.M for p in wl.profiles] if q <= 16 else f"{min(p.M for p in wl.profiles)}-"
                                                                   f"{max(p.M for p in wl.profiles)}",
            "batched": {"gcups": gb, "ms_per_step": ms_b, "kernel_launches_per_step": launches,
-                       "form": "one graph-captured plan per filter"},
-           "plain": {"gcups": gp, "ms_per_step": ms_p, "kernel_launches_per_step": 2 * q},
+                       "form": "one graph-captured plan per filter",
+                       "packed_query_filters": packed, "padding_ratio": padded_b / cells},
+           "batched_unpacked": {"gcups": gu, "ms_per_step": ms_u,
+                                "form": "the same plans, queries of fewer than 32 lanes unpacked"},
+           "plain": {"gcups": gp, "ms_per_step": ms_p, "kernel_launches_per_step": 2 * q,
+                     "padding_ratio": padded / cells},
            "batched_over_plain": gb / gp,
+           "batched_unpacked_over_plain": gu / gp,
            "spread": {"batched": (max(ms_b) - min(ms_b)) / statistics.median(ms_b),
+                      "batched_unpacked": (max(ms_u) - min(ms_u)) / statistics.median(ms_u),
                       "plain": (max(ms_p) - min(ms_p)) / statistics.median(ms_p)},
            "padding_ratio": padded / cells, "cells_per_step": cells,
-           "configs": {f"{k[0]}x{k[1]}{'+tmem' if k[2] == mpf.TABLE_TENSOR else ''}": v
-                       for k, v in sorted(groups.items())},
+           "configs": {f"{k[0]}x{k[1]}{'+tmem' if k[2] == mpf.TABLE_TENSOR else ''}"
+                       f"{f'/{k[3]}q' if k[3] > 1 else ''}": v for k, v in sorted(groups.items())},
            "generate_s": gen_s, "cpu_baseline": cpu}
-    log(f"{wl.name}: batched {gb:.0f} GCUPS, plain {gp:.0f}, ratio {gb / gp:.4f}, "
-        f"{launches} launches per batched step, padding {padded / cells:.3f}")
+    log(f"{wl.name}: batched {gb:.0f} GCUPS (unpacked {gu:.0f}), plain {gp:.0f}, ratio {gb / gp:.4f}, "
+        f"{launches} launches per batched step, {packed} packed query-filters, "
+        f"padding batched {padded_b / cells:.3f} plain {padded / cells:.3f}")
     return out
 
 

@@ -247,7 +247,13 @@ int mpf_scan_batch(mpf_ctx *ctx, int filter, const mpf_profile *const *profs, in
  * the database and the output buffers of a batch; launching it enqueues the
  * scan on the context stream without host synchronisation or allocation.
  * Queries whose kernel configurations differ run as separate kernels that
- * overlap (forked streams, joined back into the context stream).
+ * overlap (forked streams, joined back into the context stream).  In a plan
+ * of two or more queries, those with 8 or 16 lanes per sequence (integer
+ * SSV, held MSV, table memory not set to MPF_TABLE_SHARED, at least 8 words)
+ * are packed 32 / lanes to a warp: the warp scores one sequence against
+ * all of them, with the score rows in tensor memory.  Packed queries are
+ * sorted by words per lane and each takes the largest word count of its set
+ * (the added nodes score as padding: the outputs do not change).
  *   mpf_plan_create:  arguments as mpf_scan_batch; raw/overflow/nat must be
  *                     device pointers (MPF_EINVAL otherwise).  The plan keeps
  *                     pointers to the profiles and database: they must outlive it.
@@ -257,6 +263,15 @@ int mpf_scan_batch(mpf_ctx *ctx, int filter, const mpf_profile *const *profs, in
  *   mpf_plan_kernel_launches: scan kernels one run launches (>= 1), the
  *                     exact-rescoring launches after held or tiled MSV passes
  *                     included.
+ *   mpf_plan_group_count: launch groups of the plan (the kernels of one run
+ *                     before any rescoring launch); 0 for a NULL plan.
+ *   mpf_plan_group_info: group i's kernel configuration: lanes per sequence,
+ *                     words per lane (0: tiled or long-model kernel), where
+ *                     its table is read from (MPF_TABLE_SHARED or
+ *                     MPF_TABLE_TENSOR), queries scored per warp and
+ *                     sequence (1, or 32 / lanes when packed) and its number
+ *                     of queries.  Any output pointer may be NULL;
+ *                     MPF_EINVAL for a NULL plan or i out of range.
  *   mpf_plan_destroy: waits for the context stream, then frees the plan.
  */
 typedef struct mpf_plan mpf_plan;
@@ -266,6 +281,9 @@ int mpf_plan_create(mpf_ctx *ctx, int filter, const mpf_profile *const *profs, i
 int mpf_plan_launch(mpf_plan *plan);
 int mpf_plan_capture_graph(mpf_plan *plan);
 int mpf_plan_kernel_launches(const mpf_plan *plan);
+int mpf_plan_group_count(const mpf_plan *plan);
+int mpf_plan_group_info(const mpf_plan *plan, int i, int *lanes, int *words, int *table_memory,
+                        int *queries_per_warp, int *n_queries);
 void mpf_plan_destroy(mpf_plan *plan);
 
 /*

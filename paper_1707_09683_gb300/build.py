@@ -52,6 +52,7 @@ def _newest_header() -> float:
 # The scan-kernel instantiations: one source compiled once per lane-group size.
 INST_SRC = "mpf_inst.cu"
 INST_LANES = (1, 2, 4, 8, 16, 32)
+QP_LANES = (1, 2, 4, 8, 16)   # packed tensor-memory variants: 32 / lanes queries per warp
 
 
 def _units():
@@ -62,6 +63,7 @@ def _units():
         if base == INST_SRC:
             units += [(src, f"mpf_inst_lg{lg}.o", [f"-DMPF_LG={lg}"]) for lg in INST_LANES]
             units.append((src, "mpf_inst_lg32_tm.o", ["-DMPF_LG=32", "-DMPF_TM=1"]))
+            units += [(src, f"mpf_inst_qp{lg}_tm.o", [f"-DMPF_LG={lg}", "-DMPF_QP=1"]) for lg in QP_LANES]
         else:
             units.append((src, base.replace(".cu", ".o"), []))
     # The largest units first, so the parallel build ends sooner.

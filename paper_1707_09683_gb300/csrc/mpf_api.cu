@@ -40,6 +40,16 @@ KernelFn kernel_for(int lanes, int words, int mode) {
     default: return nullptr;
   }
 }
+KernelFn kernel_qp_tm(int lanes, int words, int mode) {
+  switch (lanes) {
+    case 1: return kernel_qp_tm_lg1(words, mode);
+    case 2: return kernel_qp_tm_lg2(words, mode);
+    case 4: return kernel_qp_tm_lg4(words, mode);
+    case 8: return kernel_qp_tm_lg8(words, mode);
+    case 16: return kernel_qp_tm_lg16(words, mode);
+    default: return nullptr;
+  }
+}
 }  // namespace mpf
 
 // ---------------------------------------------------------------- helpers --
@@ -143,7 +153,7 @@ int get_table(const mpf_profile *p, int lanes, int words, int fmt, DevTable *out
     *out = it->second;
     return MPF_OK;
   }
-  const TableGeom g = table_geom(lanes, words);
+  const TableGeom g = table_geom(lanes, words, fmt == TABLE_I16_PACKED);
   std::vector<uint8_t> img(g.table_bytes, 0);
   fill_table_image(p, g, fmt, img.data());
   mpf_ctx *ctx = p->ctx;
@@ -309,6 +319,9 @@ struct LaunchGroup {
   uint32_t *d_fallback = nullptr;   // tiled MSV: per query a count, then n_seqs ranks per query
   bool tm = false;                  // striped kernel with the table in tensor memory
   int shard_factor = 1;             // striped kernels: shards = factor x resident blocks
+  uint32_t n_real = 0;              // queries of the group (n_queries less empty slots of packed sets)
+  int qp = 1;                       // tensor-memory kernels: queries scored per warp and sequence
+  uint32_t qp_stride = 0;           //   and shared-memory bytes per staged table (qp > 1)
   std::shared_ptr<LaunchGroup> next;   // launched after this group on the same stream
 };
 
@@ -416,9 +429,12 @@ int configure_kernel(mpf_ctx *ctx, LaunchGroup *g) {
     g->n_shards = (uint32_t)g->grid;
     return MPF_OK;
   }
-  g->fn = g->tm ? kernel_lg32_tm(g->words, g->mode) : kernel_for(g->lanes, g->words, g->mode);
+  g->fn = g->qp > 1 ? kernel_qp_tm(g->lanes, g->words, g->mode)
+         : g->tm    ? kernel_lg32_tm(g->words, g->mode)
+                    : kernel_for(g->lanes, g->words, g->mode);
   if (!g->fn) return MPF_EINVAL;
-  g->smem = (uint32_t)smem_need(g->lanes, g->words);
+  g->smem = g->qp > 1 ? (uint32_t)g->qp * g->qp_stride : (uint32_t)smem_need(g->lanes, g->words);
+  if (g->smem > (uint32_t)ctx->max_smem) return MPF_EUNSUPPORTED;
   // A block with the table in tensor memory takes all of the SM's TMEM
   // columns: ask for more than half the shared memory, so no second block of
   // the kernel is placed on the SM.
@@ -447,12 +463,31 @@ int plan_create(mpf_ctx *ctx, int filter, const mpf_profile *const *profs, int n
   if (!pl) return MPF_ENOMEM;
   pl->ctx = ctx;
   pl->db = db;
-  // Launch groups by (lanes, words, mode, table in tensor memory).
-  using GroupKey = std::tuple<int, int, int, int>;
+  // Launch groups by (lanes, words, mode, table in tensor memory, queries
+  // per warp).
+  using GroupKey = std::tuple<int, int, int, int, int>;
   std::map<GroupKey, std::vector<QueryDesc>> byconf;
-  std::map<GroupKey, std::vector<const uint8_t *>> fb_table;   // tiled MSV: long tables
+  std::map<GroupKey, std::vector<DevTable>> fb_table;   // tables of the exact rescoring launch
   std::map<GroupKey, std::vector<uint32_t>> fb_seg_words;
   std::map<GroupKey, int> group_shards;   // largest shard factor of a group's profiles
+  // Queries that may share a warp's sequence with others (8 or 16 lanes,
+  // integer SSV or held MSV), by (lanes, mode): placed after the loop.
+  struct QpCand {
+    int words, sf;
+    const mpf_profile *p;
+    QueryDesc q;
+    DevTable fb;
+  };
+  std::map<std::pair<int, int>, std::vector<QpCand>> qp_cand;
+  auto set_table = [](QueryDesc &q, const DevTable &t) {
+    q.table = t.ptr;
+    q.table_bytes = t.geom.table_bytes;
+    q.row_bytes = t.geom.row_bytes;
+    q.copy_bytes = t.geom.copy_bytes;
+    q.smax_off = t.geom.smax_off;
+    q.tail_off = t.geom.tail_off;
+    q.tail_row_bytes = t.geom.tail_row_bytes;
+  };
   for (int i = 0; i < n_q; ++i) {
     const mpf_profile *p = profs[i];
     if (!p || p->ctx->device != ctx->device) {
@@ -460,6 +495,7 @@ int plan_create(mpf_ctx *ctx, int filter, const mpf_profile *const *profs, int n
       return MPF_EINVAL;
     }
     const int mode = kernel_mode(p, filter);
+    DevTable fb{};   // held MSV: the integer table of the rescoring launch
     QueryDesc q;
     memset(&q, 0, sizeof(q));
     int lanes = 32, words = 0;
@@ -480,8 +516,10 @@ int plan_create(mpf_ctx *ctx, int filter, const mpf_profile *const *profs, int n
           plan_free(pl);
           return rc;
         }
-        fb_table[GroupKey(lanes, words, mode, 0)].push_back(lt);
-        fb_seg_words[GroupKey(lanes, words, mode, 0)].push_back((uint32_t)p->seg_words);
+        DevTable lt_t{};
+        lt_t.ptr = reinterpret_cast<uint4 *>(const_cast<uint8_t *>(lt));
+        fb_table[GroupKey(lanes, words, mode, 0, 1)].push_back(lt_t);
+        fb_seg_words[GroupKey(lanes, words, mode, 0, 1)].push_back((uint32_t)p->seg_words);
       }
     } else if (p->seg_words) {
       const uint8_t *lt = nullptr;
@@ -507,13 +545,7 @@ int plan_create(mpf_ctx *ctx, int filter, const mpf_profile *const *profs, int n
         plan_free(pl);
         return rc;
       }
-      q.table = t.ptr;
-      q.table_bytes = t.geom.table_bytes;
-      q.row_bytes = t.geom.row_bytes;
-      q.copy_bytes = t.geom.copy_bytes;
-      q.smax_off = t.geom.smax_off;
-      q.tail_off = t.geom.tail_off;
-      q.tail_row_bytes = t.geom.tail_row_bytes;
+      set_table(q, t);
       q.M = (uint32_t)p->M;
       if (mode == MODE_MSV_HELD || mode == MODE_MSV_HELD_F16) {
         // The integer table of the same layout, for the exact kernel that
@@ -524,8 +556,7 @@ int plan_create(mpf_ctx *ctx, int filter, const mpf_profile *const *profs, int n
           plan_free(pl);
           return rc;
         }
-        const int tm_h = use_tmem(p, filter, lanes, words, mode) ? 1 : 0;
-        fb_table[GroupKey(lanes, words, mode, tm_h)].push_back(reinterpret_cast<const uint8_t *>(ti.ptr));
+        fb = ti;
       }
     }
     q.bias = p->bias;
@@ -543,9 +574,92 @@ int plan_create(mpf_ctx *ctx, int filter, const mpf_profile *const *profs, int n
     q.ranks = ranks ? ranks + off : nullptr;
     q.n_ranks = ranks ? n_ranks + i : nullptr;
     const int tm = p->seg_words ? 0 : (use_tmem(p, filter, lanes, words, mode) ? 1 : 0);
-    byconf[GroupKey(lanes, words, mode, tm)].push_back(q);
-    int &sf = group_shards[GroupKey(lanes, words, mode, tm)];
-    sf = std::max(sf, p->seg_words ? 1 : p->shard_factor[filter]);
+    const int sf = p->seg_words ? 1 : p->shard_factor[filter];
+    if (n_q >= 2 && !ranks && !p->seg_words && lanes < 32 &&
+        (mode == MODE_SSV || mode == MODE_MSV_HELD) && words >= kTmMinWords &&
+        p->table_mem[filter] != MPF_TABLE_SHARED) {
+      qp_cand[std::make_pair(lanes, mode)].push_back(QpCand{words, sf, p, q, fb});
+      continue;
+    }
+    const GroupKey key(lanes, words, mode, tm, 1);
+    byconf[key].push_back(q);
+    if (fb.ptr) fb_table[key].push_back(fb);
+    group_shards[key] = std::max(group_shards[key], sf);
+  }
+  // Several queries per warp: 32 / lanes queries of one (lanes, mode) score
+  // the same sequence in one warp, with the table rows in tensor memory.
+  // Sorted by words per lane, runs of consecutive queries form a warp's set,
+  // all padded to the run's largest word count H (padding nodes score
+  // kNegInf, so the scores are those of the query's own layout), with their
+  // tables in the packed geometry; empty slots of a set hold descriptors
+  // without a table.  The runs minimise a cost in warp-words per sequence
+  // row: a set costs (32 / lanes) x H, a query left to its one-query kernel
+  // its own words x 5/4 (those kernels read every word from shared memory
+  // and run at about 4/5 of the tensor-memory kernels' rate).  A set needs
+  // two queries, a built kernel for H and tables that fit the block's shared
+  // memory.  The held MSV pass's rescoring launch (one query per warp) reads
+  // the integer table of the usual geometry at H words.
+  for (auto &kv : qp_cand) {
+    const int lanes = kv.first.first, mode = kv.first.second, QP = 32 / lanes;
+    std::vector<QpCand> &v = kv.second;
+    std::stable_sort(v.begin(), v.end(), [](const QpCand &a, const QpCand &b) { return a.words < b.words; });
+    const size_t n = v.size();
+    auto packable = [&](int H) {
+      return kernel_qp_tm(lanes, H, mode) != nullptr &&
+             (uint64_t)QP * packed_table_stride(lanes, H) <= (uint64_t)ctx->max_smem;
+    };
+    // cost[b]: least cost of the first b queries; from[b]: start of the last
+    // run (b - 1 for a query on its own).
+    std::vector<int64_t> cost(n + 1, 0);
+    std::vector<size_t> from(n + 1, 0);
+    for (size_t b = 1; b <= n; ++b) {
+      cost[b] = cost[b - 1] + 5 * (int64_t)v[b - 1].words;   // costs x 4
+      from[b] = b - 1;
+      const int H = v[b - 1].words;
+      if (!packable(H)) continue;
+      for (size_t a = b >= (size_t)QP ? b - (size_t)QP : 0; a + 2 <= b; ++a) {
+        const int64_t c = cost[a] + 4 * (int64_t)QP * H;
+        if (c < cost[b]) {
+          cost[b] = c;
+          from[b] = a;
+        }
+      }
+    }
+    std::vector<std::pair<size_t, size_t>> runs;
+    for (size_t b = n; b > 0; b = from[b]) runs.emplace_back(from[b], b);
+    std::reverse(runs.begin(), runs.end());
+    for (const auto &r : runs) {
+      const size_t a = r.first, b = r.second;
+      const bool pack = b - a >= 2;
+      const int H = v[b - 1].words;
+      const GroupKey key0(lanes, H, mode, 1, QP);
+      for (size_t j = a; j < b; ++j) {
+        QueryDesc q = v[j].q;
+        DevTable fb = v[j].fb;
+        if (pack) {
+          DevTable t;
+          int rc = get_table(v[j].p, lanes, H, TABLE_I16_PACKED, &t);
+          if (rc == MPF_OK && mode == MODE_MSV_HELD) rc = get_table(v[j].p, lanes, H, TABLE_I16, &fb);
+          if (rc) {
+            plan_free(pl);
+            return rc;
+          }
+          set_table(q, t);
+        }
+        const GroupKey key = pack ? key0 : GroupKey(lanes, v[j].words, mode, 0, 1);
+        byconf[key].push_back(q);
+        if (mode == MODE_MSV_HELD) fb_table[key].push_back(fb);
+        group_shards[key] = std::max(group_shards[key], v[j].sf);
+      }
+      if (pack) {
+        QueryDesc empty;
+        memset(&empty, 0, sizeof(empty));
+        for (size_t j = b - a; j < (size_t)QP; ++j) {
+          byconf[key0].push_back(empty);
+          if (mode == MODE_MSV_HELD) fb_table[key0].push_back(DevTable{});
+        }
+      }
+    }
   }
   DeviceGuard dg(ctx->device);
   for (auto &kv : byconf) {
@@ -554,6 +668,8 @@ int plan_create(mpf_ctx *ctx, int filter, const mpf_profile *const *profs, int n
     g.words = std::get<1>(kv.first);
     g.mode = std::get<2>(kv.first);
     g.tm = std::get<3>(kv.first) != 0;
+    g.qp = std::get<4>(kv.first);
+    if (g.qp > 1) g.qp_stride = packed_table_stride(g.lanes, g.words);
     g.shard_factor = group_shards[kv.first];
     for (const QueryDesc &qd : kv.second) g.long_words = std::max(g.long_words, qd.seg_words);
     g.n_codes = db->n_codes;
@@ -563,6 +679,7 @@ int plan_create(mpf_ctx *ctx, int filter, const mpf_profile *const *profs, int n
       return rc;
     }
     g.n_queries = (uint32_t)kv.second.size();
+    for (const QueryDesc &qd : kv.second) g.n_real += qd.table ? 1u : 0u;
     cudaError_t e = cudaMallocAsync((void **)&g.d_queries, sizeof(QueryDesc) * kv.second.size(), ctx->stream);
     if (e == cudaSuccess) e = cudaMallocAsync((void **)&g.d_counter, sizeof(uint32_t), ctx->stream);
     if (e == cudaSuccess && (g.mode == MODE_TILE_SSV || g.mode == MODE_TILE_MSV)) {
@@ -585,15 +702,22 @@ int plan_create(mpf_ctx *ctx, int filter, const mpf_profile *const *profs, int n
         nx->lanes = g.lanes;
         nx->words = g.words;
         nx->n_codes = db->n_codes;
-        std::vector<QueryDesc> fq = kv.second;
+        std::vector<QueryDesc> fq;   // the group's queries (not the empty slots of packed sets)
         for (size_t i = 0; i < nq; ++i) {
           kv.second[i].fallback_count = g.d_fallback + i;
           kv.second[i].fallback_ranks = g.d_fallback + nq + i * ns;
-          fq[i].table = reinterpret_cast<const uint4 *>(fb_table[kv.first][i]);
-          if (!held) fq[i].seg_words = fb_seg_words[kv.first][i];
-          fq[i].ranks = kv.second[i].fallback_ranks;
-          fq[i].n_ranks = kv.second[i].fallback_count;
-          nx->long_words = std::max(nx->long_words, fq[i].seg_words);
+          if (!kv.second[i].table) continue;
+          QueryDesc f = kv.second[i];
+          if (held) {
+            set_table(f, fb_table[kv.first][i]);
+          } else {
+            f.table = fb_table[kv.first][i].ptr;
+            f.seg_words = fb_seg_words[kv.first][i];
+          }
+          f.ranks = kv.second[i].fallback_ranks;
+          f.n_ranks = kv.second[i].fallback_count;
+          nx->long_words = std::max(nx->long_words, f.seg_words);
+          fq.push_back(f);
         }
         g.next = nx;
         int rc2 = configure_kernel(ctx, nx.get());
@@ -602,12 +726,13 @@ int plan_create(mpf_ctx *ctx, int filter, const mpf_profile *const *profs, int n
           plan_free(pl);
           return rc2;
         }
-        nx->n_queries = (uint32_t)nq;
-        e = cudaMallocAsync((void **)&nx->d_queries, sizeof(QueryDesc) * nq, ctx->stream);
+        nx->n_queries = (uint32_t)fq.size();
+        nx->n_real = nx->n_queries;
+        e = cudaMallocAsync((void **)&nx->d_queries, sizeof(QueryDesc) * fq.size(), ctx->stream);
         if (e == cudaSuccess) e = cudaMallocAsync((void **)&nx->d_counter, sizeof(uint32_t), ctx->stream);
         if (e == cudaSuccess)
-          e = cudaMemcpyAsync(nx->d_queries, fq.data(), sizeof(QueryDesc) * nq, cudaMemcpyHostToDevice,
-                              ctx->stream);
+          e = cudaMemcpyAsync(nx->d_queries, fq.data(), sizeof(QueryDesc) * fq.size(),
+                              cudaMemcpyHostToDevice, ctx->stream);
       }
     }
     if (e == cudaSuccess)
@@ -664,7 +789,9 @@ int enqueue_group(const mpf_db *db, mpf_ctx *ctx, LaunchGroup &g, cudaStream_t s
   sp.tile_col = g.d_col;
   sp.tile_col_stride = g.col_stride;
   sp.tile_col_bytes = g.col_bytes;
-  const int grid = (int)std::min<uint64_t>((uint64_t)g.grid, (uint64_t)g.n_queries * g.n_shards);
+  sp.qp_table_stride = g.qp_stride;
+  const uint64_t n_items = ((uint64_t)g.n_queries + (uint64_t)g.qp - 1) / (uint64_t)g.qp * g.n_shards;
+  const int grid = (int)std::min<uint64_t>((uint64_t)g.grid, n_items);
   g.fn<<<grid, g.threads, g.smem, st>>>(sp);
   MPF_CUDA(cudaGetLastError());
   if (g.next) return enqueue_group(db, ctx, *g.next, st);
@@ -1164,6 +1291,20 @@ int mpf_plan_kernel_launches(const mpf_plan *plan) {
   for (const LaunchGroup &g0 : plan->groups)
     for (const LaunchGroup *g = &g0; g; g = g->next.get()) ++n;   // with the rescoring launches
   return n;
+}
+
+int mpf_plan_group_count(const mpf_plan *plan) { return plan ? (int)plan->groups.size() : 0; }
+
+int mpf_plan_group_info(const mpf_plan *plan, int i, int *lanes, int *words, int *table_memory,
+                        int *queries_per_warp, int *n_queries) {
+  if (!plan || i < 0 || (size_t)i >= plan->groups.size()) return MPF_EINVAL;
+  const LaunchGroup &g = plan->groups[(size_t)i];
+  if (lanes) *lanes = g.lanes;
+  if (words) *words = g.words;
+  if (table_memory) *table_memory = g.tm ? MPF_TABLE_TENSOR : MPF_TABLE_SHARED;
+  if (queries_per_warp) *queries_per_warp = g.qp;
+  if (n_queries) *n_queries = (int)g.n_real;
+  return MPF_OK;
 }
 
 int mpf_pipeline_scan(mpf_ctx *ctx, const mpf_profile *const *profs, int n_q, const mpf_db *db,

@@ -5,7 +5,9 @@
 // built word count -- multiples of four, and the counts with a two-word tail.
 // With -DMPF_LG=32 -DMPF_TM=1 it builds kernel_lg32_tm() instead: the
 // tensor-memory variants (every mode but MSV_DIRECT, at least kTmMinWords
-// words).
+// words).  With -DMPF_QP=1 (lanes 1 to 16) it builds kernel_qp_tm_lg<lanes>():
+// the tensor-memory variants that score one sequence against 32 / lanes
+// queries per warp (integer SSV and the held MSV pass).
 #include "mpf_scan_kernel.cuh"
 
 #ifndef MPF_LG
@@ -16,7 +18,43 @@
 
 namespace mpf {
 
-#if defined(MPF_TM) && MPF_LG == 32
+#if defined(MPF_QP)
+
+#define MPF_WORDS_CASE(W)                                                                             \
+  case W:                                                                                             \
+    if (mode == MODE_SSV) return scan_kernel<MPF_LG, W, MODE_SSV, true, 32 / MPF_LG>;                 \
+    if (mode == MODE_MSV_HELD) return scan_kernel<MPF_LG, W, MODE_MSV_HELD, true, 32 / MPF_LG>;       \
+    return nullptr;
+
+KernelFn MPF_CAT(kernel_qp_tm_lg, MPF_LG)(int words, int mode) {
+  switch (words) {
+    MPF_WORDS_CASE(8)
+    MPF_WORDS_CASE(10)
+    MPF_WORDS_CASE(12)
+    MPF_WORDS_CASE(14)
+    MPF_WORDS_CASE(16)
+    MPF_WORDS_CASE(18)
+    MPF_WORDS_CASE(20)
+    MPF_WORDS_CASE(22)
+    MPF_WORDS_CASE(24)
+    MPF_WORDS_CASE(26)
+    MPF_WORDS_CASE(28)
+    MPF_WORDS_CASE(30)
+    MPF_WORDS_CASE(32)
+    MPF_WORDS_CASE(34)
+    MPF_WORDS_CASE(36)
+    MPF_WORDS_CASE(38)
+    MPF_WORDS_CASE(40)
+    MPF_WORDS_CASE(42)
+    MPF_WORDS_CASE(44)
+    MPF_WORDS_CASE(46)
+    MPF_WORDS_CASE(48)
+    default:
+      return nullptr;
+  }
+}
+
+#elif defined(MPF_TM) && MPF_LG == 32
 
 #define MPF_WORDS_CASE(W)                                                                  \
   case W:                                                                                  \

@@ -70,7 +70,9 @@ constexpr int kTmMinWords = 8;      // fewer words per lane: the shared-memory k
 __host__ __device__ constexpr int tm_words(int words) { return words <= kTmWordsAll ? words : kTmWordsPart; }
 
 // Score-table formats: signed 16-bit integers, or the same integers as fp16.
-enum TableFormat : int { TABLE_I16 = 0, TABLE_F16 = 1 };
+// TABLE_I16_PACKED: integer scores in the packed geometry (one copy of each
+// region; the tables of the queries that share a warp's sequence).
+enum TableFormat : int { TABLE_I16 = 0, TABLE_F16 = 1, TABLE_I16_PACKED = 16 };
 inline int table_format(int mode) {
   return (mode == MODE_SSV_F16 || mode == MODE_MSV_FAST_F16 || mode == MODE_MSV_HELD_F16) ? TABLE_F16
                                                                                            : TABLE_I16;
@@ -121,6 +123,7 @@ struct ScanParams {
   uint8_t *tile_col;          // tiled kernel: per resident warp two columns of
   uint32_t tile_col_stride;   //   tile_col_stride bytes (an int16 per row)
   uint64_t tile_col_bytes;
+  uint32_t qp_table_stride;   // striped kernels with several queries per warp: bytes per staged table
 };
 
 typedef void (*KernelFn)(ScanParams);
@@ -231,6 +234,14 @@ int viterbi_shape_key(bool fast, int Mpad, int n_codes, int max_smem, int num_sm
 KernelFn kernel_for(int lanes, int words, int mode);
 // The tensor-memory variant (lanes = 32), or nullptr if not built.
 KernelFn kernel_lg32_tm(int words, int mode);
+// Tensor-memory variants that score one sequence against 32 / lanes queries
+// per warp (lanes 1 to 16), or nullptr if not built.
+KernelFn kernel_qp_tm(int lanes, int words, int mode);
+KernelFn kernel_qp_tm_lg1(int words, int mode);
+KernelFn kernel_qp_tm_lg2(int words, int mode);
+KernelFn kernel_qp_tm_lg4(int words, int mode);
+KernelFn kernel_qp_tm_lg8(int words, int mode);
+KernelFn kernel_qp_tm_lg16(int words, int mode);
 KernelFn kernel_lg1(int words, int mode);
 KernelFn kernel_lg2(int words, int mode);
 KernelFn kernel_lg4(int words, int mode);
@@ -251,29 +262,44 @@ KernelFn kernel_lg32(int words, int mode);
 // Tail region: a 64-bit load runs in phases of 16 lanes; each residue row is
 // 128 bytes (256 for 32-lane groups) holding 16 / lanes copies of the
 // group's 8-byte chunks side by side, and group g reads copy g mod copies.
+// Packed geometry (the tables of queries that share a warp's sequence, each
+// staged at its own offset): one copy of each region, tail rows of lanes x 8
+// bytes.
 struct TableGeom {
   int lanes, words, copies, quads, tail_words, tail_copies;
   uint32_t row_bytes, copy_bytes, tail_off, tail_row_bytes, smax_off, table_bytes;
 };
 
-inline TableGeom table_geom(int lanes, int words) {
+inline TableGeom table_geom(int lanes, int words, bool packed = false) {
   TableGeom g;
   g.lanes = lanes;
   g.words = words;
   g.quads = words / 4;
   g.tail_words = words % 4;
-  g.copies = lanes >= 8 ? 1 : 8 / lanes;
+  g.copies = (packed || lanes >= 8) ? 1 : 8 / lanes;
   uint32_t row = (uint32_t)g.quads * (uint32_t)lanes * 16u;
   if (g.copies > 1) row = (row + 127u) & ~127u;
   g.row_bytes = row;
   g.copy_bytes = (uint32_t)kTableRows * row + (g.copies > 1 ? (uint32_t)lanes * 16u : 0u);
   g.tail_off = (uint32_t)g.copies * g.copy_bytes;
   g.tail_off = (g.tail_off + 127u) & ~127u;
-  g.tail_copies = lanes >= 16 ? 1 : 16 / lanes;
-  g.tail_row_bytes = g.tail_words ? (uint32_t)(lanes >= 16 ? lanes * 8 : 128) : 0u;
+  g.tail_copies = (packed || lanes >= 16) ? 1 : 16 / lanes;
+  g.tail_row_bytes = g.tail_words ? (uint32_t)(g.tail_copies * lanes * 8) : 0u;
   g.smax_off = g.tail_off + (uint32_t)kTableRows * g.tail_row_bytes;
-  g.table_bytes = g.smax_off + 80u;   // 33 int16 rounded up to 16 bytes
+  g.table_bytes = (g.smax_off + 80u + 15u) & ~15u;   // 33 int16, whole 16-byte chunks
   return g;
+}
+
+// Shared-memory bytes between the staged tables of a packed warp set
+// (32 / lanes queries).  Rows of a phase's groups sit at the same table
+// offset, so the stride spreads them over the banks: it is a multiple of
+// 128 bytes plus lanes * 16 (at most 64; 0 for 16 lanes), which puts the
+// 8 / lanes groups of a 128-bit phase on distinct 16-byte bank groups and
+// the two 8-lane groups of a 64-bit tail phase on distinct halves.
+inline uint32_t packed_table_stride(int lanes, int words) {
+  const uint32_t tb = table_geom(lanes, words, true).table_bytes;
+  const uint32_t off = lanes >= 16 ? 0u : (uint32_t)(lanes * 16 < 64 ? lanes * 16 : 64);
+  return ((tb + 127u) & ~127u) + off;
 }
 
 }  // namespace mpf

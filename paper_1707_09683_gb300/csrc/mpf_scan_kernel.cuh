@@ -127,10 +127,12 @@ __device__ __forceinline__ uint32_t pack2_half(int v) {
   return (h << 16) | h;
 }
 
-template <int LG, int H, int MODE, bool TM = false>
+template <int LG, int H, int MODE, bool TM = false, int QP = 1>
 __global__ void __launch_bounds__(kBlockThreads, 1) scan_kernel(ScanParams p) {
   static_assert((H % 4 == 0 || H % 4 == 2) && H >= 4 && H <= kMaxWords, "words per lane");
-  static_assert(!TM || (LG == 32 && H >= kTmMinWords && MODE != MODE_MSV_DIRECT), "tensor-memory variant");
+  static_assert(!TM || ((LG == 32 || QP * LG == 32) && H >= kTmMinWords && MODE != MODE_MSV_DIRECT),
+                "tensor-memory variant");
+  static_assert(QP == 1 || (TM && QP * LG == 32), "queries per warp");
   constexpr int HT = TM ? tm_words(H) : 0;   // words per lane from TMEM
   static_assert(HT == H || HT % 4 == 0, "shared-memory words start on a chunk");
   constexpr int Q = H / 4;               // full 4-word chunks per lane and row
@@ -140,6 +142,7 @@ __global__ void __launch_bounds__(kBlockThreads, 1) scan_kernel(ScanParams p) {
   constexpr int NC = LG >= 8 ? 1 : 8 / LG;
   constexpr int G = 32 / LG;
   constexpr bool kF16 = (MODE == MODE_SSV_F16 || MODE == MODE_MSV_FAST_F16 || MODE == MODE_MSV_HELD_F16);
+  static_assert(QP == 1 || !kF16, "packed sets use integer cells");
   constexpr bool kSSV = (MODE == MODE_SSV || MODE == MODE_SSV_F16);
   constexpr bool kFast = (MODE == MODE_MSV_FAST || MODE == MODE_MSV_FAST_F16);
   constexpr bool kHeld = (MODE == MODE_MSV_HELD || MODE == MODE_MSV_HELD_F16);
@@ -157,7 +160,10 @@ __global__ void __launch_bounds__(kBlockThreads, 1) scan_kernel(ScanParams p) {
   // the group's first lane takes the sign copies of its own byte 1, which
   // are zero; fp16 cells zero it with a select instead.
   const uint32_t shift_sel = (LG > 1 && gl != 0) ? 0x5432u : 0x54ddu;
-  const uint32_t n_items = p.n_queries * p.n_shards;
+  // QP > 1: the 32 / LG groups of a warp score one sequence against QP
+  // queries (the QP consecutive queries of a work item), so every lane of
+  // the warp reads the same residue and the TMEM column of a row is uniform.
+  const uint32_t n_items = (p.n_queries + QP - 1) / QP * p.n_shards;
   const int warp = (int)(threadIdx.x >> 5);
   uint32_t tm_lane = 0;   // TMEM address of this warp's lane quarter, column 0
   if constexpr (TM) {
@@ -177,11 +183,19 @@ __global__ void __launch_bounds__(kBlockThreads, 1) scan_kernel(ScanParams p) {
     const uint32_t item = s_item;
     if (item >= n_items) break;
     const uint32_t shard = item % p.n_shards;
-    const QueryDesc *qd = p.queries + item / p.n_shards;
+    const uint32_t qbase = item / p.n_shards * QP;
+    const uint32_t qi = qbase + (QP > 1 ? (uint32_t)grp : 0u);
+    // QP > 1: a set may have empty slots (descriptors without a table, after
+    // its queries), and the last item fewer queries.
+    const bool qvalid = qi < p.n_queries && (QP == 1 || p.queries[qi].table != nullptr);
+    const QueryDesc *qd = p.queries + (qvalid ? qi : qbase);
+    const uint32_t tstride = QP > 1 ? p.qp_table_stride : 0u;   // shared-memory bytes per query's table
     // Debug builds: the table must fit the block's shared memory and the
     // selected ranks the database (the item is skipped otherwise).
-    if (!MPF_DCHECK(p.status, qd->table_bytes <= dynamic_smem_bytes() && p.pad_word < p.n_words &&
-                                  (!qd->ranks || *qd->n_ranks <= p.n_seqs))) {
+    if (!MPF_DCHECK(p.status, (QP > 1 ? qd->table_bytes <= tstride && tstride % 16 == 0 &&
+                                            QP * tstride <= dynamic_smem_bytes() && !qd->ranks
+                                      : qd->table_bytes <= dynamic_smem_bytes()) &&
+                                  p.pad_word < p.n_words && (!qd->ranks || *qd->n_ranks <= p.n_seqs))) {
       __syncthreads();
       continue;
     }
@@ -192,29 +206,40 @@ __global__ void __launch_bounds__(kBlockThreads, 1) scan_kernel(ScanParams p) {
       continue;
     }
 
-    {  // stage the striped table (16-byte vector copies, coalesced)
-      const uint32_t nvec = qd->table_bytes >> 4;
-      const uint4 *src = qd->table;
-      uint4 *dst = reinterpret_cast<uint4 *>(smem);
+    // Stage the striped table(s) (16-byte vector copies, coalesced); with
+    // QP > 1 query g's table at g * tstride.
+#pragma unroll 1
+    for (int g = 0; g < QP; ++g) {
+      if (qbase + (uint32_t)g >= p.n_queries) break;
+      const QueryDesc *qg = p.queries + qbase + g;
+      if (!qg->table) continue;
+      const uint32_t nvec = qg->table_bytes >> 4;
+      const uint4 *src = qg->table;
+      uint4 *dst = reinterpret_cast<uint4 *>(smem + (uint32_t)g * tstride);
       for (uint32_t i = threadIdx.x; i < nvec; i += blockDim.x) dst[i] = __ldg(src + i);
     }
     __syncthreads();
+    // A group past the last query computes on the first query's table and
+    // writes nothing (its lanes must still follow the warp's sequence).
+    const uint8_t *tbl_base = smem + (QP > 1 && qvalid ? (uint32_t)grp * tstride : 0u);
+    const uint8_t *tbl_lane = tbl_base + (QP > 1 ? 0u : (grp % NC) * qd->copy_bytes) + gl * 16;
+    // QP > 1: packed tables (one copy of each region; the table stride
+    // spreads the groups of a phase over the banks).
+    const uint8_t *tail_lane = tbl_base + qd->tail_off + ((QP > 1 ? 0 : grp % NT) * LG + gl) * 8;
     if constexpr (TM) {
-      // Copy the first HT words of every lane's row of the TMEM codes from the
+      // Copy the first HT words of every lane's row of every code from the
       // staged table into tensor memory: warp q < 4 writes lane quarter q.
       tm_fence_after();
       if (warp < 4) {
-        const uint8_t *lane_tbl = smem + lane * 16;
-        const uint8_t *lane_tail = smem + qd->tail_off + lane * 8;
         for (uint32_t x = 0; x < (uint32_t)kTableRows; ++x) {
           const uint32_t col = tm_lane + x * (uint32_t)HT;
 #pragma unroll
           for (int j = 0; j < HT / 4; ++j) {
-            const uint4 s4 = *reinterpret_cast<const uint4 *>(lane_tbl + x * qd->row_bytes + j * 32 * 16);
+            const uint4 s4 = *reinterpret_cast<const uint4 *>(tbl_lane + x * qd->row_bytes + j * LG * 16);
             tm_st4(col + 4 * j, s4.x, s4.y, s4.z, s4.w);
           }
           if constexpr (HT % 4 == 2) {   // HT == H: the two tail words
-            const uint2 t2 = *reinterpret_cast<const uint2 *>(lane_tail + x * qd->tail_row_bytes);
+            const uint2 t2 = *reinterpret_cast<const uint2 *>(tail_lane + x * qd->tail_row_bytes);
             tm_st2(col + 4 * (HT / 4), t2.x, t2.y);
           }
         }
@@ -234,20 +259,19 @@ __global__ void __launch_bounds__(kBlockThreads, 1) scan_kernel(ScanParams p) {
     uint8_t *out_raw = qd->raw;
     uint8_t *out_flag = qd->flag;
     float *out_nat = qd->nat;
-    const uint8_t *tbl_lane = smem + (grp % NC) * qd->copy_bytes + gl * 16;
     const uint32_t row_bytes = qd->row_bytes;
-    const uint8_t *tail_lane = smem + qd->tail_off + ((grp % NT) * LG + gl) * 8;
     const uint32_t tail_row_bytes = qd->tail_row_bytes;
-    const int16_t *smax = reinterpret_cast<const int16_t *>(smem + qd->smax_off);
+    const int16_t *smax = reinterpret_cast<const int16_t *>(tbl_base + qd->smax_off);
     const uint32_t *ranks = qd->ranks;
     const uint64_t n_sel = ranks ? (uint64_t)*qd->n_ranks : (uint64_t)p.n_seqs;
 
     for (;;) {
-      // ---- take G consecutive length ranks of this shard (one per group) ----
+      // ---- take G consecutive length ranks of this shard (one per group;
+      // QP > 1: one rank, the same sequence for every group) ----
       uint32_t k0 = 0;
-      if (lane == 0) k0 = atomicAdd(&s_next, (uint32_t)G);
+      if (lane == 0) k0 = atomicAdd(&s_next, QP > 1 ? 1u : (uint32_t)G);
       k0 = __shfl_sync(kFull, k0, 0);
-      const uint64_t kr = (uint64_t)shard + (uint64_t)(k0 + grp) * p.n_shards;
+      const uint64_t kr = (uint64_t)shard + (uint64_t)(k0 + (QP > 1 ? 0 : grp)) * p.n_shards;
       bool active = kr < n_sel;
       if (!__any_sync(kFull, active)) break;
       const uint64_t r = (ranks && active) ? (uint64_t)__ldg(ranks + kr) : kr;
@@ -443,6 +467,7 @@ __global__ void __launch_bounds__(kBlockThreads, 1) scan_kernel(ScanParams p) {
       if constexpr (TM) tm_wait_ld<HT>(TA);   // the load issued after the last row
 
       // ---- finalise the G sequences -------------------------------------
+      const bool own = active && qvalid;   // this group writes its sequence's outputs
       const int V = key_value<kF16>(group_max<LG>(half_max(vacc)));
       if (kFast || kHeld) {
         // A sequence whose cells never rose above the begin score: its best
@@ -459,7 +484,7 @@ __global__ void __launch_bounds__(kBlockThreads, 1) scan_kernel(ScanParams p) {
           }
         }
         g = group_max<LG>(g);
-        if (kHeld && active && gl == 0) {
+        if (kHeld && own && gl == 0) {
           // The begin score b was held for every row.  V, the largest cell
           // of any row, decides: at or above 255 - bias - b some row
           // overflowed (with b held or after it rose, cells only grow);
@@ -481,7 +506,7 @@ __global__ void __launch_bounds__(kBlockThreads, 1) scan_kernel(ScanParams p) {
             if (out_nat) out_nat[orig] = nat_score(raw - t - base, scale);
           }
         }
-        if (kFast && active && gl == 0) {
+        if (kFast && own && gl == 0) {
           int raw;
           uint8_t flag = 0;
           if (done) {
@@ -498,14 +523,14 @@ __global__ void __launch_bounds__(kBlockThreads, 1) scan_kernel(ScanParams p) {
           if (out_nat) out_nat[orig] = flag ? __int_as_float(0x7f800000) : nat_score(raw - t - base, scale);
         }
       } else if (kDirect) {
-        if (active && gl == 0) {
+        if (own && gl == 0) {
           const int raw = done ? 255 : xJ;
           out_raw[orig] = (uint8_t)raw;
           out_flag[orig] = done ? 1 : 0;
           if (out_nat) out_nat[orig] = done ? __int_as_float(0x7f800000) : nat_score(raw - t - base, scale);
         }
       } else {  // SSV
-        if (active && gl == 0) {
+        if (own && gl == 0) {
           const bool ovf = V >= 255;
           const int raw = ovf ? 255 : V;
           out_raw[orig] = (uint8_t)raw;

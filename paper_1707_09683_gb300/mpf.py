@@ -76,6 +76,8 @@ def load(path: str = LIB_PATH):
         "mpf_plan_launch": (i32, [vp]),
         "mpf_plan_capture_graph": (i32, [vp]),
         "mpf_plan_kernel_launches": (i32, [vp]),
+        "mpf_plan_group_count": (i32, [vp]),
+        "mpf_plan_group_info": (i32, [vp, i32, vp, vp, vp, vp, vp]),
         "mpf_plan_destroy": (None, [vp]),
         "mpf_scan_noalloc": (i32, [vp, i32, vp, vp, vp, vp, vp]),
         "mpf_profile_footprint": (i32, [vp, i32, vp, vp]),
@@ -378,6 +380,19 @@ class Plan:
     @property
     def kernel_launches(self) -> int:
         return int(load().mpf_plan_kernel_launches(self.handle))
+
+    def groups(self):
+        """Per launch group: dict(lanes, words, table, queries_per_warp,
+        n_queries), as ``mpf_plan_group_info`` reports them."""
+        lib = load()
+        out = []
+        for i in range(int(lib.mpf_plan_group_count(self.handle))):
+            v = [ctypes.c_int() for _ in range(5)]
+            _check(lib.mpf_plan_group_info(self.handle, i, *[ctypes.byref(x) for x in v]),
+                   "mpf_plan_group_info")
+            out.append(dict(zip(("lanes", "words", "table", "queries_per_warp", "n_queries"),
+                                (x.value for x in v))))
+        return out
 
     def close(self):
         if getattr(self, "handle", None):

@@ -2,7 +2,8 @@
 
 Every kernel family runs on the debug library over inputs that exercise its
 ragged edges -- striped scans in every lane-group size (and through the
-allocation-free entry point), rank lists from the
+allocation-free entry point), packed sets of queries sharing a warp's
+sequence, rank lists from the
 SSV -> MSV hand-off, long models through the tiled kernels (with the MSV
 fallback list) and the lane-segment kernel with 16-bit and byte rows, the
 Viterbi kernels and variants (rows in shared or device memory), the MSV ->
@@ -74,6 +75,30 @@ for M, lanes, words in ((48, 1, 24), (100, 2, 26), (100, 4, 14), (300, 8, 20), (
         for g, w in zip(out, want):
             assert same(g.cpu().numpy()[idx.astype(np.int64)], w), (M, gf)
     p.close()
+
+# Packed sets: queries of 1 to 16 lanes sharing a warp's sequence (one set
+# with an empty slot), in one plan per filter.
+cfgs = [(1, 14)] * 27 + [(4, 26)] * 7 + [(8, 22)] * 4 + [(16, 18)] * 2
+recs = [synth.make_profile(2 * l * w - 1, rng) for l, w in cfgs]
+profs = [mpf.Profile(ctx, r) for r in recs]
+for gf, of in ((mpf.MSV, oracle.MSV), (mpf.SSV, oracle.SSV)):
+    for pr, (l, w) in zip(profs, cfgs):
+        pr.set_config(gf, l, w)
+    q = len(profs)
+    out = [torch.empty(q * n, dtype=t, device=dev) for t in (torch.uint8, torch.uint8, torch.float32)]
+    pl = mpf.Plan(ctx, gf, profs, db, *out)
+    assert max(g["queries_per_warp"] for g in pl.groups()) == 32, pl.groups()
+    pl.launch()
+    ctx.sync()
+    pl.close()
+    idx = np.arange(0, n, 5, dtype=np.uint64)
+    for i in (0, 26, 27, 33, 34, 38, 39):
+        want = oracle.scan(of, recs[i], dbh.residues, dbh.offsets, dbh.lengths, index=idx, nthreads=8)
+        for g, w in zip(out, want):
+            got = g[i * n:(i + 1) * n].cpu().numpy()[idx.astype(np.int64)]
+            assert same(got, w), ("packed", i, gf)
+for pr in profs:
+    pr.close()
 
 # The allocation-free entry point (its kernel reports through the context's
 # status word too).

@@ -323,6 +323,96 @@ def test_batch_and_graph_equal_single_scans(ctx):
             assert_same(tuple(a[sl] for a in graph), exp, f"graph q{i}")
 
 
+def _plan_outputs(ctx, gf, profs, ddb, graph=False):
+    """Run one plan of profs; returns (its launch groups, per-query outputs)."""
+    n, q = ddb.n_seqs, len(profs)
+    dev = torch.device("cuda", 0)
+    outs = [torch.full((q * n,), 7, dtype=dt, device=dev) for dt in (torch.uint8, torch.uint8, torch.float32)]
+    plan = mpf.Plan(ctx, gf, profs, ddb, *outs)
+    groups = plan.groups()
+    if graph:
+        plan.capture_graph()
+    for _ in range(2 if graph else 1):
+        plan.launch()
+    ctx.sync()
+    res = [t.cpu().numpy() for t in outs]
+    plan.close()
+    return groups, [tuple(a[i * n:(i + 1) * n] for a in res) for i in range(q)]
+
+
+def _packed_batch(ctx, rng, configs, make):
+    """Profiles with explicit (lanes, words) for both filters."""
+    recs, profs = [], []
+    for lanes, words in configs:
+        rec = make(2 * lanes * words - int(rng.integers(0, 2 * lanes)))
+        prof = mpf.Profile(ctx, rec)
+        for gf, _ in FILTERS:
+            prof.set_config(gf, lanes, words)
+        recs.append(rec)
+        profs.append(prof)
+    return recs, profs
+
+
+def test_packed_queries_per_warp(ctx):
+    """Plans whose queries of 1 to 16 lanes share one sequence per warp
+    (32 / lanes queries, score rows in tensor memory) equal the oracle and
+    the one-query scans: full sets and a set with an empty slot, sets with
+    every word in TMEM (12-14 words) and with the rest in shared memory, with
+    and without a two-word tail, queries padded to their set's word count,
+    queries left to the one-query kernels, strong profiles that overflow and
+    chain J (the held MSV pass with its rescoring launch), a graph-captured
+    replay, and the same batch with every table set to shared memory
+    (nothing packed)."""
+    rng = np.random.default_rng(808)
+    db = synth.make_database(800, 330, 0, 4000, rng)
+    strong_db = synth.random_database(300, 500, rng, alphabet=20, min_len=0)
+    real = ([(16, 18), (16, 30), (16, 46), (16, 18), (16, 30)] + [(8, 12)] * 4 + [(8, 22)] * 4 + [(8, 38)]
+            + [(4, 26)] * 7 + [(2, 20)] * 7 + [(2, 22)] * 7 + [(1, 14)] * 27)
+    strong = [(8, 22)] * 4 + [(16, 18)] * 2 + [(4, 12)] * 8 + [(16, 26)]
+    batches = [
+        (db, _packed_batch(ctx, rng, real, lambda M: synth.make_profile(M, rng))),
+        (strong_db, _packed_batch(ctx, rng, strong, lambda M: synth.random_profile(
+            M, 20, rng, cost_hi=26, bias=20, base=190, tbm=10, tec=3, tjb=8))),
+    ]
+    # Sets (lanes, words, table, queries per warp, queries): a set costs
+    # (32 / lanes) x its words, a query alone 5/4 of its own words.
+    want_real = sorted([(16, 18, mpf.TABLE_TENSOR, 2, 2), (16, 30, mpf.TABLE_TENSOR, 2, 2),
+                        (16, 46, mpf.TABLE_SHARED, 1, 1), (8, 12, mpf.TABLE_TENSOR, 4, 4),
+                        (8, 22, mpf.TABLE_TENSOR, 4, 4), (8, 38, mpf.TABLE_SHARED, 1, 1),
+                        (4, 26, mpf.TABLE_TENSOR, 8, 7), (2, 22, mpf.TABLE_TENSOR, 16, 14),
+                        (1, 14, mpf.TABLE_TENSOR, 32, 27)])
+    seen_flag = 0
+    for bi, (sdb, (recs, profs)) in enumerate(batches):
+        ddb = mpf.Database(ctx, sdb.residues, sdb.offsets, sdb.lengths)
+        for gf, of in FILTERS:
+            groups, got = _plan_outputs(ctx, gf, profs, ddb, graph=(bi == 0))
+            key = sorted((g["lanes"], g["words"], g["table"], g["queries_per_warp"], g["n_queries"])
+                         for g in groups)
+            if bi == 0 and gf == mpf.SSV:
+                assert key == want_real, key
+            assert sum(g["n_queries"] for g in groups) == len(profs)
+            for lanes in sorted({c[0] for c in (real if bi == 0 else strong)} - {32}):
+                assert any(g["lanes"] == lanes and g["queries_per_warp"] == 32 // lanes for g in groups), \
+                    (lanes, key)
+            for pr in profs:
+                pr.set_table_memory(gf, mpf.TABLE_SHARED)
+            groups_s, got_s = _plan_outputs(ctx, gf, profs, ddb)
+            assert all(g["queries_per_warp"] == 1 for g in groups_s)
+            for pr in profs:
+                pr.set_table_memory(gf, mpf.TABLE_AUTO)
+            for i, (rec, pr) in enumerate(zip(recs, profs)):
+                exp = oracle.scan(of, rec, sdb.residues, sdb.offsets, sdb.lengths, nthreads=8)
+                what = f"batch {bi} filter {gf} q{i} cfg={pr.get_config(gf)} M={rec.M}"
+                assert_same(got[i], exp, "packed " + what)
+                assert_same(got_s[i], exp, "shared " + what)
+                assert_same(run_gpu(ctx, gf, pr, ddb), exp, "single " + what)
+                seen_flag += int(exp[1].sum()) if bi == 1 else 0
+        for pr in profs:
+            pr.close()
+        ddb.close()
+    assert seen_flag > 0
+
+
 # ------------------------------------------------------------ arguments ---
 
 def test_invalid_arguments(ctx):
