@@ -355,6 +355,47 @@ def run_mpf(args):
             b.synchronize()
             per_kernel[f].append((i, a.elapsed_time(b)))
 
+    # Both filters in one sweep (MPF_MSV_SSV): a query's two filters share a
+    # sweep when MSV holds its begin score and both use the same kernel
+    # configuration, so the SSV settings take MSV's tuned ones for this plan.
+    fused = None
+    if args.fused:
+        for pr in profs:
+            m = tuned.get("msv", {}).get(pr.M)
+            if m:
+                pr.set_config(mpf.SSV, m[0], m[1])
+                pr.set_shard_factor(mpf.SSV, m[2])
+                pr.set_table_memory(mpf.SSV, m[3])
+        f_outs = tuple(torch.empty(2 * q * n, dtype=dt, device=dev)
+                       for dt in (torch.uint8, torch.uint8, torch.float32))
+        fplan = mpf.Plan(ctx, mpf.MSV_SSV, profs, db, *f_outs)
+        fplan.capture_graph()
+        f_groups = fplan.groups()
+        for pr in profs:
+            m = tuned.get("ssv", {}).get(pr.M)
+            if m:
+                pr.set_config(mpf.SSV, m[0], m[1])
+                pr.set_shard_factor(mpf.SSV, m[2])
+                pr.set_table_memory(mpf.SSV, m[3])
+        for _ in range(args.warmup):
+            fplan.launch()
+        ctx.sync()
+        ms_fused = max_over_ranks(time_steps(fplan.launch, args.steps, "timed_fused"), world)
+        step_batched()
+        ctx.sync()
+        same = all(bool(torch.equal(f_outs[k][:q * n], outs["msv"][k]) and
+                        torch.equal(f_outs[k][q * n:], outs["ssv"][k])) for k in range(3))
+        n_fused = sum(g["n_queries"] for g in f_groups if g["filters"] == 3)
+        log(f"[rank {rank}] MSV+SSV in one sweep: {ms_fused:.2f} ms per step against batched "
+            f"{ms_batched:.2f}; {n_fused} of {q} queries in one sweep; outputs equal: {same}")
+        fused = {"ms_per_step": ms_fused, "kernel_launches_per_step": fplan.kernel_launches,
+                 "queries_in_one_sweep": n_fused, "queries": q,
+                 "sweeps_per_step": sum(g["n_queries"] for g in f_groups),
+                 "equals_one_filter_plans": same,
+                 "form": "one graph-captured MPF_MSV_SSV plan: both filters' outputs from one sweep per query "
+                         "(MSV cells less the held begin score are the SSV cells)"}
+        fplan.close()
+
     # Roofline of the dominant kernel: the (filter, query) launch with the
     # largest total device time in the plain form.
     tot = {f: sum(ms for _, ms in per_kernel[f]) for f, _ in filters}
@@ -573,6 +614,11 @@ def run_mpf(args):
             "plain": {"value": gcups_plain, "unit": "GCUPS", "ms_per_step": ms_plain,
                       "per_filter_gcups": per_filter_plain, "m_ge_400": ge400},
             "batched_over_plain": gcups_batched / gcups_plain,
+            "msv_ssv_one_sweep": fused and dict(
+                fused, value=2 * job_cells_per_filter / (fused["ms_per_step"] * 1e-3) / 1e9, unit="GCUPS",
+                over_plain=ms_plain / fused["ms_per_step"], over_batched=ms_batched / fused["ms_per_step"],
+                cells_note="GCUPS counts both filters' cells (2 x M x residues per query) as the headline "
+                           "does; one sweep updates M x residues cells for the two"),
             "f16_cells_extra_line": f16_line,
             "roofline": roofline,
             "cpu_baseline": cpu,
@@ -770,10 +816,17 @@ def run_batch_workload(args, ctx, idx, n_queries, time_steps, dev, steps=3):
         pl.capture_graph()
     plain = {f: [mpf.Plan(ctx, code, [pr], db, *(t[i * n:(i + 1) * n] for t in outs[f]))
                  for i, pr in enumerate(profs)] for f, code in filters}
+    f_outs = tuple(torch.empty(2 * q * n, dtype=dt, device=dev) for dt in (torch.uint8, torch.uint8, torch.float32))
+    fplan = mpf.Plan(ctx, mpf.MSV_SSV, profs, db, *f_outs)
+    fplan.capture_graph()
+    n_fused = sum(g["n_queries"] for g in fplan.groups() if g["filters"] == 3)
 
     def step_b():
         for f, _ in filters:
             plans[f].launch()
+
+    def step_f():
+        fplan.launch()
 
     def step_u():
         for f, _ in filters:
@@ -788,11 +841,20 @@ def run_batch_workload(args, ctx, idx, n_queries, time_steps, dev, steps=3):
         step_b()
         step_u()
         step_p()
-    ms_b, ms_u, ms_p = [], [], []
+        step_f()
+    ms_b, ms_u, ms_p, ms_f = [], [], [], []
     for _ in range(steps):            # interleaved, so drift hits every form alike
         ms_b.append(time_steps(step_b, 1))
         ms_u.append(time_steps(step_u, 1))
         ms_p.append(time_steps(step_p, 1))
+        ms_f.append(time_steps(step_f, 1))
+    step_b()
+    ctx.sync()
+    f_same = all(bool(torch.equal(f_outs[k][:q * n], outs["msv"][k]) and
+                      torch.equal(f_outs[k][q * n:], outs["ssv"][k])) for k in range(3))
+    f_launches = fplan.kernel_launches
+    fplan.close()
+    del f_outs
     cells = 2 * sum(p.M for p in wl.profiles) * res
     padded = 0                        # plain scans: each query in its own layout
     for pr, rec in zip(profs, wl.profiles):
@@ -819,6 +881,7 @@ def run_batch_workload(args, ctx, idx, n_queries, time_steps, dev, steps=3):
     db.close()
     gb = cells / (statistics.median(ms_b) * 1e-3) / 1e9
     gu = cells / (statistics.median(ms_u) * 1e-3) / 1e9
+    gf = cells / (statistics.median(ms_f) * 1e-3) / 1e9
     gp = cells / (statistics.median(ms_p) * 1e-3) / 1e9
     # The oracle on a bounded sample of the same workload (two queries).
     cpu = None
@@ -848,8 +911,13 @@ def run_batch_workload(args, ctx, idx, n_queries, time_steps, dev, steps=3):
                                 "form": "the same plans, queries of fewer than 32 lanes unpacked"},
            "plain": {"gcups": gp, "ms_per_step": ms_p, "kernel_launches_per_step": 2 * q,
                      "padding_ratio": padded / cells},
+           "msv_ssv_one_sweep": {"gcups": gf, "ms_per_step": ms_f, "kernel_launches_per_step": f_launches,
+                                 "queries_in_one_sweep": n_fused, "equals_one_filter_plans": f_same,
+                                 "form": "one graph-captured MPF_MSV_SSV plan (packed sets included); GCUPS "
+                                         "counts both filters' cells"},
            "batched_over_plain": gb / gp,
            "batched_unpacked_over_plain": gu / gp,
+           "one_sweep_over_plain": gf / gp,
            "spread": {"batched": (max(ms_b) - min(ms_b)) / statistics.median(ms_b),
                       "batched_unpacked": (max(ms_u) - min(ms_u)) / statistics.median(ms_u),
                       "plain": (max(ms_p) - min(ms_p)) / statistics.median(ms_p)},
@@ -857,6 +925,7 @@ def run_batch_workload(args, ctx, idx, n_queries, time_steps, dev, steps=3):
            "configs": {f"{k[0]}x{k[1]}{'+tmem' if k[2] == mpf.TABLE_TENSOR else ''}"
                        f"{f'/{k[3]}q' if k[3] > 1 else ''}": v for k, v in sorted(groups.items())},
            "generate_s": gen_s, "cpu_baseline": cpu}
+    log(f"{wl.name}: one sweep MSV+SSV {gf:.0f} GCUPS ({n_fused}/{q} queries, equal outputs {f_same})")
     log(f"{wl.name}: batched {gb:.0f} GCUPS (unpacked {gu:.0f}), plain {gp:.0f}, ratio {gb / gp:.4f}, "
         f"{launches} launches per batched step, {packed} packed query-filters, "
         f"padding batched {padded_b / cells:.3f} plain {padded / cells:.3f}")
@@ -1031,6 +1100,8 @@ def main():
     ap.add_argument("--no-f16-line", dest="f16_line", action="store_false",
                     help="skip the extra fp16-cell measurement")
     ap.add_argument("--no-pipeline", dest="pipeline", action="store_false")
+    ap.add_argument("--no-fused", dest="fused", action="store_false",
+                    help="skip the one-sweep MSV+SSV plan (MPF_MSV_SSV)")
     ap.add_argument("--no-viterbi", dest="viterbi", action="store_false")
     ap.add_argument("--long-m", type=int, default=5000,
                     help="model length of the long-model measurement (0: skip)")

@@ -67,7 +67,9 @@ enum {
   MPF_EDEVICE = 6       /* a kernel's index check failed (only libmpf_debug.so checks)    */
 };
 
-enum { MPF_MSV = 0, MPF_SSV = 1 };
+/* Filters.  MPF_MSV_SSV (batches and plans only) asks for both: see
+ * mpf_scan_batch. */
+enum { MPF_MSV = 0, MPF_SSV = 1, MPF_MSV_SSV = 2 };
 
 /* Largest model length M a byte-filter or Viterbi profile may have (100,000). */
 int mpf_max_model_length(void);
@@ -233,10 +235,19 @@ int mpf_ssv_scan(mpf_ctx *ctx, const mpf_profile *prof, const mpf_db *db, uint8_
  * Score the database with n_q profiles in one persistent launch per kernel
  * configuration (work items of (query, database shard) pulled by resident
  * thread blocks; launches of different configurations overlap).
- *   filter: MPF_MSV or MPF_SSV
+ *   filter: MPF_MSV, MPF_SSV or MPF_MSV_SSV
  *   raw, overflow: n_q * n_seqs bytes, nat: n_q * n_seqs floats or NULL,
- *   query-major ([q][s]).
+ *   query-major ([q][s]).  MPF_MSV_SSV: twice that, the MSV block ([q][s])
+ *   then the SSV block.
  * Results equal n_q separate mpf_msv_scan / mpf_ssv_scan calls.
+ * MPF_MSV_SSV scores a query once for both filters where it can: with the
+ * begin score held (the MSV pass used when the first begin score of every
+ * sequence is below 255 - bias, Alg. 2), the MSV cells less the begin score
+ * follow the SSV recurrence (Alg. 7), so one sweep's largest cell gives both
+ * scores.  That needs integer cells for both filters and the same
+ * configuration and table memory for both (mpf_profile_set_config,
+ * mpf_profile_set_table_memory; the MSV shard factor is used); other
+ * queries, and long models, run each filter's kernels.
  * Errors: as the single scans.
  */
 int mpf_scan_batch(mpf_ctx *ctx, int filter, const mpf_profile *const *profs, int n_q,
@@ -269,8 +280,9 @@ int mpf_scan_batch(mpf_ctx *ctx, int filter, const mpf_profile *const *profs, in
  *                     words per lane (0: tiled or long-model kernel), where
  *                     its table is read from (MPF_TABLE_SHARED or
  *                     MPF_TABLE_TENSOR), queries scored per warp and
- *                     sequence (1, or 32 / lanes when packed) and its number
- *                     of queries.  Any output pointer may be NULL;
+ *                     sequence (1, or 32 / lanes when packed), its number
+ *                     of queries and the filters it scores (1: MSV, 2: SSV,
+ *                     3: both in one sweep).  Any output pointer may be NULL;
  *                     MPF_EINVAL for a NULL plan or i out of range.
  *   mpf_plan_destroy: waits for the context stream, then frees the plan.
  */
@@ -283,7 +295,7 @@ int mpf_plan_capture_graph(mpf_plan *plan);
 int mpf_plan_kernel_launches(const mpf_plan *plan);
 int mpf_plan_group_count(const mpf_plan *plan);
 int mpf_plan_group_info(const mpf_plan *plan, int i, int *lanes, int *words, int *table_memory,
-                        int *queries_per_warp, int *n_queries);
+                        int *queries_per_warp, int *n_queries, int *filters);
 void mpf_plan_destroy(mpf_plan *plan);
 
 /*

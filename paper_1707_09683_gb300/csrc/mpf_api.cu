@@ -287,6 +287,15 @@ int kernel_mode(const mpf_profile *p, int filter) {
   return f16 ? MODE_MSV_HELD_F16 : MODE_MSV_HELD;
 }
 
+// Whether one sweep can score a profile for both filters (MODE_MSV_SSV):
+// MSV runs the held pass, SSV integer cells, and the two filters have the
+// same configuration and table memory.
+bool fused_ok(const mpf_profile *p) {
+  return !p->seg_words && kernel_mode(p, MPF_MSV) == MODE_MSV_HELD && kernel_mode(p, MPF_SSV) == MODE_SSV &&
+         p->cfg_lanes[MPF_MSV] == p->cfg_lanes[MPF_SSV] && p->cfg_words[MPF_MSV] == p->cfg_words[MPF_SSV] &&
+         p->table_mem[MPF_MSV] == p->table_mem[MPF_SSV];
+}
+
 // Whether a striped scan of this profile reads its table from tensor memory:
 // one sequence per warp, enough words per lane, a mode with a TMEM kernel,
 // and the profile's choice (automatic: yes).
@@ -457,7 +466,8 @@ int plan_create(mpf_ctx *ctx, int filter, const mpf_profile *const *profs, int n
                 const mpf_db *db, uint8_t *raw, uint8_t *flag, float *nat, mpf_plan **out,
                 const uint32_t *ranks = nullptr, const uint32_t *n_ranks = nullptr) {
   if (!ctx || !profs || n_q < 1 || !db || !raw || !flag || !out) return MPF_EINVAL;
-  if (filter != MPF_MSV && filter != MPF_SSV) return MPF_EINVAL;
+  if (filter != MPF_MSV && filter != MPF_SSV && filter != MPF_MSV_SSV) return MPF_EINVAL;
+  if (filter == MPF_MSV_SSV && ranks) return MPF_EINVAL;
   if (db->ctx->device != ctx->device) return MPF_EINVAL;
   mpf_plan *pl = new (std::nothrow) mpf_plan;
   if (!pl) return MPF_ENOMEM;
@@ -479,6 +489,28 @@ int plan_create(mpf_ctx *ctx, int filter, const mpf_profile *const *profs, int n
     DevTable fb;
   };
   std::map<std::pair<int, int>, std::vector<QpCand>> qp_cand;
+  // One job per (query, kernel mode): MPF_MSV_SSV scores a query once for
+  // both filters where it can (MODE_MSV_SSV, with the MSV settings), else
+  // runs each filter's kernel into its output block (0: MSV, 1: SSV).
+  struct Job {
+    int i, filter, mode, block;
+  };
+  std::vector<Job> jobs;
+  for (int i = 0; i < n_q; ++i) {
+    const mpf_profile *p = profs[i];
+    if (!p || p->ctx->device != ctx->device) {
+      plan_free(pl);
+      return MPF_EINVAL;
+    }
+    if (filter != MPF_MSV_SSV) {
+      jobs.push_back(Job{i, filter, kernel_mode(p, filter), 0});
+    } else if (fused_ok(p)) {
+      jobs.push_back(Job{i, MPF_MSV, MODE_MSV_SSV, 0});
+    } else {
+      jobs.push_back(Job{i, MPF_MSV, kernel_mode(p, MPF_MSV), 0});
+      jobs.push_back(Job{i, MPF_SSV, kernel_mode(p, MPF_SSV), 1});
+    }
+  }
   auto set_table = [](QueryDesc &q, const DevTable &t) {
     q.table = t.ptr;
     q.table_bytes = t.geom.table_bytes;
@@ -488,13 +520,9 @@ int plan_create(mpf_ctx *ctx, int filter, const mpf_profile *const *profs, int n
     q.tail_off = t.geom.tail_off;
     q.tail_row_bytes = t.geom.tail_row_bytes;
   };
-  for (int i = 0; i < n_q; ++i) {
+  for (const Job &jb : jobs) {
+    const int i = jb.i, f = jb.filter, mode = jb.mode;
     const mpf_profile *p = profs[i];
-    if (!p || p->ctx->device != ctx->device) {
-      plan_free(pl);
-      return MPF_EINVAL;
-    }
-    const int mode = kernel_mode(p, filter);
     DevTable fb{};   // held MSV: the integer table of the rescoring launch
     QueryDesc q;
     memset(&q, 0, sizeof(q));
@@ -532,8 +560,8 @@ int plan_create(mpf_ctx *ctx, int filter, const mpf_profile *const *profs, int n
       q.M = (uint32_t)p->M;
       q.seg_words = (uint32_t)p->seg_words;
     } else {
-      lanes = p->cfg_lanes[filter];
-      words = p->cfg_words[filter];
+      lanes = p->cfg_lanes[f];
+      words = p->cfg_words[f];
       if (!lanes) default_config(ctx, p->M, mode, &lanes, &words);
       if (!lanes || !kernel_for(lanes, words, mode)) {
         plan_free(pl);
@@ -547,7 +575,7 @@ int plan_create(mpf_ctx *ctx, int filter, const mpf_profile *const *profs, int n
       }
       set_table(q, t);
       q.M = (uint32_t)p->M;
-      if (mode == MODE_MSV_HELD || mode == MODE_MSV_HELD_F16) {
+      if (mode == MODE_MSV_HELD || mode == MODE_MSV_HELD_F16 || mode == MODE_MSV_SSV) {
         // The integer table of the same layout, for the exact kernel that
         // rescores the sequences the held pass lists.
         DevTable ti = t;
@@ -567,17 +595,23 @@ int plan_create(mpf_ctx *ctx, int filter, const mpf_profile *const *profs, int n
     q.scale = p->scale;
     q.tjb = p->d_tjb;
     q.n_tjb = p->n_tjb;
-    const size_t off = (size_t)i * db->n_seqs;
+    const size_t off = ((size_t)jb.block * (size_t)n_q + (size_t)i) * db->n_seqs;
     q.raw = raw + off;
     q.flag = flag + off;
     q.nat = nat ? nat + off : nullptr;
+    if (mode == MODE_MSV_SSV) {   // the SSV block
+      const size_t off2 = ((size_t)n_q + (size_t)i) * db->n_seqs;
+      q.raw2 = raw + off2;
+      q.flag2 = flag + off2;
+      q.nat2 = nat ? nat + off2 : nullptr;
+    }
     q.ranks = ranks ? ranks + off : nullptr;
     q.n_ranks = ranks ? n_ranks + i : nullptr;
-    const int tm = p->seg_words ? 0 : (use_tmem(p, filter, lanes, words, mode) ? 1 : 0);
-    const int sf = p->seg_words ? 1 : p->shard_factor[filter];
+    const int tm = p->seg_words ? 0 : (use_tmem(p, f, lanes, words, mode) ? 1 : 0);
+    const int sf = p->seg_words ? 1 : p->shard_factor[f];
     if (n_q >= 2 && !ranks && !p->seg_words && lanes < 32 &&
-        (mode == MODE_SSV || mode == MODE_MSV_HELD) && words >= kTmMinWords &&
-        p->table_mem[filter] != MPF_TABLE_SHARED) {
+        (mode == MODE_SSV || mode == MODE_MSV_HELD || mode == MODE_MSV_SSV) && words >= kTmMinWords &&
+        p->table_mem[f] != MPF_TABLE_SHARED) {
       qp_cand[std::make_pair(lanes, mode)].push_back(QpCand{words, sf, p, q, fb});
       continue;
     }
@@ -639,7 +673,7 @@ int plan_create(mpf_ctx *ctx, int filter, const mpf_profile *const *profs, int n
         if (pack) {
           DevTable t;
           int rc = get_table(v[j].p, lanes, H, TABLE_I16_PACKED, &t);
-          if (rc == MPF_OK && mode == MODE_MSV_HELD) rc = get_table(v[j].p, lanes, H, TABLE_I16, &fb);
+          if (rc == MPF_OK && mode != MODE_SSV) rc = get_table(v[j].p, lanes, H, TABLE_I16, &fb);
           if (rc) {
             plan_free(pl);
             return rc;
@@ -648,7 +682,7 @@ int plan_create(mpf_ctx *ctx, int filter, const mpf_profile *const *profs, int n
         }
         const GroupKey key = pack ? key0 : GroupKey(lanes, v[j].words, mode, 0, 1);
         byconf[key].push_back(q);
-        if (mode == MODE_MSV_HELD) fb_table[key].push_back(fb);
+        if (mode != MODE_SSV) fb_table[key].push_back(fb);
         group_shards[key] = std::max(group_shards[key], v[j].sf);
       }
       if (pack) {
@@ -656,7 +690,7 @@ int plan_create(mpf_ctx *ctx, int filter, const mpf_profile *const *profs, int n
         memset(&empty, 0, sizeof(empty));
         for (size_t j = b - a; j < (size_t)QP; ++j) {
           byconf[key0].push_back(empty);
-          if (mode == MODE_MSV_HELD) fb_table[key0].push_back(DevTable{});
+          if (mode != MODE_SSV) fb_table[key0].push_back(DevTable{});
         }
       }
     }
@@ -689,7 +723,7 @@ int plan_create(mpf_ctx *ctx, int filter, const mpf_profile *const *profs, int n
       g.col_bytes = (uint64_t)g.grid * kTileWarps * 2 * g.col_stride;
       e = cudaMallocAsync((void **)&g.d_col, g.col_bytes, ctx->stream);
     }
-    const bool held = g.mode == MODE_MSV_HELD || g.mode == MODE_MSV_HELD_F16;
+    const bool held = g.mode == MODE_MSV_HELD || g.mode == MODE_MSV_HELD_F16 || g.mode == MODE_MSV_SSV;
     if (e == cudaSuccess && (g.mode == MODE_TILE_MSV || held)) {
       // Fallback lists, and the launch that scores them exactly: the
       // lane-segment kernel after the tiled MSV pass, the striped kernel
@@ -831,7 +865,7 @@ int run_scan(mpf_ctx *ctx, int filter, const mpf_profile *const *profs, int n_q,
   DeviceGuard dg(ctx->device);
   const bool dev_raw = is_device_ptr(raw), dev_flag = is_device_ptr(flag);
   const bool dev_nat = nat ? is_device_ptr(nat) : true;
-  const uint64_t n = (uint64_t)n_q * db->n_seqs;
+  const uint64_t n = (uint64_t)n_q * db->n_seqs * (filter == MPF_MSV_SSV ? 2u : 1u);
   if (n == 0) return MPF_OK;
   uint8_t *k_raw = raw, *k_flag = flag;
   float *k_nat = nat;
@@ -1296,7 +1330,7 @@ int mpf_plan_kernel_launches(const mpf_plan *plan) {
 int mpf_plan_group_count(const mpf_plan *plan) { return plan ? (int)plan->groups.size() : 0; }
 
 int mpf_plan_group_info(const mpf_plan *plan, int i, int *lanes, int *words, int *table_memory,
-                        int *queries_per_warp, int *n_queries) {
+                        int *queries_per_warp, int *n_queries, int *filters) {
   if (!plan || i < 0 || (size_t)i >= plan->groups.size()) return MPF_EINVAL;
   const LaunchGroup &g = plan->groups[(size_t)i];
   if (lanes) *lanes = g.lanes;
@@ -1304,6 +1338,13 @@ int mpf_plan_group_info(const mpf_plan *plan, int i, int *lanes, int *words, int
   if (table_memory) *table_memory = g.tm ? MPF_TABLE_TENSOR : MPF_TABLE_SHARED;
   if (queries_per_warp) *queries_per_warp = g.qp;
   if (n_queries) *n_queries = (int)g.n_real;
+  if (filters) {
+    switch (g.mode) {
+      case MODE_MSV_SSV: *filters = 3; break;
+      case MODE_SSV: case MODE_SSV_F16: case MODE_TILE_SSV: *filters = 2; break;
+      default: *filters = 1;
+    }
+  }
   return MPF_OK;
 }
 

@@ -1,13 +1,13 @@
 // mpf_inst.cu -- scan-kernel instantiations for one lane-group size.
 //
 // Compiled once per size (-DMPF_LG=1, 2, 4, 8, 16, 32; see build.py) into
-// kernel_lg<MPF_LG>(): every mode of the striped scan kernel (seven) for each
+// kernel_lg<MPF_LG>(): every mode of the striped scan kernel (eight) for each
 // built word count -- multiples of four, and the counts with a two-word tail.
 // With -DMPF_LG=32 -DMPF_TM=1 it builds kernel_lg32_tm() instead: the
 // tensor-memory variants (every mode but MSV_DIRECT, at least kTmMinWords
 // words).  With -DMPF_QP=1 (lanes 1 to 16) it builds kernel_qp_tm_lg<lanes>():
 // the tensor-memory variants that score one sequence against 32 / lanes
-// queries per warp (integer SSV and the held MSV pass).
+// queries per warp (integer SSV, the held MSV pass and the two together).
 #include "mpf_scan_kernel.cuh"
 
 #ifndef MPF_LG
@@ -24,6 +24,7 @@ namespace mpf {
   case W:                                                                                             \
     if (mode == MODE_SSV) return scan_kernel<MPF_LG, W, MODE_SSV, true, 32 / MPF_LG>;                 \
     if (mode == MODE_MSV_HELD) return scan_kernel<MPF_LG, W, MODE_MSV_HELD, true, 32 / MPF_LG>;       \
+    if (mode == MODE_MSV_SSV) return scan_kernel<MPF_LG, W, MODE_MSV_SSV, true, 32 / MPF_LG>;         \
     return nullptr;
 
 KernelFn MPF_CAT(kernel_qp_tm_lg, MPF_LG)(int words, int mode) {
@@ -64,6 +65,7 @@ KernelFn MPF_CAT(kernel_qp_tm_lg, MPF_LG)(int words, int mode) {
     if (mode == MODE_MSV_FAST_F16) return scan_kernel<32, W, MODE_MSV_FAST_F16, true>;     \
     if (mode == MODE_MSV_HELD) return scan_kernel<32, W, MODE_MSV_HELD, true>;             \
     if (mode == MODE_MSV_HELD_F16) return scan_kernel<32, W, MODE_MSV_HELD_F16, true>;     \
+    if (mode == MODE_MSV_SSV) return scan_kernel<32, W, MODE_MSV_SSV, true>;               \
     return nullptr;
 
 KernelFn kernel_lg32_tm(int words, int mode) {
@@ -105,6 +107,7 @@ KernelFn kernel_lg32_tm(int words, int mode) {
     if (mode == MODE_MSV_FAST_F16) return scan_kernel<MPF_LG, W, MODE_MSV_FAST_F16>; \
     if (mode == MODE_MSV_HELD) return scan_kernel<MPF_LG, W, MODE_MSV_HELD>;         \
     if (mode == MODE_MSV_HELD_F16) return scan_kernel<MPF_LG, W, MODE_MSV_HELD_F16>; \
+    if (mode == MODE_MSV_SSV) return scan_kernel<MPF_LG, W, MODE_MSV_SSV>;           \
     return nullptr;
 
 KernelFn MPF_CAT(kernel_lg, MPF_LG)(int words, int mode) {

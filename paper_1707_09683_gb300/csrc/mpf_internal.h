@@ -53,8 +53,11 @@ enum Mode : int {
                           //   tests; sequences whose running maximum passes T are listed and
                           //   rescored by MODE_MSV_DIRECT
   MODE_MSV_HELD_F16 = 10, // MODE_MSV_HELD with cells as fp16 integers
+  MODE_MSV_SSV = 11,      // MODE_MSV_HELD and MODE_SSV from one sweep: with b held the MSV
+                          //   cells minus b follow the SSV recurrence, so the largest cell
+                          //   gives both filters' scores
 };
-constexpr int kNumModes = 7;   // modes of the striped scan kernel
+constexpr int kNumModes = 8;   // modes of the striped scan kernel
 
 // Striped kernels that read their table from tensor memory (one sequence per
 // warp): the first tm_words(words) words of each lane's row of every residue
@@ -96,6 +99,9 @@ struct QueryDesc {
   uint8_t *raw;           // outputs indexed by original sequence number
   uint8_t *flag;
   float *nat;             // nullable
+  uint8_t *raw2;          // MODE_MSV_SSV: the SSV outputs (raw, flag above: MSV)
+  uint8_t *flag2;
+  float *nat2;            // nullable
   // Nullable: score only these length ranks (ascending), *n_ranks of them
   // (a device count written by an earlier kernel on the same stream).
   const uint32_t *ranks;

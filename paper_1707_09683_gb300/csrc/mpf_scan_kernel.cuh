@@ -145,7 +145,8 @@ __global__ void __launch_bounds__(kBlockThreads, 1) scan_kernel(ScanParams p) {
   static_assert(QP == 1 || !kF16, "packed sets use integer cells");
   constexpr bool kSSV = (MODE == MODE_SSV || MODE == MODE_SSV_F16);
   constexpr bool kFast = (MODE == MODE_MSV_FAST || MODE == MODE_MSV_FAST_F16);
-  constexpr bool kHeld = (MODE == MODE_MSV_HELD || MODE == MODE_MSV_HELD_F16);
+  constexpr bool kBoth = (MODE == MODE_MSV_SSV);   // held MSV and SSV outputs from one sweep
+  constexpr bool kHeld = (MODE == MODE_MSV_HELD || MODE == MODE_MSV_HELD_F16 || kBoth);
   constexpr bool kDirect = (MODE == MODE_MSV_DIRECT);
   const uint32_t one2 = 0x3c003c00u;   // (1.0, 1.0) as half2
   extern __shared__ __align__(16) uint8_t smem[];
@@ -484,6 +485,15 @@ __global__ void __launch_bounds__(kBlockThreads, 1) scan_kernel(ScanParams p) {
           }
         }
         g = group_max<LG>(g);
+        if (kBoth && own && gl == 0) {
+          // SSV (Alg. 7) from the same largest cell: with b held the MSV
+          // cells minus b are exactly the SSV cells.
+          const bool ovf = V >= 255;
+          const int raw = ovf ? 255 : V;
+          qd->raw2[orig] = (uint8_t)raw;
+          qd->flag2[orig] = ovf ? 1 : 0;
+          if (qd->nat2) qd->nat2[orig] = ovf ? __int_as_float(0x7f800000) : nat_score(raw - tbm - tec - 2 * t, scale);
+        }
         if (kHeld && own && gl == 0) {
           // The begin score b was held for every row.  V, the largest cell
           // of any row, decides: at or above 255 - bias - b some row

@@ -22,6 +22,7 @@ DEBUG_LIB_PATH = os.path.join(_HERE, "libmpf_debug.so")
 
 MPF_OK, MPF_EINVAL, MPF_ENOMEM, MPF_ECUDA, MPF_ETIMEOUT, MPF_EUNSUPPORTED, MPF_EDEVICE = range(7)
 MSV, SSV = 0, 1
+MSV_SSV = 2   # batches and plans: both filters; outputs hold the MSV block, then the SSV block
 ARITH_AUTO, ARITH_I16, ARITH_F16 = 0, 1, 2
 TABLE_AUTO, TABLE_SHARED, TABLE_TENSOR = 0, 1, 2
 
@@ -77,7 +78,7 @@ def load(path: str = LIB_PATH):
         "mpf_plan_capture_graph": (i32, [vp]),
         "mpf_plan_kernel_launches": (i32, [vp]),
         "mpf_plan_group_count": (i32, [vp]),
-        "mpf_plan_group_info": (i32, [vp, i32, vp, vp, vp, vp, vp]),
+        "mpf_plan_group_info": (i32, [vp, i32, vp, vp, vp, vp, vp, vp]),
         "mpf_plan_destroy": (None, [vp]),
         "mpf_scan_noalloc": (i32, [vp, i32, vp, vp, vp, vp, vp]),
         "mpf_profile_footprint": (i32, [vp, i32, vp, vp]),
@@ -383,14 +384,15 @@ class Plan:
 
     def groups(self):
         """Per launch group: dict(lanes, words, table, queries_per_warp,
-        n_queries), as ``mpf_plan_group_info`` reports them."""
+        n_queries, filters), as ``mpf_plan_group_info`` reports them
+        (filters: 1 MSV, 2 SSV, 3 both in one sweep)."""
         lib = load()
         out = []
         for i in range(int(lib.mpf_plan_group_count(self.handle))):
-            v = [ctypes.c_int() for _ in range(5)]
+            v = [ctypes.c_int() for _ in range(6)]
             _check(lib.mpf_plan_group_info(self.handle, i, *[ctypes.byref(x) for x in v]),
                    "mpf_plan_group_info")
-            out.append(dict(zip(("lanes", "words", "table", "queries_per_warp", "n_queries"),
+            out.append(dict(zip(("lanes", "words", "table", "queries_per_warp", "n_queries", "filters"),
                                 (x.value for x in v))))
         return out
 

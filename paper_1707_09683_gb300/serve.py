@@ -11,9 +11,10 @@ the work is drained:
   stream and its share of the budgets;
 * admit: arrivals enter a bounded queue (a full queue rejects);
 * launch: while a stream is free, queued requests are admitted into its
-  arena by footprint and launched as one plan per filter (queries of
-  different model length M run as concurrent kernels of their
-  shared-memory configurations).
+  arena by footprint and launched as one plan for both filters
+  (``MPF_MSV_SSV``: a query whose MSV holds its begin score is swept once
+  for the two; queries of different model length M run as concurrent
+  kernels of their configurations, narrow ones packed several to a warp).
 
 Footprint of a request (``Footprint``): the HBM it holds while in flight --
 its output slot (6 bytes per sequence and filter) and the device memory of
@@ -140,8 +141,9 @@ class ScanServer:
         dev = torch.device("cuda", device)
         nf = len(self.FILTERS)
         cap = max_batch * self.n
-        # Per-stream arenas: device outputs [filter][query][sequence] and their
-        # pinned host mirrors; one request holds one slot of n sequences per filter.
+        # Per-stream arenas: device outputs of a batch of q requests as the
+        # both-filter plan writes them ([MSV: q x n][SSV: q x n]) and their
+        # pinned host mirrors; one request holds n sequences per filter.
         self.d_raw = [torch.empty(nf * cap, dtype=torch.uint8, device=dev) for _ in self.ctxs]
         self.d_flag = [torch.empty(nf * cap, dtype=torch.uint8, device=dev) for _ in self.ctxs]
         self.d_nat = [torch.empty(nf * cap, dtype=torch.float32, device=dev) if nat else None
@@ -205,15 +207,14 @@ class ScanServer:
 
     def prepare(self, records):
         """Make these query profiles resident with their score tables built
-        (creating a plan per filter builds them; nothing is launched), so the
-        requests that use them pay no set-up on the latency path."""
-        sl = slice(0, self.n)
+        (creating a plan builds them; nothing is launched), so the requests
+        that use them pay no set-up on the latency path."""
+        sl = slice(0, 2 * self.n)
         for rec in records:
             prof = self._profile(rec)
-            for f in self.FILTERS:
-                pl = mpf.Plan(self.ctxs[0], f, [prof], self.db, self.d_raw[0][sl], self.d_flag[0][sl],
-                              self.d_nat[0][sl] if self.want_nat else None)
-                pl.close()
+            pl = mpf.Plan(self.ctxs[0], mpf.MSV_SSV, [prof], self.db, self.d_raw[0][sl], self.d_flag[0][sl],
+                          self.d_nat[0][sl] if self.want_nat else None)
+            pl.close()
 
     # -------------------------------------------------------------- phases --
     def _launch(self, si: int, reqs: List[Request], now: float):
@@ -223,24 +224,19 @@ class ScanServer:
         for r in reqs:
             self._in_use[id(r.profile)] += 1
         q = len(reqs)
-        plans = []
-        for fi, filt in enumerate(self.FILTERS):
-            off = fi * self.max_batch * self.n
-            sl = slice(off, off + q * self.n)
-            nat = self.d_nat[si][sl] if self.want_nat else None
-            plans.append(mpf.Plan(ctx, filt, profs, self.db, self.d_raw[si][sl],
-                                  self.d_flag[si][sl], nat))
+        # One plan for both filters: a query whose MSV holds its begin score
+        # is swept once for the two (MPF_MSV_SSV), others run each filter.
+        sl = slice(0, 2 * q * self.n)
+        nat = self.d_nat[si][sl] if self.want_nat else None
+        plans = [mpf.Plan(ctx, mpf.MSV_SSV, profs, self.db, self.d_raw[si][sl], self.d_flag[si][sl], nat)]
         stream = ctx.torch_stream()
         with torch.cuda.stream(stream):
             for pl in plans:
                 pl.launch()
-            for fi in range(len(self.FILTERS)):
-                off = fi * self.max_batch * self.n
-                sl = slice(off, off + q * self.n)
-                self.h_raw[si][sl].copy_(self.d_raw[si][sl], non_blocking=True)
-                self.h_flag[si][sl].copy_(self.d_flag[si][sl], non_blocking=True)
-                if self.want_nat:
-                    self.h_nat[si][sl].copy_(self.d_nat[si][sl], non_blocking=True)
+            self.h_raw[si][sl].copy_(self.d_raw[si][sl], non_blocking=True)
+            self.h_flag[si][sl].copy_(self.d_flag[si][sl], non_blocking=True)
+            if self.want_nat:
+                self.h_nat[si][sl].copy_(self.d_nat[si][sl], non_blocking=True)
             ev = torch.cuda.Event()
             ev.record(stream)
         hbm = sum(r.footprint.hbm_bytes for r in reqs)
@@ -260,12 +256,13 @@ class ScanServer:
         for b in done:
             t = now_fn()
             si = b.stream_idx
+            q = len(b.requests)
             for i, r in enumerate(b.requests):
                 r.completed = t
                 if self.keep:
                     res = {}
-                    for fi, filt in enumerate(self.FILTERS):
-                        off = fi * self.max_batch * self.n + i * self.n
+                    for filt in self.FILTERS:
+                        off = ((0 if filt == mpf.MSV else q) + i) * self.n
                         sl = slice(off, off + self.n)
                         res[filt] = (self.h_raw[si][sl].numpy().copy(),
                                      self.h_flag[si][sl].numpy().copy(),

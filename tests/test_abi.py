@@ -62,7 +62,7 @@ def test_null_arguments_are_rejected_without_a_device(lib):
     assert lib.mpf_msv_scan(None, None, None, None, None, None) == mpf.MPF_EINVAL
     assert lib.mpf_plan_launch(None) == mpf.MPF_EINVAL
     assert lib.mpf_plan_group_count(None) == 0
-    assert lib.mpf_plan_group_info(None, 0, None, None, None, None, None) == mpf.MPF_EINVAL
+    assert lib.mpf_plan_group_info(None, 0, None, None, None, None, None, None) == mpf.MPF_EINVAL
     assert lib.mpf_sync(None) == mpf.MPF_EINVAL
     lib.mpf_ctx_destroy(None)
     lib.mpf_profile_destroy(None)

@@ -413,6 +413,75 @@ def test_packed_queries_per_warp(ctx):
     assert seen_flag > 0
 
 
+def test_msv_and_ssv_in_one_sweep(ctx):
+    """MPF_MSV_SSV plans and batches (one sweep for both filters where the
+    profile allows it) equal the oracle for both filters and the two
+    one-filter plans: whole-warp queries with the table in TMEM and in
+    shared memory, packed sets of narrow queries, strong profiles that
+    overflow and chain J (held-pass rescoring), and queries that cannot be
+    fused and run each filter's kernels instead: fp16 SSV cells, different
+    configurations per filter, an MSV that needs the per-row J/B update, a
+    long model.  Graph replay and host outputs too."""
+    rng = np.random.default_rng(4242)
+    db = synth.make_database(900, 330, 0, 4000, rng)
+    strong_db = synth.random_database(300, 500, rng, alphabet=20, min_len=0)
+    recs = [synth.make_profile(M, rng) for M in (60, 250, 500, 700, 1300, 2405)]
+    recs += [synth.make_profile(2 * 8 * 22 - 3, rng) for _ in range(4)]       # a packed set
+    recs += [synth.make_profile(400, rng), synth.make_profile(900, rng), synth.make_profile(3500, rng)]
+    recs.append(synth.random_profile(300, 20, rng, bias=250, base=250, tbm=0))   # MSV without held b
+    strong = [synth.random_profile(M, 20, rng, cost_hi=26, bias=20, base=190, tbm=10, tec=3, tjb=8)
+              for M in (150, 352, 352, 352, 352, 1500, 2405)]
+    for bi, (sdb, rlist) in enumerate(((db, recs), (strong_db, strong))):
+        ddb = mpf.Database(ctx, sdb.residues, sdb.offsets, sdb.lengths)
+        profs = [mpf.Profile(ctx, r) for r in rlist]
+        if bi == 0:
+            for pr in profs[6:10]:
+                for gf, _ in FILTERS:
+                    pr.set_config(gf, 8, 22)
+            profs[1].set_table_memory(mpf.MSV, mpf.TABLE_SHARED)     # table memories differ: not fused
+            profs[5].set_table_memory(mpf.MSV, mpf.TABLE_SHARED)
+            profs[5].set_table_memory(mpf.SSV, mpf.TABLE_SHARED)     # fused, shared-memory table
+            profs[10].set_arith(mpf.SSV, mpf.ARITH_F16)              # fp16 SSV: not fused
+            profs[11].set_config(mpf.SSV, 32, 16)                    # configurations differ: not fused
+        else:
+            for pr in profs[1:5]:
+                for gf, _ in FILTERS:
+                    pr.set_config(gf, 8, 22)
+        n, q = ddb.n_seqs, len(profs)
+        dev = torch.device("cuda", 0)
+        outs = [torch.full((2 * q * n,), 7, dtype=dt, device=dev) for dt in (torch.uint8, torch.uint8, torch.float32)]
+        plan = mpf.Plan(ctx, mpf.MSV_SSV, profs, ddb, *outs)
+        groups = plan.groups()
+        # Fused: every query but the five that cannot be (bi == 0) or all.
+        n_fused = sum(g["n_queries"] for g in groups if g["filters"] == 3)
+        assert n_fused == (q - 5 if bi == 0 else q), groups
+        assert sum(g["n_queries"] for g in groups if g["filters"] == 1) == q - n_fused
+        assert sum(g["n_queries"] for g in groups if g["filters"] == 2) == q - n_fused
+        assert any(g["filters"] == 3 and g["queries_per_warp"] == 4 for g in groups)
+        assert any(g["filters"] == 3 and g["table"] == mpf.TABLE_TENSOR and g["lanes"] == 32 for g in groups)
+        if bi == 0:
+            plan.capture_graph()
+        for _ in range(2):
+            plan.launch()
+        ctx.sync()
+        fused = [t.cpu().numpy() for t in outs]
+        plan.close()
+        host = (np.empty(2 * q * n, np.uint8), np.empty(2 * q * n, np.uint8), np.empty(2 * q * n, np.float32))
+        mpf.scan_batch(ctx, mpf.MSV_SSV, profs, ddb, *host)
+        for fb, (gf, of) in enumerate(FILTERS):
+            _, sep = _plan_outputs(ctx, gf, profs, ddb)
+            for i, rec in enumerate(rlist):
+                exp = oracle.scan(of, rec, sdb.residues, sdb.offsets, sdb.lengths, nthreads=8)
+                sl = slice((fb * q + i) * n, (fb * q + i + 1) * n)
+                what = f"batch {bi} filter {gf} q{i} M={rec.M}"
+                assert_same(tuple(a[sl] for a in fused), exp, "fused plan " + what)
+                assert_same(tuple(a[sl] for a in host), exp, "fused batch " + what)
+                assert_same(sep[i], exp, "one-filter plan " + what)
+        for pr in profs:
+            pr.close()
+        ddb.close()
+
+
 # ------------------------------------------------------------ arguments ---
 
 def test_invalid_arguments(ctx):
