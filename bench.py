@@ -44,11 +44,11 @@ OPS_PER_CELL = {"msv": 4, "ssv": 2}
 # length; only used while the kernel is the one that was captured.
 NCU_TRAFFIC = {
     # held MSV pass + its exact rescoring launch (profiles/scan_kernel_tmem_m2405_msweep500k.md)
-    ("scan_kernel<32,38,MSV_HELD,TMEM>", "msweep_500k", 2405): 187.824128e6 + 3.735040e6 + 0.295168e6,
-    ("scan_kernel<32,38,SSV,TMEM>", "msweep_500k", 2405): 187.740928e6 + 3.622144e6,
+    ("scan_kernel<32,38,MSV_HELD,TMEM>", "msweep_500k", 2405): 188.997120e6 + 3.679488e6 + 0.259072e6,
+    ("scan_kernel<32,38,SSV,TMEM>", "msweep_500k", 2405): 187.847168e6 + 3.696896e6,
 }
 KERNEL_SOURCE = os.path.join(ROOT, "paper_1707_09683_gb300", "csrc", "mpf_scan_kernel.cuh")
-KERNEL_SOURCE_SHA256 = "98ce1293f00f6235405e5b0120d578eabbf05726f7f19389e186d55b87bad9cc"
+KERNEL_SOURCE_SHA256 = "3c01448ed58c3c08995b25b7e662a6ad9ac66836dd28eb7990cc425fb907ed9f"
 
 
 def log(*a):
@@ -984,8 +984,15 @@ def run_small_workload(args, ctx, dev, reps=5):
 
 def run_profile_case(args):
     """Small case for ncu: the 500,000-sequence database (larger than L2) and
-    one query of M = args.profile_m; one warm-up and one measured plain launch
-    per filter (kernel launches 0-1 warm-up, 2 = MSV, 3 = SSV)."""
+    one query of M = args.profile_m; one warm-up and one measured run.
+    Forms (args.profile_form): plain -- one plan per filter (per run: the
+    held MSV pass, its rescoring launch, SSV); fused -- one MPF_MSV_SSV plan
+    (the one-sweep kernel, its rescoring launch); packed -- 32 /
+    args.profile_lanes queries of M = args.profile_m at that lane count in
+    one plan per filter, so they run as one packed set (per run: held MSV
+    set, rescoring, SSV set)."""
+    if args.profile_form != "plain":
+        return run_profile_case_batch(args)
     import torch
     from paper_1707_09683_gb300 import build, mpf, synth
     build.build()
@@ -1011,6 +1018,49 @@ def run_profile_case(args):
     print(json.dumps({"profile_case": wl.name, "M": prof_rec.M, "n_seqs": n,
                       "residues": db.n_residues, "config_msv": prof.get_config(mpf.MSV),
                       "config_ssv": prof.get_config(mpf.SSV)}))
+
+
+def run_profile_case_batch(args):
+    import torch
+    from paper_1707_09683_gb300 import build, mpf, synth
+    build.build()
+    wl = synth.make_workload(1)
+    rng = np.random.default_rng(0)
+    ctx = mpf.Context(0)
+    k = min(args.profile_seqs or wl.db.n_seqs, wl.db.n_seqs)
+    db = mpf.Database(ctx, wl.db.residues, wl.db.offsets[:k], wl.db.lengths[:k])
+    n = db.n_seqs
+    dev = torch.device("cuda", 0)
+    if args.profile_form == "fused":
+        recs = [next((p for p in wl.profiles if p.M == args.profile_m), None) or
+                synth.make_profile(args.profile_m, rng)]
+    else:
+        recs = [synth.make_profile(args.profile_m, rng) for _ in range(32 // args.profile_lanes)]
+    profs = [mpf.Profile(ctx, r) for r in recs]
+    if args.profile_form == "packed":
+        words = -(-args.profile_m // (2 * args.profile_lanes))
+        words += words % 2
+        for pr in profs:
+            for f in (mpf.MSV, mpf.SSV):
+                pr.set_config(f, args.profile_lanes, words)
+    q = len(profs)
+    if args.profile_form == "fused":
+        outs = [torch.empty(2 * q * n, dtype=dt, device=dev) for dt in (torch.uint8, torch.uint8, torch.float32)]
+        plans = [mpf.Plan(ctx, mpf.MSV_SSV, profs, db, *outs)]
+    else:
+        outs = [torch.empty(q * n, dtype=dt, device=dev) for dt in (torch.uint8, torch.uint8, torch.float32)]
+        plans = [mpf.Plan(ctx, f, profs, db, *outs) for f in (mpf.MSV, mpf.SSV)]
+    groups = [g for pl in plans for g in pl.groups()]
+    for rep in range(2):
+        for pl in plans:
+            pl.launch()
+        ctx.sync()
+    launches = sum(pl.kernel_launches for pl in plans)
+    for pl in plans:
+        pl.close()
+    print(json.dumps({"profile_case": wl.name, "form": args.profile_form, "M": args.profile_m, "queries": q,
+                      "n_seqs": n, "residues": db.n_residues, "groups": groups,
+                      "kernel_launches_per_run": launches}))
 
 
 def run_profile_viterbi(args):
@@ -1107,7 +1157,7 @@ def main():
                     help="model length of the long-model measurement (0: skip)")
     ap.add_argument("--long-vit-seqs", type=int, default=40000,
                     help="sequences of the long-model Viterbi measurement")
-    ap.add_argument("--serve-rates", type=float, nargs="+", default=[5, 8, 12, 20, 500])
+    ap.add_argument("--serve-rates", type=float, nargs="+", default=[5, 10, 15, 20, 25, 500])
     ap.add_argument("--serve-requests", type=int, default=200)
     ap.add_argument("--serve-workload", type=int, default=3,
                     help="workload whose database the serving measurement uses (3: 5 M sequences)")
@@ -1116,6 +1166,8 @@ def main():
                     help="serving: work budget in mean-query units (default: none)")
     ap.add_argument("--profile-case", action="store_true")
     ap.add_argument("--profile-m", type=int, default=2405)
+    ap.add_argument("--profile-form", default="plain", choices=["plain", "fused", "packed"])
+    ap.add_argument("--profile-lanes", type=int, default=8, help="packed profile case: lanes per sequence")
     ap.add_argument("--profile-seqs", type=int, default=0,
                     help="profile case: first N sequences of the database (0: all)")
     ap.add_argument("--profile-viterbi", action="store_true")
