@@ -699,8 +699,11 @@ def run_long_model(args, ctx, db, wl, time_steps, clocks, dev):
     nsm = torch.cuda.get_device_properties(dev).multi_processor_count
     sm_mhz = clocks.get("sm_mhz") or 2070.0
     out = {"M": args.long_m, "config": list(prof.get_config(mpf.MSV)), "n_seqs": n,
-           "cells_per_launch": args.long_m * res, "kernel": "MSV: long_kernel (lane segments, DP row in shared memory, costs through L1); "
-                     "SSV: tile_ssv_kernel (1,024-node tiles, DP row in registers)"}
+           "cells_per_launch": args.long_m * res,
+           "kernel": ("MSV: " + ("tile_kernel_tm<MSV> (1,024-node tiles in TMEM, b held) + long_kernel over the "
+                                 "sequences it lists" if prof.get_table_memory(mpf.MSV) == mpf.TABLE_TENSOR else
+                                 "long_kernel (lane segments, DP row in shared memory)") +
+                      "; SSV: tile_kernel_tm<SSV> (1,024-node tiles in TMEM, DP row in registers)")}
     steps = max(1, min(args.steps, 3))
     for name, code in (("msv", mpf.MSV), ("ssv", mpf.SSV)):
         pl = mpf.Plan(ctx, code, [prof], db, *outs)
@@ -710,7 +713,8 @@ def run_long_model(args, ctx, db, wl, time_steps, clocks, dev):
         g = args.long_m * res / (ms * 1e-3) / 1e9
         peak = nsm * INT_LANES_PER_SM_CLK * CELLS_PER_LANE_OP / OPS_PER_CELL[name] * sm_mhz * 1e6 / 1e9
         out[name] = {"gcups": g, "ms_per_launch": ms, "roofline_frac": g / peak, "peak": peak,
-                     "kernel": "long_kernel" if name == "msv" else "tile_ssv_kernel"}
+                     "kernel": ("tile_kernel_tm<MSV>" if prof.get_table_memory(mpf.MSV) == mpf.TABLE_TENSOR
+                                else "long_kernel") if name == "msv" else "tile_kernel_tm<SSV>"}
         log(f"long model M={args.long_m}: {name} {g:.1f} GCUPS ({ms:.1f} ms per launch)")
     prof.close()
     out["roofline_basis"] = "integer-SIMD roofline of the striped kernels (same formula as roofline.peak)"

@@ -173,13 +173,15 @@ enum { MPF_ARITH_AUTO = 0, MPF_ARITH_I16 = 1, MPF_ARITH_F16 = 2 };
 int mpf_profile_set_arith(mpf_profile *prof, int filter, int arith);
 
 /*
- * Where a striped scan reads its score table (not in the paper, whose Alg. 4
- * reads it through the read-only cache).  Every kernel stages the table in
+ * Where a scan reads its score table (not in the paper, whose Alg. 4 reads
+ * it through the read-only cache).  Every striped kernel stages the table in
  * shared memory; with one sequence per warp (lanes 32, words >= 8) the
  * automatic choice also copies the first words of each lane's row (all of
  * them up to 14 words per lane, else 12) into the SM's tensor memory (TMEM,
  * read by tcgen05.ld at about three times the shared-memory rate) and reads
- * those words from there.  Results are identical either way.
+ * those words from there.  For long models the tiled kernels' automatic
+ * choice holds each 1,024-node tile in TMEM instead of shared memory (one
+ * block of 16 warps per SM).  Results are identical either way.
  *   set: MPF_TABLE_AUTO (default) or MPF_TABLE_SHARED (shared memory only).
  *   get: MPF_TABLE_TENSOR or MPF_TABLE_SHARED, for the configuration the
  *        next scan will use.
@@ -246,8 +248,9 @@ int mpf_ssv_scan(mpf_ctx *ctx, const mpf_profile *prof, const mpf_db *db, uint8_
  * follow the SSV recurrence (Alg. 7), so one sweep's largest cell gives both
  * scores.  That needs integer cells for both filters and the same
  * configuration and table memory for both (mpf_profile_set_config,
- * mpf_profile_set_table_memory; the MSV shard factor is used); other
- * queries, and long models, run each filter's kernels.
+ * mpf_profile_set_table_memory; the MSV shard factor is used); long models
+ * whose MSV runs the held tiled pass sweep their tiles once for both.  Other
+ * queries run each filter's kernels.
  * Errors: as the single scans.
  */
 int mpf_scan_batch(mpf_ctx *ctx, int filter, const mpf_profile *const *profs, int n_q,
@@ -259,12 +262,14 @@ int mpf_scan_batch(mpf_ctx *ctx, int filter, const mpf_profile *const *profs, in
  * scan on the context stream without host synchronisation or allocation.
  * Queries whose kernel configurations differ run as separate kernels that
  * overlap (forked streams, joined back into the context stream).  In a plan
- * of two or more queries, those with 8 or 16 lanes per sequence (integer
- * SSV, held MSV, table memory not set to MPF_TABLE_SHARED, at least 8 words)
- * are packed 32 / lanes to a warp: the warp scores one sequence against
- * all of them, with the score rows in tensor memory.  Packed queries are
- * sorted by words per lane and each takes the largest word count of its set
- * (the added nodes score as padding: the outputs do not change).
+ * of two or more queries, those with fewer than 32 lanes per sequence
+ * (integer SSV, held MSV or both, table memory not set to MPF_TABLE_SHARED,
+ * at least 8 words) may be packed 32 / lanes to a warp: the warp scores one
+ * sequence against all of them, with the score rows in tensor memory.
+ * Packed queries are sorted by words per lane; runs of them form sets where
+ * a cost model in warp-words per row says a set pays, and each takes the
+ * largest word count of its set (the added nodes score as padding: the
+ * outputs do not change).
  *   mpf_plan_create:  arguments as mpf_scan_batch; raw/overflow/nat must be
  *                     device pointers (MPF_EINVAL otherwise).  The plan keeps
  *                     pointers to the profiles and database: they must outlive it.

@@ -287,13 +287,16 @@ int kernel_mode(const mpf_profile *p, int filter) {
   return f16 ? MODE_MSV_HELD_F16 : MODE_MSV_HELD;
 }
 
-// Whether one sweep can score a profile for both filters (MODE_MSV_SSV):
-// MSV runs the held pass, SSV integer cells, and the two filters have the
-// same configuration and table memory.
-bool fused_ok(const mpf_profile *p) {
-  return !p->seg_words && kernel_mode(p, MPF_MSV) == MODE_MSV_HELD && kernel_mode(p, MPF_SSV) == MODE_SSV &&
-         p->cfg_lanes[MPF_MSV] == p->cfg_lanes[MPF_SSV] && p->cfg_words[MPF_MSV] == p->cfg_words[MPF_SSV] &&
-         p->table_mem[MPF_MSV] == p->table_mem[MPF_SSV];
+// The mode that scores a profile for both filters in one sweep, or -1:
+// MSV runs a held pass (striped or tiled) and SSV the matching integer
+// kernel; striped profiles also need the same configuration and table
+// memory for both filters.
+int fused_mode(const mpf_profile *p) {
+  const int mm = kernel_mode(p, MPF_MSV), ms = kernel_mode(p, MPF_SSV);
+  if (mm == MODE_TILE_MSV && ms == MODE_TILE_SSV) return MODE_TILE_MSV_SSV;
+  const bool same = p->cfg_lanes[MPF_MSV] == p->cfg_lanes[MPF_SSV] && p->cfg_words[MPF_MSV] == p->cfg_words[MPF_SSV] &&
+                    p->table_mem[MPF_MSV] == p->table_mem[MPF_SSV];
+  return (mm == MODE_MSV_HELD && ms == MODE_SSV && same) ? MODE_MSV_SSV : -1;
 }
 
 // Whether a striped scan of this profile reads its table from tensor memory:
@@ -370,18 +373,21 @@ int free_pending(mpf_ctx *ctx) {
 }
 
 int configure_kernel(mpf_ctx *ctx, LaunchGroup *g) {
-  if (g->mode == MODE_TILE_SSV || g->mode == MODE_TILE_MSV) {
-    // Blocks of kTileWarps warps with one tile's scores in shared memory.
-    g->fn = tile_kernel_fn(g->mode == MODE_TILE_MSV);
-    g->threads = kTileWarps * 32;
-    g->smem = (uint32_t)kTileTableBytes;
+  if (g->mode == MODE_TILE_SSV || g->mode == MODE_TILE_MSV || g->mode == MODE_TILE_MSV_SSV) {
+    // Blocks of kTileWarps warps with one tile's scores in shared memory, or
+    // (tm) one block of kTileWarpsTm warps per SM with the tile in TMEM: it
+    // asks for more than half the shared memory so that no second block of
+    // the kernel shares the SM.
+    g->fn = tile_kernel_fn(g->mode, g->tm);
+    g->threads = (g->tm ? kTileWarpsTm : kTileWarps) * 32;
+    g->smem = g->tm ? (uint32_t)ctx->max_smem / 2 + 1024 : (uint32_t)kTileTableBytes;
     MPF_CUDA(cudaFuncSetAttribute((const void *)g->fn, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                   (int)g->smem));
     MPF_CUDA(cudaFuncSetAttribute((const void *)g->fn, cudaFuncAttributePreferredSharedMemoryCarveout, 100));
     int per_sm = 0;
     MPF_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, (const void *)g->fn, g->threads,
                                                            g->smem));
-    if (per_sm < 1) return MPF_EUNSUPPORTED;
+    if (per_sm < 1 || (g->tm && per_sm != 1)) return MPF_EUNSUPPORTED;
     g->grid = ctx->num_sms * per_sm;
     g->n_shards = (uint32_t)g->grid;
     return MPF_OK;
@@ -504,8 +510,8 @@ int plan_create(mpf_ctx *ctx, int filter, const mpf_profile *const *profs, int n
     }
     if (filter != MPF_MSV_SSV) {
       jobs.push_back(Job{i, filter, kernel_mode(p, filter), 0});
-    } else if (fused_ok(p)) {
-      jobs.push_back(Job{i, MPF_MSV, MODE_MSV_SSV, 0});
+    } else if (fused_mode(p) >= 0) {
+      jobs.push_back(Job{i, MPF_MSV, fused_mode(p), 0});
     } else {
       jobs.push_back(Job{i, MPF_MSV, kernel_mode(p, MPF_MSV), 0});
       jobs.push_back(Job{i, MPF_SSV, kernel_mode(p, MPF_SSV), 1});
@@ -527,7 +533,7 @@ int plan_create(mpf_ctx *ctx, int filter, const mpf_profile *const *profs, int n
     QueryDesc q;
     memset(&q, 0, sizeof(q));
     int lanes = 32, words = 0;
-    if (mode == MODE_TILE_SSV || mode == MODE_TILE_MSV) {
+    if (mode == MODE_TILE_SSV || mode == MODE_TILE_MSV || mode == MODE_TILE_MSV_SSV) {
       const uint4 *tt = nullptr;
       int rc = get_tile_table(p, &tt);
       if (rc) {
@@ -537,7 +543,8 @@ int plan_create(mpf_ctx *ctx, int filter, const mpf_profile *const *profs, int n
       q.table = tt;
       q.M = (uint32_t)p->M;
       q.smax_off = (uint32_t)(((size_t)(p->M + kTileNodes - 1) / kTileNodes) * kTileTableBytes);
-      if (mode == MODE_TILE_MSV) {   // the lane-segment kernel's table, for the fallback
+      const int ttm = p->table_mem[f] == MPF_TABLE_SHARED ? 0 : 1;   // tiles in TMEM
+      if (mode != MODE_TILE_SSV) {   // the lane-segment kernel's table, for the fallback
         const uint8_t *lt = nullptr;
         rc = get_long_table(p, &lt);
         if (rc) {
@@ -546,8 +553,8 @@ int plan_create(mpf_ctx *ctx, int filter, const mpf_profile *const *profs, int n
         }
         DevTable lt_t{};
         lt_t.ptr = reinterpret_cast<uint4 *>(const_cast<uint8_t *>(lt));
-        fb_table[GroupKey(lanes, words, mode, 0, 1)].push_back(lt_t);
-        fb_seg_words[GroupKey(lanes, words, mode, 0, 1)].push_back((uint32_t)p->seg_words);
+        fb_table[GroupKey(lanes, words, mode, ttm, 1)].push_back(lt_t);
+        fb_seg_words[GroupKey(lanes, words, mode, ttm, 1)].push_back((uint32_t)p->seg_words);
       }
     } else if (p->seg_words) {
       const uint8_t *lt = nullptr;
@@ -599,7 +606,7 @@ int plan_create(mpf_ctx *ctx, int filter, const mpf_profile *const *profs, int n
     q.raw = raw + off;
     q.flag = flag + off;
     q.nat = nat ? nat + off : nullptr;
-    if (mode == MODE_MSV_SSV) {   // the SSV block
+    if (mode == MODE_MSV_SSV || mode == MODE_TILE_MSV_SSV) {   // the SSV block
       const size_t off2 = ((size_t)n_q + (size_t)i) * db->n_seqs;
       q.raw2 = raw + off2;
       q.flag2 = flag + off2;
@@ -607,7 +614,9 @@ int plan_create(mpf_ctx *ctx, int filter, const mpf_profile *const *profs, int n
     }
     q.ranks = ranks ? ranks + off : nullptr;
     q.n_ranks = ranks ? n_ranks + i : nullptr;
-    const int tm = p->seg_words ? 0 : (use_tmem(p, f, lanes, words, mode) ? 1 : 0);
+    const bool tiled = mode == MODE_TILE_SSV || mode == MODE_TILE_MSV || mode == MODE_TILE_MSV_SSV;
+    const int tm = tiled ? (p->table_mem[f] == MPF_TABLE_SHARED ? 0 : 1)
+                         : p->seg_words ? 0 : (use_tmem(p, f, lanes, words, mode) ? 1 : 0);
     const int sf = p->seg_words ? 1 : p->shard_factor[f];
     if (n_q >= 2 && !ranks && !p->seg_words && lanes < 32 &&
         (mode == MODE_SSV || mode == MODE_MSV_HELD || mode == MODE_MSV_SSV) && words >= kTmMinWords &&
@@ -716,15 +725,15 @@ int plan_create(mpf_ctx *ctx, int filter, const mpf_profile *const *profs, int n
     for (const QueryDesc &qd : kv.second) g.n_real += qd.table ? 1u : 0u;
     cudaError_t e = cudaMallocAsync((void **)&g.d_queries, sizeof(QueryDesc) * kv.second.size(), ctx->stream);
     if (e == cudaSuccess) e = cudaMallocAsync((void **)&g.d_counter, sizeof(uint32_t), ctx->stream);
-    if (e == cudaSuccess && (g.mode == MODE_TILE_SSV || g.mode == MODE_TILE_MSV)) {
+    if (e == cudaSuccess && (g.mode == MODE_TILE_SSV || g.mode == MODE_TILE_MSV || g.mode == MODE_TILE_MSV_SSV)) {
       // Per resident warp two columns of int16 (positions 0..max_len and
       // the prefetch's overrun), col_stride bytes each.
       g.col_stride = (uint32_t)((((uint64_t)db->max_len + 12) * 2 + 15) & ~(uint64_t)15);
-      g.col_bytes = (uint64_t)g.grid * kTileWarps * 2 * g.col_stride;
+      g.col_bytes = (uint64_t)g.grid * (uint64_t)(g.threads / 32) * 2 * g.col_stride;
       e = cudaMallocAsync((void **)&g.d_col, g.col_bytes, ctx->stream);
     }
     const bool held = g.mode == MODE_MSV_HELD || g.mode == MODE_MSV_HELD_F16 || g.mode == MODE_MSV_SSV;
-    if (e == cudaSuccess && (g.mode == MODE_TILE_MSV || held)) {
+    if (e == cudaSuccess && (g.mode == MODE_TILE_MSV || g.mode == MODE_TILE_MSV_SSV || held)) {
       // Fallback lists, and the launch that scores them exactly: the
       // lane-segment kernel after the tiled MSV pass, the striped kernel
       // with the J/B update every row after the held pass.
@@ -1111,12 +1120,13 @@ int mpf_profile_set_table_memory(mpf_profile *p, int filter, int where) {
 
 int mpf_profile_get_table_memory(const mpf_profile *p, int filter, int *where) {
   if (!p || !where || (filter != MPF_MSV && filter != MPF_SSV)) return MPF_EINVAL;
-  if (p->seg_words) {
-    *where = MPF_TABLE_SHARED;
+  const int mode = kernel_mode(p, filter);
+  if (p->seg_words) {   // tiled kernels: the tile in TMEM unless set to shared; lane segments: shared
+    *where = (mode != MODE_LONG_MSV && p->table_mem[filter] != MPF_TABLE_SHARED) ? MPF_TABLE_TENSOR
+                                                                                 : MPF_TABLE_SHARED;
     return MPF_OK;
   }
   int lanes = p->cfg_lanes[filter], words = p->cfg_words[filter];
-  const int mode = kernel_mode(p, filter);
   if (!lanes) default_config(p->ctx, p->M, mode, &lanes, &words);
   *where = use_tmem(p, filter, lanes, words, mode) ? MPF_TABLE_TENSOR : MPF_TABLE_SHARED;
   return MPF_OK;
@@ -1146,7 +1156,10 @@ int mpf_profile_footprint(const mpf_profile *p, int filter, uint32_t *smem_bytes
       *smem_bytes = (uint32_t)long_smem_per_warp(p->seg_words, 4 * long_smem_per_warp(p->seg_words, false) > 228 * 1024);
       *table_bytes = long_table;
     } else {
-      *smem_bytes = (uint32_t)kTileTableBytes;
+      // The TMEM variant holds the tile in tensor memory and asks for more
+      // than half the shared memory (one block per SM).
+      *smem_bytes = p->table_mem[filter] == MPF_TABLE_SHARED ? (uint32_t)kTileTableBytes
+                                                             : (uint32_t)p->ctx->max_smem / 2 + 1024;
       *table_bytes = tiles * kTileTableBytes + 64 + (mode == MODE_TILE_MSV ? long_table : 0);
     }
     return MPF_OK;
@@ -1340,7 +1353,7 @@ int mpf_plan_group_info(const mpf_plan *plan, int i, int *lanes, int *words, int
   if (n_queries) *n_queries = (int)g.n_real;
   if (filters) {
     switch (g.mode) {
-      case MODE_MSV_SSV: *filters = 3; break;
+      case MODE_MSV_SSV: case MODE_TILE_MSV_SSV: *filters = 3; break;
       case MODE_SSV: case MODE_SSV_F16: case MODE_TILE_SSV: *filters = 2; break;
       default: *filters = 1;
     }

@@ -56,6 +56,7 @@ enum Mode : int {
   MODE_MSV_SSV = 11,      // MODE_MSV_HELD and MODE_SSV from one sweep: with b held the MSV
                           //   cells minus b follow the SSV recurrence, so the largest cell
                           //   gives both filters' scores
+  MODE_TILE_MSV_SSV = 12, // MODE_TILE_MSV and MODE_TILE_SSV from one sweep (the same reason)
 };
 constexpr int kNumModes = 8;   // modes of the striped scan kernel
 
@@ -149,8 +150,11 @@ size_t long_smem_per_warp(int seg_words, bool bytes);
 constexpr int kTileC = 32;
 constexpr int kTileNodes = 32 * kTileC;
 constexpr int kTileWarps = 8;
+constexpr int kTileWarpsTm = 16;
 constexpr size_t kTileTableBytes = (size_t)32 * kTileNodes * 2;   // per tile
-KernelFn tile_kernel_fn(bool msv);
+// The tiled kernel for a mode (MODE_TILE_*); tm: the tensor-memory variant
+// (blocks of kTileWarpsTm warps, one per SM, the tile's scores in TMEM).
+KernelFn tile_kernel_fn(int mode, bool tm);
 
 // Stage-to-stage hand-off (mpf_pipeline.cu): SSV -> MSV (raw_bytes 1) and
 // MSV -> Viterbi (raw_bytes 2).

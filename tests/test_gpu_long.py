@@ -33,9 +33,12 @@ def _dev(n, dtype):
     return torch.empty(max(n, 1), dtype=dtype, device=torch.device("cuda", 0))
 
 
-def _check_filter(ctx, gf, of, recs, dbh, nthreads=16):
+def _check_filter(ctx, gf, of, recs, dbh, nthreads=16, table=None):
     db = mpf.Database(ctx, dbh.residues, dbh.offsets, dbh.lengths)
     profs = [mpf.Profile(ctx, r) for r in recs]
+    if table is not None:
+        for pr in profs:
+            pr.set_table_memory(gf, table)
     n, q = db.n_seqs, len(profs)
     raw, flag, nat = _dev(q * n, torch.uint8), _dev(q * n, torch.uint8), _dev(q * n, torch.float32)
     mpf.scan_batch(ctx, gf, profs, db, raw, flag, nat)
@@ -202,3 +205,44 @@ def test_long_profiles_take_one_configuration(ctx):
     with pytest.raises(mpf.MpfError) as e:
         mpf.scan_noalloc(ctx, mpf.MSV, p, db, _dev(n, torch.uint8), _dev(n, torch.uint8))
     assert e.value.status == mpf.MPF_EUNSUPPORTED
+
+
+@pytest.mark.parametrize("table", [mpf.TABLE_AUTO, mpf.TABLE_SHARED])
+def test_tiles_in_tensor_and_shared_memory(ctx, table):
+    """The tiled kernels with the tile's scores in tensor memory (the
+    automatic choice: one block of 16 warps per SM) and in shared memory:
+    ragged last tiles, planted hits that send sequences from the tiled MSV
+    pass to the exact kernel, a strong profile that overflows, and the
+    both-filter sweep of the same profiles; all against the oracle."""
+    rng = np.random.default_rng(91 + table)
+    recs = [synth.make_profile(M, rng) for M in (3073, 4100, 5000)]
+    recs.append(synth.random_profile(3500, 20, rng, cost_hi=26, bias=20, base=190, tbm=10, tec=3, tjb=8))
+    dbh = synth.make_database(700, 400, 0, 3000, rng)
+    synth.plant_segments(dbh, recs[:3], 0.1, rng, seg=(30, 300))
+    n_flag = 0
+    for gf, of in ((mpf.MSV, oracle.MSV), (mpf.SSV, oracle.SSV)):
+        n_flag += _check_filter(ctx, gf, of, recs, dbh, table=table)
+    assert n_flag > 0
+    db = mpf.Database(ctx, dbh.residues, dbh.offsets, dbh.lengths)
+    profs = [mpf.Profile(ctx, r) for r in recs]
+    for pr in profs:
+        for gf in (mpf.MSV, mpf.SSV):
+            pr.set_table_memory(gf, table)
+            assert pr.get_table_memory(gf) == (mpf.TABLE_TENSOR if table == mpf.TABLE_AUTO else mpf.TABLE_SHARED)
+    n, q = db.n_seqs, len(profs)
+    outs = [_dev(2 * q * n, dt) for dt in (torch.uint8, torch.uint8, torch.float32)]
+    plan = mpf.Plan(ctx, mpf.MSV_SSV, profs, db, *outs)
+    assert all(g["filters"] == 3 for g in plan.groups())
+    plan.launch()
+    ctx.sync()
+    got = [t.cpu().numpy() for t in outs]
+    plan.close()
+    for fb, of in enumerate((oracle.MSV, oracle.SSV)):
+        for i, r in enumerate(recs):
+            er, ef, en = oracle.scan(of, r, dbh.residues, dbh.offsets, dbh.lengths, nthreads=16)
+            sl = slice((fb * q + i) * n, (fb * q + i + 1) * n)
+            assert np.array_equal(got[1][sl], ef) and np.array_equal(got[0][sl], er), (fb, r.M)
+            assert np.array_equal(got[2][sl].view(np.uint32), en.view(np.uint32)), (fb, r.M)
+    for pr in profs:
+        pr.close()
+    db.close()

@@ -417,11 +417,13 @@ def test_msv_and_ssv_in_one_sweep(ctx):
     """MPF_MSV_SSV plans and batches (one sweep for both filters where the
     profile allows it) equal the oracle for both filters and the two
     one-filter plans: whole-warp queries with the table in TMEM and in
-    shared memory, packed sets of narrow queries, strong profiles that
-    overflow and chain J (held-pass rescoring), and queries that cannot be
-    fused and run each filter's kernels instead: fp16 SSV cells, different
-    configurations per filter, an MSV that needs the per-row J/B update, a
-    long model.  Graph replay and host outputs too."""
+    shared memory, packed sets of narrow queries, a long model (the tiled
+    sweep, with the lane-segment kernel rescoring what it lists), strong
+    profiles that overflow and chain J (held-pass rescoring), and queries
+    that cannot be fused and run each filter's kernels instead: table
+    memories that differ, fp16 SSV cells, different configurations per
+    filter, an MSV that needs the per-row J/B update.  Graph replay and host
+    outputs too."""
     rng = np.random.default_rng(4242)
     db = synth.make_database(900, 330, 0, 4000, rng)
     strong_db = synth.random_database(300, 500, rng, alphabet=20, min_len=0)
@@ -430,7 +432,7 @@ def test_msv_and_ssv_in_one_sweep(ctx):
     recs += [synth.make_profile(400, rng), synth.make_profile(900, rng), synth.make_profile(3500, rng)]
     recs.append(synth.random_profile(300, 20, rng, bias=250, base=250, tbm=0))   # MSV without held b
     strong = [synth.random_profile(M, 20, rng, cost_hi=26, bias=20, base=190, tbm=10, tec=3, tjb=8)
-              for M in (150, 352, 352, 352, 352, 1500, 2405)]
+              for M in (150, 352, 352, 352, 352, 1500, 2405, 3300)]
     for bi, (sdb, rlist) in enumerate(((db, recs), (strong_db, strong))):
         ddb = mpf.Database(ctx, sdb.residues, sdb.offsets, sdb.lengths)
         profs = [mpf.Profile(ctx, r) for r in rlist]
@@ -452,9 +454,11 @@ def test_msv_and_ssv_in_one_sweep(ctx):
         outs = [torch.full((2 * q * n,), 7, dtype=dt, device=dev) for dt in (torch.uint8, torch.uint8, torch.float32)]
         plan = mpf.Plan(ctx, mpf.MSV_SSV, profs, ddb, *outs)
         groups = plan.groups()
-        # Fused: every query but the five that cannot be (bi == 0) or all.
+        # Fused: every query but the four that cannot be (bi == 0) or all.
         n_fused = sum(g["n_queries"] for g in groups if g["filters"] == 3)
-        assert n_fused == (q - 5 if bi == 0 else q), groups
+        assert n_fused == (q - 4 if bi == 0 else q), groups
+        if bi == 0:   # the long model's tiled sweep
+            assert any(g["filters"] == 3 and g["words"] == 0 for g in groups), groups
         assert sum(g["n_queries"] for g in groups if g["filters"] == 1) == q - n_fused
         assert sum(g["n_queries"] for g in groups if g["filters"] == 2) == q - n_fused
         assert any(g["filters"] == 3 and g["queries_per_warp"] == 4 for g in groups)
