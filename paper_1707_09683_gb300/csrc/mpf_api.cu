@@ -486,8 +486,8 @@ int plan_create(mpf_ctx *ctx, int filter, const mpf_profile *const *profs, int n
   std::map<GroupKey, std::vector<DevTable>> fb_table;   // tables of the exact rescoring launch
   std::map<GroupKey, std::vector<uint32_t>> fb_seg_words;
   std::map<GroupKey, int> group_shards;   // largest shard factor of a group's profiles
-  // Queries that may share a warp's sequence with others (8 or 16 lanes,
-  // integer SSV or held MSV), by (lanes, mode): placed after the loop.
+  // Queries that may share a warp's sequence with others (fewer than 32
+  // lanes; integer SSV, held MSV or both), by (lanes, mode): placed after the loop.
   struct QpCand {
     int words, sf;
     const mpf_profile *p;

@@ -3,7 +3,7 @@
 Every kernel family runs on the debug library over inputs that exercise its
 ragged edges -- striped scans in every lane-group size (and through the
 allocation-free entry point), packed sets of queries sharing a warp's
-sequence, rank lists from the
+sequence, both filters from one sweep (striped, packed and tiled), rank lists from the
 SSV -> MSV hand-off, long models through the tiled kernels (with the MSV
 fallback list) and the lane-segment kernel with 16-bit and byte rows, the
 Viterbi kernels and variants (rows in shared or device memory), the MSV ->
@@ -97,7 +97,25 @@ for gf, of in ((mpf.MSV, oracle.MSV), (mpf.SSV, oracle.SSV)):
         for g, w in zip(out, want):
             got = g[i * n:(i + 1) * n].cpu().numpy()[idx.astype(np.int64)]
             assert same(got, w), ("packed", i, gf)
-for pr in profs:
+# Both filters in one sweep: the packed set above, whole-warp queries with
+# the table in TMEM, and a long model (tiles in TMEM), in one plan.
+recs2 = recs[27:38] + [synth.make_profile(M, rng) for M in (1500, 2405, 3500)]
+profs2 = profs[27:38] + [mpf.Profile(ctx, r) for r in recs2[11:]]
+q = len(profs2)
+out = [torch.empty(2 * q * n, dtype=t, device=dev) for t in (torch.uint8, torch.uint8, torch.float32)]
+pl = mpf.Plan(ctx, mpf.MSV_SSV, profs2, db, *out)
+assert all(g["filters"] == 3 for g in pl.groups()), pl.groups()
+pl.launch()
+ctx.sync()
+pl.close()
+idx = np.arange(0, n, 5, dtype=np.uint64)
+for fb, of in enumerate((oracle.MSV, oracle.SSV)):
+    for i in (0, 7, 11, 12, 13):
+        want = oracle.scan(of, recs2[i], dbh.residues, dbh.offsets, dbh.lengths, index=idx, nthreads=8)
+        for g, w in zip(out, want):
+            got = g[(fb * q + i) * n:(fb * q + i + 1) * n].cpu().numpy()[idx.astype(np.int64)]
+            assert same(got, w), ("one sweep", i, fb)
+for pr in profs + profs2[11:]:
     pr.close()
 
 # The allocation-free entry point (its kernel reports through the context's
