@@ -289,6 +289,17 @@ int mpf_scan_batch(mpf_ctx *ctx, int filter, const mpf_profile *const *profs, in
  *                     of queries and the filters it scores (1: MSV, 2: SSV,
  *                     3: both in one sweep).  Any output pointer may be NULL;
  *                     MPF_EINVAL for a NULL plan or i out of range.
+ *   mpf_plan_pack_sets: the packed sets a plan forms among n queries of
+ *                     `lanes` lanes per sequence (1, 2, 4, 8 or 16) with
+ *                     these words per lane (ascending), blocks having
+ *                     max_smem bytes of shared memory: set_start[i] is the
+ *                     index of the first query of query i's set, or -1 when
+ *                     query i keeps its one-query kernel.  The sets are runs
+ *                     of at most 32 / lanes queries that minimise a cost in
+ *                     warp-words per row: (32 / lanes) x the set's largest
+ *                     words for a set, 5/4 of its own words for a query
+ *                     alone.  Host only.  MPF_EINVAL for other lanes, n < 0,
+ *                     NULL arrays, or words not ascending or below 1.
  *   mpf_plan_destroy: waits for the context stream, then frees the plan.
  */
 typedef struct mpf_plan mpf_plan;
@@ -299,6 +310,7 @@ int mpf_plan_launch(mpf_plan *plan);
 int mpf_plan_capture_graph(mpf_plan *plan);
 int mpf_plan_kernel_launches(const mpf_plan *plan);
 int mpf_plan_group_count(const mpf_plan *plan);
+int mpf_plan_pack_sets(int lanes, const int *words, int n, int max_smem, int *set_start);
 int mpf_plan_group_info(const mpf_plan *plan, int i, int *lanes, int *words, int *table_memory,
                         int *queries_per_warp, int *n_queries, int *filters);
 void mpf_plan_destroy(mpf_plan *plan);

@@ -308,6 +308,44 @@ bool use_tmem(const mpf_profile *p, int filter, int lanes, int words, int mode) 
          kernel_lg32_tm(words, mode) != nullptr;
 }
 
+// Packed sets of the candidates of one (lanes, mode), their word counts
+// ascending: runs [a, b) of consecutive queries; a run of two or more is a
+// set, padded to its largest word count, a run of one keeps its one-query
+// kernel.  The runs minimise a cost in warp-words per sequence row (times 4
+// below): a set costs (32 / lanes) x H, a query alone 5/4 of its own words
+// (the one-query kernels read every word from shared memory and run at about
+// 4/5 of the tensor-memory kernels' rate).  A set holds at most 32 / lanes
+// queries and needs a built kernel for H and tables that fit max_smem.
+std::vector<std::pair<size_t, size_t>> pack_runs(int lanes, int mode, const std::vector<int> &words,
+                                                 int max_smem) {
+  const size_t n = words.size();
+  const int QP = 32 / lanes;
+  auto packable = [&](int H) {
+    return kernel_qp_tm(lanes, H, mode) != nullptr &&
+           (uint64_t)QP * packed_table_stride(lanes, H) <= (uint64_t)max_smem;
+  };
+  // cost[b]: least cost of the first b queries; from[b]: start of the last run.
+  std::vector<int64_t> cost(n + 1, 0);
+  std::vector<size_t> from(n + 1, 0);
+  for (size_t b = 1; b <= n; ++b) {
+    cost[b] = cost[b - 1] + 5 * (int64_t)words[b - 1];
+    from[b] = b - 1;
+    const int H = words[b - 1];
+    if (!packable(H)) continue;
+    for (size_t a = b >= (size_t)QP ? b - (size_t)QP : 0; a + 2 <= b; ++a) {
+      const int64_t c = cost[a] + 4 * (int64_t)QP * H;
+      if (c < cost[b]) {
+        cost[b] = c;
+        from[b] = a;
+      }
+    }
+  }
+  std::vector<std::pair<size_t, size_t>> runs;
+  for (size_t b = n; b > 0; b = from[b]) runs.emplace_back(from[b], b);
+  std::reverse(runs.begin(), runs.end());
+  return runs;
+}
+
 }  // namespace host
 }  // namespace mpf
 
@@ -631,46 +669,19 @@ int plan_create(mpf_ctx *ctx, int filter, const mpf_profile *const *profs, int n
   }
   // Several queries per warp: 32 / lanes queries of one (lanes, mode) score
   // the same sequence in one warp, with the table rows in tensor memory.
-  // Sorted by words per lane, runs of consecutive queries form a warp's set,
-  // all padded to the run's largest word count H (padding nodes score
-  // kNegInf, so the scores are those of the query's own layout), with their
-  // tables in the packed geometry; empty slots of a set hold descriptors
-  // without a table.  The runs minimise a cost in warp-words per sequence
-  // row: a set costs (32 / lanes) x H, a query left to its one-query kernel
-  // its own words x 5/4 (those kernels read every word from shared memory
-  // and run at about 4/5 of the tensor-memory kernels' rate).  A set needs
-  // two queries, a built kernel for H and tables that fit the block's shared
-  // memory.  The held MSV pass's rescoring launch (one query per warp) reads
-  // the integer table of the usual geometry at H words.
+  // Sorted by words per lane, runs of consecutive queries form a warp's set
+  // (pack_runs), all padded to the run's largest word count H (padding nodes
+  // score kNegInf, so the scores are those of the query's own layout), with
+  // their tables in the packed geometry; empty slots of a set hold
+  // descriptors without a table.  The held MSV pass's rescoring launch (one
+  // query per warp) reads the integer table of the usual geometry at H words.
   for (auto &kv : qp_cand) {
     const int lanes = kv.first.first, mode = kv.first.second, QP = 32 / lanes;
     std::vector<QpCand> &v = kv.second;
     std::stable_sort(v.begin(), v.end(), [](const QpCand &a, const QpCand &b) { return a.words < b.words; });
-    const size_t n = v.size();
-    auto packable = [&](int H) {
-      return kernel_qp_tm(lanes, H, mode) != nullptr &&
-             (uint64_t)QP * packed_table_stride(lanes, H) <= (uint64_t)ctx->max_smem;
-    };
-    // cost[b]: least cost of the first b queries; from[b]: start of the last
-    // run (b - 1 for a query on its own).
-    std::vector<int64_t> cost(n + 1, 0);
-    std::vector<size_t> from(n + 1, 0);
-    for (size_t b = 1; b <= n; ++b) {
-      cost[b] = cost[b - 1] + 5 * (int64_t)v[b - 1].words;   // costs x 4
-      from[b] = b - 1;
-      const int H = v[b - 1].words;
-      if (!packable(H)) continue;
-      for (size_t a = b >= (size_t)QP ? b - (size_t)QP : 0; a + 2 <= b; ++a) {
-        const int64_t c = cost[a] + 4 * (int64_t)QP * H;
-        if (c < cost[b]) {
-          cost[b] = c;
-          from[b] = a;
-        }
-      }
-    }
-    std::vector<std::pair<size_t, size_t>> runs;
-    for (size_t b = n; b > 0; b = from[b]) runs.emplace_back(from[b], b);
-    std::reverse(runs.begin(), runs.end());
+    std::vector<int> words(v.size());
+    for (size_t j = 0; j < v.size(); ++j) words[j] = v[j].words;
+    const std::vector<std::pair<size_t, size_t>> runs = pack_runs(lanes, mode, words, ctx->max_smem);
     for (const auto &r : runs) {
       const size_t a = r.first, b = r.second;
       const bool pack = b - a >= 2;
@@ -1338,6 +1349,17 @@ int mpf_plan_kernel_launches(const mpf_plan *plan) {
   for (const LaunchGroup &g0 : plan->groups)
     for (const LaunchGroup *g = &g0; g; g = g->next.get()) ++n;   // with the rescoring launches
   return n;
+}
+
+int mpf_plan_pack_sets(int lanes, const int *words, int n, int max_smem, int *set_start) {
+  if ((lanes != 1 && lanes != 2 && lanes != 4 && lanes != 8 && lanes != 16) || n < 0 || (n && (!words || !set_start)))
+    return MPF_EINVAL;
+  std::vector<int> w(words, words + n);
+  for (int i = 0; i < n; ++i)
+    if (w[i] < 1 || (i && w[i] < w[i - 1])) return MPF_EINVAL;
+  for (const auto &r : pack_runs(lanes, MODE_SSV, w, max_smem))
+    for (size_t j = r.first; j < r.second; ++j) set_start[j] = r.second - r.first >= 2 ? (int)r.first : -1;
+  return MPF_OK;
 }
 
 int mpf_plan_group_count(const mpf_plan *plan) { return plan ? (int)plan->groups.size() : 0; }

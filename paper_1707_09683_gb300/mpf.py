@@ -78,6 +78,7 @@ def load(path: str = LIB_PATH):
         "mpf_plan_capture_graph": (i32, [vp]),
         "mpf_plan_kernel_launches": (i32, [vp]),
         "mpf_plan_group_count": (i32, [vp]),
+        "mpf_plan_pack_sets": (i32, [i32, vp, i32, i32, vp]),
         "mpf_plan_group_info": (i32, [vp, i32, vp, vp, vp, vp, vp, vp]),
         "mpf_plan_destroy": (None, [vp]),
         "mpf_scan_noalloc": (i32, [vp, i32, vp, vp, vp, vp, vp]),
@@ -407,6 +408,18 @@ class Plan:
             self.close()
         except Exception:
             pass
+
+
+def pack_sets(lanes: int, words, max_smem: int = 232448):
+    """``mpf_plan_pack_sets``: per query (words ascending) the index of the
+    first query of its packed set, or -1 for a query left to its one-query
+    kernel."""
+    w = np.ascontiguousarray(words, dtype=np.int32)
+    out = np.full(w.size, -2, dtype=np.int32)
+    _check(load().mpf_plan_pack_sets(int(lanes), w.ctypes.data if w.size else None, int(w.size),
+                                     int(max_smem), out.ctypes.data if w.size else None),
+           "mpf_plan_pack_sets")
+    return out
 
 
 def scan_noalloc(ctx: Context, filter: int, prof: Profile, db: Database, raw, overflow, nat=None):
