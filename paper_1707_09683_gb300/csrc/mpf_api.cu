@@ -737,9 +737,10 @@ int plan_create(mpf_ctx *ctx, int filter, const mpf_profile *const *profs, int n
     cudaError_t e = cudaMallocAsync((void **)&g.d_queries, sizeof(QueryDesc) * kv.second.size(), ctx->stream);
     if (e == cudaSuccess) e = cudaMallocAsync((void **)&g.d_counter, sizeof(uint32_t), ctx->stream);
     if (e == cudaSuccess && (g.mode == MODE_TILE_SSV || g.mode == MODE_TILE_MSV || g.mode == MODE_TILE_MSV_SSV)) {
-      // Per resident warp two columns of int16 (positions 0..max_len and
-      // the prefetch's overrun), col_stride bytes each.
-      g.col_stride = (uint32_t)((((uint64_t)db->max_len + 12) * 2 + 15) & ~(uint64_t)15);
+      // Per resident warp two columns (positions 0..max_len and the
+      // prefetch's overrun), col_stride bytes each: int16, or for the TMEM
+      // kernel the 32-bit pair holding the node.
+      g.col_stride = (uint32_t)((((uint64_t)db->max_len + 12) * (g.tm ? 4 : 2) + 15) & ~(uint64_t)15);
       g.col_bytes = (uint64_t)g.grid * (uint64_t)(g.threads / 32) * 2 * g.col_stride;
       e = cudaMallocAsync((void **)&g.d_col, g.col_bytes, ctx->stream);
     }

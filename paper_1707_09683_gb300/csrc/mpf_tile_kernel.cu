@@ -100,6 +100,23 @@ __device__ __forceinline__ void tile_row_regs(uint32_t (&v)[kPairs], uint32_t in
   }
 }
 
+// The same with the node before the segment in the high half of `in_word`
+// (the lane before's pair 15, or a boundary-column word): no extraction.
+__device__ __forceinline__ void tile_row_regs_w(uint32_t (&v)[kPairs], uint32_t in_word,
+                                                const uint32_t (&sc)[kPairs], uint32_t &rmax) {
+  const uint32_t d0 = __byte_perm(in_word, v[kPairs - 1], 0x5432);
+#pragma unroll
+  for (int q = kChunks - 1; q >= 0; --q) {
+#pragma unroll
+    for (int e = 3; e >= 0; --e) {
+      const int p = q * 4 + e;
+      v[p] = __viaddmax_s16x2(p > 0 ? v[p - 1] : d0, sc[p], 0u);
+    }
+    rmax = __vimax3_s16x2(rmax, v[q * 4], v[q * 4 + 1]);
+    rmax = __vimax3_s16x2(rmax, v[q * 4 + 2], v[q * 4 + 3]);
+  }
+}
+
 // MSV result of one sequence, by the whole warp: frow / fval, this lane's
 // first row with a cell above T and its largest cell there (kNone: none),
 // V this lane's largest cell.
@@ -333,8 +350,10 @@ __global__ void __launch_bounds__(kTileWarpsTm * 32, 1) tile_kernel_tm(ScanParam
   const int W = blockDim.x >> 5;
   constexpr int kTileWords = 32 * kChunks * 32;   // uint4 per tile
   const uint64_t cw = (uint64_t)blockIdx.x * W + warp;
-  int16_t *colbuf = reinterpret_cast<int16_t *>(sp.tile_col + cw * 2 * (uint64_t)sp.tile_col_stride);
-  const uint32_t col_elems = sp.tile_col_stride / 2;
+  // Boundary columns of 32-bit words: position i + 1 holds row i's pair 15
+  // of lane 31 (node 31 in the high half), read by the next tile's lane 0.
+  uint32_t *colbuf = reinterpret_cast<uint32_t *>(sp.tile_col + cw * 2 * (uint64_t)sp.tile_col_stride);
+  const uint32_t col_elems = sp.tile_col_stride / 4;
   // Debug builds: the block shape and the block's columns within their
   // buffers (a block-uniform test, before the allocation).
   if (!MPF_DCHECK(sp.status, W == kTileWarpsTm &&
@@ -409,17 +428,17 @@ __global__ void __launch_bounds__(kTileWarpsTm * 32, 1) tile_kernel_tm(ScanParam
       __syncthreads();
       tm_fence_after();
       if (!active) continue;
-      const int16_t *cin = colbuf + (size_t)((t + 1) & 1) * col_elems;
-      int16_t *cout = colbuf + (size_t)(t & 1) * col_elems;
+      const uint32_t *cin = colbuf + (size_t)((t + 1) & 1) * col_elems;
+      uint32_t *cout = colbuf + (size_t)(t & 1) * col_elems;
       const bool first = t == 0, write = t + 1 < nt;
       if (write && lane == 31) cout[0] = 0;
       uint32_t v[kPairs];
 #pragma unroll
       for (int p = 0; p < kPairs; ++p) v[p] = 0u;
-      uint2 cur = make_uint2(0, 0), nxt = make_uint2(0, 0);
+      uint4 cur = make_uint4(0, 0, 0, 0), nxt = make_uint4(0, 0, 0, 0);
       if (lane == 0 && !first) {
-        cur = __ldcg(reinterpret_cast<const uint2 *>(cin));
-        nxt = __ldcg(reinterpret_cast<const uint2 *>(cin) + 1);
+        cur = __ldcg(reinterpret_cast<const uint4 *>(cin));
+        nxt = __ldcg(reinterpret_cast<const uint4 *>(cin) + 1);
       }
       // Score rows of the current and the next row.  Codes are < 32 in a
       // sequence; the load issued for the row after the last one takes any
@@ -429,12 +448,12 @@ __global__ void __launch_bounds__(kTileWarpsTm * 32, 1) tile_kernel_tm(ScanParam
       tm_ld<kPairs>(TA, tm_lane + (word & 31u) * (uint32_t)kPairs);
       for (uint32_t i0 = 0; i0 < len; i0 += 4) {
         const uint32_t nword = i0 + 4 < len ? __ldg(sp.residues + w0 + (i0 >> 2) + 1) : 0u;
-        uint2 c = cur;
+        const uint4 c = cur;
         if (lane == 0 && !first) {
           cur = nxt;
-          nxt = __ldcg(reinterpret_cast<const uint2 *>(cin) + (i0 >> 2) + 2);
+          nxt = __ldcg(reinterpret_cast<const uint4 *>(cin) + (i0 >> 2) + 2);
         }
-        const uint32_t cs[4] = {c.x & 0xffffu, c.x >> 16, c.y & 0xffffu, c.y >> 16};
+        const uint32_t cs[4] = {c.x, c.y, c.z, c.w};
         uint32_t rq[4] = {0u, 0u, 0u, 0u};
         // One row: wait for its scores, issue the next row's load, update.
         // The next row's code is masked to 0..31 (a column of the tile): in
@@ -445,11 +464,10 @@ __global__ void __launch_bounds__(kTileWarpsTm * 32, 1) tile_kernel_tm(ScanParam
           MPF_DCHECK(sp.status, __byte_perm(word, 0u, 0x4440 + u) < 32u);
           const uint32_t xn = (u < 3 ? __byte_perm(word, 0u, 0x4441 + u) : nword) & 31u;
           tm_ld<kPairs>(Tn, tm_lane + xn * (uint32_t)kPairs);
-          const uint32_t top = v[kPairs - 1] >> 16;   // node 31 of the lane, previous row
-          uint32_t in = __shfl_up_sync(kAll, top, 1);
+          uint32_t in = __shfl_up_sync(kAll, v[kPairs - 1], 1);   // node 31 (high half), previous row
           if (lane == 0) in = cs[u];
-          tile_row_regs(v, in, Tc, MSV ? rq[u] : rmax);
-          if (write && lane == 31) cout[i0 + u + 1] = (int16_t)(v[kPairs - 1] >> 16);
+          tile_row_regs_w(v, in, Tc, MSV ? rq[u] : rmax);
+          if (write && lane == 31) cout[i0 + u + 1] = v[kPairs - 1];
         };
         if (i0 + 4 <= len) {   // warp-uniform: four rows, no row test
           one_row(0, TA, TB);
