@@ -197,3 +197,41 @@ def test_packed_threshold_test_equals_the_halfwise_comparison():
     packed = (lo | (hi << 16)) + ((0x7fff - K) | ((0x7fff - K) << 16))
     got = (packed & 0x80008000) != 0
     assert np.array_equal(got, (lo > K) | (hi > K))
+
+
+def held_sweep_max(rec, seq):
+    """The largest cell V of the held-b sweep (the recurrence both the held
+    MSV pass and SSV run: v = max(0, v'[k-1] + s))."""
+    M = rec.M
+    s = rec.bias - np.vstack([rec.cost.astype(np.int64), np.full((32 - rec.K, M), 255, np.int64)])
+    v = np.zeros(M, np.int64)
+    V = 0
+    for x in seq:
+        v = np.maximum(0, np.concatenate(([0], v[:-1])) + s[x])
+        V = max(V, int(v.max()))
+    return V
+
+
+@pytest.mark.parametrize("seed", range(3))
+def test_one_sweep_gives_both_filters(seed):
+    """Both filters from one sweep (MPF_MSV_SSV): the held sweep's largest
+    cell V gives SSV as Alg. 7 defines it (raw = min(V, 255), overflow iff
+    V >= 255) and the held MSV decision, on the same profiles and planted
+    sequences as above; every SSV score and flag of the oracle is matched."""
+    oracle.build()
+    rng = np.random.default_rng(4040 + seed)
+    checked = flags = 0
+    for rec, db in _cases(rng):
+        sraw, sflag, _ = oracle.ssv(rec, db.residues, db.offsets, db.lengths)
+        raw, flag, _ = oracle.msv(rec, db.residues, db.offsets, db.lengths)
+        for k in range(db.n_seqs):
+            o, L = int(db.offsets[k]), int(db.lengths[k])
+            sq = db.residues[o:o + L]
+            V = held_sweep_max(rec, sq)
+            assert (min(V, 255), int(V >= 255)) == (int(sraw[k]), int(sflag[k])), (rec.M, k, V)
+            got = held_msv(rec, sq)
+            if got is not None:
+                assert got == (int(raw[k]), int(flag[k]))
+            checked += 1
+            flags += int(V >= 255)
+    assert checked > 500 and flags > 0
