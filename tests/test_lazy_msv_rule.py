@@ -217,11 +217,15 @@ def test_one_sweep_gives_both_filters(seed):
     """Both filters from one sweep (MPF_MSV_SSV): the held sweep's largest
     cell V gives SSV as Alg. 7 defines it (raw = min(V, 255), overflow iff
     V >= 255) and the held MSV decision, on the same profiles and planted
-    sequences as above; every SSV score and flag of the oracle is matched."""
+    sequences as above and on strong profiles whose segments overflow;
+    every SSV score and flag of the oracle is matched."""
     oracle.build()
     rng = np.random.default_rng(4040 + seed)
     checked = flags = 0
-    for rec, db in _cases(rng):
+    strong = [(synth.random_profile(int(rng.integers(5, 60)), 20, rng, cost_hi=26, bias=20, base=190, tbm=10,
+                                    tec=3, tjb=8), synth.random_database(40, 120, rng, alphabet=20, min_len=0))
+              for _ in range(4)]
+    for rec, db in _cases(rng) + [c for c in strong if _holds_b(c[0])]:
         sraw, sflag, _ = oracle.ssv(rec, db.residues, db.offsets, db.lengths)
         raw, flag, _ = oracle.msv(rec, db.residues, db.offsets, db.lengths)
         for k in range(db.n_seqs):
