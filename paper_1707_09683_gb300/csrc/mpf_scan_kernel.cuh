@@ -319,12 +319,22 @@ __global__ void __launch_bounds__(kBlockThreads, 1) scan_kernel(ScanParams p) {
       // Tensor-memory words of the current and the next row: the loads of
       // row i + 1 are issued while row i is computed.  Every residue code,
       // the padding code included, has a TMEM row (code x: columns x * HT ..).
-      uint32_t TA[TM ? HT : 1], TB[TM ? HT : 1];
+      // Whole-warp kernels of up to 16 words per lane: one 16-column load per
+      // row (tcgen05.ld .x16, one uniform address) in place of two or three
+      // narrower ones; the columns past a code's HT words belong to the next
+      // code (or lie past the 33 codes, inside the allocation) and are not
+      // used.  Measured per row of M = 600-1000: 3.5-8.5% faster; from 22
+      // words on, where a row has more work to hide the loads behind, the
+      // exact-width loads were up to 2% faster.  Packed kernels load HT
+      // columns (their group state leaves no registers for wider buffers).
+      constexpr int HL = TM ? ((QP == 1 && H <= 16) ? 16 : HT) : 1;
+      static_assert(!TM || (HT <= 16 && (kTableRows - 1) * HT + 16 <= (int)kTmemColumns), "load width");
+      uint32_t TA[HL], TB[HL];
       auto tm_col = [&](uint32_t xc) -> uint32_t {
         if (!MPF_DCHECK(p.status, xc < (uint32_t)kTableRows)) xc = kPadCode;
         return tm_lane + xc * (uint32_t)HT;
       };
-      if constexpr (TM) tm_ld<HT>(TA, tm_col(cur & 0xffu));   // first row of the sequence
+      if constexpr (TM) tm_ld<HL>(TA, tm_col(cur & 0xffu));   // first row of the sequence
 
       // Four rows of one residue word (nxt: the next word).  CHECK: test every
       // row for the MSV threshold (only needed when some lane is near it, or
@@ -342,8 +352,8 @@ __global__ void __launch_bounds__(kBlockThreads, 1) scan_kernel(ScanParams p) {
           if constexpr (TM) {
             // This row's TMEM words (issued one row earlier), then the next
             // row's loads: a wait covers every earlier load of the thread.
-            tm_wait_ld<HT>(Tc);
-            tm_ld<HT>(Tn, tm_col(rr < 3 ? __byte_perm(cur, 0u, 0x4440u + rr + 1) : nxt & 0xffu));
+            tm_wait_ld<HL>(Tc);
+            tm_ld<HL>(Tn, tm_col(rr < 3 ? __byte_perm(cur, 0u, 0x4440u + rr + 1) : nxt & 0xffu));
           }
           const uint8_t *rowp = tbl_lane + x * row_bytes;
           // Diagonal shift (Alg. 5): cell k-1 of the previous row feeds cell k.
@@ -465,7 +475,7 @@ __global__ void __launch_bounds__(kBlockThreads, 1) scan_kernel(ScanParams p) {
         cur = nxt;
       }
 
-      if constexpr (TM) tm_wait_ld<HT>(TA);   // the load issued after the last row
+      if constexpr (TM) tm_wait_ld<HL>(TA);   // the load issued after the last row
 
       // ---- finalise the G sequences -------------------------------------
       const bool own = active && qvalid;   // this group writes its sequence's outputs
