@@ -1097,6 +1097,87 @@ def run_profile_case_batch(args):
                       "kernel_launches_per_run": launches}))
 
 
+def run_throughput_all_queries(args):
+    """The 1,000-query throughput workload end to end: every query against
+    the whole 10 M-sequence database (3.5 G residues), both filters, once as
+    one plan per filter (batched) and once as one both-filter plan (one
+    sweep), each timed over one run with CUDA events (minutes each, so no
+    repetition; raw and flag outputs, no nat).  The two forms' outputs are
+    compared in full; three queries (shortest, median and longest M) are
+    checked against the oracle on 2,000 random sequences."""
+    import torch
+    import oracle
+    from paper_1707_09683_gb300 import build, mpf, synth
+    build.build()
+    oracle.build()
+    t0 = time.time()
+    wl = synth.make_workload(4)
+    gen_s = time.time() - t0
+    ctx = mpf.Context(0)
+    db = mpf.Database(ctx, wl.db.residues, wl.db.offsets, wl.db.lengths)
+    n, res, q = db.n_seqs, db.n_residues, len(wl.profiles)
+    profs = [mpf.Profile(ctx, p) for p in wl.profiles]
+    dev = torch.device("cuda", 0)
+    cells = 2 * sum(p.M for p in wl.profiles) * res
+    stream = ctx.torch_stream()
+
+    def timed(fn):
+        a = torch.cuda.Event(enable_timing=True)
+        b = torch.cuda.Event(enable_timing=True)
+        ctx.sync()
+        with torch.cuda.stream(stream):
+            a.record(stream)
+            fn()
+            b.record(stream)
+        b.synchronize()
+        ctx.sync()
+        return a.elapsed_time(b)
+
+    filters = (("msv", mpf.MSV), ("ssv", mpf.SSV))
+    outs = {f: (torch.empty(q * n, dtype=torch.uint8, device=dev), torch.empty(q * n, dtype=torch.uint8, device=dev))
+            for f, _ in filters}
+    t_p = time.time()
+    plans = {f: mpf.Plan(ctx, code, profs, db, *outs[f], None) for f, code in filters}
+    f_outs = (torch.empty(2 * q * n, dtype=torch.uint8, device=dev),
+              torch.empty(2 * q * n, dtype=torch.uint8, device=dev))
+    fplan = mpf.Plan(ctx, mpf.MSV_SSV, profs, db, *f_outs, None)
+    plan_s = time.time() - t_p
+    groups = {f: pl.groups() for f, pl in plans.items()}
+    with ClockSampler(0) as clk:
+        ms_b = timed(lambda: [pl.launch() for pl in plans.values()])
+        ms_f = timed(fplan.launch)
+    same = all(bool(torch.equal(f_outs[k][:q * n], outs["msv"][k]) and torch.equal(f_outs[k][q * n:], outs["ssv"][k]))
+               for k in range(2))
+    rng = np.random.default_rng(5)
+    idx = np.sort(rng.choice(n, size=2000, replace=False)).astype(np.uint64)
+    order = np.argsort([p.M for p in wl.profiles])
+    picks = [int(order[0]), int(order[len(order) // 2]), int(order[-1])]
+    ok = True
+    for i in picks:
+        for f, of in (("msv", oracle.MSV), ("ssv", oracle.SSV)):
+            er, ef, _ = oracle.scan(of, wl.profiles[i], wl.db.residues, wl.db.offsets, wl.db.lengths, index=idx,
+                                    nthreads=os.cpu_count() or 1)
+            sl = slice(i * n, (i + 1) * n)
+            ok = ok and np.array_equal(outs[f][0][sl].cpu().numpy()[idx.astype(np.int64)], er) and \
+                np.array_equal(outs[f][1][sl].cpu().numpy()[idx.astype(np.int64)], ef)
+    print(json.dumps({
+        "workload": wl.name, "queries": q, "n_seqs": n, "residues": res, "cells_both_filters": cells,
+        "generate_s": gen_s, "plan_create_s": plan_s,
+        "batched": {"ms": ms_b, "gcups": cells / (ms_b * 1e-3) / 1e9,
+                    "kernel_launches": sum(pl.kernel_launches for pl in plans.values()),
+                    "launch_groups_per_filter": len(groups["msv"]),
+                    "packed_query_filters": sum(g["n_queries"] for f in groups for g in groups[f]
+                                                if g["queries_per_warp"] > 1)},
+        "one_sweep": {"ms": ms_f, "gcups": cells / (ms_f * 1e-3) / 1e9, "kernel_launches": fplan.kernel_launches,
+                      "queries_in_one_sweep": sum(g["n_queries"] for g in fplan.groups() if g["filters"] == 3),
+                      "equals_batched": same,
+                      "cells_note": "GCUPS count both filters' cells"},
+        "oracle_sample": {"ok": ok, "queries_M": [wl.profiles[i].M for i in picks], "sequences": int(idx.size)},
+        "clocks": clk.summary()}), flush=True)
+    for pl in list(plans.values()) + [fplan]:
+        pl.close()
+
+
 def run_profile_viterbi(args):
     """Small case for ncu: the first args.profile_vit_seqs sequences of the
     500,000-sequence database against one Viterbi profile of M =
@@ -1211,9 +1292,14 @@ def main():
     ap.add_argument("--profile-vit-seqs", type=int, default=20000)
     ap.add_argument("--ubench", action="store_true",
                     help="run the issue-rate / on-chip bandwidth microbenchmarks and exit")
+    ap.add_argument("--throughput-all-queries", action="store_true",
+                    help="the 1,000-query, 10 M-sequence workload end to end (one run per form, about 5 "
+                         "minutes) and exit")
     args = ap.parse_args()
     if args.ubench:
         run_ubench(args)
+    elif args.throughput_all_queries:
+        run_throughput_all_queries(args)
     elif args.profile_viterbi:
         run_profile_viterbi(args)
     elif args.profile_case:
