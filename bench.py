@@ -1099,10 +1099,10 @@ def run_profile_case_batch(args):
 
 def run_throughput_all_queries(args):
     """The 1,000-query throughput workload end to end: every query against
-    the whole 10 M-sequence database (3.5 G residues), both filters, once as
-    one plan per filter (batched) and once as one both-filter plan (one
-    sweep), each timed over one run with CUDA events (minutes each, so no
-    repetition; raw and flag outputs, no nat).  The two forms' outputs are
+    the whole 10 M-sequence database (3.5 G residues), both filters, as one
+    plan per query and filter (plain), one plan per filter (batched) and one
+    both-filter plan (one sweep), each timed over one run with CUDA events
+    (minutes each, so no repetition; raw and flag outputs, no nat).  The two forms' outputs are
     compared in full; three queries (shortest, median and longest M) are
     checked against the oracle on 2,000 random sequences."""
     import torch
@@ -1143,9 +1143,15 @@ def run_throughput_all_queries(args):
     fplan = mpf.Plan(ctx, mpf.MSV_SSV, profs, db, *f_outs, None)
     plan_s = time.time() - t_p
     groups = {f: pl.groups() for f, pl in plans.items()}
+    # Plain: one plan per query and filter, writing into the same outputs.
+    plain = [mpf.Plan(ctx, code, [pr], db, outs[f][0][i * n:(i + 1) * n], outs[f][1][i * n:(i + 1) * n], None)
+             for f, code in filters for i, pr in enumerate(profs)]
     with ClockSampler(0) as clk:
+        ms_p = timed(lambda: [pl.launch() for pl in plain])
         ms_b = timed(lambda: [pl.launch() for pl in plans.values()])
         ms_f = timed(fplan.launch)
+    for pl in plain:
+        pl.close()
     same = all(bool(torch.equal(f_outs[k][:q * n], outs["msv"][k]) and torch.equal(f_outs[k][q * n:], outs["ssv"][k]))
                for k in range(2))
     rng = np.random.default_rng(5)
@@ -1168,6 +1174,8 @@ def run_throughput_all_queries(args):
                     "launch_groups_per_filter": len(groups["msv"]),
                     "packed_query_filters": sum(g["n_queries"] for f in groups for g in groups[f]
                                                 if g["queries_per_warp"] > 1)},
+        "plain": {"ms": ms_p, "gcups": cells / (ms_p * 1e-3) / 1e9, "kernel_launches": 2 * q},
+        "batched_over_plain": ms_p / ms_b, "one_sweep_over_plain": ms_p / ms_f,
         "one_sweep": {"ms": ms_f, "gcups": cells / (ms_f * 1e-3) / 1e9, "kernel_launches": fplan.kernel_launches,
                       "queries_in_one_sweep": sum(g["n_queries"] for g in fplan.groups() if g["filters"] == 3),
                       "equals_batched": same,
@@ -1293,7 +1301,7 @@ def main():
     ap.add_argument("--ubench", action="store_true",
                     help="run the issue-rate / on-chip bandwidth microbenchmarks and exit")
     ap.add_argument("--throughput-all-queries", action="store_true",
-                    help="the 1,000-query, 10 M-sequence workload end to end (one run per form, about 5 "
+                    help="the 1,000-query, 10 M-sequence workload end to end (one run per form, about 9 "
                          "minutes) and exit")
     args = ap.parse_args()
     if args.ubench:
