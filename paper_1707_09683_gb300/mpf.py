@@ -352,7 +352,8 @@ def _handles(profs: Sequence[Profile]):
 
 def scan_batch(ctx: Context, filter: int, profs: Sequence[Profile], db: Database, raw, overflow,
                nat=None):
-    """``mpf_scan_batch``: outputs are [n_q][n_seqs]."""
+    """``mpf_scan_batch``: outputs are [n_q][n_seqs]; with filter MSV_SSV
+    [2][n_q][n_seqs] (the MSV block, then the SSV block)."""
     arr = _handles(profs)
     _check(load().mpf_scan_batch(ctx.handle, int(filter), arr, len(profs), db.handle, _ptr(raw),
                                  _ptr(overflow), _ptr(nat)), "mpf_scan_batch")
